@@ -1,0 +1,313 @@
+/*
+ * gridff.h - C ABI of libgridff, a GB300 (sm_103a) implementation of the hot
+ * path of GridFF: molecule-substrate interaction by tricubic B-spline
+ * interpolation of precomputed substrate grids, fused with an intramolecular
+ * force field and FIRE relaxation / NVE dynamics over many independent
+ * replicas of a molecule (arXiv 2508.15522).
+ *
+ * Paper passages that define the operations (section / equation):
+ *   E = sum_i E_i(r_i, t_i, Q_i)                               Sec. 3, Eq. E
+ *   E_i^C = Q_i V^C(r_i)                                       Sec. 3, Eq. E_Coulomb
+ *   E_i^M = P_i V^P(r_i) + L_i V^L(r_i),
+ *     P_i = eps_i e^{2 alpha R_i}, L_i = -2 eps_i e^{alpha R_i},
+ *     V^P = sum_j eps_j e^{-2 alpha (|r - r_j| - R_j)},
+ *     V^L = sum_j eps_j e^{-alpha (|r - r_j| - R_j)}           Sec. 3, Eqs. E_Morse, V_Morse
+ *   periodic substrate, vacuum padding, monopole/dipole
+ *     correction; molecule folded into the surface cell       Sec. 4
+ *   cubic B-spline basis, 4x4x4 stencil, z fastest in memory,
+ *     forces = analytic gradient of the interpolant,
+ *     coefficients fitted to reproduce the node values       Sec. 5, Eqs. Bspline1D, Bspline
+ *   FIRE relaxation, force threshold                          Sec. 6, Sec. 7
+ *   replicas run entirely on the GPU                          Sec. 7
+ *
+ * Units: Angstrom, eV, elementary charge e, fs, amu.  V^C is stored in volts
+ * (the Coulomb constant k_e = 14.399645 eV A / e^2 is folded into it).
+ *
+ * Conventions
+ *  - Every function returns a gridff_status; GRIDFF_OK is 0.  On failure
+ *    gridff_last_error(ctx) returns a message (valid until the next call on
+ *    that context).  Problems of single replicas (an atom below the grid, a
+ *    non-finite force) never fail a call: they are reported in the
+ *    per-replica status word (GRIDFF_REP_* bits).
+ *  - The caller owns every array it passes.  Handles (context, grid,
+ *    replicas) own the device memory they allocate; *_destroy frees it.
+ *  - Array arguments are host pointers unless GRIDFF_DEVICE_PTRS is set in
+ *    `flags`, in which case they are device pointers (e.g. torch CUDA
+ *    tensors) and are used in place without copies.
+ *  - All work is ordered on the context's CUDA stream.  Calls synchronise
+ *    that stream before returning unless GRIDFF_ASYNC is set (device
+ *    pointers only).
+ *  - Layouts: "replica-major CSR": the atoms of replica r occupy rows
+ *    atom_offset[r] .. atom_offset[r+1]-1 of every per-atom array; a 3-vector
+ *    per atom is stored as 3 consecutive floats (x, y, z).
+ *  - Not thread-safe per context; different contexts are independent.
+ */
+#ifndef GRIDFF_H
+#define GRIDFF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GRIDFF_OK = 0,
+  GRIDFF_EINVAL = 1,      /* invalid argument (message says which) */
+  GRIDFF_ENOMEM = 2,      /* device or host allocation failed */
+  GRIDFF_ECUDA = 3,       /* CUDA runtime error (message has cudaGetErrorString) */
+  GRIDFF_EABORTED = 4,    /* the host abort flag stopped a relax/run call */
+  GRIDFF_ESTEPLIMIT = 5,  /* the clock budget of a relax/run call ran out */
+  GRIDFF_ENOTSUP = 6      /* combination not supported by this build */
+} gridff_status;
+
+/* per-replica status bits (status_out arrays, gridff_get_fire_state) */
+#define GRIDFF_REP_CONVERGED 1   /* FIRE force norm fell below f_conv */
+#define GRIDFF_REP_BELOW 2       /* an atom was below the grid (clamped to its bottom) */
+#define GRIDFF_REP_NONFINITE 4   /* a force or position was NaN/Inf: replica frozen */
+#define GRIDFF_REP_ABORTED 8     /* stopped by the abort flag before finishing */
+#define GRIDFF_REP_STEPLIMIT 16  /* stopped by the clock budget before finishing */
+
+/* flags */
+#define GRIDFF_DEVICE_PTRS 1     /* array arguments are device pointers */
+#define GRIDFF_ASYNC 2           /* do not synchronise before returning */
+#define GRIDFF_CONTINUE 4        /* relax: keep FIRE scalars and status from the last call */
+#define GRIDFF_NO_GRID 8         /* eval/relax/run: skip the grid term */
+#define GRIDFF_NO_INTRA 16       /* eval/relax/run: skip the intramolecular terms */
+
+/* grid channels */
+#define GRIDFF_CH_C 1            /* Coulomb V^C (volts) */
+#define GRIDFF_CH_P 2            /* Pauli V^P */
+#define GRIDFF_CH_L 4            /* London V^L */
+
+/* coefficient storage */
+#define GRIDFF_STORE_F32 0       /* float32 records, one 16-byte record per node */
+
+typedef struct gridff_ctx gridff_ctx;
+typedef struct gridff_grid gridff_grid;
+typedef struct gridff_replicas gridff_replicas;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a
+ * cudaStream_t to order all work on, or NULL to let the context create and
+ * own one.  Allocates a small host-mapped control block (abort flag).
+ * Errors: EINVAL (bad device), ECUDA. */
+gridff_status gridff_create(int device, void* cuda_stream, gridff_ctx** out);
+void gridff_destroy(gridff_ctx* ctx);
+/* Message of the last failing call on ctx ("" if none); never NULL. */
+const char* gridff_last_error(const gridff_ctx* ctx);
+/* The stream the context orders work on (a cudaStream_t). */
+void* gridff_stream(const gridff_ctx* ctx);
+/* Raise (1) or clear (0) the abort flag read by running relax/run kernels
+ * (host-mapped memory; may be called from another host thread). */
+void gridff_set_abort(gridff_ctx* ctx, int value);
+
+/* ------------------------------------------------------------------- grid */
+
+/* Rigid substrate: n atoms of one periodic supercell (Sec. 3, Sec. 4). */
+typedef struct {
+  int32_t n_atoms;
+  const double* xyz;   /* [n*3] positions (A) */
+  const double* q;     /* [n] charges (e) */
+  const double* R;     /* [n] Morse radii R_j (A); pair distance R_i + R_j */
+  const double* eps;   /* [n] Morse eps_j (sqrt eV); pair depth eps_i eps_j */
+  double cell[9];      /* rows A1, A2 (in-plane, z = 0) and A3 = (0, 0, Lz):
+                          the 3D-periodic Ewald cell with vacuum padding */
+} gridff_substrate;
+
+typedef struct {
+  double origin[3];    /* lower corner of the grid box (A) */
+  double length[3];    /* box lengths; x and y must be a lattice period of the
+                          substrate (the grid is periodic in x, y) */
+  double spacing;      /* target spacing h: n = ceil(L/h - 1e-9), dx = L/n */
+  double alpha;        /* Morse alpha (1/A), default 1.5 (Sec. 6) */
+  double rcut;         /* hard cutoff of the Morse sums (A), default 17 (Sec. 6) */
+  double ewald_tol;    /* real/reciprocal tail tolerance, default 1e-10 */
+  double ewald_rcut;   /* Ewald real-space cutoff (A), default 12 */
+  int32_t channels;    /* GRIDFF_CH_* mask; default C|P|L; C is skipped when
+                          all substrate charges are zero */
+  int32_t storage;     /* GRIDFF_STORE_*, default F32 */
+  int32_t keep_f64;    /* keep the FP64 node values and coefficients for
+                          gridff_grid_download_f64 */
+} gridff_grid_opts;
+
+/* Fill opts with the defaults above (origin/length/spacing zeroed). */
+void gridff_grid_opts_default(gridff_grid_opts* opts);
+
+/* Build the coefficient grid of a substrate on the GPU (Sec. 3-5):
+ * node values V^C (3D Ewald sum with the slab dipole correction, FP64),
+ * V^P, V^L (direct sums over atoms and in-plane images within rcut, FP64),
+ * then the exact B-spline coefficients (separable line solves, FP64:
+ * periodic in x, y; clamped end coefficients in z), stored as `storage`.
+ * Substrate arrays are host pointers.  Errors: EINVAL (sizes, cell, box),
+ * ENOMEM, ECUDA. */
+gridff_status gridff_build_grid(gridff_ctx* ctx, const gridff_substrate* sub,
+                                const gridff_grid_opts* opts, gridff_grid** out);
+
+/* Make a grid from given coefficients (host array, FP64, layout
+ * [channel][ix][iy][iz], channels in the order C, P, L of `channels`).
+ * Grid nodes are origin + k*spacing; x, y periodic with period dims*spacing. */
+gridff_status gridff_grid_from_coefs(gridff_ctx* ctx, const double origin[3],
+                                     const double spacing[3], const int32_t dims[3],
+                                     int32_t channels, const double* coefs,
+                                     int32_t storage, gridff_grid** out);
+
+/* Grid metadata; any output pointer may be NULL. */
+gridff_status gridff_grid_info(const gridff_grid* grid, int32_t dims[3], double origin[3],
+                               double spacing[3], int32_t* channels, size_t* device_bytes);
+
+/* Copy FP64 node values (what = 0) or coefficients (what = 1), layout
+ * [channel][ix][iy][iz], to a host array.  Needs keep_f64 at build time.
+ * Errors: EINVAL if not kept. */
+gridff_status gridff_grid_download_f64(const gridff_grid* grid, int what, double* host_out);
+void gridff_grid_destroy(gridff_grid* grid);
+
+/* --------------------------------------------------------------- replicas */
+
+/* One molecule template (host arrays).  Per-atom parameters of Sec. 3:
+ * charge Q_i, Morse R_i and eps_i (the library forms P_i and L_i).
+ * Intramolecular terms (reduced UFF-like form; Sec. 6 and Sec. 8 name UFF
+ * without its terms):
+ *   bond     k (r - r0)^2
+ *   angle    k (cos(theta) - cos0)^2
+ *   torsion  V/2 (1 - cos(n phi0) cos(n phi))
+ *   nonbonded Morse (eps_i eps_j, R_i + R_j, alpha) + k_e q_i q_j / r on every
+ *            pair more than two bonds apart (derived from the bonds).
+ * Rigid molecules ignore the terms; their `xyz` must be the body frame:
+ * principal axes, centred at the centre of mass. */
+typedef struct {
+  int32_t n_atoms;            /* 1..128 */
+  const float* xyz;           /* [n*3] reference/body coordinates */
+  const float* q;             /* [n] */
+  const float* R;             /* [n] */
+  const float* eps;           /* [n] */
+  const float* mass;          /* [n] amu, > 0 */
+  int32_t n_bonds;
+  const int32_t* bonds;       /* [n_bonds*2] */
+  const float* bond_k;
+  const float* bond_r0;
+  int32_t n_angles;
+  const int32_t* angles;      /* [n_angles*3], vertex in the middle */
+  const float* angle_k;
+  const float* angle_cos0;
+  int32_t n_torsions;
+  const int32_t* torsions;    /* [n_torsions*4] */
+  const float* torsion_V;
+  const int32_t* torsion_n;
+  const float* torsion_cos_nphi0;
+} gridff_molecule;
+
+/* Create a replica set: n_rep replicas, replica r is a copy of template
+ * template_of[r].  rigid != 0: every replica is a rigid body (state =
+ * pose); else flexible (state = atom positions).  Positions and velocities
+ * start at zero; set them with gridff_set_state.  Errors: EINVAL, ENOMEM. */
+gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
+                                     const gridff_molecule* templates, int32_t n_rep,
+                                     const int32_t* template_of, int32_t rigid,
+                                     double alpha, gridff_replicas** out);
+void gridff_replicas_destroy(gridff_replicas* reps);
+
+/* Sizes: number of replicas and total atoms; atom_offset[n_rep+1] (host
+ * array, may be NULL) receives the replica-major CSR offsets. */
+gridff_status gridff_replicas_info(const gridff_replicas* reps, int32_t* n_rep,
+                                   int32_t* n_atoms_total, int32_t* atom_offset);
+
+/* State.  Flexible: x, v are [n_atoms_total*3] (A, A/fs).
+ * Rigid: x is [n_rep*7] = centre of mass (3) + orientation quaternion
+ * (w, x, y, z), v is [n_rep*6] = COM velocity (A/fs) + body-frame angular
+ * velocity (rad/fs).  v may be NULL (set: zero; get: skipped). */
+gridff_status gridff_set_state(gridff_replicas* reps, const float* x, const float* v, int flags);
+gridff_status gridff_get_state(gridff_replicas* reps, float* x, float* v, int flags);
+
+/* Atom positions of every replica ([n_atoms_total*3]; for rigid replicas
+ * r_i = R(q) b_i + com). */
+gridff_status gridff_get_positions(gridff_replicas* reps, float* x, int flags);
+
+/* FIRE scalars and status of every replica; any pointer may be NULL. */
+gridff_status gridff_get_fire_state(gridff_replicas* reps, float* dt, float* alpha,
+                                    int32_t* nplus, int32_t* status, int32_t* steps,
+                                    double* energy, int flags);
+
+/* ------------------------------------------------------------- evaluation */
+
+/* Energies and forces at the current state (Sec. 3, Sec. 5):
+ * E_out[n_rep]      total energy per replica (grid + intramolecular), FP64
+ * F_out[n_atoms*3]  force per atom (eV/A)
+ * Eatom_out[n_atoms] grid energy per atom (may be NULL)
+ * status_out[n_rep] GRIDFF_REP_* bits (may be NULL)
+ * grid may be NULL with GRIDFF_NO_GRID.  Errors: EINVAL, ECUDA. */
+gridff_status gridff_eval(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* reps,
+                          int flags, double* E_out, float* F_out, float* Eatom_out,
+                          int32_t* status_out);
+
+typedef struct {
+  float dt_start;      /* fs, default 0.5 */
+  float dt_max;        /* fs, default 2.0 */
+  int32_t n_min;       /* default 5 */
+  float f_inc;         /* default 1.1 */
+  float f_dec;         /* default 0.5 */
+  float alpha_start;   /* default 0.1 */
+  float f_alpha;       /* default 0.99 */
+  float d_max;         /* per-atom displacement cap (A), default 0.1 */
+  float f_conv;        /* convergence on the force 2-norm (eV/A), default 1e-3;
+                          0 runs exactly nsteps */
+  double clock_budget_s;  /* stop after this many seconds of kernel time
+                             (0 = none): status ESTEPLIMIT */
+} gridff_fire_params;
+
+void gridff_fire_params_default(gridff_fire_params* p);
+
+typedef struct {
+  int64_t atom_evals;      /* sum over replicas of atoms x evaluations done */
+  int32_t n_converged;     /* replicas with GRIDFF_REP_CONVERGED */
+  int32_t max_steps;       /* most evaluations done by one replica */
+} gridff_relax_result;
+
+/* FIRE relaxation of every replica for up to nsteps iterations in one
+ * persistent launch (one warp per replica; state kept in registers).
+ * Iteration: forces; convergence test |F|_2 < f_conv (rigid: |F_tot|^2 +
+ * |tau|^2); P = F.v; P > 0: mix v towards F, grow dt after n_min steps;
+ * else v = 0, dt *= f_dec; semi-implicit Euler with per-atom cap d_max.
+ * Rigid replicas apply the rule to (COM velocity, total force) and (body
+ * angular velocity, body torque).  Without GRIDFF_CONTINUE the FIRE
+ * scalars and status are reset first.  result may be NULL.
+ * Errors: EINVAL, ECUDA, EABORTED, ESTEPLIMIT (state is consistent). */
+gridff_status gridff_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* reps,
+                           int32_t nsteps, const gridff_fire_params* params, int flags,
+                           gridff_relax_result* result);
+
+typedef struct {
+  float dt;               /* fs */
+  int32_t record_every;   /* energy trace cadence in steps (0 = no trace) */
+  double clock_budget_s;  /* as in gridff_fire_params */
+} gridff_md_params;
+
+/* NVE dynamics for nsteps: velocity Verlet (flexible) or the NO_SQUISH
+ * symplectic rigid-body splitting (rigid).  energy_trace (may be NULL)
+ * receives [(nsteps/record_every + 1) * n_rep] total energies (FP64, eV),
+ * record k of replica r at [k*n_rep + r]; record 0 is the start.
+ * Errors: EINVAL, ECUDA, EABORTED, ESTEPLIMIT. */
+gridff_status gridff_run(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* reps,
+                         int32_t nsteps, const gridff_md_params* params, int flags,
+                         double* energy_trace);
+
+/* ------------------------------------------------------------ measurement */
+
+/* Read `bytes` of a device buffer `iters` times with a streaming kernel and
+ * return the achieved read bandwidth (GB/s) measured with CUDA events on the
+ * context stream.  `device_buf` must hold at least `bytes` (16-byte aligned,
+ * multiple of 16 bytes).  Used as the L2 roofline denominator when the
+ * buffer fits in L2. */
+gridff_status gridff_probe_read_bandwidth(gridff_ctx* ctx, const void* device_buf,
+                                          size_t bytes, int32_t iters, double* gbs_out);
+
+/* Milliseconds of the last relax/run kernel, measured with CUDA events
+ * around the launch on the context stream (0 if none yet). */
+double gridff_last_kernel_ms(const gridff_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRIDFF_H */

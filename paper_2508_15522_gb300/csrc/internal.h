@@ -1,0 +1,129 @@
+// Internal declarations of libgridff (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+
+#include "gridff.h"
+
+#define GRIDFF_MAX_ATOMS 128          // atoms per molecule template
+#define GRIDFF_ATOMS_PER_LANE 4       // GRIDFF_MAX_ATOMS / 32
+#define GRIDFF_KE 14.399645f          // eV*A/e^2
+#define GRIDFF_ACC 9.648533e-3f       // A/fs^2 per eV/(A*amu)
+
+struct gridff_ctx {
+  int device = 0;
+  int n_sm = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  volatile int* ctrl_host = nullptr;  // host-mapped: [0] abort flag
+  int* ctrl_dev = nullptr;            // device alias of ctrl_host
+  int* result_dev = nullptr;          // device word: OR of per-replica stop bits
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double last_ms = 0.0;
+  std::string err;
+};
+
+// Coefficient grid as the kernels see it (passed by value).
+// Node records are float4 {C, P, L, 0}; the record array is padded so that
+// every 4x4x4 stencil is a set of 16 contiguous runs of 4 records:
+//   padded x index p <-> logical (p - 1) mod nx, p in [0, nx + 3)
+//   padded y index    likewise
+//   padded z index p <-> logical clamp(p - 1, 0, nz - 1), p in [0, nz + 2)
+struct GridView {
+  const float4* rec;
+  int nx, ny, nz;
+  int nyp, nzp;
+  long long sx;          // record stride between x planes = nyp * nzp
+  float x0, y0, z0;
+  float inv_dx, inv_dy, inv_dz;
+  float Lx, Ly, inv_Lx, inv_Ly;
+};
+
+struct gridff_grid {
+  gridff_ctx* ctx = nullptr;
+  int dims[3] = {0, 0, 0};
+  double origin[3] = {0, 0, 0};
+  double spacing[3] = {0, 0, 0};
+  int channels = 0;
+  int storage = 0;
+  float4* rec = nullptr;
+  size_t rec_bytes = 0;
+  int nxp = 0, nyp = 0, nzp = 0;
+  double* f64_values = nullptr;   // [C][nx][ny][nz] if kept
+  double* f64_coefs = nullptr;
+  int n_ch = 0;                   // channels present, in order C, P, L
+  GridView view() const;
+};
+
+// Per-atom bonded term records (template-local atom indices).
+struct BondRec { int j; int own; float k; float r0; };   // own: count the energy here
+struct AngleRec { int a, b, c, role; float k, cos0, pad0, pad1; };
+struct TorsionRec { int a, b, c, d; int role; int n; float V, cn0; };
+
+// Molecule templates as the kernels see them (all device pointers).
+struct TemplateView {
+  const int* natoms;        // [T]
+  const int* atom_off;      // [T+1] offsets into the per-atom arrays
+  const float4* body;       // [A] {x, y, z, mass}
+  const float4* par;        // [A] {Q, P, L, 0}   (grid factors, Eqs. E_Coulomb, V_Morse)
+  const float4* nb;         // [A] {q, R, eps, 0} (intramolecular nonbonded)
+  const uint32_t* excl;     // [A*4] bit j set: pair (i, j) excluded
+  const int* bond_off;      // [A+1]
+  const BondRec* bonds;
+  const int* angle_off;     // [A+1]
+  const AngleRec* angles;
+  const int* tors_off;      // [A+1]
+  const TorsionRec* tors;
+  const float4* rigid;      // [T] {M, I1, I2, I3}
+  const float* rmax;        // [T]
+  float alpha;
+};
+
+// Accumulated results of one relax/run launch (device memory of the context).
+struct DevResult {
+  unsigned long long atom_evals;
+  int stop_bits;      // OR of GRIDFF_REP_ABORTED / GRIDFF_REP_STEPLIMIT over replicas
+  int n_converged;
+  int max_steps;
+  int pad[3];
+};
+
+struct gridff_replicas {
+  gridff_ctx* ctx = nullptr;
+  int n_rep = 0;
+  int n_atoms = 0;          // total atoms over replicas
+  int n_tmpl = 0;
+  int rigid = 0;
+  float alpha = 1.5f;
+  int max_natoms = 0;
+  // device
+  void* tmpl_blob = nullptr;   // one allocation holding every template array
+  TemplateView tv{};
+  int* rep_tmpl = nullptr;     // [n_rep]
+  int* rep_off = nullptr;      // [n_rep+1]
+  float* x = nullptr;          // flexible [3N]; rigid [7 n_rep]
+  float* v = nullptr;          // flexible [3N]; rigid [6 n_rep]
+  float* fire_dt = nullptr;
+  float* fire_alpha = nullptr;
+  int* fire_nplus = nullptr;
+  int* status = nullptr;
+  int* steps = nullptr;
+  double* energy = nullptr;
+  // host copy of offsets
+  int* h_rep_off = nullptr;
+};
+
+// error helpers -------------------------------------------------------------
+gridff_status set_err(gridff_ctx* ctx, gridff_status st, const char* fmt, ...);
+#define GRIDFF_CUDA(ctx, call)                                                     \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return set_err((ctx), GRIDFF_ECUDA, "%s failed: %s (%s:%d)", #call,          \
+                     cudaGetErrorString(e_), __FILE__, __LINE__);                  \
+  } while (0)
+

@@ -1,0 +1,390 @@
+"""Thin Python binding of libgridff (ctypes; argument marshalling only).
+
+Every computation runs in the CUDA library behind the C ABI declared in
+``include/gridff.h``; this module converts numpy arrays / torch tensors to
+pointers and raises on non-OK statuses.  Importing it loads the library and
+fails loudly if it has not been built (no CPU fallback exists).
+
+Arrays: numpy arrays are host memory; torch CUDA tensors are passed as
+device pointers (``GRIDFF_DEVICE_PTRS``) and used in place.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgridff.so")
+
+# status codes and flags (mirror gridff.h)
+OK, EINVAL, ENOMEM, ECUDA, EABORTED, ESTEPLIMIT, ENOTSUP = range(7)
+REP_CONVERGED, REP_BELOW, REP_NONFINITE, REP_ABORTED, REP_STEPLIMIT = 1, 2, 4, 8, 16
+DEVICE_PTRS, ASYNC, CONTINUE, NO_GRID, NO_INTRA = 1, 2, 4, 8, 16
+CH_C, CH_P, CH_L = 1, 2, 4
+STORE_F32 = 0
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EABORTED", 5: "ESTEPLIMIT",
+                6: "ENOTSUP"}
+
+
+class GridffError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Substrate(C.Structure):
+    _fields_ = [("n_atoms", C.c_int32), ("xyz", C.POINTER(C.c_double)), ("q", C.POINTER(C.c_double)),
+                ("R", C.POINTER(C.c_double)), ("eps", C.POINTER(C.c_double)), ("cell", C.c_double * 9)]
+
+
+class GridOpts(C.Structure):
+    _fields_ = [("origin", C.c_double * 3), ("length", C.c_double * 3), ("spacing", C.c_double),
+                ("alpha", C.c_double), ("rcut", C.c_double), ("ewald_tol", C.c_double),
+                ("ewald_rcut", C.c_double), ("channels", C.c_int32), ("storage", C.c_int32),
+                ("keep_f64", C.c_int32)]
+
+
+class Molecule(C.Structure):
+    _fields_ = [("n_atoms", C.c_int32), ("xyz", C.c_void_p), ("q", C.c_void_p), ("R", C.c_void_p),
+                ("eps", C.c_void_p), ("mass", C.c_void_p),
+                ("n_bonds", C.c_int32), ("bonds", C.c_void_p), ("bond_k", C.c_void_p),
+                ("bond_r0", C.c_void_p),
+                ("n_angles", C.c_int32), ("angles", C.c_void_p), ("angle_k", C.c_void_p),
+                ("angle_cos0", C.c_void_p),
+                ("n_torsions", C.c_int32), ("torsions", C.c_void_p), ("torsion_V", C.c_void_p),
+                ("torsion_n", C.c_void_p), ("torsion_cos_nphi0", C.c_void_p)]
+
+
+class FireParams(C.Structure):
+    _fields_ = [("dt_start", C.c_float), ("dt_max", C.c_float), ("n_min", C.c_int32),
+                ("f_inc", C.c_float), ("f_dec", C.c_float), ("alpha_start", C.c_float),
+                ("f_alpha", C.c_float), ("d_max", C.c_float), ("f_conv", C.c_float),
+                ("clock_budget_s", C.c_double)]
+
+
+class RelaxResult(C.Structure):
+    _fields_ = [("atom_evals", C.c_int64), ("n_converged", C.c_int32), ("max_steps", C.c_int32)]
+
+
+class MDParams(C.Structure):
+    _fields_ = [("dt", C.c_float), ("record_every", C.c_int32), ("clock_budget_s", C.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+    lib = C.CDLL(LIB_PATH)
+    P, I32, F64 = C.c_void_p, C.c_int32, C.c_double
+    sig = {
+        "gridff_create": (I32, [C.c_int, P, C.POINTER(P)]),
+        "gridff_destroy": (None, [P]),
+        "gridff_last_error": (C.c_char_p, [P]),
+        "gridff_stream": (P, [P]),
+        "gridff_set_abort": (None, [P, C.c_int]),
+        "gridff_grid_opts_default": (None, [C.POINTER(GridOpts)]),
+        "gridff_build_grid": (I32, [P, C.POINTER(Substrate), C.POINTER(GridOpts), C.POINTER(P)]),
+        "gridff_grid_from_coefs": (I32, [P, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                         C.POINTER(C.c_int32), I32, C.POINTER(C.c_double), I32,
+                                         C.POINTER(P)]),
+        "gridff_grid_info": (I32, [P, C.POINTER(C.c_int32), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_size_t)]),
+        "gridff_grid_download_f64": (I32, [P, C.c_int, C.POINTER(C.c_double)]),
+        "gridff_grid_destroy": (None, [P]),
+        "gridff_replicas_create": (I32, [P, I32, C.POINTER(Molecule), I32, C.POINTER(C.c_int32), I32,
+                                         F64, C.POINTER(P)]),
+        "gridff_replicas_destroy": (None, [P]),
+        "gridff_replicas_info": (I32, [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+        "gridff_set_state": (I32, [P, P, P, C.c_int]),
+        "gridff_get_state": (I32, [P, P, P, C.c_int]),
+        "gridff_get_positions": (I32, [P, P, C.c_int]),
+        "gridff_get_fire_state": (I32, [P, P, P, P, P, P, P, C.c_int]),
+        "gridff_eval": (I32, [P, P, P, C.c_int, P, P, P, P]),
+        "gridff_fire_params_default": (None, [C.POINTER(FireParams)]),
+        "gridff_relax": (I32, [P, P, P, I32, C.POINTER(FireParams), C.c_int, C.POINTER(RelaxResult)]),
+        "gridff_run": (I32, [P, P, P, I32, C.POINTER(MDParams), C.c_int, P]),
+        "gridff_probe_read_bandwidth": (I32, [P, P, C.c_size_t, I32, C.POINTER(C.c_double)]),
+        "gridff_last_kernel_ms": (F64, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+EXPORTED = (
+    "gridff_create", "gridff_destroy", "gridff_last_error", "gridff_stream", "gridff_set_abort",
+    "gridff_grid_opts_default", "gridff_build_grid", "gridff_grid_from_coefs", "gridff_grid_info",
+    "gridff_grid_download_f64", "gridff_grid_destroy", "gridff_replicas_create",
+    "gridff_replicas_destroy", "gridff_replicas_info", "gridff_set_state", "gridff_get_state",
+    "gridff_get_positions", "gridff_get_fire_state", "gridff_eval", "gridff_fire_params_default",
+    "gridff_relax", "gridff_run", "gridff_probe_read_bandwidth", "gridff_last_kernel_ms",
+)
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, dtype):
+    """(pointer, is_device, keepalive) of a numpy array or torch tensor."""
+    if a is None:
+        return None, False, None
+    if _is_torch(a):
+        import torch
+        want = {np.float32: torch.float32, np.float64: torch.float64, np.int32: torch.int32}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"tensor must be contiguous {want}")
+        return C.c_void_p(a.data_ptr()), a.is_cuda, a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data_as(C.c_void_p), False, arr
+
+
+class Context:
+    """CUDA context of the library: device, stream, abort flag."""
+
+    def __init__(self, device: int = 0, stream=None):
+        h = C.c_void_p()
+        st = lib.gridff_create(int(device), C.c_void_p(stream) if stream else None, C.byref(h))
+        if st != OK:
+            raise GridffError(st, f"gridff_create(device={device}) failed")
+        self.h = h
+
+    def check(self, st):
+        if st != OK:
+            raise GridffError(st, lib.gridff_last_error(self.h).decode())
+        return st
+
+    @property
+    def stream(self):
+        return lib.gridff_stream(self.h)
+
+    def set_abort(self, value=True):
+        lib.gridff_set_abort(self.h, int(bool(value)))
+
+    def last_kernel_ms(self):
+        return float(lib.gridff_last_kernel_ms(self.h))
+
+    def probe_read_bandwidth(self, tensor, iters=50):
+        out = C.c_double()
+        self.check(lib.gridff_probe_read_bandwidth(self.h, C.c_void_p(tensor.data_ptr()),
+                                                   tensor.numel() * tensor.element_size(), iters,
+                                                   C.byref(out)))
+        return out.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.gridff_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Grid:
+    def __init__(self, ctx: Context, handle):
+        self.ctx, self.h = ctx, handle
+        dims = (C.c_int32 * 3)(); org = (C.c_double * 3)(); sp = (C.c_double * 3)()
+        ch = C.c_int32(); nb = C.c_size_t()
+        ctx.check(lib.gridff_grid_info(handle, dims, org, sp, C.byref(ch), C.byref(nb)))
+        self.dims, self.origin, self.spacing = tuple(dims), tuple(org), tuple(sp)
+        self.channels, self.device_bytes = ch.value, nb.value
+
+    @property
+    def n_channels(self):
+        return bin(self.channels).count("1")
+
+    def download_f64(self, what="coefs"):
+        out = np.empty((self.n_channels,) + self.dims, np.float64)
+        self.ctx.check(lib.gridff_grid_download_f64(self.h, 1 if what == "coefs" else 0,
+                                                     out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.gridff_grid_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build_grid(ctx: Context, sub, origin, length, spacing, channels=CH_C | CH_P | CH_L,
+               alpha=1.5, rcut=17.0, ewald_tol=1e-10, ewald_rcut=12.0, keep_f64=False) -> Grid:
+    """gridff_build_grid: substrate (object with xyz, q, R, eps, cell) -> Grid."""
+    xyz = np.ascontiguousarray(sub.xyz, np.float64).ravel()
+    q = np.ascontiguousarray(sub.q, np.float64)
+    R = np.ascontiguousarray(sub.R, np.float64)
+    eps = np.ascontiguousarray(sub.eps, np.float64)
+    s = Substrate(len(q), xyz.ctypes.data_as(C.POINTER(C.c_double)), q.ctypes.data_as(C.POINTER(C.c_double)),
+                  R.ctypes.data_as(C.POINTER(C.c_double)), eps.ctypes.data_as(C.POINTER(C.c_double)),
+                  (C.c_double * 9)(*np.asarray(sub.cell, np.float64).ravel()))
+    o = GridOpts()
+    lib.gridff_grid_opts_default(C.byref(o))
+    o.origin = (C.c_double * 3)(*origin)
+    o.length = (C.c_double * 3)(*length)
+    o.spacing, o.alpha, o.rcut = spacing, alpha, rcut
+    o.ewald_tol, o.ewald_rcut, o.channels, o.keep_f64 = ewald_tol, ewald_rcut, channels, int(keep_f64)
+    h = C.c_void_p()
+    ctx.check(lib.gridff_build_grid(ctx.h, C.byref(s), C.byref(o), C.byref(h)))
+    return Grid(ctx, h)
+
+
+def grid_from_coefs(ctx: Context, coefs, origin, spacing, channels) -> Grid:
+    """gridff_grid_from_coefs: FP64 coefficients (C, nx, ny, nz) -> Grid."""
+    c = np.ascontiguousarray(coefs, np.float64)
+    dims = (C.c_int32 * 3)(*c.shape[1:])
+    h = C.c_void_p()
+    ctx.check(lib.gridff_grid_from_coefs(ctx.h, (C.c_double * 3)(*origin), (C.c_double * 3)(*spacing), dims,
+                                         channels, c.ctypes.data_as(C.POINTER(C.c_double)), STORE_F32,
+                                         C.byref(h)))
+    return Grid(ctx, h)
+
+
+def _mol_struct(m, keep):
+    def f32(a):
+        arr = np.ascontiguousarray(np.asarray(a, np.float32).ravel())
+        keep.append(arr)
+        return arr.ctypes.data_as(C.c_void_p)
+
+    def i32(a):
+        arr = np.ascontiguousarray(np.asarray(a, np.int32).ravel())
+        keep.append(arr)
+        return arr.ctypes.data_as(C.c_void_p)
+
+    return Molecule(m.n, f32(m.xyz), f32(m.q), f32(m.R), f32(m.eps), f32(m.mass),
+                    len(m.bonds), i32(m.bonds), f32(m.bond_k), f32(m.bond_r0),
+                    len(m.angles), i32(m.angles), f32(m.angle_k), f32(m.angle_cos0),
+                    len(m.torsions), i32(m.torsions), f32(m.torsion_V), i32(m.torsion_n),
+                    f32(m.torsion_cos_nphi0))
+
+
+class Replicas:
+    """gridff_replicas: n_rep replicas of molecule templates (rigid or flexible)."""
+
+    def __init__(self, ctx: Context, templates, template_of, rigid=False, alpha=1.5):
+        keep = []
+        mols = (Molecule * len(templates))(*[_mol_struct(m, keep) for m in templates])
+        tof = np.ascontiguousarray(template_of, np.int32)
+        h = C.c_void_p()
+        ctx.check(lib.gridff_replicas_create(ctx.h, len(templates), mols, len(tof),
+                                             tof.ctypes.data_as(C.POINTER(C.c_int32)), int(bool(rigid)),
+                                             float(alpha), C.byref(h)))
+        self.ctx, self.h, self.rigid = ctx, h, bool(rigid)
+        n_rep = C.c_int32(); n_at = C.c_int32()
+        ctx.check(lib.gridff_replicas_info(h, C.byref(n_rep), C.byref(n_at), None))
+        self.n_rep, self.n_atoms = n_rep.value, n_at.value
+        off = np.empty(self.n_rep + 1, np.int32)
+        ctx.check(lib.gridff_replicas_info(h, None, None, off.ctypes.data_as(C.POINTER(C.c_int32))))
+        self.atom_offset = off
+
+    @property
+    def state_sizes(self):
+        if self.rigid:
+            return 7 * self.n_rep, 6 * self.n_rep
+        return 3 * self.n_atoms, 3 * self.n_atoms
+
+    def set_state(self, x, v=None, flags=0):
+        px, dx, kx = _ptr(x, np.float32)
+        pv, dv, kv = _ptr(v, np.float32)
+        nx, nv = self.state_sizes
+        if not dx and np.asarray(kx).size != nx:
+            raise ValueError(f"x must have {nx} floats")
+        if v is not None and not dv and np.asarray(kv).size != nv:
+            raise ValueError(f"v must have {nv} floats")
+        flags |= DEVICE_PTRS if dx else 0
+        self.ctx.check(lib.gridff_set_state(self.h, px, pv, flags))
+
+    def get_state(self):
+        nx, nv = self.state_sizes
+        x = np.empty(nx, np.float32); v = np.empty(nv, np.float32)
+        self.ctx.check(lib.gridff_get_state(self.h, x.ctypes.data_as(C.c_void_p), v.ctypes.data_as(C.c_void_p), 0))
+        return x, v
+
+    def positions(self):
+        x = np.empty(3 * self.n_atoms, np.float32)
+        self.ctx.check(lib.gridff_get_positions(self.h, x.ctypes.data_as(C.c_void_p), 0))
+        return x.reshape(-1, 3)
+
+    def fire_state(self):
+        n = self.n_rep
+        out = dict(dt=np.empty(n, np.float32), alpha=np.empty(n, np.float32), nplus=np.empty(n, np.int32),
+                   status=np.empty(n, np.int32), steps=np.empty(n, np.int32), energy=np.empty(n, np.float64))
+        p = {k: v.ctypes.data_as(C.c_void_p) for k, v in out.items()}
+        self.ctx.check(lib.gridff_get_fire_state(self.h, p["dt"], p["alpha"], p["nplus"], p["status"],
+                                                 p["steps"], p["energy"], 0))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.gridff_replicas_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def eval(ctx: Context, grid, reps: Replicas, flags=0, out=None):
+    """gridff_eval -> (E per replica, F (n_atoms, 3), per-atom grid energy, status)."""
+    if out is not None:                    # device tensors: (E, F, Eatom, status)
+        E, F, Ea, S = out
+        ctx.check(lib.gridff_eval(ctx.h, grid.h if grid else None, reps.h, flags | DEVICE_PTRS,
+                                  C.c_void_p(E.data_ptr()), C.c_void_p(F.data_ptr()),
+                                  C.c_void_p(Ea.data_ptr()) if Ea is not None else None,
+                                  C.c_void_p(S.data_ptr()) if S is not None else None))
+        return out
+    E = np.empty(reps.n_rep, np.float64)
+    F = np.empty(3 * reps.n_atoms, np.float32)
+    Ea = np.empty(reps.n_atoms, np.float32)
+    S = np.empty(reps.n_rep, np.int32)
+    ctx.check(lib.gridff_eval(ctx.h, grid.h if grid else None, reps.h, flags,
+                              E.ctypes.data_as(C.c_void_p), F.ctypes.data_as(C.c_void_p),
+                              Ea.ctypes.data_as(C.c_void_p), S.ctypes.data_as(C.c_void_p)))
+    return E, F.reshape(-1, 3), Ea, S
+
+
+def fire_params(**kw) -> FireParams:
+    p = FireParams()
+    lib.gridff_fire_params_default(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def relax(ctx: Context, grid, reps: Replicas, nsteps: int, params: FireParams | None = None,
+          flags: int = 0, check: bool = True):
+    """gridff_relax -> (status, RelaxResult)."""
+    res = RelaxResult()
+    st = lib.gridff_relax(ctx.h, grid.h if grid else None, reps.h, int(nsteps),
+                          C.byref(params) if params is not None else None, flags, C.byref(res))
+    if check and st not in (OK,):
+        ctx.check(st)
+    return st, res
+
+
+def run(ctx: Context, grid, reps: Replicas, nsteps: int, dt: float, record_every: int = 0,
+        flags: int = 0, clock_budget_s: float = 0.0, check: bool = True):
+    """gridff_run -> (status, energy trace (n_records, n_rep) or None)."""
+    p = MDParams(float(dt), int(record_every), float(clock_budget_s))
+    trace = None
+    tp = None
+    if record_every > 0:
+        trace = np.empty((nsteps // record_every + 1, reps.n_rep), np.float64)
+        tp = trace.ctypes.data_as(C.c_void_p)
+    st = lib.gridff_run(ctx.h, grid.h if grid else None, reps.h, int(nsteps), C.byref(p), flags, tp)
+    if check and st != OK:
+        ctx.check(st)
+    return st, trace
