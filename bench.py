@@ -221,11 +221,12 @@ def run_gpu(args):
     reps = G.Replicas(ctx, [mol], [0] * N_REP, rigid=True)
     pose_dev = torch.from_numpy(pose.ravel()).to(dev)
     params = G.fire_params(f_conv=0.0)
+    iters = args.fire_iters
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step():
         reps.set_state(pose_dev)
-        st, res = G.relax(ctx, grid, reps, FIRE_ITERS, params)
+        st, res = G.relax(ctx, grid, reps, iters, params)
         return res
 
     for _ in range(args.warmup):
@@ -260,30 +261,33 @@ def run_gpu(args):
     value = evals_all / total_s
 
     # end to end through the public API with host buffers (pinned)
-    host_pose = torch.from_numpy(pose.ravel()).pin_memory()
-    out_pose = torch.empty(7 * N_REP, dtype=torch.float32).pin_memory()
-    out_E = np.empty(N_REP, np.float64)
-    e2e_s = []
-    for i in range(max(1, min(args.steps, 5))):
-        flush.fill_(float(i))
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        reps.set_state(host_pose.numpy())
-        G.relax(ctx, grid, reps, FIRE_ITERS, params)
-        x, v = reps.get_state()
-        out_E[:] = reps.fire_state()["energy"]
-        e2e_s.append(time.perf_counter() - t0)
-    e2e_value = N_REP * mol.n * FIRE_ITERS / statistics.mean(e2e_s) * world
+    e2e_value = None
+    if not args.quick:
+        host_pose = torch.from_numpy(pose.ravel()).pin_memory()
+        out_E = np.empty(N_REP, np.float64)
+        e2e_s = []
+        for i in range(max(1, min(args.steps, 5))):
+            flush.fill_(float(i))
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            reps.set_state(host_pose.numpy())
+            G.relax(ctx, grid, reps, iters, params)
+            x, v = reps.get_state()
+            out_E[:] = reps.fire_state()["energy"]
+            e2e_s.append(time.perf_counter() - t0)
+        e2e_value = N_REP * mol.n * iters / statistics.mean(e2e_s) * world
 
     # roofline of the dominant kernel (the fused relax kernel)
-    l2_buf = torch.empty(48 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    l2_peak = ctx.probe_read_bandwidth(l2_buf, iters=200)
-    del l2_buf
-    hbm_buf = torch.empty(2 * 1024 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    hbm_read = ctx.probe_read_bandwidth(hbm_buf, iters=5)
-    del hbm_buf
+    l2_peak = hbm_read = None
+    if not args.quick:
+        l2_buf = torch.empty(48 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        l2_peak = ctx.probe_read_bandwidth(l2_buf, iters=200)
+        del l2_buf
+        hbm_buf = torch.empty(2 * 1024 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        hbm_read = ctx.probe_read_bandwidth(hbm_buf, iters=5)
+        del hbm_buf
     k_ms = statistics.mean(kernel_ms)
-    per_launch_evals = N_REP * mol.n * FIRE_ITERS
+    per_launch_evals = N_REP * mol.n * iters
     achieved = BYTES_PER_EVAL * per_launch_evals / (k_ms * 1e-3) / 1e9
     tpe = ncu_traffic()
     peaks = measured_peaks()
@@ -292,10 +296,11 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config({"grid_bytes_fp32_padded": grid.device_bytes, "parallelism": "replicas only"}),
+        "config": config({"grid_bytes_fp32_padded": grid.device_bytes, "parallelism": "replicas only",
+                          "fire_iterations_per_step": iters}),
         "replica_steps_per_s": value / mol.n,
         "roofline": {"bound": "l2", "achieved": achieved, "peak": l2_peak, "unit": "GB/s",
-                     "frac": achieved / l2_peak, "traffic": (tpe * per_launch_evals) if tpe else None,
+                     "frac": (achieved / l2_peak) if l2_peak else None, "traffic": (tpe * per_launch_evals) if tpe else None,
                      "kernel": "relax_rigid_kernel", "bytes_per_unit": BYTES_PER_EVAL,
                      "units_per_launch": per_launch_evals, "kernel_ms": k_ms,
                      "peak_source": "measured in this run: streaming read of a 48 MB L2-resident buffer "
@@ -306,7 +311,7 @@ def run_gpu(args):
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.quick:
         cv, cdt, cdesc = oracle_sample()
         line["cpu_baseline"] = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cdesc}
     if rank == 0:
@@ -322,6 +327,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gridff", choices=["gridff", "reference"])
+    ap.add_argument("--fire-iters", type=int, default=FIRE_ITERS,
+                    help="FIRE iterations per step (profiling runs use a short step)")
+    ap.add_argument("--quick", action="store_true",
+                    help="skip the e2e leg, the bandwidth probes and the CPU baseline (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
