@@ -154,6 +154,32 @@ gridff_status gridff_grid_from_coefs(gridff_ctx* ctx, const double origin[3],
                                      int32_t channels, const double* coefs,
                                      int32_t storage, gridff_grid** out);
 
+/* Allocation-free B-spline coefficient fit.  Some callers cannot allocate
+ * device memory at the point where they fit: the device memory is already
+ * reserved by another allocator (a framework's caching pool) so cudaMalloc
+ * would fail, or the caller runs a latency-bound loop in which cudaFree's
+ * implicit device synchronisation is not acceptable.  This entry point does
+ * the fit step of gridff_build_grid without any allocation.  The paper has
+ * no counterpart.  It solves the same separable collocation system
+ * (periodic x, y; clamped z) for n_channels channels of FP64 node values,
+ * layout [channel][ix][iy][iz]:
+ *   values  device pointer to the node values (read; may equal coefs)
+ *   coefs   device pointer receiving the coefficients (same layout)
+ *   dims    nx, ny, nz, each in 4..4096
+ * Work is ordered on the context stream; without GRIDFF_ASYNC the call
+ * synchronises it.  The line-solve tables live in one fixed device array
+ * of about 288 KB inside the library (every GPU that loads the library
+ * holds it until the process exits); no call allocates or frees memory.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress), so make the first call on each device before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * tables (each call rewrites them before use): calls that overlap on the
+ * GPU (different streams or contexts on one device) race.
+ * Errors: EINVAL (null pointer, n_channels < 1, or a dimension outside
+ * 4..4096, with a message naming it), ECUDA. */
+gridff_status gridff_fit_coefs_noalloc(gridff_ctx* ctx, const double* values, double* coefs,
+                                       const int32_t dims[3], int32_t n_channels, int flags);
+
 /* Grid metadata; any output pointer may be NULL. */
 gridff_status gridff_grid_info(const gridff_grid* grid, int32_t dims[3], double origin[3],
                                double spacing[3], int32_t* channels, size_t* device_bytes);

@@ -6,6 +6,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -365,6 +366,102 @@ gridff_status fit_and_pack(gridff_ctx* ctx, gridff_grid* g, double* data, DevFre
 
 bool dims_ok(const int* d) { return d[0] >= 4 && d[1] >= 4 && d[2] >= 4; }
 
+// --------------------------------------------------------------------------
+// Allocation-free coefficient fit (gridff_fit_coefs_noalloc)
+// --------------------------------------------------------------------------
+// The per-axis line-solve tables live in this file-scope device array
+// instead of memory allocated per call.  Layout per axis a (0 = x, 1 = y,
+// 2 = z): inv[n], cp[n], zc[n], then fac and a_over_gamma, at a * kNoAllocStride.
+constexpr int kNoAllocMaxN = 4096;
+constexpr int kNoAllocStride = 3 * kNoAllocMaxN + 2;
+__device__ __align__(256) double g_noalloc_tables[3 * kNoAllocStride];
+
+// One thread per axis builds that axis' tables (same recurrences as host_tables).
+__global__ void noalloc_tables_kernel(double* tab, int nx, int ny, int nz) {
+  int a = threadIdx.x;
+  if (a > 2) return;
+  int n = a == 0 ? nx : a == 1 ? ny : nz;
+  bool cyclic = a < 2;
+  double* inv = tab + (size_t)a * kNoAllocStride;
+  double* cp = inv + kNoAllocMaxN;
+  double* zc = cp + kNoAllocMaxN;
+  double* scal = zc + kNoAllocMaxN;
+  const double lo = 1.0 / 6.0, up = 1.0 / 6.0, b = 2.0 / 3.0, gamma = -b;
+  for (int k = 0; k < n; ++k) {
+    double bd = b;
+    if (k == 0) bd = cyclic ? b - gamma : b + lo;
+    if (k == n - 1) bd = cyclic ? b - lo * up / gamma : b + up;
+    double den = k == 0 ? bd : bd - lo * cp[k - 1];
+    inv[k] = 1.0 / den;
+    cp[k] = up * inv[k];
+  }
+  scal[0] = 0.0;
+  scal[1] = 0.0;
+  if (cyclic) {
+    double prev = 0.0;
+    for (int k = 0; k < n; ++k) {
+      double u = k == 0 ? gamma : (k == n - 1 ? up : 0.0);
+      zc[k] = (u - lo * prev) * inv[k];
+      prev = zc[k];
+    }
+    for (int k = n - 2; k >= 0; --k) zc[k] -= cp[k] * zc[k + 1];
+    scal[1] = lo / gamma;
+    scal[0] = 1.0 / (1.0 + zc[0] + scal[1] * zc[n - 1]);
+  }
+}
+
+// Line solve that reads its tables (and the cyclic correction scalars) from
+// device memory; `cyclic` selects the Sherman-Morrison correction.
+__global__ void noalloc_line_kernel(double* __restrict__ data, int n, long long stride, long long n_lines,
+                                    int inner, long long inner_stride, long long outer_stride,
+                                    const double* __restrict__ tab, int cyclic) {
+  long long line = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (line >= n_lines) return;
+  const double* inv = tab;
+  const double* cp = tab + kNoAllocMaxN;
+  const double* zc = cp + kNoAllocMaxN;
+  const double* scal = zc + kNoAllocMaxN;
+  long long o = line / inner, i = line % inner;
+  double* d = data + o * outer_stride + i * inner_stride;
+  const double a = 1.0 / 6.0;
+  double prev = 0.0;
+  for (int k = 0; k < n; ++k) {
+    double v = (d[k * stride] - a * prev) * inv[k];
+    d[k * stride] = v;
+    prev = v;
+  }
+  double next = d[(long long)(n - 1) * stride];
+  for (int k = n - 2; k >= 0; --k) {
+    double v = d[k * stride] - cp[k] * next;
+    d[k * stride] = v;
+    next = v;
+  }
+  if (cyclic) {
+    double s = scal[0] * (d[0] + scal[1] * d[(long long)(n - 1) * stride]);
+    for (int k = 0; k < n; ++k) d[k * stride] -= s * zc[k];
+  }
+}
+
+// Device address of g_noalloc_tables, looked up once per device (the host
+// symbol g_noalloc_tables is only a stand-in, never a device address).
+double* noalloc_tables_address(int device, cudaError_t* err) {
+  static std::mutex mu;
+  static double* addr[64] = {nullptr};
+  *err = cudaSuccess;
+  if (device < 0 || device >= 64) {
+    *err = cudaErrorInvalidDevice;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[device]) {
+    void* p = nullptr;
+    *err = cudaGetSymbolAddress(&p, g_noalloc_tables);
+    if (*err != cudaSuccess) return nullptr;
+    addr[device] = (double*)p;
+  }
+  return addr[device];
+}
+
 }  // namespace
 
 GridView gridff_grid::view() const {
@@ -655,6 +752,41 @@ gridff_status gridff_grid_from_coefs(gridff_ctx* ctx, const double origin[3], co
     return set_err(ctx, GRIDFF_ECUDA, "pack: %s", cudaGetErrorString(e));
   }
   *out = g;
+  return GRIDFF_OK;
+}
+
+gridff_status gridff_fit_coefs_noalloc(gridff_ctx* ctx, const double* values, double* coefs,
+                                       const int32_t dims[3], int32_t n_channels, int flags) {
+  if (!ctx || !values || !coefs || !dims) return set_err(ctx, GRIDFF_EINVAL, "null argument");
+  if (n_channels < 1) return set_err(ctx, GRIDFF_EINVAL, "n_channels must be >= 1");
+  for (int a = 0; a < 3; ++a)
+    if (dims[a] < 4 || dims[a] > kNoAllocMaxN)
+      return set_err(ctx, GRIDFF_EINVAL,
+                     "gridff_fit_coefs_noalloc: dims[%d] = %d outside 4..%d (the size of its fixed "
+                     "device table)", a, dims[a], kNoAllocMaxN);
+  GRIDFF_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaError_t e;
+  double* tab = noalloc_tables_address(ctx->device, &e);
+  if (!tab) return set_err(ctx, GRIDFF_ECUDA, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+  cudaStream_t s = ctx->stream;
+  int nx = dims[0], ny = dims[1], nz = dims[2];
+  long long N = (long long)nx * ny * nz;
+  if (values != coefs)
+    GRIDFF_CUDA(ctx, cudaMemcpyAsync(coefs, values, (size_t)N * n_channels * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, s));
+  noalloc_tables_kernel<<<1, 32, 0, s>>>(tab, nx, ny, nz);
+  const int TB = 128;
+  long long lines = (long long)n_channels * nx * ny;   // z: contiguous lines
+  noalloc_line_kernel<<<(unsigned)((lines + TB - 1) / TB), TB, 0, s>>>(
+      coefs, nz, 1, lines, 1, 0, nz, tab + 2 * kNoAllocStride, 0);
+  lines = (long long)n_channels * nx * nz;             // y
+  noalloc_line_kernel<<<(unsigned)((lines + TB - 1) / TB), TB, 0, s>>>(
+      coefs, ny, nz, lines, nz, 1, (long long)ny * nz, tab + kNoAllocStride, 1);
+  lines = (long long)n_channels * ny * nz;             // x
+  noalloc_line_kernel<<<(unsigned)((lines + TB - 1) / TB), TB, 0, s>>>(
+      coefs, nx, (long long)ny * nz, lines, ny * nz, 1, N, tab, 1);
+  GRIDFF_CUDA(ctx, cudaGetLastError());
+  if (!(flags & GRIDFF_ASYNC)) GRIDFF_CUDA(ctx, cudaStreamSynchronize(s));
   return GRIDFF_OK;
 }
 

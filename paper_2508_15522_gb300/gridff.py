@@ -89,6 +89,7 @@ def _load():
         "gridff_grid_from_coefs": (I32, [P, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                          C.POINTER(C.c_int32), I32, C.POINTER(C.c_double), I32,
                                          C.POINTER(P)]),
+        "gridff_fit_coefs_noalloc": (I32, [P, P, P, C.POINTER(C.c_int32), I32, C.c_int]),
         "gridff_grid_info": (I32, [P, C.POINTER(C.c_int32), C.POINTER(C.c_double),
                                    C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_size_t)]),
         "gridff_grid_download_f64": (I32, [P, C.c_int, C.POINTER(C.c_double)]),
@@ -119,6 +120,7 @@ lib = _load()
 EXPORTED = (
     "gridff_create", "gridff_destroy", "gridff_last_error", "gridff_stream", "gridff_set_abort",
     "gridff_grid_opts_default", "gridff_build_grid", "gridff_grid_from_coefs", "gridff_grid_info",
+    "gridff_fit_coefs_noalloc",
     "gridff_grid_download_f64", "gridff_grid_destroy", "gridff_replicas_create",
     "gridff_replicas_destroy", "gridff_replicas_info", "gridff_set_state", "gridff_get_state",
     "gridff_get_positions", "gridff_get_fire_state", "gridff_eval", "gridff_fire_params_default",
@@ -249,6 +251,13 @@ def grid_from_coefs(ctx: Context, coefs, origin, spacing, channels) -> Grid:
                                          channels, c.ctypes.data_as(C.POINTER(C.c_double)), STORE_F32,
                                          C.byref(h)))
     return Grid(ctx, h)
+
+
+def fit_coefs_noalloc(ctx: Context, values, coefs, flags: int = 0):
+    """gridff_fit_coefs_noalloc on device tensors (float64, shape (C, nx, ny, nz))."""
+    dims = (C.c_int32 * 3)(*values.shape[1:])
+    return lib.gridff_fit_coefs_noalloc(ctx.h, C.c_void_p(values.data_ptr()), C.c_void_p(coefs.data_ptr()),
+                                        dims, int(values.shape[0]), flags)
 
 
 def _mol_struct(m, keep):
