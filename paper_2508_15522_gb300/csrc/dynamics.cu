@@ -1,6 +1,14 @@
 // Fused hot path: per-atom tricubic B-spline interpolation of the substrate
 // grid (Sec. 3, Sec. 5), intramolecular forces, per-replica warp reductions
 // and FIRE / NVE updates (Sec. 6, Sec. 7), one warp per replica.
+//
+// Work split inside a warp: the 32 lanes form 8 quads; each quad evaluates
+// one atom at a time.  Lane q of a quad gathers record q of each of the 16
+// z-runs of the atom's 4x4x4 stencil, so one warp-wide load instruction
+// fetches 8 whole runs (8 contiguous 64-byte segments) instead of 32
+// scattered 16-byte pieces; the quad then sums its partial contractions with
+// two shuffles.  Flexible replicas keep positions, velocities and forces in
+// shared memory; the integrator updates run with lanes over atoms.
 #include <math.h>
 
 #include <vector>
@@ -11,7 +19,15 @@ namespace {
 
 constexpr int kWarpsPerBlock = 4;
 constexpr int kThreads = 32 * kWarpsPerBlock;
-constexpr int KPL = GRIDFF_ATOMS_PER_LANE;   // atoms per lane
+#ifndef GRIDFF_MIN_BLOCKS_PER_SM
+#define GRIDFF_MIN_BLOCKS_PER_SM 4
+#endif
+constexpr int kMinBlocksPerSM = GRIDFF_MIN_BLOCKS_PER_SM;
+#ifndef GRIDFF_STAGED_NB
+#define GRIDFF_STAGED_NB 0
+#endif
+constexpr int kQuads = 8;                 // atoms evaluated per warp at a time
+constexpr int kMaxA = GRIDFF_MAX_ATOMS;
 constexpr unsigned kFull = 0xffffffffu;
 
 struct FireP {
@@ -23,6 +39,14 @@ struct Control {
   const volatile int* abort_flag;   // host-mapped
   unsigned long long budget_ns;     // 0 = none
   DevResult* res;
+};
+
+// per-warp shared state of a flexible replica
+struct WarpState {
+  float x[3 * kMaxA];
+  float v[3 * kMaxA];
+  float f[3 * kMaxA];
+  float eg[kMaxA];     // grid energy per atom
 };
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -39,6 +63,11 @@ __device__ __forceinline__ float wsum(float v) {
 __device__ __forceinline__ double wsum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+__device__ __forceinline__ float qsum(float v) {
+  v += __shfl_xor_sync(kFull, v, 1);
+  v += __shfl_xor_sync(kFull, v, 2);
   return v;
 }
 
@@ -58,74 +87,63 @@ __device__ __forceinline__ void bspline_weights(float t, float w[4], float dw[4]
 }
 
 // Energy and force of one atom in the substrate field (Eqs. E, E_Coulomb,
-// E_Morse): the three channels are combined per node with the atom's
-// factors (Q, P, L) and the 4x4x4 stencil is contracted along z (16 runs),
-// then y (4), then x (1); the force is minus the analytic gradient.
-__device__ __forceinline__ void grid_atom(const GridView& g, float x, float y, float z, float4 par,
-                                          float& e, float& fx, float& fy, float& fz, int& flags) {
-  e = fx = fy = fz = 0.f;
+// E_Morse), evaluated by the 4 lanes of a quad (q = lane & 3); every lane of
+// the quad returns the full result.  The channels are combined per node with
+// the atom's factors (Q, P, L); lane q accumulates the x/y-weighted sums of
+// node z+q-1 over the 16 runs, applies its own z weight, and the quad sums.
+// The force is minus the analytic gradient of the interpolant (Sec. 5).
+// `act` false: the quad has no atom (it still takes part in the shuffles).
+__device__ __forceinline__ void grid_quad(const GridView& g, int q, bool act, float x, float y, float z,
+                                          float4 par, float& e, float& fx, float& fy, float& fz,
+                                          int& flags) {
   // fold into the periodic tile (Sec. 4)
   float xr = x - g.x0, yr = y - g.y0;
   xr = fmaf(-g.Lx, floorf(xr * g.inv_Lx), xr);
   yr = fmaf(-g.Ly, floorf(yr * g.inv_Ly), yr);
   float ux = xr * g.inv_dx, uy = yr * g.inv_dy, uz = (z - g.z0) * g.inv_dz;
   float flx = floorf(ux), fly = floorf(uy);
-  float tx = ux - flx, ty = uy - fly;
+  float tx = fminf(fmaxf(ux - flx, 0.f), 1.f), ty = fminf(fmaxf(uy - fly, 0.f), 1.f);
   int ix = (int)flx, iy = (int)fly;
   if (ix >= g.nx) ix -= g.nx;
   if (iy >= g.ny) iy -= g.ny;
   ix = min(max(ix, 0), g.nx - 1);     // any input, even non-finite, stays in bounds
   iy = min(max(iy, 0), g.ny - 1);
-  tx = fminf(fmaxf(tx, 0.f), 1.f);
-  ty = fminf(fmaxf(ty, 0.f), 1.f);
-  if (uz < 0.f) {
-    flags |= GRIDFF_REP_BELOW;
-    uz = 0.f;
-  }
-  if (!(uz < (float)(g.nz - 1))) return;   // above the grid: field ~ 0
-  float flz = floorf(uz);
-  float tz = uz - flz;
-  int iz = (int)flz;
+  if (act && uz < 0.f) flags |= GRIDFF_REP_BELOW;
+  uz = fmaxf(uz, 0.f);
+  bool inside = act && (uz < (float)(g.nz - 1));   // above the grid (or NaN): field ~ 0
+  float flz = floorf(inside ? uz : 0.f);
+  float tz = (inside ? uz : 0.f) - flz;
+  int iz = min(max((int)flz, 0), g.nz - 2);
   float wx[4], dwx[4], wy[4], dwy[4], wz[4], dwz[4];
   bspline_weights(tx, wx, dwx);
   bspline_weights(ty, wy, dwy);
   bspline_weights(tz, wz, dwz);
-  const float4* base = g.rec + ((long long)ix * g.nyp + iy) * g.nzp + iz;
-  float gx = 0.f, gy = 0.f, gz = 0.f, v = 0.f;
+  float S0 = 0.f, Sx = 0.f, Sy = 0.f;
+  if (inside) {
+    const float4* p0 = g.rec + ((long long)ix * g.nyp + iy) * g.nzp + iz + q;
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    float4 r[4][4];
+    for (int a = 0; a < 4; ++a) {
+      float4 r[4];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const float4* p = base + a * g.sx + b * g.nzp;
+      for (int b = 0; b < 4; ++b) r[b] = __ldg(p0 + a * g.sx + b * g.nzp);
+      float s = 0.f, sy = 0.f;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) r[b][c] = __ldg(p + c);
-    }
-    float sy = 0.f, syy = 0.f, syz = 0.f;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      float cz[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) cz[c] = fmaf(par.x, r[b][c].x, fmaf(par.y, r[b][c].y, par.z * r[b][c].z));
-      float s = wz[0] * cz[0], ds = dwz[0] * cz[0];
-#pragma unroll
-      for (int c = 1; c < 4; ++c) {
-        s = fmaf(wz[c], cz[c], s);
-        ds = fmaf(dwz[c], cz[c], ds);
+      for (int b = 0; b < 4; ++b) {
+        float c = fmaf(par.x, r[b].x, fmaf(par.y, r[b].y, par.z * r[b].z));
+        s = fmaf(wy[b], c, s);
+        sy = fmaf(dwy[b], c, sy);
       }
-      sy = fmaf(wy[b], s, sy);
-      syy = fmaf(dwy[b], s, syy);
-      syz = fmaf(wy[b], ds, syz);
+      S0 = fmaf(wx[a], s, S0);
+      Sx = fmaf(dwx[a], s, Sx);
+      Sy = fmaf(wx[a], sy, Sy);
     }
-    v = fmaf(wx[a], sy, v);
-    gx = fmaf(dwx[a], sy, gx);
-    gy = fmaf(wx[a], syy, gy);
-    gz = fmaf(wx[a], syz, gz);
   }
-  e = v;
-  fx = -gx * g.inv_dx;
-  fy = -gy * g.inv_dy;
-  fz = -gz * g.inv_dz;
+  const float wq = q == 0 ? wz[0] : q == 1 ? wz[1] : q == 2 ? wz[2] : wz[3];
+  const float dwq = q == 0 ? dwz[0] : q == 1 ? dwz[1] : q == 2 ? dwz[2] : dwz[3];
+  e = qsum(wq * S0);
+  fx = -qsum(wq * Sx) * g.inv_dx;
+  fy = -qsum(wq * Sy) * g.inv_dy;
+  fz = -qsum(dwq * S0) * g.inv_dz;
 }
 
 __device__ __forceinline__ float3 ld3(const float* s, int i) {
@@ -137,15 +155,16 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
   return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 
-// Intramolecular force on template atom i (all terms that involve i) and the
-// energy share counted at i: bonded terms once (at their first atom),
-// nonbonded pairs half at each atom.  s_x holds the molecule's positions.
-__device__ void intra_atom(const TemplateView& tv, int ab, int n, int i, const float* s_x, float& Fx,
-                           float& Fy, float& Fz, double& E) {
+// This lane's share (terms q, q+4, ... of each list; partners q, q+4, ...)
+// of the intramolecular force on template atom i, and of the energy counted
+// at i: bonded terms once (at their first atom), nonbonded pairs half at
+// each atom.  s_x holds the molecule's positions.
+__device__ void intra_quad(const TemplateView& tv, int ab, int n, int i, int q, const float* s_x, float& Fx,
+                           float& Fy, float& Fz, float& E) {
   const float3 xi = ld3(s_x, i);
   const int gi = ab + i;
   float fx = 0.f, fy = 0.f, fz = 0.f, e = 0.f;
-  for (int t = tv.bond_off[gi]; t < tv.bond_off[gi + 1]; ++t) {
+  for (int t = tv.bond_off[gi] + q; t < tv.bond_off[gi + 1]; t += 4) {
     BondRec b = tv.bonds[t];
     float3 d = sub3(xi, ld3(s_x, b.j));
     float r = sqrtf(dot3(d, d));
@@ -156,7 +175,7 @@ __device__ void intra_atom(const TemplateView& tv, int ab, int n, int i, const f
     fz += c * d.z;
     if (b.own) e += b.k * dr * dr;
   }
-  for (int t = tv.angle_off[gi]; t < tv.angle_off[gi + 1]; ++t) {
+  for (int t = tv.angle_off[gi] + q; t < tv.angle_off[gi + 1]; t += 4) {
     AngleRec A = tv.angles[t];
     float3 xa = ld3(s_x, A.a), xb = ld3(s_x, A.b), xc = ld3(s_x, A.c);
     float3 u = sub3(xa, xb), w = sub3(xc, xb);
@@ -172,7 +191,7 @@ __device__ void intra_atom(const TemplateView& tv, int ab, int n, int i, const f
     fz -= dEdc * gr.z;
     if (A.role == 0) e += A.k * (c - A.cos0) * (c - A.cos0);
   }
-  for (int t = tv.tors_off[gi]; t < tv.tors_off[gi + 1]; ++t) {
+  for (int t = tv.tors_off[gi] + q; t < tv.tors_off[gi + 1]; t += 4) {
     TorsionRec T = tv.tors[t];
     float3 xa = ld3(s_x, T.a), xb = ld3(s_x, T.b), xc = ld3(s_x, T.c), xd = ld3(s_x, T.d);
     float3 F = sub3(xa, xb), G = sub3(xb, xc), H = sub3(xd, xc);
@@ -209,10 +228,10 @@ __device__ void intra_atom(const TemplateView& tv, int ab, int n, int i, const f
   // nonbonded: Morse (eps_i eps_j, R_i + R_j) + Coulomb on pairs > 2 bonds apart
   const float4 nbi = tv.nb[gi];
   const uint32_t* ex = tv.excl + 4 * (size_t)gi;
-  uint32_t exw[4] = {ex[0], ex[1], ex[2], ex[3]};
+  const uint32_t exw[4] = {ex[0], ex[1], ex[2], ex[3]};
   const float alpha = tv.alpha;
   float enb = 0.f;
-  for (int j = 0; j < n; ++j) {
+  for (int j = q; j < n; j += 4) {
     if ((exw[j >> 5] >> (j & 31)) & 1u) continue;
     float4 nbj = tv.nb[ab + j];
     float3 d = sub3(xi, ld3(s_x, j));
@@ -233,7 +252,7 @@ __device__ void intra_atom(const TemplateView& tv, int ab, int n, int i, const f
   Fx += fx;
   Fy += fy;
   Fz += fz;
-  E += (double)e + 0.5 * (double)enb;
+  E += e + 0.5f * enb;
 }
 
 __device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float R[9]) {
@@ -278,110 +297,278 @@ __device__ __forceinline__ int stop_bits(const Control& ctl, unsigned long long 
   return __shfl_sync(kFull, bits, 0);
 }
 
-__device__ __forceinline__ void report(const Control& ctl, int lane, int n, int evals, int st, int steps) {
-  if (lane == 0) {
-    atomicAdd(&ctl.res->atom_evals, (unsigned long long)n * (unsigned long long)evals);
-    if (st & GRIDFF_REP_CONVERGED) atomicAdd(&ctl.res->n_converged, 1);
-    atomicMax(&ctl.res->max_steps, steps);
-    int sb = st & (GRIDFF_REP_ABORTED | GRIDFF_REP_STEPLIMIT);
-    if (sb) atomicOr(&ctl.res->stop_bits, sb);
-  }
+__device__ __forceinline__ void report(const Control& ctl, int n, int evals, int st, int steps) {
+  atomicAdd(&ctl.res->atom_evals, (unsigned long long)n * (unsigned long long)evals);
+  if (st & GRIDFF_REP_CONVERGED) atomicAdd(&ctl.res->n_converged, 1);
+  atomicMax(&ctl.res->max_steps, steps);
+  int sb = st & (GRIDFF_REP_ABORTED | GRIDFF_REP_STEPLIMIT);
+  if (sb) atomicOr(&ctl.res->stop_bits, sb);
 }
 
-// Forces on one flexible replica: grid term + intramolecular terms.  Lane l
-// owns atoms l, l+32, ...; s_x (per warp) receives all positions first.
-__device__ __forceinline__ void flex_forces(const GridView& g, bool use_grid, bool use_intra,
-                                            const TemplateView& tv, int ab, int n, int lane,
-                                            const float (&x)[KPL][3], float (&F)[KPL][3],
-                                            float (&eg)[KPL], float4 (&par)[KPL], float* s_x,
-                                            double& E, int& flags) {
+// Forces of one flexible replica whose positions are in s.x: grid term
+// (quads over atoms) + intramolecular terms; writes s.f and s.eg and
+// returns this lane's share of the energy (the caller sums the warp).
+__device__ __forceinline__ double flex_forces(const GridView& g, bool use_grid, bool use_intra,
+                                              const TemplateView& tv, int ab, int n, int lane, WarpState& s,
+                                              int& flags) {
   __syncwarp();
-#pragma unroll
-  for (int k = 0; k < KPL; ++k) {
-    int i = lane + 32 * k;
-    if (i < n) {
-      s_x[3 * i] = x[k][0];
-      s_x[3 * i + 1] = x[k][1];
-      s_x[3 * i + 2] = x[k][2];
+  const int quad = lane >> 2, q = lane & 3;
+  double e = 0.0;
+  for (int base = 0; base < n; base += kQuads) {
+    const int i = base + quad;
+    const bool act = i < n;
+    float x = 0.f, y = 0.f, z = 0.f;
+    float4 par = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (act) {
+      x = s.x[3 * i];
+      y = s.x[3 * i + 1];
+      z = s.x[3 * i + 2];
+      par = __ldg(&tv.par[ab + i]);
+      if (!finite3(x, y, z)) flags |= GRIDFF_REP_NONFINITE;
+    }
+    float eg = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+    if (use_grid) grid_quad(g, q, act, x, y, z, par, eg, fx, fy, fz, flags);
+    float ix = 0.f, iy = 0.f, iz = 0.f, ie = 0.f;
+    if (use_intra && act) intra_quad(tv, ab, n, i, q, s.x, ix, iy, iz, ie);
+    ix = qsum(ix);
+    iy = qsum(iy);
+    iz = qsum(iz);
+    e += (double)ie;
+    if (act && q == 0) {
+      s.f[3 * i] = fx + ix;
+      s.f[3 * i + 1] = fy + iy;
+      s.f[3 * i + 2] = fz + iz;
+      s.eg[i] = eg;
+      e += (double)eg;
     }
   }
   __syncwarp();
-  E = 0.0;
+  return e;
+}
+
+// Grid forces of a rigid replica: total force (lab), body-frame torque and
+// this lane's share of the energy.
+__device__ __forceinline__ void rigid_forces(const GridView& g, const TemplateView& tv, int ab, int n, int lane,
+                                             const float c[3], const float Rm[9], float Ft[3], float tq[3],
+                                             double& e, int& flags) {
+  const int quad = lane >> 2, q = lane & 3;
+  for (int a = 0; a < 3; ++a) Ft[a] = tq[a] = 0.f;
+  e = 0.0;
+  for (int base = 0; base < n; base += kQuads) {
+    const int i = base + quad;
+    const bool act = i < n;
+    float4 b = make_float4(0.f, 0.f, 0.f, 0.f), par = b;
+    if (act) {
+      b = __ldg(&tv.body[ab + i]);
+      par = __ldg(&tv.par[ab + i]);
+    }
+    float px = Rm[0] * b.x + Rm[1] * b.y + Rm[2] * b.z + c[0];
+    float py = Rm[3] * b.x + Rm[4] * b.y + Rm[5] * b.z + c[1];
+    float pz = Rm[6] * b.x + Rm[7] * b.y + Rm[8] * b.z + c[2];
+    float ei, fx, fy, fz;
+    grid_quad(g, q, act, px, py, pz, par, ei, fx, fy, fz, flags);
+    if (act && q == 0) {
+      e += (double)ei;
+      Ft[0] += fx;
+      Ft[1] += fy;
+      Ft[2] += fz;
+      // body-frame force R^T f and torque b x (R^T f)
+      float gx = Rm[0] * fx + Rm[3] * fy + Rm[6] * fz;
+      float gy = Rm[1] * fx + Rm[4] * fy + Rm[7] * fz;
+      float gz = Rm[2] * fx + Rm[5] * fy + Rm[8] * fz;
+      tq[0] += b.y * gz - b.z * gy;
+      tq[1] += b.z * gx - b.x * gz;
+      tq[2] += b.x * gy - b.y * gx;
+    }
+  }
+  for (int a = 0; a < 3; ++a) {
+    Ft[a] = wsum(Ft[a]);
+    tq[a] = wsum(tq[a]);
+  }
+  e = wsum(e);
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory staged gather (cp.async): the stencil records of up to NB
+// rounds of 8 atoms are in flight per warp without holding registers.
+// Slot layout per stage: record j of lane l at float4 index j * 32 + l, so
+// both the asynchronous writes and the reads are bank-conflict free.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+struct StencilPos {   // fold and cell of one atom (shared by issue and compute)
+  int ix, iy, iz;
+  float tx, ty, tz;
+  bool inside;
+};
+
+__device__ __forceinline__ StencilPos locate(const GridView& g, bool act, float x, float y, float z, int& flags) {
+  StencilPos sp;
+  float xr = x - g.x0, yr = y - g.y0;
+  xr = fmaf(-g.Lx, floorf(xr * g.inv_Lx), xr);
+  yr = fmaf(-g.Ly, floorf(yr * g.inv_Ly), yr);
+  float ux = xr * g.inv_dx, uy = yr * g.inv_dy, uz = (z - g.z0) * g.inv_dz;
+  float flx = floorf(ux), fly = floorf(uy);
+  sp.tx = fminf(fmaxf(ux - flx, 0.f), 1.f);
+  sp.ty = fminf(fmaxf(uy - fly, 0.f), 1.f);
+  int ix = (int)flx, iy = (int)fly;
+  if (ix >= g.nx) ix -= g.nx;
+  if (iy >= g.ny) iy -= g.ny;
+  sp.ix = min(max(ix, 0), g.nx - 1);
+  sp.iy = min(max(iy, 0), g.ny - 1);
+  if (act && uz < 0.f) flags |= GRIDFF_REP_BELOW;
+  uz = fmaxf(uz, 0.f);
+  sp.inside = act && (uz < (float)(g.nz - 1));
+  float flz = floorf(sp.inside ? uz : 0.f);
+  sp.tz = (sp.inside ? uz : 0.f) - flz;
+  sp.iz = min(max((int)flz, 0), g.nz - 2);
+  return sp;
+}
+
+template <int NB>
+__device__ __forceinline__ void rigid_forces_staged(const GridView& g, const TemplateView& tv, int ab, int n,
+                                                    int lane, const float c[3], const float Rm[9], float Ft[3],
+                                                    float tq[3], double& e, int& flags, float4* sbuf) {
+  const int quad = lane >> 2, q = lane & 3;
+  const int R = (n + kQuads - 1) / kQuads;
+  for (int a = 0; a < 3; ++a) Ft[a] = tq[a] = 0.f;
+  e = 0.0;
+  auto atom = [&](int k, float4& b, float4& par, float p[3]) {
+    const int i = k * kQuads + quad;
+    const bool act = i < n;
+    b = make_float4(0.f, 0.f, 0.f, 0.f);
+    par = b;
+    if (act) {
+      b = __ldg(&tv.body[ab + i]);
+      par = __ldg(&tv.par[ab + i]);
+    }
+    p[0] = Rm[0] * b.x + Rm[1] * b.y + Rm[2] * b.z + c[0];
+    p[1] = Rm[3] * b.x + Rm[4] * b.y + Rm[5] * b.z + c[1];
+    p[2] = Rm[6] * b.x + Rm[7] * b.y + Rm[8] * b.z + c[2];
+    return act;
+  };
+  auto issue = [&](int k) {
+    if (k < R) {
+      float4 b, par;
+      float p[3];
+      int dummy = 0;
+      bool act = atom(k, b, par, p);
+      StencilPos sp = locate(g, act, p[0], p[1], p[2], dummy);
+      if (sp.inside) {
+        const float4* p0 = g.rec + ((long long)sp.ix * g.nyp + sp.iy) * g.nzp + sp.iz + q;
+        float4* dst = sbuf + (k % NB) * 512 + lane;
 #pragma unroll
-  for (int k = 0; k < KPL; ++k) {
-    int i = lane + 32 * k;
-    F[k][0] = F[k][1] = F[k][2] = 0.f;
-    eg[k] = 0.f;
-    if (i < n) {
-      if (!finite3(x[k][0], x[k][1], x[k][2])) flags |= GRIDFF_REP_NONFINITE;
-      if (use_grid) {
-        grid_atom(g, x[k][0], x[k][1], x[k][2], par[k], eg[k], F[k][0], F[k][1], F[k][2], flags);
-        E += (double)eg[k];
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int bb = 0; bb < 4; ++bb) cp_async16(dst + (a * 4 + bb) * 32, p0 + a * g.sx + bb * g.nzp);
       }
-      if (use_intra) intra_atom(tv, ab, n, i, s_x, F[k][0], F[k][1], F[k][2], E);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int k = 0; k < NB; ++k) issue(k);
+  for (int k = 0; k < R; ++k) {
+    cp_async_wait<NB - 1>();
+    float4 b, par;
+    float p[3];
+    bool act = atom(k, b, par, p);
+    StencilPos sp = locate(g, act, p[0], p[1], p[2], flags);
+    float wx[4], dwx[4], wy[4], dwy[4], wz[4], dwz[4];
+    bspline_weights(sp.tx, wx, dwx);
+    bspline_weights(sp.ty, wy, dwy);
+    bspline_weights(sp.tz, wz, dwz);
+    float S0 = 0.f, Sx = 0.f, Sy = 0.f;
+    if (sp.inside) {
+      const float4* src = sbuf + (k % NB) * 512 + lane;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        float s = 0.f, sy = 0.f;
+#pragma unroll
+        for (int bb = 0; bb < 4; ++bb) {
+          float4 r = src[(a * 4 + bb) * 32];
+          float cc = fmaf(par.x, r.x, fmaf(par.y, r.y, par.z * r.z));
+          s = fmaf(wy[bb], cc, s);
+          sy = fmaf(dwy[bb], cc, sy);
+        }
+        S0 = fmaf(wx[a], s, S0);
+        Sx = fmaf(dwx[a], s, Sx);
+        Sy = fmaf(wx[a], sy, Sy);
+      }
+    }
+    issue(k + NB);
+    const float wq = q == 0 ? wz[0] : q == 1 ? wz[1] : q == 2 ? wz[2] : wz[3];
+    const float dwq = q == 0 ? dwz[0] : q == 1 ? dwz[1] : q == 2 ? dwz[2] : dwz[3];
+    float ei = qsum(wq * S0);
+    float fx = -qsum(wq * Sx) * g.inv_dx;
+    float fy = -qsum(wq * Sy) * g.inv_dy;
+    float fz = -qsum(dwq * S0) * g.inv_dz;
+    if (act && q == 0) {
+      e += (double)ei;
+      Ft[0] += fx;
+      Ft[1] += fy;
+      Ft[2] += fz;
+      float gx = Rm[0] * fx + Rm[3] * fy + Rm[6] * fz;
+      float gy = Rm[1] * fx + Rm[4] * fy + Rm[7] * fz;
+      float gz = Rm[2] * fx + Rm[5] * fy + Rm[8] * fz;
+      tq[0] += b.y * gz - b.z * gy;
+      tq[1] += b.z * gx - b.x * gz;
+      tq[2] += b.x * gy - b.y * gx;
     }
   }
+  cp_async_wait<0>();
+  for (int a = 0; a < 3; ++a) {
+    Ft[a] = wsum(Ft[a]);
+    tq[a] = wsum(tq[a]);
+  }
+  e = wsum(e);
 }
 
 // ---------------------------------------------------------------------------
 // evaluation (no update)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, kMinBlocksPerSM)
 eval_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
             const int* __restrict__ rep_off, int n_rep, int rigid, const float* __restrict__ xs,
             int use_grid, int use_intra, double* __restrict__ E_out, float* __restrict__ F_out,
             float* __restrict__ Ea_out, int* __restrict__ st_out) {
-  __shared__ float s_x[kWarpsPerBlock][3 * GRIDFF_MAX_ATOMS];
+  __shared__ WarpState s_all[kWarpsPerBlock];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  WarpState& s = s_all[wib];
   const int warp = blockIdx.x * kWarpsPerBlock + wib;
   const int n_warps = gridDim.x * kWarpsPerBlock;
   for (int r = warp; r < n_rep; r += n_warps) {
     const int t = rep_tmpl[r], n = tv.natoms[t], ab = tv.atom_off[t], off = rep_off[r];
-    float x[KPL][3], F[KPL][3], eg[KPL];
-    float4 par[KPL];
-    float Rm[9];
-    float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+    __syncwarp();
     if (rigid) {
       const float* p = xs + 7 * (size_t)r;
+      float Rm[9];
       quat_rot(p[3], p[4], p[5], p[6], Rm);
-      c0 = p[0];
-      c1 = p[1];
-      c2 = p[2];
-    }
-#pragma unroll
-    for (int k = 0; k < KPL; ++k) {
-      int i = lane + 32 * k;
-      par[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-      x[k][0] = x[k][1] = x[k][2] = 0.f;
-      if (i < n) {
-        par[k] = tv.par[ab + i];
-        if (rigid) {
-          float4 b = tv.body[ab + i];
-          x[k][0] = Rm[0] * b.x + Rm[1] * b.y + Rm[2] * b.z + c0;
-          x[k][1] = Rm[3] * b.x + Rm[4] * b.y + Rm[5] * b.z + c1;
-          x[k][2] = Rm[6] * b.x + Rm[7] * b.y + Rm[8] * b.z + c2;
-        } else {
-          const float* p = xs + 3 * ((size_t)off + i);
-          x[k][0] = p[0];
-          x[k][1] = p[1];
-          x[k][2] = p[2];
-        }
+      for (int i = lane; i < n; i += 32) {
+        float4 b = tv.body[ab + i];
+        s.x[3 * i] = Rm[0] * b.x + Rm[1] * b.y + Rm[2] * b.z + p[0];
+        s.x[3 * i + 1] = Rm[3] * b.x + Rm[4] * b.y + Rm[5] * b.z + p[1];
+        s.x[3 * i + 2] = Rm[6] * b.x + Rm[7] * b.y + Rm[8] * b.z + p[2];
       }
+    } else {
+      for (int k = lane; k < 3 * n; k += 32) s.x[k] = xs[3 * (size_t)off + k];
     }
-    double E = 0.0;
     int flags = 0;
-    flex_forces(g, use_grid, use_intra && !rigid, tv, ab, n, lane, x, F, eg, par, s_x[wib], E, flags);
-#pragma unroll
-    for (int k = 0; k < KPL; ++k) {
-      int i = lane + 32 * k;
-      if (i < n) {
-        float* f = F_out + 3 * ((size_t)off + i);
-        f[0] = F[k][0];
-        f[1] = F[k][1];
-        f[2] = F[k][2];
-        if (Ea_out) Ea_out[off + i] = eg[k];
-        if (!finite3(F[k][0], F[k][1], F[k][2])) flags |= GRIDFF_REP_NONFINITE;
-      }
+    double E = flex_forces(g, use_grid, use_intra && !rigid, tv, ab, n, lane, s, flags);
+    for (int i = lane; i < n; i += 32) {
+      float* f = F_out + 3 * ((size_t)off + i);
+      f[0] = s.f[3 * i];
+      f[1] = s.f[3 * i + 1];
+      f[2] = s.f[3 * i + 2];
+      if (Ea_out) Ea_out[off + i] = s.eg[i];
+      if (!finite3(f[0], f[1], f[2])) flags |= GRIDFF_REP_NONFINITE;
     }
     E = wsum(E);
     flags = __reduce_or_sync(kFull, flags);
@@ -396,10 +583,13 @@ eval_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
 // ---------------------------------------------------------------------------
 // FIRE, rigid replicas
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, kMinBlocksPerSM)
 relax_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, int n_rep,
                    float* pose, float* vel, float* fdt, float* falpha, int* fnp, int* status,
                    int* steps, double* energy, int nsteps, FireP fp, Control ctl, int use_grid) {
+#if GRIDFF_STAGED_NB > 0
+  extern __shared__ float4 s_stage[];
+#endif
   const int lane = threadIdx.x & 31;
   const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   const int n_warps = gridDim.x * kWarpsPerBlock;
@@ -408,21 +598,6 @@ relax_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl
     const int t = rep_tmpl[r], n = tv.natoms[t], ab = tv.atom_off[t];
     const float4 rig = tv.rigid[t];
     const float rmax = tv.rmax[t];
-    float b[KPL][3];
-    float4 par[KPL];
-#pragma unroll
-    for (int k = 0; k < KPL; ++k) {
-      int i = lane + 32 * k;
-      b[k][0] = b[k][1] = b[k][2] = 0.f;
-      par[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (i < n) {
-        float4 bb = tv.body[ab + i];
-        b[k][0] = bb.x;
-        b[k][1] = bb.y;
-        b[k][2] = bb.z;
-        par[k] = tv.par[ab + i];
-      }
-    }
     float c[3], q[4], v[3], w[3];
     for (int a = 0; a < 3; ++a) {
       c[a] = pose[7 * (size_t)r + a];
@@ -444,36 +619,19 @@ relax_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl
       }
       float Rm[9];
       quat_rot(q[0], q[1], q[2], q[3], Rm);
-      float Ft[3] = {0.f, 0.f, 0.f}, tq[3] = {0.f, 0.f, 0.f};
+      float Ft[3], tq[3];
       double e = 0.0;
       int flags = 0;
-#pragma unroll
-      for (int k = 0; k < KPL; ++k) {
-        int i = lane + 32 * k;
-        if (i < n && use_grid) {
-          float px = Rm[0] * b[k][0] + Rm[1] * b[k][1] + Rm[2] * b[k][2] + c[0];
-          float py = Rm[3] * b[k][0] + Rm[4] * b[k][1] + Rm[5] * b[k][2] + c[1];
-          float pz = Rm[6] * b[k][0] + Rm[7] * b[k][1] + Rm[8] * b[k][2] + c[2];
-          float ei, fx, fy, fz;
-          grid_atom(g, px, py, pz, par[k], ei, fx, fy, fz, flags);
-          e += (double)ei;
-          Ft[0] += fx;
-          Ft[1] += fy;
-          Ft[2] += fz;
-          // body-frame force R^T f and torque b x (R^T f)
-          float gx = Rm[0] * fx + Rm[3] * fy + Rm[6] * fz;
-          float gy = Rm[1] * fx + Rm[4] * fy + Rm[7] * fz;
-          float gz = Rm[2] * fx + Rm[5] * fy + Rm[8] * fz;
-          tq[0] += b[k][1] * gz - b[k][2] * gy;
-          tq[1] += b[k][2] * gx - b[k][0] * gz;
-          tq[2] += b[k][0] * gy - b[k][1] * gx;
-        }
+      if (use_grid) {
+#if GRIDFF_STAGED_NB > 0
+        rigid_forces_staged<GRIDFF_STAGED_NB>(g, tv, ab, n, lane, c, Rm, Ft, tq, e, flags,
+                                              s_stage + (threadIdx.x >> 5) * GRIDFF_STAGED_NB * 512);
+#else
+        rigid_forces(g, tv, ab, n, lane, c, Rm, Ft, tq, e, flags);
+#endif
+      } else {
+        for (int a = 0; a < 3; ++a) Ft[a] = tq[a] = 0.f;
       }
-      for (int a = 0; a < 3; ++a) {
-        Ft[a] = wsum(Ft[a]);
-        tq[a] = wsum(tq[a]);
-      }
-      e = wsum(e);
       st |= __reduce_or_sync(kFull, flags);
       ++evals;
       Elast = e;
@@ -488,16 +646,17 @@ relax_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl
         st |= GRIDFF_REP_CONVERGED;
         break;
       }
+      // FIRE decision (identical in every lane: the sums are bitwise equal)
       float P = Ft[0] * v[0] + Ft[1] * v[1] + Ft[2] * v[2] + tq[0] * w[0] + tq[1] * w[1] + tq[2] * w[2];
       if (P > 0.f) {
         float fn = sqrtf(Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2]);
         float tn = sqrtf(tq[0] * tq[0] + tq[1] * tq[1] + tq[2] * tq[2]);
         float vn = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
         float wn = sqrtf(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-        float sf = fn > 0.f ? al * vn / fn : 0.f, st_ = tn > 0.f ? al * wn / tn : 0.f;
+        float sf = fn > 0.f ? al * vn / fn : 0.f, sw = tn > 0.f ? al * wn / tn : 0.f;
         for (int a = 0; a < 3; ++a) {
           v[a] = (1.f - al) * v[a] + sf * Ft[a];
-          w[a] = (1.f - al) * w[a] + st_ * tq[a];
+          w[a] = (1.f - al) * w[a] + sw * tq[a];
         }
         if (np > fp.n_min) {
           dt = fminf(dt * fp.f_inc, fp.dt_max);
@@ -541,7 +700,7 @@ relax_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl
       int total = steps[r] + evals;
       steps[r] = total;
       energy[r] = Elast;
-      report(ctl, lane, n, evals, st, total);
+      report(ctl, n, evals, st, total);
     }
   }
 }
@@ -549,59 +708,44 @@ relax_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl
 // ---------------------------------------------------------------------------
 // FIRE, flexible replicas
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, kMinBlocksPerSM)
 relax_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
                   const int* __restrict__ rep_off, int n_rep, float* xs, float* vs, float* fdt,
                   float* falpha, int* fnp, int* status, int* steps, double* energy, int nsteps,
                   FireP fp, Control ctl, int use_grid, int use_intra) {
-  __shared__ float s_x[kWarpsPerBlock][3 * GRIDFF_MAX_ATOMS];
+  __shared__ WarpState s_all[kWarpsPerBlock];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  WarpState& s = s_all[wib];
   const int warp = blockIdx.x * kWarpsPerBlock + wib;
   const int n_warps = gridDim.x * kWarpsPerBlock;
   const unsigned long long t0 = gtimer();
   for (int r = warp; r < n_rep; r += n_warps) {
     const int t = rep_tmpl[r], n = tv.natoms[t], ab = tv.atom_off[t], off = rep_off[r];
-    float x[KPL][3], v[KPL][3], F[KPL][3], eg[KPL], im[KPL];
-    float4 par[KPL];
-#pragma unroll
-    for (int k = 0; k < KPL; ++k) {
-      int i = lane + 32 * k;
-      im[k] = 0.f;
-      par[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int a = 0; a < 3; ++a) x[k][a] = v[k][a] = 0.f;
-      if (i < n) {
-        par[k] = tv.par[ab + i];
-        im[k] = 1.f / tv.body[ab + i].w;
-        for (int a = 0; a < 3; ++a) {
-          x[k][a] = xs[3 * ((size_t)off + i) + a];
-          v[k][a] = vs[3 * ((size_t)off + i) + a];
-        }
-      }
+    __syncwarp();
+    for (int k = lane; k < 3 * n; k += 32) {
+      s.x[k] = xs[3 * (size_t)off + k];
+      s.v[k] = vs[3 * (size_t)off + k];
     }
     float dt = fdt[r], al = falpha[r];
     int np = fnp[r], st = status[r], evals = 0;
     double Elast = energy[r];
-    for (int s = 0; s < nsteps; ++s) {
+    for (int it = 0; it < nsteps; ++it) {
       if (st & (GRIDFF_REP_CONVERGED | GRIDFF_REP_NONFINITE)) break;
-      if ((s & 31) == 0) {
+      if ((it & 31) == 0) {
         int sb = stop_bits(ctl, t0, lane);
         if (sb) {
           st |= sb;
           break;
         }
       }
-      double e = 0.0;
       int flags = 0;
-      flex_forces(g, use_grid, use_intra, tv, ab, n, lane, x, F, eg, par, s_x[wib], e, flags);
+      double e = flex_forces(g, use_grid, use_intra, tv, ab, n, lane, s, flags);
       float f2 = 0.f, P = 0.f, v2 = 0.f;
-#pragma unroll
-      for (int k = 0; k < KPL; ++k) {
-        if (!finite3(F[k][0], F[k][1], F[k][2])) flags |= GRIDFF_REP_NONFINITE;
-        for (int a = 0; a < 3; ++a) {
-          f2 += F[k][a] * F[k][a];
-          P += F[k][a] * v[k][a];
-          v2 += v[k][a] * v[k][a];
-        }
+      for (int k = lane; k < 3 * n; k += 32) {
+        float f = s.f[k], v = s.v[k];
+        f2 = fmaf(f, f, f2);
+        P = fmaf(f, v, P);
+        v2 = fmaf(v, v, v2);
       }
       f2 = wsum(f2);
       P = wsum(P);
@@ -635,28 +779,25 @@ relax_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
         al = fp.alpha_start;
         np = 0;
       }
-#pragma unroll
-      for (int k = 0; k < KPL; ++k) {
+      for (int i = lane; i < n; i += 32) {
+        const float im = 1.f / __ldg(&tv.body[ab + i]).w;
         float d[3];
         for (int a = 0; a < 3; ++a) {
-          float vv = keep * v[k][a] + mixf * F[k][a];
-          vv += GRIDFF_ACC * F[k][a] * im[k] * dt;
-          v[k][a] = vv;
+          float f = s.f[3 * i + a];
+          float vv = keep * s.v[3 * i + a] + mixf * f;
+          vv += GRIDFF_ACC * f * im * dt;
+          s.v[3 * i + a] = vv;
           d[a] = vv * dt;
         }
         float dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         float sc = dn > fp.d_max ? fp.d_max / dn : 1.f;
-        for (int a = 0; a < 3; ++a) x[k][a] += d[a] * sc;
+        for (int a = 0; a < 3; ++a) s.x[3 * i + a] += d[a] * sc;
       }
     }
-#pragma unroll
-    for (int k = 0; k < KPL; ++k) {
-      int i = lane + 32 * k;
-      if (i < n)
-        for (int a = 0; a < 3; ++a) {
-          xs[3 * ((size_t)off + i) + a] = x[k][a];
-          vs[3 * ((size_t)off + i) + a] = v[k][a];
-        }
+    __syncwarp();
+    for (int k = lane; k < 3 * n; k += 32) {
+      xs[3 * (size_t)off + k] = s.x[k];
+      vs[3 * (size_t)off + k] = s.v[k];
     }
     if (lane == 0) {
       fdt[r] = dt;
@@ -666,7 +807,7 @@ relax_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
       int total = steps[r] + evals;
       steps[r] = total;
       energy[r] = Elast;
-      report(ctl, lane, n, evals, st, total);
+      report(ctl, n, evals, st, total);
     }
   }
 }
@@ -674,94 +815,80 @@ relax_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
 // ---------------------------------------------------------------------------
 // NVE, flexible replicas: velocity Verlet
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, kMinBlocksPerSM)
 run_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
                 const int* __restrict__ rep_off, int n_rep, float* xs, float* vs, int* status,
                 double* energy, int nsteps, float dt, int rec_every, double* trace, Control ctl,
                 int use_grid, int use_intra) {
-  __shared__ float s_x[kWarpsPerBlock][3 * GRIDFF_MAX_ATOMS];
+  __shared__ WarpState s_all[kWarpsPerBlock];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  WarpState& s = s_all[wib];
   const int warp = blockIdx.x * kWarpsPerBlock + wib;
   const int n_warps = gridDim.x * kWarpsPerBlock;
   const unsigned long long t0 = gtimer();
   for (int r = warp; r < n_rep; r += n_warps) {
     const int t = rep_tmpl[r], n = tv.natoms[t], ab = tv.atom_off[t], off = rep_off[r];
-    float x[KPL][3], v[KPL][3], F[KPL][3], eg[KPL], m[KPL];
-    float4 par[KPL];
-#pragma unroll
-    for (int k = 0; k < KPL; ++k) {
-      int i = lane + 32 * k;
-      m[k] = 0.f;
-      par[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-      for (int a = 0; a < 3; ++a) x[k][a] = v[k][a] = 0.f;
-      if (i < n) {
-        par[k] = tv.par[ab + i];
-        m[k] = tv.body[ab + i].w;
-        for (int a = 0; a < 3; ++a) {
-          x[k][a] = xs[3 * ((size_t)off + i) + a];
-          v[k][a] = vs[3 * ((size_t)off + i) + a];
-        }
-      }
+    __syncwarp();
+    for (int k = lane; k < 3 * n; k += 32) {
+      s.x[k] = xs[3 * (size_t)off + k];
+      s.v[k] = vs[3 * (size_t)off + k];
     }
     int st = status[r] & ~(GRIDFF_REP_ABORTED | GRIDFF_REP_STEPLIMIT);
     int flags = 0, evals = 0;
-    double e = 0.0;
-    flex_forces(g, use_grid, use_intra, tv, ab, n, lane, x, F, eg, par, s_x[wib], e, flags);
-    auto total = [&](double epot) {
+    double e = flex_forces(g, use_grid, use_intra, tv, ab, n, lane, s, flags);
+    auto total = [&](double epot_lane) {
       double ke = 0.0;
-#pragma unroll
-      for (int k = 0; k < KPL; ++k)
-        ke += 0.5 * (double)m[k] * (double)(v[k][0] * v[k][0] + v[k][1] * v[k][1] + v[k][2] * v[k][2]);
-      return wsum(epot) + wsum(ke) / (double)GRIDFF_ACC;
+      for (int i = lane; i < n; i += 32) {
+        double m = __ldg(&tv.body[ab + i]).w;
+        double vx = s.v[3 * i], vy = s.v[3 * i + 1], vz = s.v[3 * i + 2];
+        ke += 0.5 * m * (vx * vx + vy * vy + vz * vz);
+      }
+      return wsum(epot_lane) + wsum(ke) / (double)GRIDFF_ACC;
     };
     double Etot = total(e);
     if (trace && lane == 0) trace[r] = Etot;
     int rec = 1;
-    for (int s = 0; s < nsteps; ++s) {
-      if ((s & 31) == 0) {
+    for (int it = 0; it < nsteps; ++it) {
+      if ((it & 31) == 0) {
         int sb = stop_bits(ctl, t0, lane);
         if (sb) {
           st |= sb;
           break;
         }
       }
-#pragma unroll
-      for (int k = 0; k < KPL; ++k) {
-        float h = 0.5f * dt * GRIDFF_ACC / (m[k] > 0.f ? m[k] : 1.f);
+      for (int i = lane; i < n; i += 32) {
+        const float h = 0.5f * dt * GRIDFF_ACC / __ldg(&tv.body[ab + i]).w;
         for (int a = 0; a < 3; ++a) {
-          v[k][a] += h * F[k][a];
-          x[k][a] += dt * v[k][a];
+          float vv = s.v[3 * i + a] + h * s.f[3 * i + a];
+          s.v[3 * i + a] = vv;
+          s.x[3 * i + a] += dt * vv;
         }
       }
-      flex_forces(g, use_grid, use_intra, tv, ab, n, lane, x, F, eg, par, s_x[wib], e, flags);
+      e = flex_forces(g, use_grid, use_intra, tv, ab, n, lane, s, flags);
       ++evals;
-#pragma unroll
-      for (int k = 0; k < KPL; ++k) {
-        float h = 0.5f * dt * GRIDFF_ACC / (m[k] > 0.f ? m[k] : 1.f);
-        for (int a = 0; a < 3; ++a) v[k][a] += h * F[k][a];
+      for (int i = lane; i < n; i += 32) {
+        const float h = 0.5f * dt * GRIDFF_ACC / __ldg(&tv.body[ab + i]).w;
+        for (int a = 0; a < 3; ++a) s.v[3 * i + a] += h * s.f[3 * i + a];
       }
-      if (rec_every > 0 && (s + 1) % rec_every == 0) {
+      __syncwarp();
+      if (rec_every > 0 && (it + 1) % rec_every == 0) {
         Etot = total(e);
         if (trace && lane == 0) trace[(size_t)rec * n_rep + r] = Etot;
         ++rec;
       }
     }
-#pragma unroll
-    for (int k = 0; k < KPL; ++k) {
-      int i = lane + 32 * k;
-      if (i < n)
-        for (int a = 0; a < 3; ++a) {
-          xs[3 * ((size_t)off + i) + a] = x[k][a];
-          vs[3 * ((size_t)off + i) + a] = v[k][a];
-        }
+    __syncwarp();
+    for (int k = lane; k < 3 * n; k += 32) {
+      xs[3 * (size_t)off + k] = s.x[k];
+      vs[3 * (size_t)off + k] = s.v[k];
     }
     st |= __reduce_or_sync(kFull, flags);
     e = wsum(e);
     if (lane == 0) {
       status[r] = st;
       energy[r] = e;
+      report(ctl, n, evals, st & ~GRIDFF_REP_CONVERGED, evals);
     }
-    report(ctl, lane, n, evals, st & ~GRIDFF_REP_CONVERGED, evals);
   }
 }
 
@@ -810,42 +937,7 @@ __device__ __forceinline__ void body_L(const float q[4], const float p[4], float
   }
 }
 
-__device__ __forceinline__ void rigid_forces(const GridView& g, int n, int lane, const float (&b)[KPL][3],
-                                             const float4 (&par)[KPL], const float c[3], const float q[4],
-                                             float Ft[3], float tq[3], double& e, int& flags) {
-  float Rm[9];
-  quat_rot(q[0], q[1], q[2], q[3], Rm);
-  for (int a = 0; a < 3; ++a) Ft[a] = tq[a] = 0.f;
-  e = 0.0;
-#pragma unroll
-  for (int k = 0; k < KPL; ++k) {
-    int i = lane + 32 * k;
-    if (i < n) {
-      float px = Rm[0] * b[k][0] + Rm[1] * b[k][1] + Rm[2] * b[k][2] + c[0];
-      float py = Rm[3] * b[k][0] + Rm[4] * b[k][1] + Rm[5] * b[k][2] + c[1];
-      float pz = Rm[6] * b[k][0] + Rm[7] * b[k][1] + Rm[8] * b[k][2] + c[2];
-      float ei, fx, fy, fz;
-      grid_atom(g, px, py, pz, par[k], ei, fx, fy, fz, flags);
-      e += (double)ei;
-      Ft[0] += fx;
-      Ft[1] += fy;
-      Ft[2] += fz;
-      float gx = Rm[0] * fx + Rm[3] * fy + Rm[6] * fz;
-      float gy = Rm[1] * fx + Rm[4] * fy + Rm[7] * fz;
-      float gz = Rm[2] * fx + Rm[5] * fy + Rm[8] * fz;
-      tq[0] += b[k][1] * gz - b[k][2] * gy;
-      tq[1] += b[k][2] * gx - b[k][0] * gz;
-      tq[2] += b[k][0] * gy - b[k][1] * gx;
-    }
-  }
-  for (int a = 0; a < 3; ++a) {
-    Ft[a] = wsum(Ft[a]);
-    tq[a] = wsum(tq[a]);
-  }
-  e = wsum(e);
-}
-
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, kMinBlocksPerSM)
 run_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, int n_rep,
                  float* pose, float* vel, int* status, double* energy, int nsteps, float dt,
                  int rec_every, double* trace, Control ctl) {
@@ -857,21 +949,6 @@ run_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, 
     const int t = rep_tmpl[r], n = tv.natoms[t], ab = tv.atom_off[t];
     const float4 rig = tv.rigid[t];
     const float I[3] = {rig.y, rig.z, rig.w};
-    float b[KPL][3];
-    float4 par[KPL];
-#pragma unroll
-    for (int k = 0; k < KPL; ++k) {
-      int i = lane + 32 * k;
-      b[k][0] = b[k][1] = b[k][2] = 0.f;
-      par[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (i < n) {
-        float4 bb = tv.body[ab + i];
-        b[k][0] = bb.x;
-        b[k][1] = bb.y;
-        b[k][2] = bb.z;
-        par[k] = tv.par[ab + i];
-      }
-    }
     float c[3], q[4], v[3], p[4];
     for (int a = 0; a < 3; ++a) {
       c[a] = pose[7 * (size_t)r + a];
@@ -889,7 +966,9 @@ run_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, 
     int flags = 0, evals = 0;
     float Ft[3], tq[3];
     double e;
-    rigid_forces(g, n, lane, b, par, c, q, Ft, tq, e, flags);
+    float Rm[9];
+    quat_rot(q[0], q[1], q[2], q[3], Rm);
+    rigid_forces(g, tv, ab, n, lane, c, Rm, Ft, tq, e, flags);
     auto total = [&](double epot) {
       float L[3];
       body_L(q, p, L);
@@ -899,8 +978,8 @@ run_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, 
     };
     if (trace && lane == 0) trace[r] = total(e);
     int rec = 1;
-    for (int s = 0; s < nsteps; ++s) {
-      if ((s & 31) == 0) {
+    for (int it = 0; it < nsteps; ++it) {
+      if ((it & 31) == 0) {
         int sb = stop_bits(ctl, t0, lane);
         if (sb) {
           st |= sb;
@@ -917,12 +996,13 @@ run_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, 
       free_rot(1, dt, I[0], q, p);
       free_rot(2, h, I[1], q, p);
       free_rot(3, h, I[2], q, p);
-      rigid_forces(g, n, lane, b, par, c, q, Ft, tq, e, flags);
+      quat_rot(q[0], q[1], q[2], q[3], Rm);
+      rigid_forces(g, tv, ab, n, lane, c, Rm, Ft, tq, e, flags);
       ++evals;
       for (int a = 0; a < 3; ++a) v[a] += h * GRIDFF_ACC * Ft[a] / rig.x;
       float tb2[3] = {GRIDFF_ACC * tq[0], GRIDFF_ACC * tq[1], GRIDFF_ACC * tq[2]};
       kick_rot(p, q, tb2, h);
-      if (rec_every > 0 && (s + 1) % rec_every == 0) {
+      if (rec_every > 0 && (it + 1) % rec_every == 0) {
         if (trace && lane == 0) trace[(size_t)rec * n_rep + r] = total(e);
         ++rec;
       }
@@ -939,8 +1019,8 @@ run_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, 
       for (int a = 0; a < 4; ++a) pose[7 * (size_t)r + 3 + a] = q[a];
       status[r] = st;
       energy[r] = e;
+      report(ctl, n, evals, st & ~GRIDFF_REP_CONVERGED, evals);
     }
-    report(ctl, lane, n, evals, st & ~GRIDFF_REP_CONVERGED, evals);
   }
 }
 
@@ -956,9 +1036,9 @@ struct Staging {
   }
 };
 
-int persistent_blocks(gridff_ctx* ctx, const void* kernel, int n_rep) {
+int persistent_blocks(gridff_ctx* ctx, const void* kernel, int n_rep, size_t dyn_smem = 0) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, dyn_smem);
   if (per_sm < 1) per_sm = 1;
   int need = (n_rep + kWarpsPerBlock - 1) / kWarpsPerBlock;
   int cap = per_sm * ctx->n_sm;
@@ -1071,8 +1151,11 @@ gridff_status gridff_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_repl
   int use_grid = !(flags & GRIDFF_NO_GRID), use_intra = !(flags & GRIDFF_NO_INTRA);
   GRIDFF_CUDA(ctx, cudaEventRecord(ctx->ev0, s));
   if (R->rigid) {
-    int blocks = persistent_blocks(ctx, (const void*)relax_rigid_kernel, R->n_rep);
-    relax_rigid_kernel<<<blocks, kThreads, 0, s>>>(gv, R->tv, R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt,
+    size_t dyn = (size_t)GRIDFF_STAGED_NB * 512 * sizeof(float4) * kWarpsPerBlock;
+    if (dyn > 48 * 1024)
+      GRIDFF_CUDA(ctx, cudaFuncSetAttribute(relax_rigid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    int blocks = persistent_blocks(ctx, (const void*)relax_rigid_kernel, R->n_rep, dyn);
+    relax_rigid_kernel<<<blocks, kThreads, dyn, s>>>(gv, R->tv, R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt,
                                                    R->fire_alpha, R->fire_nplus, R->status, R->steps,
                                                    R->energy, nsteps, fp, ctl, use_grid);
   } else {
