@@ -179,8 +179,9 @@ def kernel_source_hash():
 
 
 def ncu_traffic():
-    """DRAM bytes per atom-eval of the relax kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
+    """DRAM bytes (read + write) per launch of the relax kernel from the
+    committed ncu summary, if it was taken on the current kernel source
+    (else None)."""
     p = os.path.join(ROOT, "profiles", "relax_rigid_c24h8o6_4096.json")
     try:
         d = json.load(open(p))
@@ -188,7 +189,7 @@ def ncu_traffic():
         return None
     if d.get("kernel_source_hash") != kernel_source_hash():
         return None
-    return d.get("dram_bytes_per_atom_eval")
+    return d.get("dram_bytes_per_launch")
 
 
 def measured_peaks():
@@ -300,11 +301,11 @@ def run_gpu(args):
                           "fire_iterations_per_step": iters}),
         "replica_steps_per_s": value / mol.n,
         "roofline": {"bound": "l2", "achieved": achieved, "peak": l2_peak, "unit": "GB/s",
-                     "frac": (achieved / l2_peak) if l2_peak else None, "traffic": (tpe * per_launch_evals) if tpe else None,
-                     "kernel": "relax_rigid_kernel", "bytes_per_unit": BYTES_PER_EVAL,
+                     "frac": (achieved / l2_peak) if l2_peak else None, "traffic": tpe,
+                     "kernel": "relax_rigid_sw_kernel<16>", "bytes_per_unit": BYTES_PER_EVAL,
                      "units_per_launch": per_launch_evals, "kernel_ms": k_ms,
                      "peak_source": "measured in this run: streaming read of a 48 MB L2-resident buffer "
-                                    "(gridff_probe_read_bandwidth)",
+                                    "(gridff_probe_read_bandwidth, best of 3 launch shapes)",
                      "hbm_peak_measured": peaks.get("hbm_gbs"), "hbm_read_this_run": hbm_read},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 7 * 4 * N_REP,
                 "d2h_bytes_per_step": (7 + 6) * 4 * N_REP + (5 * 4 + 8) * N_REP},

@@ -31,6 +31,9 @@
  *    per-replica status word (GRIDFF_REP_* bits).
  *  - The caller owns every array it passes.  Handles (context, grid,
  *    replicas) own the device memory they allocate; *_destroy frees it.
+ *    Grids and replica sets must not be used after their context is
+ *    destroyed; destroying them afterwards is allowed (it needs only the
+ *    device id they recorded).
  *  - Array arguments are host pointers unless GRIDFF_DEVICE_PTRS is set in
  *    `flags`, in which case they are device pointers (e.g. torch CUDA
  *    tensors) and are used in place without copies.
@@ -82,7 +85,7 @@ typedef enum {
 #define GRIDFF_CH_L 4            /* London V^L */
 
 /* coefficient storage */
-#define GRIDFF_STORE_F32 0       /* float32 records, one 16-byte record per node */
+#define GRIDFF_STORE_F32 0       /* float32, one 16-byte record {C, P, L, 0} per node */
 
 typedef struct gridff_ctx gridff_ctx;
 typedef struct gridff_grid gridff_grid;
@@ -322,8 +325,8 @@ gridff_status gridff_run(gridff_ctx* ctx, const gridff_grid* grid, gridff_replic
 /* ------------------------------------------------------------ measurement */
 
 /* Read `bytes` of a device buffer `iters` times with a streaming kernel and
- * return the achieved read bandwidth (GB/s) measured with CUDA events on the
- * context stream.  `device_buf` must hold at least `bytes` (16-byte aligned,
+ * return the achieved read bandwidth (GB/s, best of a few launch shapes)
+ * measured with CUDA events on the context stream.  `device_buf` must hold at least `bytes` (16-byte aligned,
  * multiple of 16 bytes).  Used as the L2 roofline denominator when the
  * buffer fits in L2. */
 gridff_status gridff_probe_read_bandwidth(gridff_ctx* ctx, const void* device_buf,

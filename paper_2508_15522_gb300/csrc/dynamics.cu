@@ -23,9 +23,6 @@ constexpr int kThreads = 32 * kWarpsPerBlock;
 #define GRIDFF_MIN_BLOCKS_PER_SM 4
 #endif
 constexpr int kMinBlocksPerSM = GRIDFF_MIN_BLOCKS_PER_SM;
-#ifndef GRIDFF_STAGED_NB
-#define GRIDFF_STAGED_NB 0
-#endif
 constexpr int kQuads = 8;                 // atoms evaluated per warp at a time
 constexpr int kMaxA = GRIDFF_MAX_ATOMS;
 constexpr unsigned kFull = 0xffffffffu;
@@ -86,64 +83,147 @@ __device__ __forceinline__ void bspline_weights(float t, float w[4], float dw[4]
   dw[3] = 0.5f * t2;
 }
 
-// Energy and force of one atom in the substrate field (Eqs. E, E_Coulomb,
-// E_Morse), evaluated by the 4 lanes of a quad (q = lane & 3); every lane of
-// the quad returns the full result.  The channels are combined per node with
-// the atom's factors (Q, P, L); lane q accumulates the x/y-weighted sums of
-// node z+q-1 over the 16 runs, applies its own z weight, and the quad sums.
-// The force is minus the analytic gradient of the interpolant (Sec. 5).
-// `act` false: the quad has no atom (it still takes part in the shuffles).
-__device__ __forceinline__ void grid_quad(const GridView& g, int q, bool act, float x, float y, float z,
-                                          float4 par, float& e, float& fx, float& fy, float& fz,
-                                          int& flags) {
-  // fold into the periodic tile (Sec. 4)
+// Per-warp stencil cache in shared memory.  Slot i (i < S) holds, for the
+// atom evaluated by a quad, the 64 node values c = Q b^C + P b^P + L b^L
+// of its 4x4x4 stencil (combined with that atom's fixed factors) and the
+// cell they belong to.  Between consecutive steps an atom usually stays in
+// its cell, so the gather is served from shared memory; it goes to global
+// memory only when the cell changes.  Layout: lane q of the quad holds the
+// 16 values of node z+q-1 for the 16 (x, y) runs, as 4 float4; float4 j of
+// lane q of slot i sits at index (j * S + i) * 4 + q, so a warp access to 8
+// consecutive slots is contiguous (no bank conflicts).
+struct StencilCache {
+  float4* val;   // [4 * S * 4]
+  int* key;      // [S] packed cell index, -1 = empty
+  int S;
+};
+
+// Fold into the periodic tile (Sec. 4), cell index and fractional
+// coordinates of one atom.
+struct Cell {
+  int ix, iy, iz;
+  float tx, ty, tz;
+  bool inside;   // inside the grid's z range (else the field is ~0)
+};
+
+__device__ __forceinline__ Cell locate(const GridView& g, bool act, float x, float y, float z, int& flags) {
+  Cell c;
   float xr = x - g.x0, yr = y - g.y0;
   xr = fmaf(-g.Lx, floorf(xr * g.inv_Lx), xr);
   yr = fmaf(-g.Ly, floorf(yr * g.inv_Ly), yr);
   float ux = xr * g.inv_dx, uy = yr * g.inv_dy, uz = (z - g.z0) * g.inv_dz;
   float flx = floorf(ux), fly = floorf(uy);
-  float tx = fminf(fmaxf(ux - flx, 0.f), 1.f), ty = fminf(fmaxf(uy - fly, 0.f), 1.f);
+  c.tx = fminf(fmaxf(ux - flx, 0.f), 1.f);
+  c.ty = fminf(fmaxf(uy - fly, 0.f), 1.f);
   int ix = (int)flx, iy = (int)fly;
   if (ix >= g.nx) ix -= g.nx;
   if (iy >= g.ny) iy -= g.ny;
-  ix = min(max(ix, 0), g.nx - 1);     // any input, even non-finite, stays in bounds
-  iy = min(max(iy, 0), g.ny - 1);
+  c.ix = min(max(ix, 0), g.nx - 1);     // any input, even non-finite, stays in bounds
+  c.iy = min(max(iy, 0), g.ny - 1);
   if (act && uz < 0.f) flags |= GRIDFF_REP_BELOW;
   uz = fmaxf(uz, 0.f);
-  bool inside = act && (uz < (float)(g.nz - 1));   // above the grid (or NaN): field ~ 0
-  float flz = floorf(inside ? uz : 0.f);
-  float tz = (inside ? uz : 0.f) - flz;
-  int iz = min(max((int)flz, 0), g.nz - 2);
+  c.inside = act && (uz < (float)(g.nz - 1));   // above the grid (or NaN): field ~ 0
+  float flz = floorf(c.inside ? uz : 0.f);
+  c.tz = (c.inside ? uz : 0.f) - flz;
+  c.iz = min(max((int)flz, 0), g.nz - 2);
+  return c;
+}
+
+// Energy and force of one atom in the substrate field (Eqs. E, E_Coulomb,
+// E_Morse), evaluated by the 4 lanes of a quad (q = lane & 3); every lane of
+// the quad returns the full result.  Lane q gathers record q of each of
+// the 16 z-runs (one warp load fetches 8 whole 64-byte runs), combines the
+// channels with the atom's factors (Q, P, L), accumulates the x/y-weighted
+// sums for node z+q-1, applies its own z weight, and the quad sums.  The
+// force is minus the analytic gradient of the interpolant (Sec. 5).
+// `act` false: the quad has no atom (it still takes part in the shuffles).
+// `slot` >= 0: the atom may use stencil-cache slot `slot`.
+// kPartial: return this lane's share (the 4 shares of a quad sum to the
+// atom's value) instead of the quad sum.
+template <bool kPartial = false>
+__device__ __forceinline__ void grid_quad(const GridView& g, int q, bool act, float x, float y, float z,
+                                          float4 par, float& e, float& fx, float& fy, float& fz, int& flags,
+                                          const StencilCache& sc, int slot) {
+  const Cell cl = locate(g, act, x, y, z, flags);
   float wx[4], dwx[4], wy[4], dwy[4], wz[4], dwz[4];
-  bspline_weights(tx, wx, dwx);
-  bspline_weights(ty, wy, dwy);
-  bspline_weights(tz, wz, dwz);
-  float S0 = 0.f, Sx = 0.f, Sy = 0.f;
-  if (inside) {
-    const float4* p0 = g.rec + ((long long)ix * g.nyp + iy) * g.nzp + iz + q;
+  bspline_weights(cl.tx, wx, dwx);
+  bspline_weights(cl.ty, wy, dwy);
+  bspline_weights(cl.tz, wz, dwz);
+  float cv[16];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      float4 r[4];
+  for (int j = 0; j < 16; ++j) cv[j] = 0.f;
+  if (cl.inside) {
+    const int key = (cl.ix * g.ny + cl.iy) * g.nz + cl.iz;
+    const bool cached = slot >= 0 && slot < sc.S;
+    if (cached && sc.key[slot] == key) {
 #pragma unroll
-      for (int b = 0; b < 4; ++b) r[b] = __ldg(p0 + a * g.sx + b * g.nzp);
-      float s = 0.f, sy = 0.f;
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        float c = fmaf(par.x, r[b].x, fmaf(par.y, r[b].y, par.z * r[b].z));
-        s = fmaf(wy[b], c, s);
-        sy = fmaf(dwy[b], c, sy);
+      for (int j = 0; j < 4; ++j) {
+        float4 v = sc.val[(j * sc.S + slot) * 4 + q];
+        cv[4 * j] = v.x;
+        cv[4 * j + 1] = v.y;
+        cv[4 * j + 2] = v.z;
+        cv[4 * j + 3] = v.w;
       }
-      S0 = fmaf(wx[a], s, S0);
-      Sx = fmaf(dwx[a], s, Sx);
-      Sy = fmaf(wx[a], sy, Sy);
+    } else {
+      const float4* p0 = g.rec + ((long long)cl.ix * g.nyp + cl.iy) * g.nzp + cl.iz + q;
+      float4 r[16];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) r[4 * a + b] = __ldg(p0 + a * g.sx + b * g.nzp);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) cv[j] = fmaf(par.x, r[j].x, fmaf(par.y, r[j].y, par.z * r[j].z));
+      if (cached) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          sc.val[(j * sc.S + slot) * 4 + q] = make_float4(cv[4 * j], cv[4 * j + 1], cv[4 * j + 2], cv[4 * j + 3]);
+        if (q == 0) sc.key[slot] = key;
+      }
     }
+  }
+  float S0 = 0.f, Sx = 0.f, Sy = 0.f;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    float s = 0.f, sy = 0.f;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      s = fmaf(wy[b], cv[4 * a + b], s);
+      sy = fmaf(dwy[b], cv[4 * a + b], sy);
+    }
+    S0 = fmaf(wx[a], s, S0);
+    Sx = fmaf(dwx[a], s, Sx);
+    Sy = fmaf(wx[a], sy, Sy);
   }
   const float wq = q == 0 ? wz[0] : q == 1 ? wz[1] : q == 2 ? wz[2] : wz[3];
   const float dwq = q == 0 ? dwz[0] : q == 1 ? dwz[1] : q == 2 ? dwz[2] : dwz[3];
-  e = qsum(wq * S0);
-  fx = -qsum(wq * Sx) * g.inv_dx;
-  fy = -qsum(wq * Sy) * g.inv_dy;
-  fz = -qsum(dwq * S0) * g.inv_dz;
+  e = wq * S0;
+  fx = -wq * Sx * g.inv_dx;
+  fy = -wq * Sy * g.inv_dy;
+  fz = -dwq * S0 * g.inv_dz;
+  if (!kPartial) {
+    e = qsum(e);
+    fx = qsum(fx);
+    fy = qsum(fy);
+    fz = qsum(fz);
+  }
+}
+
+// Bytes of one warp's cache with S slots (a multiple of 16).
+__host__ __device__ constexpr size_t cache_bytes(int S) { return (size_t)S * 256 + (((size_t)S * 4 + 15) & ~size_t(15)); }
+
+__device__ __forceinline__ StencilCache warp_cache(unsigned char* dyn, int S, int wib) {
+  StencilCache sc;
+  unsigned char* base = dyn + (size_t)wib * cache_bytes(S);
+  sc.val = (float4*)base;
+  sc.key = (int*)(base + (size_t)S * 256);
+  sc.S = S;
+  return sc;
+}
+
+// Empty every slot of this warp's cache (at the start of a replica).
+__device__ __forceinline__ void cache_reset(const StencilCache& sc, int lane) {
+  for (int i = lane; i < sc.S; i += 32) sc.key[i] = -1;
+  __syncwarp();
 }
 
 __device__ __forceinline__ float3 ld3(const float* s, int i) {
@@ -307,13 +387,15 @@ __device__ __forceinline__ void report(const Control& ctl, int n, int evals, int
 
 // Forces of one flexible replica whose positions are in s.x: grid term
 // (quads over atoms) + intramolecular terms; writes s.f and s.eg and
-// returns this lane's share of the energy (the caller sums the warp).
-__device__ __forceinline__ double flex_forces(const GridView& g, bool use_grid, bool use_intra,
-                                              const TemplateView& tv, int ab, int n, int lane, WarpState& s,
-                                              int& flags) {
+// returns this lane's share of the energy (the caller sums the warp),
+// accumulated in Acc.
+template <class Acc = double>
+__device__ __forceinline__ Acc flex_forces(const GridView& g, bool use_grid, bool use_intra,
+                                           const TemplateView& tv, int ab, int n, int lane, WarpState& s,
+                                           int& flags, const StencilCache& sc) {
   __syncwarp();
   const int quad = lane >> 2, q = lane & 3;
-  double e = 0.0;
+  Acc e = Acc(0);
   for (int base = 0; base < n; base += kQuads) {
     const int i = base + quad;
     const bool act = i < n;
@@ -327,33 +409,39 @@ __device__ __forceinline__ double flex_forces(const GridView& g, bool use_grid, 
       if (!finite3(x, y, z)) flags |= GRIDFF_REP_NONFINITE;
     }
     float eg = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
-    if (use_grid) grid_quad(g, q, act, x, y, z, par, eg, fx, fy, fz, flags);
+    if (use_grid) grid_quad(g, q, act, x, y, z, par, eg, fx, fy, fz, flags, sc, i);
     float ix = 0.f, iy = 0.f, iz = 0.f, ie = 0.f;
     if (use_intra && act) intra_quad(tv, ab, n, i, q, s.x, ix, iy, iz, ie);
     ix = qsum(ix);
     iy = qsum(iy);
     iz = qsum(iz);
-    e += (double)ie;
+    e += (Acc)ie;
     if (act && q == 0) {
       s.f[3 * i] = fx + ix;
       s.f[3 * i + 1] = fy + iy;
       s.f[3 * i + 2] = fz + iz;
       s.eg[i] = eg;
-      e += (double)eg;
+      e += (Acc)eg;
     }
   }
   __syncwarp();
   return e;
 }
 
-// Grid forces of a rigid replica: total force (lab), body-frame torque and
-// this lane's share of the energy.
+// Grid forces of a rigid replica: total force (lab) and body-frame torque
+// (warp-reduced), and this lane's share of the energy (not reduced),
+// accumulated per atom in Acc (double for the NVE energy trace, float for
+// relaxations, where only the final value is reported).  Force, torque and
+// energy are linear in the per-atom forces, so each lane accumulates its
+// quad share of every atom and the warp sums once per step.
+template <class Acc>
 __device__ __forceinline__ void rigid_forces(const GridView& g, const TemplateView& tv, int ab, int n, int lane,
                                              const float c[3], const float Rm[9], float Ft[3], float tq[3],
-                                             double& e, int& flags) {
+                                             Acc& e, int& flags, const StencilCache& sc) {
   const int quad = lane >> 2, q = lane & 3;
+  __syncwarp();   // cache keys written by one lane of a quad in the previous step
   for (int a = 0; a < 3; ++a) Ft[a] = tq[a] = 0.f;
-  e = 0.0;
+  e = Acc(0);
   for (int base = 0; base < n; base += kQuads) {
     const int i = base + quad;
     const bool act = i < n;
@@ -366,9 +454,9 @@ __device__ __forceinline__ void rigid_forces(const GridView& g, const TemplateVi
     float py = Rm[3] * b.x + Rm[4] * b.y + Rm[5] * b.z + c[1];
     float pz = Rm[6] * b.x + Rm[7] * b.y + Rm[8] * b.z + c[2];
     float ei, fx, fy, fz;
-    grid_quad(g, q, act, px, py, pz, par, ei, fx, fy, fz, flags);
-    if (act && q == 0) {
-      e += (double)ei;
+    grid_quad<true>(g, q, act, px, py, pz, par, ei, fx, fy, fz, flags, sc, i);   // this lane's share
+    if (act) {
+      e += (Acc)ei;
       Ft[0] += fx;
       Ft[1] += fy;
       Ft[2] += fz;
@@ -385,150 +473,6 @@ __device__ __forceinline__ void rigid_forces(const GridView& g, const TemplateVi
     Ft[a] = wsum(Ft[a]);
     tq[a] = wsum(tq[a]);
   }
-  e = wsum(e);
-}
-
-// ---------------------------------------------------------------------------
-// Shared-memory staged gather (cp.async): the stencil records of up to NB
-// rounds of 8 atoms are in flight per warp without holding registers.
-// Slot layout per stage: record j of lane l at float4 index j * 32 + l, so
-// both the asynchronous writes and the reads are bank-conflict free.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  unsigned a = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
-}
-
-struct StencilPos {   // fold and cell of one atom (shared by issue and compute)
-  int ix, iy, iz;
-  float tx, ty, tz;
-  bool inside;
-};
-
-__device__ __forceinline__ StencilPos locate(const GridView& g, bool act, float x, float y, float z, int& flags) {
-  StencilPos sp;
-  float xr = x - g.x0, yr = y - g.y0;
-  xr = fmaf(-g.Lx, floorf(xr * g.inv_Lx), xr);
-  yr = fmaf(-g.Ly, floorf(yr * g.inv_Ly), yr);
-  float ux = xr * g.inv_dx, uy = yr * g.inv_dy, uz = (z - g.z0) * g.inv_dz;
-  float flx = floorf(ux), fly = floorf(uy);
-  sp.tx = fminf(fmaxf(ux - flx, 0.f), 1.f);
-  sp.ty = fminf(fmaxf(uy - fly, 0.f), 1.f);
-  int ix = (int)flx, iy = (int)fly;
-  if (ix >= g.nx) ix -= g.nx;
-  if (iy >= g.ny) iy -= g.ny;
-  sp.ix = min(max(ix, 0), g.nx - 1);
-  sp.iy = min(max(iy, 0), g.ny - 1);
-  if (act && uz < 0.f) flags |= GRIDFF_REP_BELOW;
-  uz = fmaxf(uz, 0.f);
-  sp.inside = act && (uz < (float)(g.nz - 1));
-  float flz = floorf(sp.inside ? uz : 0.f);
-  sp.tz = (sp.inside ? uz : 0.f) - flz;
-  sp.iz = min(max((int)flz, 0), g.nz - 2);
-  return sp;
-}
-
-template <int NB>
-__device__ __forceinline__ void rigid_forces_staged(const GridView& g, const TemplateView& tv, int ab, int n,
-                                                    int lane, const float c[3], const float Rm[9], float Ft[3],
-                                                    float tq[3], double& e, int& flags, float4* sbuf) {
-  const int quad = lane >> 2, q = lane & 3;
-  const int R = (n + kQuads - 1) / kQuads;
-  for (int a = 0; a < 3; ++a) Ft[a] = tq[a] = 0.f;
-  e = 0.0;
-  auto atom = [&](int k, float4& b, float4& par, float p[3]) {
-    const int i = k * kQuads + quad;
-    const bool act = i < n;
-    b = make_float4(0.f, 0.f, 0.f, 0.f);
-    par = b;
-    if (act) {
-      b = __ldg(&tv.body[ab + i]);
-      par = __ldg(&tv.par[ab + i]);
-    }
-    p[0] = Rm[0] * b.x + Rm[1] * b.y + Rm[2] * b.z + c[0];
-    p[1] = Rm[3] * b.x + Rm[4] * b.y + Rm[5] * b.z + c[1];
-    p[2] = Rm[6] * b.x + Rm[7] * b.y + Rm[8] * b.z + c[2];
-    return act;
-  };
-  auto issue = [&](int k) {
-    if (k < R) {
-      float4 b, par;
-      float p[3];
-      int dummy = 0;
-      bool act = atom(k, b, par, p);
-      StencilPos sp = locate(g, act, p[0], p[1], p[2], dummy);
-      if (sp.inside) {
-        const float4* p0 = g.rec + ((long long)sp.ix * g.nyp + sp.iy) * g.nzp + sp.iz + q;
-        float4* dst = sbuf + (k % NB) * 512 + lane;
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int bb = 0; bb < 4; ++bb) cp_async16(dst + (a * 4 + bb) * 32, p0 + a * g.sx + bb * g.nzp);
-      }
-    }
-    cp_async_commit();
-  };
-#pragma unroll
-  for (int k = 0; k < NB; ++k) issue(k);
-  for (int k = 0; k < R; ++k) {
-    cp_async_wait<NB - 1>();
-    float4 b, par;
-    float p[3];
-    bool act = atom(k, b, par, p);
-    StencilPos sp = locate(g, act, p[0], p[1], p[2], flags);
-    float wx[4], dwx[4], wy[4], dwy[4], wz[4], dwz[4];
-    bspline_weights(sp.tx, wx, dwx);
-    bspline_weights(sp.ty, wy, dwy);
-    bspline_weights(sp.tz, wz, dwz);
-    float S0 = 0.f, Sx = 0.f, Sy = 0.f;
-    if (sp.inside) {
-      const float4* src = sbuf + (k % NB) * 512 + lane;
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        float s = 0.f, sy = 0.f;
-#pragma unroll
-        for (int bb = 0; bb < 4; ++bb) {
-          float4 r = src[(a * 4 + bb) * 32];
-          float cc = fmaf(par.x, r.x, fmaf(par.y, r.y, par.z * r.z));
-          s = fmaf(wy[bb], cc, s);
-          sy = fmaf(dwy[bb], cc, sy);
-        }
-        S0 = fmaf(wx[a], s, S0);
-        Sx = fmaf(dwx[a], s, Sx);
-        Sy = fmaf(wx[a], sy, Sy);
-      }
-    }
-    issue(k + NB);
-    const float wq = q == 0 ? wz[0] : q == 1 ? wz[1] : q == 2 ? wz[2] : wz[3];
-    const float dwq = q == 0 ? dwz[0] : q == 1 ? dwz[1] : q == 2 ? dwz[2] : dwz[3];
-    float ei = qsum(wq * S0);
-    float fx = -qsum(wq * Sx) * g.inv_dx;
-    float fy = -qsum(wq * Sy) * g.inv_dy;
-    float fz = -qsum(dwq * S0) * g.inv_dz;
-    if (act && q == 0) {
-      e += (double)ei;
-      Ft[0] += fx;
-      Ft[1] += fy;
-      Ft[2] += fz;
-      float gx = Rm[0] * fx + Rm[3] * fy + Rm[6] * fz;
-      float gy = Rm[1] * fx + Rm[4] * fy + Rm[7] * fz;
-      float gz = Rm[2] * fx + Rm[5] * fy + Rm[8] * fz;
-      tq[0] += b.y * gz - b.z * gy;
-      tq[1] += b.z * gx - b.x * gz;
-      tq[2] += b.x * gy - b.y * gx;
-    }
-  }
-  cp_async_wait<0>();
-  for (int a = 0; a < 3; ++a) {
-    Ft[a] = wsum(Ft[a]);
-    tq[a] = wsum(tq[a]);
-  }
-  e = wsum(e);
 }
 
 // ---------------------------------------------------------------------------
@@ -561,7 +505,8 @@ eval_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
       for (int k = lane; k < 3 * n; k += 32) s.x[k] = xs[3 * (size_t)off + k];
     }
     int flags = 0;
-    double E = flex_forces(g, use_grid, use_intra && !rigid, tv, ab, n, lane, s, flags);
+    const StencilCache nocache{nullptr, nullptr, 0};
+    double E = flex_forces(g, use_grid, use_intra && !rigid, tv, ab, n, lane, s, flags, nocache);
     for (int i = lane; i < n; i += 32) {
       float* f = F_out + 3 * ((size_t)off + i);
       f[0] = s.f[3 * i];
@@ -586,11 +531,10 @@ eval_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
 __global__ void __launch_bounds__(kThreads, kMinBlocksPerSM)
 relax_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, int n_rep,
                    float* pose, float* vel, float* fdt, float* falpha, int* fnp, int* status,
-                   int* steps, double* energy, int nsteps, FireP fp, Control ctl, int use_grid) {
-#if GRIDFF_STAGED_NB > 0
-  extern __shared__ float4 s_stage[];
-#endif
+                   int* steps, double* energy, int nsteps, FireP fp, Control ctl, int use_grid, int S) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
   const int lane = threadIdx.x & 31;
+  const StencilCache sc = warp_cache(dyn_smem, S, threadIdx.x >> 5);
   const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   const int n_warps = gridDim.x * kWarpsPerBlock;
   const unsigned long long t0 = gtimer();
@@ -598,6 +542,7 @@ relax_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl
     const int t = rep_tmpl[r], n = tv.natoms[t], ab = tv.atom_off[t];
     const float4 rig = tv.rigid[t];
     const float rmax = tv.rmax[t];
+    cache_reset(sc, lane);
     float c[3], q[4], v[3], w[3];
     for (int a = 0; a < 3; ++a) {
       c[a] = pose[7 * (size_t)r + a];
@@ -607,7 +552,7 @@ relax_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl
     for (int a = 0; a < 4; ++a) q[a] = pose[7 * (size_t)r + 3 + a];
     float dt = fdt[r], al = falpha[r];
     int np = fnp[r], st = status[r], evals = 0;
-    double Elast = energy[r];
+    float elane = 0.f;          // this lane's share of the last evaluated energy
     for (int s = 0; s < nsteps; ++s) {
       if (st & (GRIDFF_REP_CONVERGED | GRIDFF_REP_NONFINITE)) break;
       if ((s & 31) == 0) {
@@ -620,23 +565,17 @@ relax_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl
       float Rm[9];
       quat_rot(q[0], q[1], q[2], q[3], Rm);
       float Ft[3], tq[3];
-      double e = 0.0;
+      float e = 0.f;
       int flags = 0;
       if (use_grid) {
-#if GRIDFF_STAGED_NB > 0
-        rigid_forces_staged<GRIDFF_STAGED_NB>(g, tv, ab, n, lane, c, Rm, Ft, tq, e, flags,
-                                              s_stage + (threadIdx.x >> 5) * GRIDFF_STAGED_NB * 512);
-#else
-        rigid_forces(g, tv, ab, n, lane, c, Rm, Ft, tq, e, flags);
-#endif
+        rigid_forces(g, tv, ab, n, lane, c, Rm, Ft, tq, e, flags, sc);
       } else {
         for (int a = 0; a < 3; ++a) Ft[a] = tq[a] = 0.f;
       }
       st |= __reduce_or_sync(kFull, flags);
       ++evals;
-      Elast = e;
-      if (!(finite3(Ft[0], Ft[1], Ft[2]) && finite3(tq[0], tq[1], tq[2]) && isfinite(e) &&
-            finite3(c[0], c[1], c[2]))) {
+      elane = e;
+      if (!(finite3(Ft[0], Ft[1], Ft[2]) && finite3(tq[0], tq[1], tq[2]) && finite3(c[0], c[1], c[2]))) {
         st |= GRIDFF_REP_NONFINITE;
         break;
       }
@@ -686,6 +625,8 @@ relax_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl
         quat_advance(q, w[0] / wn, w[1] / wn, w[2] / wn, ang);
       }
     }
+    const double Etot = evals > 0 ? wsum((double)elane) : energy[r];
+    if (evals > 0 && !isfinite(Etot)) st |= GRIDFF_REP_NONFINITE;
     if (lane == 0) {
       for (int a = 0; a < 3; ++a) {
         pose[7 * (size_t)r + a] = c[a];
@@ -699,9 +640,254 @@ relax_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl
       status[r] = st;
       int total = steps[r] + evals;
       steps[r] = total;
-      energy[r] = Elast;
+      energy[r] = Etot;
       report(ctl, n, evals, st, total);
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FIRE, rigid replicas, sub-warp form: each replica is handled by W lanes
+// (W = 8, 16 or 32; 32/W replicas per warp), one lane per atom.  Per step
+// and per round of W atoms: the lane places its atom and finds its cell;
+// atoms whose cell is not in the stencil cache are refilled cooperatively
+// (the quads of the sub-warp gather the 16 z-runs, lane q taking record q
+// of each run, and store the channel-combined node values); then every lane
+// contracts its own atom's 64 cached values (16 z passes, 4 y, 1 x) with
+// no work repeated across lanes.  Cache layout of a replica (S >= atoms
+// slots): float4 m = 4a + b (the (x, y) run a, b) holds the run's 4 z-nodes
+// and sits at index m * S + i.
+// ---------------------------------------------------------------------------
+template <int W, int WPB, int MINB>
+__global__ void __launch_bounds__(32 * WPB, MINB)
+relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, int n_rep,
+                      float* pose, float* vel, float* fdt, float* falpha, int* fnp, int* status,
+                      int* steps, double* energy, int nsteps, FireP fp, Control ctl, int S) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  constexpr int RPW = 32 / W;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int sw = lane / W, l = lane % W;
+  const StencilCache sc = warp_cache(dyn_smem, S, wib * RPW + sw);
+  float* const cval = (float*)sc.val;
+  const int warp = blockIdx.x * WPB + wib;
+  const int n_warps = gridDim.x * WPB;
+  const unsigned long long t0 = gtimer();
+  for (int r0 = warp * RPW; r0 < n_rep; r0 += n_warps * RPW) {      // uniform over the warp
+    const int r = r0 + sw;
+    const bool valid = r < n_rep;
+    int n = 0, ab = 0;
+    float4 rig = make_float4(1.f, 1.f, 1.f, 1.f);
+    float rmax = 1.f;
+    float c[3] = {0.f, 0.f, 0.f}, q[4] = {1.f, 0.f, 0.f, 0.f}, v[3] = {0.f, 0.f, 0.f}, w[3] = {0.f, 0.f, 0.f};
+    float dt = 0.f, al = 0.f;
+    int np = 0, st = 0, evals = 0;
+    if (valid) {
+      const int t = rep_tmpl[r];
+      n = tv.natoms[t];
+      ab = tv.atom_off[t];
+      rig = tv.rigid[t];
+      rmax = tv.rmax[t];
+      for (int a = 0; a < 3; ++a) {
+        c[a] = pose[7 * (size_t)r + a];
+        v[a] = vel[6 * (size_t)r + a];
+        w[a] = vel[6 * (size_t)r + 3 + a];
+      }
+      for (int a = 0; a < 4; ++a) q[a] = pose[7 * (size_t)r + 3 + a];
+      dt = fdt[r];
+      al = falpha[r];
+      np = fnp[r];
+      st = status[r];
+    }
+    for (int i = l; i < S; i += W) sc.key[i] = -1;
+    __syncwarp();
+    const int rounds = __reduce_max_sync(kFull, (n + W - 1) / W);
+    float elane = 0.f;
+    bool done = !valid;
+    for (int it = 0; it < nsteps; ++it) {
+      if ((it & 31) == 0) {
+        int sb = 0;
+        if (l == 0 && !done) {
+          if (*ctl.abort_flag) sb |= GRIDFF_REP_ABORTED;
+          if (ctl.budget_ns && gtimer() - t0 > ctl.budget_ns) sb |= GRIDFF_REP_STEPLIMIT;
+        }
+        sb = __shfl_sync(kFull, sb, sw * W);
+        if (sb) {
+          st |= sb;
+          done = true;
+        }
+      }
+      if (st & (GRIDFF_REP_CONVERGED | GRIDFF_REP_NONFINITE)) done = true;
+      if (!__any_sync(kFull, !done)) break;
+      const bool run = !done;
+      float Rm[9];
+      quat_rot(q[0], q[1], q[2], q[3], Rm);
+      float Ft[3] = {0.f, 0.f, 0.f}, tq[3] = {0.f, 0.f, 0.f};
+      float e = 0.f;
+      int flags = 0;
+      for (int k = 0; k < rounds; ++k) {
+        const int i = k * W + l;
+        const bool act = run && i < n;
+        float4 b = make_float4(0.f, 0.f, 0.f, 0.f), par = b;
+        if (act) {
+          b = __ldg(&tv.body[ab + i]);
+          par = __ldg(&tv.par[ab + i]);
+        }
+        const float px = Rm[0] * b.x + Rm[1] * b.y + Rm[2] * b.z + c[0];
+        const float py = Rm[3] * b.x + Rm[4] * b.y + Rm[5] * b.z + c[1];
+        const float pz = Rm[6] * b.x + Rm[7] * b.y + Rm[8] * b.z + c[2];
+        const Cell cl = locate(g, act, px, py, pz, flags);
+        const int key = (cl.ix * g.ny + cl.iy) * g.nz + cl.iz;
+        const bool miss = cl.inside && sc.key[i < S ? i : 0] != key;
+        // refill the missing stencils, W/4 atoms at a time (one per quad)
+        unsigned msub = __ballot_sync(kFull, miss);
+        if (W < 32) msub = (msub >> (sw * W)) & ((1u << W) - 1u);
+        while (__any_sync(kFull, msub != 0)) {
+          const int qd = l >> 2, qq = l & 3;
+          unsigned m = msub;
+          for (int j = 0; j < qd && m; ++j) m &= m - 1;
+          const int owner = m ? __ffs(m) - 1 : -1;
+          const int src = sw * W + (owner < 0 ? 0 : owner);
+          const int oix = __shfl_sync(kFull, cl.ix, src), oiy = __shfl_sync(kFull, cl.iy, src);
+          const int oiz = __shfl_sync(kFull, cl.iz, src), okey = __shfl_sync(kFull, key, src);
+          const float oQ = __shfl_sync(kFull, par.x, src), oP = __shfl_sync(kFull, par.y, src);
+          const float oL = __shfl_sync(kFull, par.z, src);
+          if (owner >= 0) {
+            const int slot = k * W + owner;
+            const float4* p0 = g.rec + ((long long)oix * g.nyp + oiy) * g.nzp + oiz + qq;
+            float4 rr[16];
+#pragma unroll
+            for (int mm = 0; mm < 16; ++mm) rr[mm] = __ldg(p0 + (mm >> 2) * g.sx + (mm & 3) * g.nzp);
+#pragma unroll
+            for (int mm = 0; mm < 16; ++mm)
+              cval[((size_t)mm * S + slot) * 4 + qq] = fmaf(oQ, rr[mm].x, fmaf(oP, rr[mm].y, oL * rr[mm].z));
+            if (qq == 0) sc.key[slot] = okey;
+          }
+          for (int j = 0; j < W / 4 && msub; ++j) msub &= msub - 1;
+        }
+        __syncwarp();
+        if (cl.inside) {
+          float wx[4], dwx[4], wy[4], dwy[4], wz[4], dwz[4];
+          bspline_weights(cl.tx, wx, dwx);
+          bspline_weights(cl.ty, wy, dwy);
+          bspline_weights(cl.tz, wz, dwz);
+          float ev = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            float sv = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+            for (int bb = 0; bb < 4; ++bb) {
+              const float4 rr = sc.val[(4 * a + bb) * S + i];
+              const float zv = fmaf(wz[0], rr.x, fmaf(wz[1], rr.y, fmaf(wz[2], rr.z, wz[3] * rr.w)));
+              const float zd = fmaf(dwz[0], rr.x, fmaf(dwz[1], rr.y, fmaf(dwz[2], rr.z, dwz[3] * rr.w)));
+              sv = fmaf(wy[bb], zv, sv);
+              sy = fmaf(dwy[bb], zv, sy);
+              sz = fmaf(wy[bb], zd, sz);
+            }
+            ev = fmaf(wx[a], sv, ev);
+            gx = fmaf(dwx[a], sv, gx);
+            gy = fmaf(wx[a], sy, gy);
+            gz = fmaf(wx[a], sz, gz);
+          }
+          const float fx = -gx * g.inv_dx, fy = -gy * g.inv_dy, fz = -gz * g.inv_dz;
+          e += ev;
+          Ft[0] += fx;
+          Ft[1] += fy;
+          Ft[2] += fz;
+          const float hx = Rm[0] * fx + Rm[3] * fy + Rm[6] * fz;
+          const float hy = Rm[1] * fx + Rm[4] * fy + Rm[7] * fz;
+          const float hz = Rm[2] * fx + Rm[5] * fy + Rm[8] * fz;
+          tq[0] += b.y * hz - b.z * hy;
+          tq[1] += b.z * hx - b.x * hz;
+          tq[2] += b.x * hy - b.y * hx;
+        }
+      }
+      // sums over the sub-warp (xor offsets below W stay inside it)
+#pragma unroll
+      for (int o = W / 2; o > 0; o >>= 1) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          Ft[a] += __shfl_xor_sync(kFull, Ft[a], o);
+          tq[a] += __shfl_xor_sync(kFull, tq[a], o);
+        }
+        flags |= __shfl_xor_sync(kFull, flags, o);
+      }
+      if (!run) continue;
+      st |= flags;
+      ++evals;
+      elane = e;
+      if (!(finite3(Ft[0], Ft[1], Ft[2]) && finite3(tq[0], tq[1], tq[2]) && finite3(c[0], c[1], c[2]))) {
+        st |= GRIDFF_REP_NONFINITE;
+        continue;
+      }
+      const float f2 = Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2] + tq[0] * tq[0] + tq[1] * tq[1] +
+                       tq[2] * tq[2];
+      if (f2 < fp.f_conv2) {
+        st |= GRIDFF_REP_CONVERGED;
+        continue;
+      }
+      // FIRE decision (identical in every lane of the sub-warp)
+      const float P = Ft[0] * v[0] + Ft[1] * v[1] + Ft[2] * v[2] + tq[0] * w[0] + tq[1] * w[1] + tq[2] * w[2];
+      if (P > 0.f) {
+        const float fn = sqrtf(Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2]);
+        const float tn = sqrtf(tq[0] * tq[0] + tq[1] * tq[1] + tq[2] * tq[2]);
+        const float vn = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        const float wn = sqrtf(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+        const float sf = fn > 0.f ? al * vn / fn : 0.f, sw_ = tn > 0.f ? al * wn / tn : 0.f;
+        for (int a = 0; a < 3; ++a) {
+          v[a] = (1.f - al) * v[a] + sf * Ft[a];
+          w[a] = (1.f - al) * w[a] + sw_ * tq[a];
+        }
+        if (np > fp.n_min) {
+          dt = fminf(dt * fp.f_inc, fp.dt_max);
+          al *= fp.f_alpha;
+        }
+        ++np;
+      } else {
+        for (int a = 0; a < 3; ++a) v[a] = w[a] = 0.f;
+        dt *= fp.f_dec;
+        al = fp.alpha_start;
+        np = 0;
+      }
+      const float aM = GRIDFF_ACC * dt / rig.x;
+      v[0] += aM * Ft[0];
+      v[1] += aM * Ft[1];
+      v[2] += aM * Ft[2];
+      w[0] += GRIDFF_ACC * dt * tq[0] / rig.y;
+      w[1] += GRIDFF_ACC * dt * tq[1] / rig.z;
+      w[2] += GRIDFF_ACC * dt * tq[2] / rig.w;
+      const float dr[3] = {v[0] * dt, v[1] * dt, v[2] * dt};
+      const float dn = sqrtf(dr[0] * dr[0] + dr[1] * dr[1] + dr[2] * dr[2]);
+      const float scl = dn > fp.d_max ? fp.d_max / dn : 1.f;
+      for (int a = 0; a < 3; ++a) c[a] += dr[a] * scl;
+      const float wn = sqrtf(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+      if (wn > 0.f) {
+        const float ang = fminf(wn * dt, fp.d_max / rmax);
+        quat_advance(q, w[0] / wn, w[1] / wn, w[2] / wn, ang);
+      }
+    }
+    // energy of the last evaluation: sum over the sub-warp in FP64
+    double et = (double)elane;
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) et += __shfl_xor_sync(kFull, et, o);
+    if (valid && l == 0) {
+      const double Etot = evals > 0 ? et : energy[r];
+      if (evals > 0 && !isfinite(Etot)) st |= GRIDFF_REP_NONFINITE;
+      for (int a = 0; a < 3; ++a) {
+        pose[7 * (size_t)r + a] = c[a];
+        vel[6 * (size_t)r + a] = v[a];
+        vel[6 * (size_t)r + 3 + a] = w[a];
+      }
+      for (int a = 0; a < 4; ++a) pose[7 * (size_t)r + 3 + a] = q[a];
+      fdt[r] = dt;
+      falpha[r] = al;
+      fnp[r] = np;
+      status[r] = st;
+      const int total = steps[r] + evals;
+      steps[r] = total;
+      energy[r] = Etot;
+      report(ctl, n, evals, st, total);
+    }
+    __syncwarp();
   }
 }
 
@@ -712,23 +898,26 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSM)
 relax_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
                   const int* __restrict__ rep_off, int n_rep, float* xs, float* vs, float* fdt,
                   float* falpha, int* fnp, int* status, int* steps, double* energy, int nsteps,
-                  FireP fp, Control ctl, int use_grid, int use_intra) {
+                  FireP fp, Control ctl, int use_grid, int use_intra, int S) {
   __shared__ WarpState s_all[kWarpsPerBlock];
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   WarpState& s = s_all[wib];
+  const StencilCache sc = warp_cache(dyn_smem, S, wib);
   const int warp = blockIdx.x * kWarpsPerBlock + wib;
   const int n_warps = gridDim.x * kWarpsPerBlock;
   const unsigned long long t0 = gtimer();
   for (int r = warp; r < n_rep; r += n_warps) {
     const int t = rep_tmpl[r], n = tv.natoms[t], ab = tv.atom_off[t], off = rep_off[r];
     __syncwarp();
+    cache_reset(sc, lane);
     for (int k = lane; k < 3 * n; k += 32) {
       s.x[k] = xs[3 * (size_t)off + k];
       s.v[k] = vs[3 * (size_t)off + k];
     }
     float dt = fdt[r], al = falpha[r];
     int np = fnp[r], st = status[r], evals = 0;
-    double Elast = energy[r];
+    float elane = 0.f;          // this lane's share of the last evaluated energy
     for (int it = 0; it < nsteps; ++it) {
       if (st & (GRIDFF_REP_CONVERGED | GRIDFF_REP_NONFINITE)) break;
       if ((it & 31) == 0) {
@@ -739,7 +928,7 @@ relax_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
         }
       }
       int flags = 0;
-      double e = flex_forces(g, use_grid, use_intra, tv, ab, n, lane, s, flags);
+      const float e = flex_forces<float>(g, use_grid, use_intra, tv, ab, n, lane, s, flags, sc);
       float f2 = 0.f, P = 0.f, v2 = 0.f;
       for (int k = lane; k < 3 * n; k += 32) {
         float f = s.f[k], v = s.v[k];
@@ -750,11 +939,10 @@ relax_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
       f2 = wsum(f2);
       P = wsum(P);
       v2 = wsum(v2);
-      e = wsum(e);
       st |= __reduce_or_sync(kFull, flags);
       ++evals;
-      Elast = e;
-      if ((st & GRIDFF_REP_NONFINITE) || !isfinite(f2) || !isfinite(e)) {
+      elane = e;
+      if ((st & GRIDFF_REP_NONFINITE) || !isfinite(f2)) {
         st |= GRIDFF_REP_NONFINITE;
         break;
       }
@@ -799,6 +987,8 @@ relax_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
       xs[3 * (size_t)off + k] = s.x[k];
       vs[3 * (size_t)off + k] = s.v[k];
     }
+    const double Etot = evals > 0 ? wsum((double)elane) : energy[r];
+    if (evals > 0 && !isfinite(Etot)) st |= GRIDFF_REP_NONFINITE;
     if (lane == 0) {
       fdt[r] = dt;
       falpha[r] = al;
@@ -806,7 +996,7 @@ relax_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
       status[r] = st;
       int total = steps[r] + evals;
       steps[r] = total;
-      energy[r] = Elast;
+      energy[r] = Etot;
       report(ctl, n, evals, st, total);
     }
   }
@@ -819,23 +1009,26 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksPerSM)
 run_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
                 const int* __restrict__ rep_off, int n_rep, float* xs, float* vs, int* status,
                 double* energy, int nsteps, float dt, int rec_every, double* trace, Control ctl,
-                int use_grid, int use_intra) {
+                int use_grid, int use_intra, int S) {
   __shared__ WarpState s_all[kWarpsPerBlock];
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   WarpState& s = s_all[wib];
+  const StencilCache sc = warp_cache(dyn_smem, S, wib);
   const int warp = blockIdx.x * kWarpsPerBlock + wib;
   const int n_warps = gridDim.x * kWarpsPerBlock;
   const unsigned long long t0 = gtimer();
   for (int r = warp; r < n_rep; r += n_warps) {
     const int t = rep_tmpl[r], n = tv.natoms[t], ab = tv.atom_off[t], off = rep_off[r];
     __syncwarp();
+    cache_reset(sc, lane);
     for (int k = lane; k < 3 * n; k += 32) {
       s.x[k] = xs[3 * (size_t)off + k];
       s.v[k] = vs[3 * (size_t)off + k];
     }
     int st = status[r] & ~(GRIDFF_REP_ABORTED | GRIDFF_REP_STEPLIMIT);
     int flags = 0, evals = 0;
-    double e = flex_forces(g, use_grid, use_intra, tv, ab, n, lane, s, flags);
+    double e = flex_forces(g, use_grid, use_intra, tv, ab, n, lane, s, flags, sc);
     auto total = [&](double epot_lane) {
       double ke = 0.0;
       for (int i = lane; i < n; i += 32) {
@@ -864,7 +1057,7 @@ run_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
           s.x[3 * i + a] += dt * vv;
         }
       }
-      e = flex_forces(g, use_grid, use_intra, tv, ab, n, lane, s, flags);
+      e = flex_forces(g, use_grid, use_intra, tv, ab, n, lane, s, flags, sc);
       ++evals;
       for (int i = lane; i < n; i += 32) {
         const float h = 0.5f * dt * GRIDFF_ACC / __ldg(&tv.body[ab + i]).w;
@@ -940,8 +1133,10 @@ __device__ __forceinline__ void body_L(const float q[4], const float p[4], float
 __global__ void __launch_bounds__(kThreads, kMinBlocksPerSM)
 run_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, int n_rep,
                  float* pose, float* vel, int* status, double* energy, int nsteps, float dt,
-                 int rec_every, double* trace, Control ctl) {
+                 int rec_every, double* trace, Control ctl, int S) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
   const int lane = threadIdx.x & 31;
+  const StencilCache sc = warp_cache(dyn_smem, S, threadIdx.x >> 5);
   const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   const int n_warps = gridDim.x * kWarpsPerBlock;
   const unsigned long long t0 = gtimer();
@@ -968,7 +1163,9 @@ run_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, 
     double e;
     float Rm[9];
     quat_rot(q[0], q[1], q[2], q[3], Rm);
-    rigid_forces(g, tv, ab, n, lane, c, Rm, Ft, tq, e, flags);
+    cache_reset(sc, lane);
+    rigid_forces(g, tv, ab, n, lane, c, Rm, Ft, tq, e, flags, sc);
+    e = wsum(e);
     auto total = [&](double epot) {
       float L[3];
       body_L(q, p, L);
@@ -997,7 +1194,8 @@ run_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, 
       free_rot(2, h, I[1], q, p);
       free_rot(3, h, I[2], q, p);
       quat_rot(q[0], q[1], q[2], q[3], Rm);
-      rigid_forces(g, tv, ab, n, lane, c, Rm, Ft, tq, e, flags);
+      rigid_forces(g, tv, ab, n, lane, c, Rm, Ft, tq, e, flags, sc);
+      e = wsum(e);
       ++evals;
       for (int a = 0; a < 3; ++a) v[a] += h * GRIDFF_ACC * Ft[a] / rig.x;
       float tb2[3] = {GRIDFF_ACC * tq[0], GRIDFF_ACC * tq[1], GRIDFF_ACC * tq[2]};
@@ -1036,10 +1234,51 @@ struct Staging {
   }
 };
 
+#ifndef GRIDFF_BLOCK_CAP
+#define GRIDFF_BLOCK_CAP 0
+#endif
+#ifndef GRIDFF_CACHE_CAP
+#define GRIDFF_CACHE_CAP 128
+#endif
+
+// Stencil-cache slots per warp: every atom of the largest template, up to a
+// cap (rigid kernels keep no other per-warp shared state; flexible kernels
+// also hold positions, velocities and forces).
+int cache_slots(const gridff_replicas* R, bool rigid) {
+  int cap = rigid ? GRIDFF_CACHE_CAP : (GRIDFF_CACHE_CAP < 48 ? GRIDFF_CACHE_CAP : 48);
+  return R->max_natoms < cap ? R->max_natoms : cap;
+}
+
+#ifndef GRIDFF_SW_WARPS
+#define GRIDFF_SW_WARPS 4
+#endif
+#ifndef GRIDFF_SW_MINB
+#define GRIDFF_SW_MINB 2
+#endif
+constexpr int kSwWarps = GRIDFF_SW_WARPS;
+constexpr int kSwMinBlocks = GRIDFF_SW_MINB;
+#ifndef GRIDFF_RIGID_SUBWARP
+#define GRIDFF_RIGID_SUBWARP -1      // -1: chosen from the molecule size; 0: quad kernel
+#endif
+// Sub-warp width of the rigid relaxation kernel: the smallest of 8, 16, 32
+// lanes whose rounds of atoms waste at most a quarter of the lanes (0 = the
+// quad kernel, used when the cache would not fit).
+int rigid_subwarp_width(const gridff_replicas* R) {
+  if (GRIDFF_RIGID_SUBWARP >= 0) return GRIDFF_RIGID_SUBWARP;
+  const int n = R->max_natoms;
+  const int W = n <= 12 ? 8 : n <= 48 ? 16 : 32;
+  return cache_bytes(n) * kSwWarps * (32 / W) <= 200 * 1024 ? W : 0;
+}
+
+cudaError_t set_dyn_smem(const void* kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 int persistent_blocks(gridff_ctx* ctx, const void* kernel, int n_rep, size_t dyn_smem = 0) {
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, dyn_smem);
   if (per_sm < 1) per_sm = 1;
+  if (GRIDFF_BLOCK_CAP > 0 && per_sm > GRIDFF_BLOCK_CAP) per_sm = GRIDFF_BLOCK_CAP;
   int need = (n_rep + kWarpsPerBlock - 1) / kWarpsPerBlock;
   int cap = per_sm * ctx->n_sm;
   return need < cap ? need : cap;
@@ -1151,18 +1390,50 @@ gridff_status gridff_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_repl
   int use_grid = !(flags & GRIDFF_NO_GRID), use_intra = !(flags & GRIDFF_NO_INTRA);
   GRIDFF_CUDA(ctx, cudaEventRecord(ctx->ev0, s));
   if (R->rigid) {
-    size_t dyn = (size_t)GRIDFF_STAGED_NB * 512 * sizeof(float4) * kWarpsPerBlock;
-    if (dyn > 48 * 1024)
-      GRIDFF_CUDA(ctx, cudaFuncSetAttribute(relax_rigid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-    int blocks = persistent_blocks(ctx, (const void*)relax_rigid_kernel, R->n_rep, dyn);
-    relax_rigid_kernel<<<blocks, kThreads, dyn, s>>>(gv, R->tv, R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt,
-                                                   R->fire_alpha, R->fire_nplus, R->status, R->steps,
-                                                   R->energy, nsteps, fp, ctl, use_grid);
+    const int W = rigid_subwarp_width(R);
+    if (use_grid && W > 0) {
+      // one sub-warp of W lanes per replica, every atom cached
+      const int S = R->max_natoms;
+      const size_t dyn = cache_bytes(S) * kSwWarps * (32 / W);
+      const void* k = W == 8 ? (const void*)relax_rigid_sw_kernel<8, kSwWarps, kSwMinBlocks>
+                    : W == 16 ? (const void*)relax_rigid_sw_kernel<16, kSwWarps, kSwMinBlocks>
+                              : (const void*)relax_rigid_sw_kernel<32, kSwWarps, kSwMinBlocks>;
+      GRIDFF_CUDA(ctx, set_dyn_smem(k, dyn));
+      const int per_block = kSwWarps * (32 / W);
+      int per_sm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * kSwWarps, dyn);
+      if (per_sm < 1) per_sm = 1;
+      int need = (R->n_rep + per_block - 1) / per_block;
+      int blocks = need < per_sm * ctx->n_sm ? need : per_sm * ctx->n_sm;
+      if (W == 8)
+        relax_rigid_sw_kernel<8, kSwWarps, kSwMinBlocks><<<blocks, 32 * kSwWarps, dyn, s>>>(gv, R->tv,
+            R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha, R->fire_nplus, R->status, R->steps,
+            R->energy, nsteps, fp, ctl, S);
+      else if (W == 16)
+        relax_rigid_sw_kernel<16, kSwWarps, kSwMinBlocks><<<blocks, 32 * kSwWarps, dyn, s>>>(gv, R->tv,
+            R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha, R->fire_nplus, R->status, R->steps,
+            R->energy, nsteps, fp, ctl, S);
+      else
+        relax_rigid_sw_kernel<32, kSwWarps, kSwMinBlocks><<<blocks, 32 * kSwWarps, dyn, s>>>(gv, R->tv,
+            R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha, R->fire_nplus, R->status, R->steps,
+            R->energy, nsteps, fp, ctl, S);
+    } else {
+      const int S = cache_slots(R, true);
+      const size_t dyn = cache_bytes(S) * kWarpsPerBlock;
+      GRIDFF_CUDA(ctx, set_dyn_smem((const void*)relax_rigid_kernel, dyn));
+      int blocks = persistent_blocks(ctx, (const void*)relax_rigid_kernel, R->n_rep, dyn);
+      relax_rigid_kernel<<<blocks, kThreads, dyn, s>>>(gv, R->tv, R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt,
+                                                       R->fire_alpha, R->fire_nplus, R->status, R->steps,
+                                                       R->energy, nsteps, fp, ctl, use_grid, S);
+    }
   } else {
-    int blocks = persistent_blocks(ctx, (const void*)relax_flex_kernel, R->n_rep);
-    relax_flex_kernel<<<blocks, kThreads, 0, s>>>(gv, R->tv, R->rep_tmpl, R->rep_off, R->n_rep, R->x, R->v,
-                                                  R->fire_dt, R->fire_alpha, R->fire_nplus, R->status,
-                                                  R->steps, R->energy, nsteps, fp, ctl, use_grid, use_intra);
+    const int S = cache_slots(R, false);
+    const size_t dyn = cache_bytes(S) * kWarpsPerBlock;
+    GRIDFF_CUDA(ctx, set_dyn_smem((const void*)relax_flex_kernel, dyn));
+    int blocks = persistent_blocks(ctx, (const void*)relax_flex_kernel, R->n_rep, dyn);
+    relax_flex_kernel<<<blocks, kThreads, dyn, s>>>(gv, R->tv, R->rep_tmpl, R->rep_off, R->n_rep, R->x, R->v,
+                                                    R->fire_dt, R->fire_alpha, R->fire_nplus, R->status,
+                                                    R->steps, R->energy, nsteps, fp, ctl, use_grid, use_intra, S);
   }
   DevResult h{};
   gridff_status rs = finish_launch(ctx, &h);
@@ -1207,14 +1478,20 @@ gridff_status gridff_run(gridff_ctx* ctx, const gridff_grid* grid, gridff_replic
   GRIDFF_CUDA(ctx, cudaEventRecord(ctx->ev0, s));
   if (R->rigid) {
     if (!use_grid) return set_err(ctx, GRIDFF_EINVAL, "rigid replicas need the grid term");
-    int blocks = persistent_blocks(ctx, (const void*)run_rigid_kernel, R->n_rep);
-    run_rigid_kernel<<<blocks, kThreads, 0, s>>>(gv, R->tv, R->rep_tmpl, R->n_rep, R->x, R->v, R->status,
-                                                 R->energy, nsteps, prm->dt, rec_every, dtrace, ctl);
+    const int S = cache_slots(R, true);
+    const size_t dyn = cache_bytes(S) * kWarpsPerBlock;
+    GRIDFF_CUDA(ctx, set_dyn_smem((const void*)run_rigid_kernel, dyn));
+    int blocks = persistent_blocks(ctx, (const void*)run_rigid_kernel, R->n_rep, dyn);
+    run_rigid_kernel<<<blocks, kThreads, dyn, s>>>(gv, R->tv, R->rep_tmpl, R->n_rep, R->x, R->v, R->status,
+                                                   R->energy, nsteps, prm->dt, rec_every, dtrace, ctl, S);
   } else {
-    int blocks = persistent_blocks(ctx, (const void*)run_flex_kernel, R->n_rep);
-    run_flex_kernel<<<blocks, kThreads, 0, s>>>(gv, R->tv, R->rep_tmpl, R->rep_off, R->n_rep, R->x, R->v,
-                                                R->status, R->energy, nsteps, prm->dt, rec_every, dtrace, ctl,
-                                                use_grid, use_intra);
+    const int S = cache_slots(R, false);
+    const size_t dyn = cache_bytes(S) * kWarpsPerBlock;
+    GRIDFF_CUDA(ctx, set_dyn_smem((const void*)run_flex_kernel, dyn));
+    int blocks = persistent_blocks(ctx, (const void*)run_flex_kernel, R->n_rep, dyn);
+    run_flex_kernel<<<blocks, kThreads, dyn, s>>>(gv, R->tv, R->rep_tmpl, R->rep_off, R->n_rep, R->x, R->v,
+                                                  R->status, R->energy, nsteps, prm->dt, rec_every, dtrace, ctl,
+                                                  use_grid, use_intra, S);
   }
   DevResult h{};
   gridff_status rs = finish_launch(ctx, &h);

@@ -303,6 +303,27 @@ void channel_slots(int channels, int& sC, int& sP, int& sL, int& n_ch) {
   if (channels & GRIDFF_CH_L) sL = n_ch++;
 }
 
+// Allocate grid->rec for the grid's storage layout and pack FP64
+// coefficients ([C][nx][ny][nz], device) into it.
+gridff_status pack_records(gridff_ctx* ctx, gridff_grid* g, const double* data) {
+  int nx = g->dims[0], ny = g->dims[1], nz = g->dims[2];
+  cudaStream_t s = ctx->stream;
+  g->nxp = nx + 3;
+  g->nyp = ny + 3;
+  g->nzp = nz + 2;
+  int sC, sP, sL, nch;
+  channel_slots(g->channels, sC, sP, sL, nch);
+  long long n_rec = (long long)g->nxp * g->nyp * g->nzp;
+  g->rec_bytes = (size_t)n_rec * sizeof(float4);
+  GRIDFF_CUDA(ctx, cudaMalloc(&g->rec, g->rec_bytes));
+  pack_kernel<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(data, nx, ny, nz, g->nyp, g->nzp, n_rec,
+                                                                sC, sP, sL, g->rec);
+  GRIDFF_CUDA(ctx, cudaGetLastError());
+  return GRIDFF_OK;
+}
+
+bool storage_ok(int st) { return st == GRIDFF_STORE_F32; }
+
 // Fit coefficients in place (3 passes) and pack them into grid->rec.
 gridff_status fit_and_pack(gridff_ctx* ctx, gridff_grid* g, double* data, DevFree& df) {
   int nx = g->dims[0], ny = g->dims[1], nz = g->dims[2];
@@ -349,19 +370,7 @@ gridff_status fit_and_pack(gridff_ctx* ctx, gridff_grid* g, double* data, DevFre
         data, nx, (long long)ny * nz, lines, ny * nz, 1, N, t);
   }
   GRIDFF_CUDA(ctx, cudaGetLastError());
-  // pack
-  g->nxp = nx + 3;
-  g->nyp = ny + 3;
-  g->nzp = nz + 2;
-  long long n_rec = (long long)g->nxp * g->nyp * g->nzp;
-  g->rec_bytes = (size_t)n_rec * sizeof(float4);
-  GRIDFF_CUDA(ctx, cudaMalloc(&g->rec, g->rec_bytes));
-  int sC, sP, sL, nch;
-  channel_slots(g->channels, sC, sP, sL, nch);
-  pack_kernel<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(data, nx, ny, nz, g->nyp, g->nzp,
-                                                                n_rec, sC, sP, sL, g->rec);
-  GRIDFF_CUDA(ctx, cudaGetLastError());
-  return GRIDFF_OK;
+  return pack_records(ctx, g, data);
 }
 
 bool dims_ok(const int* d) { return d[0] >= 4 && d[1] >= 4 && d[2] >= 4; }
@@ -494,7 +503,7 @@ gridff_status gridff_build_grid(gridff_ctx* ctx, const gridff_substrate* sub,
   *out = nullptr;
   if (sub->n_atoms <= 0 || !sub->xyz || !sub->q || !sub->R || !sub->eps)
     return set_err(ctx, GRIDFF_EINVAL, "substrate needs n_atoms > 0 and all arrays");
-  if (opts->storage != GRIDFF_STORE_F32) return set_err(ctx, GRIDFF_ENOTSUP, "storage not supported");
+  if (!storage_ok(opts->storage)) return set_err(ctx, GRIDFF_ENOTSUP, "storage not supported");
   if (!(opts->spacing > 0) || !(opts->length[0] > 0) || !(opts->length[1] > 0) ||
       !(opts->length[2] > 0))
     return set_err(ctx, GRIDFF_EINVAL, "grid box lengths and spacing must be > 0");
@@ -507,6 +516,7 @@ gridff_status gridff_build_grid(gridff_ctx* ctx, const gridff_substrate* sub,
 
   gridff_grid* g = new gridff_grid();
   g->ctx = ctx;
+  g->device = ctx->device;
   g->storage = opts->storage;
   bool charged = false;
   double Qtot = 0.0, Mz = 0.0;
@@ -705,7 +715,7 @@ gridff_status gridff_grid_from_coefs(gridff_ctx* ctx, const double origin[3], co
   if (!ctx || !origin || !spacing || !dims || !coefs || !out)
     return set_err(ctx, GRIDFF_EINVAL, "null argument");
   *out = nullptr;
-  if (storage != GRIDFF_STORE_F32) return set_err(ctx, GRIDFF_ENOTSUP, "storage not supported");
+  if (!storage_ok(storage)) return set_err(ctx, GRIDFF_ENOTSUP, "storage not supported");
   if (!dims_ok(dims)) return set_err(ctx, GRIDFF_EINVAL, "grid needs at least 4 nodes per axis");
   if (!(channels & 7) || (channels & ~7)) return set_err(ctx, GRIDFF_EINVAL, "bad channel mask");
   for (int a = 0; a < 3; ++a)
@@ -713,6 +723,7 @@ gridff_status gridff_grid_from_coefs(gridff_ctx* ctx, const double origin[3], co
   GRIDFF_CUDA(ctx, cudaSetDevice(ctx->device));
   gridff_grid* g = new gridff_grid();
   g->ctx = ctx;
+  g->device = ctx->device;
   g->channels = channels;
   g->storage = storage;
   int sC, sP, sL;
@@ -734,17 +745,11 @@ gridff_status gridff_grid_from_coefs(gridff_ctx* ctx, const double origin[3], co
     return set_err(ctx, GRIDFF_ECUDA, "coefficient upload");
   }
   // reuse the packing step only (coefficients are given)
-  g->nxp = dims[0] + 3;
-  g->nyp = dims[1] + 3;
-  g->nzp = dims[2] + 2;
-  long long n_rec = (long long)g->nxp * g->nyp * g->nzp;
-  g->rec_bytes = (size_t)n_rec * sizeof(float4);
-  if (cudaMalloc(&g->rec, g->rec_bytes) != cudaSuccess) {
-    delete g;
-    return set_err(ctx, GRIDFF_ENOMEM, "grid records");
+  gridff_status pst = pack_records(ctx, g, d);
+  if (pst != GRIDFF_OK) {
+    gridff_grid_destroy(g);
+    return pst;
   }
-  pack_kernel<<<(unsigned)((n_rec + 255) / 256), 256, 0, ctx->stream>>>(
-      d, dims[0], dims[1], dims[2], g->nyp, g->nzp, n_rec, sC, sP, sL, g->rec);
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -817,10 +822,14 @@ gridff_status gridff_grid_download_f64(const gridff_grid* g, int what, double* h
 
 void gridff_grid_destroy(gridff_grid* g) {
   if (!g) return;
-  if (g->ctx) cudaSetDevice(g->ctx->device);
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(g->device);
   if (g->rec) cudaFree(g->rec);
   if (g->f64_values) cudaFree(g->f64_values);
   if (g->f64_coefs) cudaFree(g->f64_coefs);
+  cudaSetDevice(prev);
+  cudaGetLastError();   // leave no error of this teardown behind
   delete g;
 }
 

@@ -45,6 +45,7 @@ struct GridView {
 
 struct gridff_grid {
   gridff_ctx* ctx = nullptr;
+  int device = 0;                 // kept here so that destroy never reads ctx
   int dims[3] = {0, 0, 0};
   double origin[3] = {0, 0, 0};
   double spacing[3] = {0, 0, 0};
@@ -94,6 +95,7 @@ struct DevResult {
 
 struct gridff_replicas {
   gridff_ctx* ctx = nullptr;
+  int device = 0;              // kept here so that destroy never reads ctx
   int n_rep = 0;
   int n_atoms = 0;          // total atoms over replicas
   int n_tmpl = 0;

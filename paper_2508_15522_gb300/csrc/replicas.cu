@@ -217,6 +217,7 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
          o_rig = push(blob, rig), o_rmax = push(blob, rmax);
   gridff_replicas* R = new gridff_replicas();
   R->ctx = ctx;
+  R->device = ctx->device;
   R->n_rep = n_rep;
   R->n_atoms = rep_off[n_rep];
   R->n_tmpl = n_templates;
@@ -281,11 +282,15 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
 
 void gridff_replicas_destroy(gridff_replicas* R) {
   if (!R) return;
-  if (R->ctx) cudaSetDevice(R->ctx->device);
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(R->device);
   void* ptrs[] = {R->tmpl_blob, R->rep_tmpl, R->rep_off, R->x, R->v, R->fire_dt, R->fire_alpha,
                   R->fire_nplus, R->status, R->steps, R->energy};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  cudaSetDevice(prev);
+  cudaGetLastError();   // leave no error of this teardown behind
   delete[] R->h_rep_off;
   delete R;
 }

@@ -222,7 +222,8 @@ class Grid:
 
 
 def build_grid(ctx: Context, sub, origin, length, spacing, channels=CH_C | CH_P | CH_L,
-               alpha=1.5, rcut=17.0, ewald_tol=1e-10, ewald_rcut=12.0, keep_f64=False) -> Grid:
+               alpha=1.5, rcut=17.0, ewald_tol=1e-10, ewald_rcut=12.0, keep_f64=False,
+               storage=STORE_F32) -> Grid:
     """gridff_build_grid: substrate (object with xyz, q, R, eps, cell) -> Grid."""
     xyz = np.ascontiguousarray(sub.xyz, np.float64).ravel()
     q = np.ascontiguousarray(sub.q, np.float64)
@@ -237,18 +238,19 @@ def build_grid(ctx: Context, sub, origin, length, spacing, channels=CH_C | CH_P 
     o.length = (C.c_double * 3)(*length)
     o.spacing, o.alpha, o.rcut = spacing, alpha, rcut
     o.ewald_tol, o.ewald_rcut, o.channels, o.keep_f64 = ewald_tol, ewald_rcut, channels, int(keep_f64)
+    o.storage = storage
     h = C.c_void_p()
     ctx.check(lib.gridff_build_grid(ctx.h, C.byref(s), C.byref(o), C.byref(h)))
     return Grid(ctx, h)
 
 
-def grid_from_coefs(ctx: Context, coefs, origin, spacing, channels) -> Grid:
+def grid_from_coefs(ctx: Context, coefs, origin, spacing, channels, storage=STORE_F32) -> Grid:
     """gridff_grid_from_coefs: FP64 coefficients (C, nx, ny, nz) -> Grid."""
     c = np.ascontiguousarray(coefs, np.float64)
     dims = (C.c_int32 * 3)(*c.shape[1:])
     h = C.c_void_p()
     ctx.check(lib.gridff_grid_from_coefs(ctx.h, (C.c_double * 3)(*origin), (C.c_double * 3)(*spacing), dims,
-                                         channels, c.ctypes.data_as(C.POINTER(C.c_double)), STORE_F32,
+                                         channels, c.ctypes.data_as(C.POINTER(C.c_double)), storage,
                                          C.byref(h)))
     return Grid(ctx, h)
 

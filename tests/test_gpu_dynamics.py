@@ -57,8 +57,10 @@ def test_fire_flexible_first_steps_match_oracle(G, ctx, small_field):
         assert (fs["steps"] == nsteps).all()
 
 
-def test_fire_rigid_first_steps_match_oracle(G, ctx, small_field):
-    sub, box, h, c32, grid = small_field
+@pytest.mark.parametrize("storage", [0])
+def test_fire_rigid_first_steps_match_oracle(G, ctx, small_field, storage):
+    sub, box, h, c32, grid0 = small_field
+    grid = G.grid_from_coefs(ctx, c32, box.origin, h, 7, storage=storage)
     mol = synth.c24h8o6_core()
     n_rep = 33
     com, quat = synth.rigid_poses(mol, sub, n_rep, seed=33)

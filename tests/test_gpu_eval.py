@@ -46,15 +46,16 @@ def _oracle_grid(coefs, chans, origin, h, pts, mol_q, mol_R, mol_eps, dtype):
     return ogrid.grid_energy_forces(coefs, chans, origin, h, pts, mol_q, mol_R, mol_eps, dtype=dtype)
 
 
-@pytest.mark.parametrize("shape", [(17, 13, 21), (8, 9, 6)])
-def test_eval_random_field_matches_fp32_oracle(G, ctx, shape):
+@pytest.mark.parametrize("storage", [0])
+@pytest.mark.parametrize("shape", [(17, 13, 21), (8, 9, 6), (9, 7, 5)])
+def test_eval_random_field_matches_fp32_oracle(G, ctx, shape, storage):
     """Random coefficients, points spanning periodic wraps, the clamped z
     ends, below and above the grid; several tiles and a ragged tail of
     atoms per warp (n = 70 atoms per replica)."""
     h = (0.21, 0.17, 0.19)
     origin = (0.3, -1.1, 2.0)
     coefs = synth.random_coefficients(shape, 3, seed=13, scale=(0.8, 2.0, 1.0))
-    grid = G.grid_from_coefs(ctx, coefs, origin, h, G.CH_C | G.CH_P | G.CH_L)
+    grid = G.grid_from_coefs(ctx, coefs, origin, h, G.CH_C | G.CH_P | G.CH_L, storage=storage)
     n_at, n_rep = 70, 9
     mol = _point_molecule(n_at)
     g = synth.rng(14)
@@ -75,10 +76,11 @@ def test_eval_random_field_matches_fp32_oracle(G, ctx, shape):
     assert np.array_equal((S & G.REP_BELOW) != 0, below_rep)
 
 
-def test_eval_two_channel_grid(G, ctx):
+@pytest.mark.parametrize("storage", [0])
+def test_eval_two_channel_grid(G, ctx, storage):
     shape, h, origin = (12, 10, 16), (0.25, 0.3, 0.2), (0.0, 0.0, 1.0)
     coefs = synth.random_coefficients(shape, 2, seed=15, scale=(1.0, 0.5))
-    grid = G.grid_from_coefs(ctx, coefs, origin, h, G.CH_P | G.CH_L)
+    grid = G.grid_from_coefs(ctx, coefs, origin, h, G.CH_P | G.CH_L, storage=storage)
     mol = _point_molecule(33)
     pts = synth.uniform_points(33 * 4, synth.GridBox(origin, (3.0, 3.0, 3.2), 0.25), 16, zband=(0.2, 2.8))
     reps = G.Replicas(ctx, [mol], [0] * 4)
@@ -107,13 +109,14 @@ def test_eval_intramolecular_matches_oracle(G, ctx):
         assert np.abs(F[off[r]:off[r + 1]] - Fi[0]).max() <= TOL_F * max(1, np.abs(Fi).max())
 
 
-def test_eval_rigid_pose_matches_oracle(G, ctx):
+@pytest.mark.parametrize("storage", [0])
+def test_eval_rigid_pose_matches_oracle(G, ctx, storage):
     mol = synth.c24h8o6_core()
     sub = synth.rocksalt_slab(ncell=2)
     box = synth.grid_box_for(sub, 0.2, height=8.0)
     n, h = ogrid.grid_dims(box.length, box.spacing)
     coefs = synth.random_coefficients(n, 3, seed=18, scale=(0.05, 0.05, 0.05))
-    grid = G.grid_from_coefs(ctx, coefs, box.origin, h, 7)
+    grid = G.grid_from_coefs(ctx, coefs, box.origin, h, 7, storage=storage)
     com, quat = synth.rigid_poses(mol, sub, 40, seed=19)
     reps = G.Replicas(ctx, [mol], [0] * 40, rigid=True)
     reps.set_state(np.concatenate([com, quat], 1).astype(np.float32).ravel())
@@ -167,13 +170,14 @@ def test_build_grid_full_size_sampled_nodes_and_fit_property(G, ctx):
     assert np.abs(back - vals).max() <= 1e-10 * np.abs(vals).max()
 
 
-def test_interpolation_error_against_pairwise_reference(G, ctx):
+@pytest.mark.parametrize("storage", [0])
+def test_interpolation_error_against_pairwise_reference(G, ctx, storage):
     """The 0.1 A GPU grid against the FP64 pairwise reference (direct Morse
     + Ewald) for molecules 2-5 A above the surface; the paper reports
     ~1e-5 eV differences for whole molecules at this spacing (Sec. 6)."""
     sub = synth.rocksalt_slab(ncell=8, layers=3)
     box = synth.grid_box_for(sub, 0.1)
-    grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing)
+    grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, storage=storage)
     mol = synth.c24h8o6_core()
     com, quat = synth.rigid_poses(mol, sub, 6, seed=22, h_lo=3.5, h_hi=4.0, min_clear=2.8)
     reps = G.Replicas(ctx, [mol], [0] * 6, rigid=True)
