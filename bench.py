@@ -81,7 +81,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -199,6 +199,44 @@ def measured_peaks():
         return {}
 
 
+def reduce_over_ranks(seconds, evals, dist=None, device=None):
+    """Whole-job figures of one timed region: (max seconds over ranks, sum of
+    evaluations over ranks).  Replicas are independent, so this is the only
+    cross-rank step (no data-path collective)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(seconds), float(evals)
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e = torch.tensor([float(evals)], dtype=torch.float64, device=device)
+    dist.all_reduce(e)
+    return float(t.item()), float(e.item())
+
+
+def nve_drift(G, ctx, grid, reps, mol, pose, n_steps=10_000, dt=1.0, seed=SEED):
+    """10k-step NVE (NO_SQUISH, 1 fs) of the relaxed replicas with 300 K
+    Maxwell-Boltzmann velocities; returns the energy drift statistics and
+    the NVE throughput (outside the timed region)."""
+    kT, acc = 0.025852, 9.648533e-3
+    M = float(mol.mass.sum())
+    b = mol.xyz
+    I = np.array([np.sum(mol.mass * (np.sum(b * b, 1) - b[:, k] ** 2)) for k in range(3)])
+    g = np.random.Generator(np.random.PCG64(seed + 7))
+    n = len(pose)
+    vel = np.concatenate([g.standard_normal((n, 3)) * np.sqrt(kT * acc / M),
+                          g.standard_normal((n, 3)) * np.sqrt(kT * acc / I)], 1).astype(np.float32)
+    x, _ = reps.get_state()
+    reps.set_state(x, vel.ravel())
+    t0 = time.perf_counter()
+    st, trace = G.run(ctx, grid, reps, n_steps, dt=dt, record_every=1000)
+    wall = time.perf_counter() - t0
+    d = np.abs(trace - trace[0:1])
+    return {"steps": n_steps, "dt_fs": dt, "temperature_K": 300.0, "replicas": n,
+            "max_abs_drift_eV": float(d.max()), "median_max_abs_drift_eV": float(np.median(d.max(0))),
+            "atom_evals_per_s": n * mol.n * n_steps / (ctx.last_kernel_ms() * 1e-3),
+            "wall_s": wall}
+
+
 def run_gpu(args):
     import torch
     import __graft_entry__ as ge
@@ -249,16 +287,7 @@ def run_gpu(args):
             kernel_ms.append(ctx.last_kernel_ms())
         torch.cuda.synchronize(dev)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-        e = torch.tensor([float(evals)], device=dev)
-        dist.all_reduce(e)
-        evals_all = float(e.item())
-    else:
-        evals_all = float(evals)
+    total_s, evals_all = reduce_over_ranks(sum(step_ms) / 1e3, evals, dist, dev)
     value = evals_all / total_s
 
     # end to end through the public API with host buffers (pinned)
@@ -312,6 +341,10 @@ def run_gpu(args):
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
+    if not args.quick:
+        reps.set_state(pose_dev)
+        G.relax(ctx, grid, reps, FIRE_ITERS, G.fire_params())
+        line["nve_drift"] = nve_drift(G, ctx, grid, reps, mol, pose)
     if rank == 0 and world == 1 and not args.quick:
         cv, cdt, cdesc = oracle_sample()
         line["cpu_baseline"] = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cdesc}
