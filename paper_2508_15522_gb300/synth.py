@@ -487,3 +487,23 @@ def random_coefficients(shape, n_channels: int, seed: int, scale=(1.0, 0.3, 0.1)
 def atom_params(mol: Molecule):
     """(q, R, eps, mass) float64 arrays of a molecule template."""
     return mol.q.copy(), mol.R.copy(), mol.eps.copy(), mol.mass.copy()
+
+
+# ---------------------------------------------------------------------------
+# learned pose proposal: initial weights and training inputs
+# ---------------------------------------------------------------------------
+def mlp_weights(sizes, seed: int):
+    """He-uniform initial weights W_l [out][in] and zero biases of an MLP with
+    layer widths ``sizes`` (float64)."""
+    g = rng(seed)
+    Ws, bs = [], []
+    for n_in, n_out in zip(sizes[:-1], sizes[1:]):
+        lim = math.sqrt(6.0 / n_in)
+        Ws.append(g.uniform(-lim, lim, (n_out, n_in)))
+        bs.append(np.zeros(n_out))
+    return Ws, bs
+
+
+def noise(n: int, dim: int, seed: int) -> np.ndarray:
+    """Standard-normal noise inputs (n, dim), float32."""
+    return rng(seed).standard_normal((n, dim)).astype(np.float32)
