@@ -322,6 +322,93 @@ gridff_status gridff_run(gridff_ctx* ctx, const gridff_grid* grid, gridff_replic
                          int32_t nsteps, const gridff_md_params* params, int flags,
                          double* energy_trace);
 
+/* --------------------------------------------------------- pose proposal */
+
+/* Learned proposal of starting poses for relaxations.  The paper has no
+ * counterpart: its sampling starts from random poses and Langevin heating
+ * (Sec. 7); this network learns where relaxed minima lie and proposes
+ * starting poses near them.
+ *
+ * Network: sizes[0] inputs (molecule descriptor followed by N(0,1) noise),
+ * n_layers fully connected layers a_l = h_{l-1} W_l^T + b_l, ReLU on the
+ * hidden layers, linear output of GRIDFF_MLP_OUT = 19 values:
+ * centre of mass (3, A), orientation (4, normalised on use), torsions (12,
+ * rad).  W_l is [sizes[l+1]][sizes[l]] row-major.  Parameters are held in
+ * FP32 (master copy, Adam moments); every GEMM runs with bfloat16 operands
+ * (round to nearest even) and FP32 accumulation on the tensor cores.
+ * The flat parameter order is W_0, b_0, W_1, b_1, ...  */
+#define GRIDFF_MLP_OUT 19
+#define GRIDFF_MLP_NO_UPDATE 1   /* train_step: gradients only, no Adam step */
+
+typedef struct gridff_mlp gridff_mlp;
+
+typedef struct {
+  float lr;          /* Adam learning rate */
+  float beta1;       /* default 0.9 */
+  float beta2;       /* default 0.999 */
+  float eps;         /* default 1e-8 */
+  float w_q;         /* weight of the orientation term, default 1 */
+  float w_t;         /* weight of the torsion terms, default 0.25 */
+  double tile[2];    /* periodic tile (Lx, Ly) of the substrate, A */
+} gridff_train_params;
+
+/* Create a network with n_layers layers of widths sizes[0..n_layers]
+ * (sizes[n_layers] must be 19, widths 1..4096).  Parameters start at zero;
+ * set them with gridff_mlp_set_params.  Errors: EINVAL, ENOMEM, ECUDA. */
+gridff_status gridff_mlp_create(gridff_ctx* ctx, int32_t n_layers, const int32_t* sizes,
+                                gridff_mlp** out);
+void gridff_mlp_destroy(gridff_mlp* mlp);
+int64_t gridff_mlp_num_params(const gridff_mlp* mlp);
+
+/* Copy FP32 parameters in (host array, flat order above); resets the Adam
+ * moments and step counter.  get_params copies parameters and/or the
+ * gradients of the last train step out (either pointer may be NULL). */
+gridff_status gridff_mlp_set_params(gridff_mlp* mlp, const float* params);
+gridff_status gridff_mlp_get_params(gridff_mlp* mlp, float* params, float* grads);
+
+/* Forward pass: x [rows][sizes[0]] (host, FP32) -> y [rows][19] (host). */
+gridff_status gridff_mlp_forward(gridff_mlp* mlp, int32_t rows, const float* x, float* y);
+
+/* One training step with the winner-takes-all pose loss.  x holds
+ * n_targets*K input rows (row b*K + k is proposal k of target b);
+ * targets [n_targets][19] are relaxed poses (unit quaternion);
+ * tors_mask [n_targets][12] (may be NULL = no torsions) selects the live
+ * torsions.  Distance of an output o to a target t:
+ *   |c - t_c|^2 (x, y by minimum image on the tile)
+ *   + w_q (1 - (q . t_q)^2), q = o_q / |o_q|
+ *   + w_t sum_j mask_j (1 - cos(o_j - t_j));
+ * loss = mean over targets of the minimum over its K proposals; only the
+ * winning proposal back-propagates.  Then one Adam step (unless
+ * GRIDFF_MLP_NO_UPDATE).  loss_out (may be NULL) receives the loss.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+gridff_status gridff_mlp_train_step(gridff_mlp* mlp, int32_t n_targets, int32_t K, const float* x,
+                                    const float* targets, const float* tors_mask,
+                                    const gridff_train_params* params, float* loss_out, int flags);
+
+/* Propose one pose per replica of a rigid replica set: inputs are the
+ * descriptor (n_desc <= sizes[0] floats, host) followed by
+ * sizes[0] - n_desc <= 64 standard normal draws from a counter-based
+ * generator: for row r (= replica) and noise index j,
+ *   s = splitmix64(seed XOR splitmix64(64 r + j))   (splitmix64(x): the
+ *       output of Steele-Lea-Flood SplitMix64 from state x),
+ *   u1 = ((s >> 40) + 1) / 2^24,  u2 = ((s >> 16) mod 2^24) / 2^24,
+ *   z = sqrt(-2 ln u1) cos(2 pi u2)   (Box-Muller, FP32).  The output's
+ * centre of mass is folded into the tile [origin, origin + tile) in x and
+ * y; the quaternion is normalised (identity if zero).  Writes the replica
+ * poses and zero velocities.  Errors: EINVAL, ENOTSUP (flexible replicas),
+ * ENOMEM, ECUDA. */
+gridff_status gridff_mlp_propose(gridff_mlp* mlp, gridff_replicas* reps, const float* descriptor,
+                                 int32_t n_desc, uint64_t seed, const double origin_xy[2],
+                                 const double tile_xy[2]);
+
+/* 64-float descriptor of a molecule template (host computation): atom
+ * count / 128; fractions of atoms by mass class (< 4, 4-13, 13-15, 15-17,
+ * >= 17 amu); net charge; dipole about the centre of mass / 10; square
+ * roots of the principal moments of inertia per mass / 5 (ascending);
+ * radius of gyration / 5; largest distance from the centre of mass / 10;
+ * torsion count / 12; zero padding.  Errors: EINVAL. */
+gridff_status gridff_molecule_descriptor(const gridff_molecule* mol, float* out);
+
 /* ------------------------------------------------------------ measurement */
 
 /* Read `bytes` of a device buffer `iters` times with a streaming kernel and

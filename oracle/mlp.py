@@ -106,3 +106,29 @@ def adam(params, grads, state, lr, t, b1=0.9, b2=0.999, eps=1e-8):
         v = b2 * v + (1 - b2) * g * g
         state[k] = (m, v)
         p -= lr * (m / (1 - b1 ** t)) / (np.sqrt(v / (1 - b2 ** t)) + eps)
+
+
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(x: int) -> int:
+    """Output of the SplitMix64 generator (Steele, Lea and Flood, 2014) whose
+    state is x: advance by the golden gamma, then the variant-13 mix."""
+    z = (x + 0x9E3779B97F4A7C15) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def counter_normal(seed: int, rows: int, dim: int) -> np.ndarray:
+    """Standard normal draws of the proposal noise: entry (r, j) from the
+    counter 64 r + j hashed with the seed, then Box-Muller (float64 here;
+    the device evaluates the same formula in float32)."""
+    out = np.empty((rows, dim))
+    for r in range(rows):
+        for j in range(dim):
+            s = splitmix64(seed ^ splitmix64(64 * r + j))
+            u1 = ((s >> 40) + 1) / 2.0 ** 24
+            u2 = ((s >> 16) & 0xFFFFFF) / 2.0 ** 24
+            out[r, j] = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    return out

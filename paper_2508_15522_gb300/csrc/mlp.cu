@@ -1,0 +1,632 @@
+// Learned pose proposal: a small MLP (molecule descriptor + noise in,
+// centre of mass + orientation quaternion + torsions out) with bfloat16
+// weights and FP32 accumulation on the tensor cores (mma.sync m16n8k16),
+// trained on the device with a winner-takes-all pose loss and Adam, and a
+// proposal kernel that writes replica poses for gridff_relax.
+// Not from the paper: it chooses where GridFF relaxations start.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int kOut = 19;      // 3 position + 4 quaternion + 12 torsions
+constexpr int kTors = 12;
+
+inline int pad16(int n) { return (n + 15) & ~15; }
+
+// ---------------------------------------------------------------------------
+// C[M][N] (FP32) = A[M][K] * B, A row-major bf16 (lda), B given as Bt[N][K]
+// row-major bf16 (ldb), i.e. B is K x N column-major.  M % 16 == 0,
+// N % 8 == 0, K % 16 == 0.  One warp per 16 x 8 output tile, K in steps of
+// 16 with one tensor-core mma per step.
+// ---------------------------------------------------------------------------
+__global__ void gemm_bf16_kernel(const __nv_bfloat16* __restrict__ A, int lda,
+                                 const __nv_bfloat16* __restrict__ Bt, int ldb, float* __restrict__ C,
+                                 int ldc, int M, int N, int K, int accumulate) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int tiles_n = N / 8;
+  if (warp >= (M / 16) * tiles_n) return;
+  const int tm = warp / tiles_n, tn = warp % tiles_n;
+  const int g = lane >> 2, t = lane & 3;
+  float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+  const __nv_bfloat16* a0p = A + (size_t)(tm * 16 + g) * lda + 2 * t;
+  const __nv_bfloat16* a1p = a0p + (size_t)8 * lda;
+  const __nv_bfloat16* bp = Bt + (size_t)(tn * 8 + g) * ldb + 2 * t;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    const unsigned a0 = *(const unsigned*)(a0p + k0);
+    const unsigned a1 = *(const unsigned*)(a1p + k0);
+    const unsigned a2 = *(const unsigned*)(a0p + k0 + 8);
+    const unsigned a3 = *(const unsigned*)(a1p + k0 + 8);
+    const unsigned b0 = *(const unsigned*)(bp + k0);
+    const unsigned b1 = *(const unsigned*)(bp + k0 + 8);
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c0), "+f"(c1), "+f"(c2), "+f"(c3)
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+  }
+  float* r0 = C + (size_t)(tm * 16 + g) * ldc + tn * 8 + 2 * t;
+  float* r1 = r0 + (size_t)8 * ldc;
+  if (accumulate) {
+    r0[0] += c0; r0[1] += c1; r1[0] += c2; r1[1] += c3;
+  } else {
+    r0[0] = c0; r0[1] = c1; r1[0] = c2; r1[1] = c3;
+  }
+}
+
+// Input rows (FP32 [rows][n_in]) -> bf16 layer input, row-major [Mp][in_p]
+// and transposed [in_p][Mp]; padding zero.
+__global__ void input_kernel(const float* __restrict__ X, int rows, int n_in, int Mp, int in_p,
+                             __nv_bfloat16* __restrict__ H, __nv_bfloat16* __restrict__ HT) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Mp * in_p) return;
+  const int m = idx / in_p, k = idx % in_p;
+  const float v = (m < rows && k < n_in) ? X[(size_t)m * n_in + k] : 0.f;
+  const __nv_bfloat16 b = __float2bfloat16(v);
+  H[idx] = b;
+  HT[(size_t)k * Mp + m] = b;
+}
+
+// a = C + bias (pre-activation kept for the ReLU mask); hidden layers emit
+// bf16 h = max(a, 0) (row-major and transposed) for the next layer; the last
+// layer emits FP32 outputs [rows][n_out].  Padded rows/columns are zero.
+__global__ void bias_act_kernel(const float* __restrict__ C, const float* __restrict__ b, int rows, int n_out,
+                                int Mp, int out_p, float* __restrict__ Apre, __nv_bfloat16* __restrict__ Hn,
+                                __nv_bfloat16* __restrict__ HnT, float* __restrict__ Y) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Mp * out_p) return;
+  const int m = idx / out_p, j = idx % out_p;
+  const bool live = m < rows && j < n_out;
+  const float a = live ? C[idx] + b[j] : 0.f;
+  Apre[idx] = a;
+  if (Hn) {
+    const __nv_bfloat16 h = __float2bfloat16(fmaxf(a, 0.f));
+    Hn[idx] = h;
+    HnT[(size_t)j * Mp + m] = h;
+  } else if (live) {
+    Y[(size_t)m * n_out + j] = a;
+  }
+}
+
+// Winner-takes-all pose loss (see gridff.h): one thread per target; writes
+// dL/dY for the winning proposal rows (dY zeroed before) and the target's
+// loss share.
+__global__ void wta_kernel(const float* __restrict__ Y, const float* __restrict__ T,
+                           const float* __restrict__ mask, int n_targets, int K, int out_p, float w_q,
+                           float w_t, float tile_x, float tile_y, float* __restrict__ dY,
+                           float* __restrict__ loss, int* __restrict__ winner) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_targets) return;
+  const float* t = T + (size_t)b * kOut;
+  const float* mk = mask ? mask + (size_t)b * kTors : nullptr;
+  float best = INFINITY;
+  int kb = 0;
+  for (int k = 0; k < K; ++k) {
+    const float* o = Y + ((size_t)b * K + k) * kOut;
+    float dx = o[0] - t[0], dy = o[1] - t[1], dz = o[2] - t[2];
+    dx -= tile_x * rintf(dx / tile_x);
+    dy -= tile_y * rintf(dy / tile_y);
+    float nu = sqrtf(o[3] * o[3] + o[4] * o[4] + o[5] * o[5] + o[6] * o[6]);
+    nu = fmaxf(nu, 1e-12f);
+    const float s = (o[3] * t[3] + o[4] * t[4] + o[5] * t[5] + o[6] * t[6]) / nu;
+    float d = dx * dx + dy * dy + dz * dz + w_q * (1.f - s * s);
+    if (mk)
+      for (int j = 0; j < kTors; ++j) d += w_t * mk[j] * (1.f - cosf(o[7 + j] - t[7 + j]));
+    if (d < best) {
+      best = d;
+      kb = k;
+    }
+  }
+  winner[b] = kb;
+  loss[b] = best;
+  const float* o = Y + ((size_t)b * K + kb) * kOut;
+  float* g = dY + ((size_t)b * K + kb) * out_p;
+  const float inv_b = 1.f / n_targets;
+  float dx = o[0] - t[0], dy = o[1] - t[1], dz = o[2] - t[2];
+  dx -= tile_x * rintf(dx / tile_x);
+  dy -= tile_y * rintf(dy / tile_y);
+  g[0] = 2.f * dx * inv_b;
+  g[1] = 2.f * dy * inv_b;
+  g[2] = 2.f * dz * inv_b;
+  float nu = sqrtf(o[3] * o[3] + o[4] * o[4] + o[5] * o[5] + o[6] * o[6]);
+  nu = fmaxf(nu, 1e-12f);
+  float q[4] = {o[3] / nu, o[4] / nu, o[5] / nu, o[6] / nu};
+  const float s = q[0] * t[3] + q[1] * t[4] + q[2] * t[5] + q[3] * t[6];
+  for (int a = 0; a < 4; ++a) g[3 + a] = -2.f * w_q * s * (t[3 + a] - s * q[a]) / nu * inv_b;
+  for (int j = 0; j < kTors; ++j) g[7 + j] = mk ? w_t * mk[j] * sinf(o[7 + j] - t[7 + j]) * inv_b : 0.f;
+}
+
+// G (FP32 [Mp][out_p], dL/da of this layer) -> bf16 row-major and transposed.
+// If `mask_pre` is given, G is first multiplied by (pre-activation > 0).
+__global__ void grad_prep_kernel(float* __restrict__ G, const float* __restrict__ mask_pre, int rows, int n_out,
+                                 int Mp, int out_p, __nv_bfloat16* __restrict__ Gb, __nv_bfloat16* __restrict__ GbT) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Mp * out_p) return;
+  const int m = idx / out_p, j = idx % out_p;
+  float v = (m < rows && j < n_out) ? G[idx] : 0.f;
+  if (mask_pre && !(mask_pre[idx] > 0.f)) v = 0.f;
+  G[idx] = v;
+  const __nv_bfloat16 b = __float2bfloat16(v);
+  Gb[idx] = b;
+  GbT[(size_t)j * Mp + m] = b;
+}
+
+// db[j] = sum_m G[m][j]
+__global__ void colsum_kernel(const float* __restrict__ G, int Mp, int out_p, int n_out, float* __restrict__ db) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_out) return;
+  float s = 0.f;
+  for (int m = 0; m < Mp; ++m) s += G[(size_t)m * out_p + j];
+  db[j] = s;
+}
+
+// Adam on FP32 master parameters; c1 = lr / (1 - b1^t), c2 = 1 / (1 - b2^t).
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, int n, float b1, float b2, float eps, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= c1 * mi / (sqrtf(vi * c2) + eps);
+}
+
+// FP32 master W [out][in] -> bf16 padded copies Wb [out_p][in_p] and
+// WbT [in_p][out_p].
+__global__ void weights_bf16_kernel(const float* __restrict__ W, int n_out, int n_in, int out_p, int in_p,
+                                    __nv_bfloat16* __restrict__ Wb, __nv_bfloat16* __restrict__ WbT) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= out_p * in_p) return;
+  const int o = idx / in_p, i = idx % in_p;
+  const float v = (o < n_out && i < n_in) ? W[(size_t)o * n_in + i] : 0.f;
+  const __nv_bfloat16 b = __float2bfloat16(v);
+  Wb[idx] = b;
+  WbT[(size_t)i * out_p + o] = b;
+}
+
+// Counter-based standard normal: splitmix64 of (seed, counter), Box-Muller.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+__device__ __forceinline__ float normal01(unsigned long long seed, unsigned long long counter) {
+  const unsigned long long r = splitmix64(seed ^ splitmix64(counter));
+  const float u1 = (float)((r >> 40) + 1) * (1.0f / 16777216.0f);    // (0, 1]
+  const float u2 = (float)((r >> 16) & 0xFFFFFF) * (1.0f / 16777216.0f);  // [0, 1)
+  return sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
+}
+
+// Proposal inputs: row r = [descriptor (n_desc), noise (n_noise)].
+__global__ void propose_input_kernel(const float* __restrict__ desc, int n_desc, int n_noise, int rows,
+                                     unsigned long long seed, int Mp, int in_p, __nv_bfloat16* __restrict__ H,
+                                     __nv_bfloat16* __restrict__ HT) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Mp * in_p) return;
+  const int m = idx / in_p, k = idx % in_p;
+  float v = 0.f;
+  if (m < rows) {
+    if (k < n_desc) v = desc[k];
+    else if (k < n_desc + n_noise) v = normal01(seed, (unsigned long long)m * 64 + (k - n_desc));
+  }
+  const __nv_bfloat16 b = __float2bfloat16(v);
+  H[idx] = b;
+  HT[(size_t)k * Mp + m] = b;
+}
+
+// Network outputs -> rigid poses: centre of mass (x, y folded into the tile
+// starting at origin), normalised quaternion (identity if degenerate).
+__global__ void pose_kernel(const float* __restrict__ Y, int rows, float ox, float oy, float tile_x, float tile_y,
+                            float* __restrict__ pose) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  const float* o = Y + (size_t)r * kOut;
+  float x = o[0] - ox, y = o[1] - oy;
+  x -= tile_x * floorf(x / tile_x);
+  y -= tile_y * floorf(y / tile_y);
+  float nu = sqrtf(o[3] * o[3] + o[4] * o[4] + o[5] * o[5] + o[6] * o[6]);
+  float* p = pose + 7 * (size_t)r;
+  p[0] = x + ox;
+  p[1] = y + oy;
+  p[2] = o[2];
+  if (nu > 1e-12f) {
+    p[3] = o[3] / nu; p[4] = o[4] / nu; p[5] = o[5] / nu; p[6] = o[6] / nu;
+  } else {
+    p[3] = 1.f; p[4] = p[5] = p[6] = 0.f;
+  }
+}
+
+inline unsigned grid1(long long n, int b = 256) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+struct gridff_mlp {
+  gridff_ctx* ctx = nullptr;
+  int device = 0;
+  int L = 0;                       // layers
+  std::vector<int> sizes, pads;    // widths and padded widths (L + 1)
+  std::vector<size_t> woff, boff;  // offsets of W_l, b_l in the flat parameter array
+  size_t n_params = 0;
+  float* P = nullptr;              // FP32 master parameters [n_params]
+  float* Gr = nullptr;             // gradients
+  float* Am = nullptr;             // Adam first moments
+  float* Av = nullptr;             // Adam second moments
+  std::vector<__nv_bfloat16*> Wb, WbT;
+  long long t = 0;                 // Adam step counter
+  // batch workspace
+  int cap = 0;                     // padded rows
+  std::vector<__nv_bfloat16*> H, HT;   // layer inputs (L)
+  std::vector<float*> Apre;             // pre-activations (L)
+  float* C = nullptr;              // GEMM output scratch [cap][max_pad]
+  float* G = nullptr;              // gradient scratch [cap][max_pad]
+  float* G2 = nullptr;
+  __nv_bfloat16* Gb = nullptr;
+  __nv_bfloat16* GbT = nullptr;
+  float* Y = nullptr;              // outputs [cap][kOut]
+  float* Xs = nullptr;             // staged host inputs [cap][n_in]
+  float* Ts = nullptr;             // staged targets
+  float* Ms = nullptr;             // staged torsion masks
+  float* loss = nullptr;           // [cap]
+  int* winner = nullptr;           // [cap]
+  float* desc = nullptr;           // [n_in]
+  std::vector<void*> owned;
+};
+
+namespace {
+
+template <class T>
+cudaError_t dalloc(gridff_mlp* m, T** p, size_t n) {
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e == cudaSuccess) m->owned.push_back(*p);
+  return e;
+}
+
+gridff_status ensure_batch(gridff_mlp* m, int rows) {
+  const int Mp = pad16(rows);
+  if (Mp <= m->cap) return GRIDFF_OK;
+  gridff_ctx* ctx = m->ctx;
+  // release the old workspace (parameters stay)
+  std::vector<void*> keep;
+  auto is_ws = [&](void* p) {
+    for (auto* h : m->H) if (p == h) return true;
+    for (auto* h : m->HT) if (p == h) return true;
+    for (auto* a : m->Apre) if (p == a) return true;
+    return p == m->C || p == m->G || p == m->G2 || p == m->Gb || p == m->GbT || p == m->Y || p == m->Xs ||
+           p == m->Ts || p == m->Ms || p == m->loss || p == m->winner;
+  };
+  cudaStreamSynchronize(ctx->stream);
+  for (void* p : m->owned) {
+    if (is_ws(p)) cudaFree(p);
+    else keep.push_back(p);
+  }
+  m->owned = keep;
+  int maxp = *std::max_element(m->pads.begin(), m->pads.end());
+  m->H.assign(m->L, nullptr);
+  m->HT.assign(m->L, nullptr);
+  m->Apre.assign(m->L, nullptr);
+  bool ok = true;
+  for (int l = 0; l < m->L; ++l) {
+    ok &= dalloc(m, &m->H[l], (size_t)Mp * m->pads[l]) == cudaSuccess;
+    ok &= dalloc(m, &m->HT[l], (size_t)Mp * m->pads[l]) == cudaSuccess;
+    ok &= dalloc(m, &m->Apre[l], (size_t)Mp * m->pads[l + 1]) == cudaSuccess;
+  }
+  // C also holds a weight gradient [out_p][in_p], which can exceed Mp rows
+  ok &= dalloc(m, &m->C, (size_t)std::max(Mp, maxp) * maxp) == cudaSuccess;
+  ok &= dalloc(m, &m->G, (size_t)Mp * maxp) == cudaSuccess;
+  ok &= dalloc(m, &m->G2, (size_t)Mp * maxp) == cudaSuccess;
+  ok &= dalloc(m, &m->Gb, (size_t)Mp * maxp) == cudaSuccess;
+  ok &= dalloc(m, &m->GbT, (size_t)Mp * maxp) == cudaSuccess;
+  ok &= dalloc(m, &m->Y, (size_t)Mp * kOut) == cudaSuccess;
+  ok &= dalloc(m, &m->Xs, (size_t)Mp * m->sizes[0]) == cudaSuccess;
+  ok &= dalloc(m, &m->Ts, (size_t)Mp * kOut) == cudaSuccess;
+  ok &= dalloc(m, &m->Ms, (size_t)Mp * kTors) == cudaSuccess;
+  ok &= dalloc(m, &m->loss, (size_t)Mp) == cudaSuccess;
+  ok &= dalloc(m, &m->winner, (size_t)Mp) == cudaSuccess;
+  if (!ok) return set_err(ctx, GRIDFF_ENOMEM, "MLP workspace for %d rows", rows);
+  m->cap = Mp;
+  return GRIDFF_OK;
+}
+
+void gemm(cudaStream_t s, const __nv_bfloat16* A, int lda, const __nv_bfloat16* Bt, int ldb, float* C, int ldc,
+          int M, int N, int K) {
+  const long long warps = (long long)(M / 16) * (N / 8);
+  gemm_bf16_kernel<<<grid1(warps * 32, 128), 128, 0, s>>>(A, lda, Bt, ldb, C, ldc, M, N, K, 0);
+}
+
+void refresh_bf16(gridff_mlp* m) {
+  for (int l = 0; l < m->L; ++l) {
+    const int in = m->sizes[l], out = m->sizes[l + 1], ip = m->pads[l], op = m->pads[l + 1];
+    weights_bf16_kernel<<<grid1((long long)op * ip), 256, 0, m->ctx->stream>>>(m->P + m->woff[l], out, in, op,
+                                                                                ip, m->Wb[l], m->WbT[l]);
+  }
+}
+
+// Forward of `rows` rows whose layer-0 input is already in H[0]/HT[0].
+void forward_rows(gridff_mlp* m, int rows) {
+  cudaStream_t s = m->ctx->stream;
+  const int Mp = pad16(rows);
+  for (int l = 0; l < m->L; ++l) {
+    const int ip = m->pads[l], op = m->pads[l + 1];
+    gemm(s, m->H[l], ip, m->Wb[l], ip, m->C, op, Mp, op, ip);
+    const bool last = l == m->L - 1;
+    bias_act_kernel<<<grid1((long long)Mp * op), 256, 0, s>>>(
+        m->C, m->P + m->boff[l], rows, m->sizes[l + 1], Mp, op, m->Apre[l], last ? nullptr : m->H[l + 1],
+        last ? nullptr : m->HT[l + 1], m->Y);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+gridff_status gridff_mlp_create(gridff_ctx* ctx, int32_t n_layers, const int32_t* sizes, gridff_mlp** out) {
+  if (!ctx || !sizes || !out || n_layers < 1 || n_layers > 16) return set_err(ctx, GRIDFF_EINVAL, "bad MLP shape");
+  *out = nullptr;
+  if (sizes[n_layers] != kOut) return set_err(ctx, GRIDFF_EINVAL, "the output width must be %d", kOut);
+  for (int l = 0; l <= n_layers; ++l)
+    if (sizes[l] < 1 || sizes[l] > 4096) return set_err(ctx, GRIDFF_EINVAL, "layer width %d", sizes[l]);
+  GRIDFF_CUDA(ctx, cudaSetDevice(ctx->device));
+  gridff_mlp* m = new gridff_mlp();
+  m->ctx = ctx;
+  m->device = ctx->device;
+  m->L = n_layers;
+  for (int l = 0; l <= n_layers; ++l) {
+    m->sizes.push_back(sizes[l]);
+    m->pads.push_back(pad16(sizes[l]));
+  }
+  size_t off = 0;
+  for (int l = 0; l < n_layers; ++l) {
+    m->woff.push_back(off);
+    off += (size_t)sizes[l] * sizes[l + 1];
+    m->boff.push_back(off);
+    off += sizes[l + 1];
+  }
+  m->n_params = off;
+  bool ok = dalloc(m, &m->P, off) == cudaSuccess && dalloc(m, &m->Gr, off) == cudaSuccess &&
+            dalloc(m, &m->Am, off) == cudaSuccess && dalloc(m, &m->Av, off) == cudaSuccess &&
+            dalloc(m, &m->desc, (size_t)sizes[0]) == cudaSuccess;
+  m->Wb.assign(n_layers, nullptr);
+  m->WbT.assign(n_layers, nullptr);
+  for (int l = 0; l < n_layers && ok; ++l) {
+    ok &= dalloc(m, &m->Wb[l], (size_t)m->pads[l] * m->pads[l + 1]) == cudaSuccess;
+    ok &= dalloc(m, &m->WbT[l], (size_t)m->pads[l] * m->pads[l + 1]) == cudaSuccess;
+  }
+  if (!ok) {
+    gridff_mlp_destroy(m);
+    return set_err(ctx, GRIDFF_ENOMEM, "MLP parameters");
+  }
+  cudaMemsetAsync(m->P, 0, off * sizeof(float), ctx->stream);
+  cudaMemsetAsync(m->Am, 0, off * sizeof(float), ctx->stream);
+  cudaMemsetAsync(m->Av, 0, off * sizeof(float), ctx->stream);
+  refresh_bf16(m);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    gridff_mlp_destroy(m);
+    return set_err(ctx, GRIDFF_ECUDA, "MLP init");
+  }
+  *out = m;
+  return GRIDFF_OK;
+}
+
+void gridff_mlp_destroy(gridff_mlp* m) {
+  if (!m) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(m->device);
+  for (void* p : m->owned) cudaFree(p);
+  cudaSetDevice(prev);
+  cudaGetLastError();
+  delete m;
+}
+
+int64_t gridff_mlp_num_params(const gridff_mlp* m) { return m ? (int64_t)m->n_params : 0; }
+
+gridff_status gridff_mlp_set_params(gridff_mlp* m, const float* params) {
+  if (!m || !params) return GRIDFF_EINVAL;
+  gridff_ctx* ctx = m->ctx;
+  GRIDFF_CUDA(ctx, cudaSetDevice(ctx->device));
+  GRIDFF_CUDA(ctx, cudaMemcpyAsync(m->P, params, m->n_params * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  GRIDFF_CUDA(ctx, cudaMemsetAsync(m->Am, 0, m->n_params * sizeof(float), ctx->stream));
+  GRIDFF_CUDA(ctx, cudaMemsetAsync(m->Av, 0, m->n_params * sizeof(float), ctx->stream));
+  m->t = 0;
+  refresh_bf16(m);
+  GRIDFF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return GRIDFF_OK;
+}
+
+gridff_status gridff_mlp_get_params(gridff_mlp* m, float* params, float* grads) {
+  if (!m) return GRIDFF_EINVAL;
+  gridff_ctx* ctx = m->ctx;
+  GRIDFF_CUDA(ctx, cudaSetDevice(ctx->device));
+  if (params)
+    GRIDFF_CUDA(ctx, cudaMemcpyAsync(params, m->P, m->n_params * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+  if (grads)
+    GRIDFF_CUDA(ctx, cudaMemcpyAsync(grads, m->Gr, m->n_params * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+  GRIDFF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return GRIDFF_OK;
+}
+
+gridff_status gridff_mlp_forward(gridff_mlp* m, int32_t rows, const float* x, float* y) {
+  if (!m || !x || !y || rows < 1) return set_err(m ? m->ctx : nullptr, GRIDFF_EINVAL, "bad argument");
+  gridff_ctx* ctx = m->ctx;
+  GRIDFF_CUDA(ctx, cudaSetDevice(ctx->device));
+  gridff_status st = ensure_batch(m, rows);
+  if (st != GRIDFF_OK) return st;
+  cudaStream_t s = ctx->stream;
+  const int Mp = pad16(rows), n_in = m->sizes[0];
+  GRIDFF_CUDA(ctx, cudaMemcpyAsync(m->Xs, x, (size_t)rows * n_in * sizeof(float), cudaMemcpyHostToDevice, s));
+  input_kernel<<<grid1((long long)Mp * m->pads[0]), 256, 0, s>>>(m->Xs, rows, n_in, Mp, m->pads[0], m->H[0],
+                                                                  m->HT[0]);
+  forward_rows(m, rows);
+  GRIDFF_CUDA(ctx, cudaGetLastError());
+  GRIDFF_CUDA(ctx, cudaMemcpyAsync(y, m->Y, (size_t)rows * kOut * sizeof(float), cudaMemcpyDeviceToHost, s));
+  GRIDFF_CUDA(ctx, cudaStreamSynchronize(s));
+  return GRIDFF_OK;
+}
+
+gridff_status gridff_mlp_train_step(gridff_mlp* m, int32_t n_targets, int32_t K, const float* x,
+                                    const float* targets, const float* tors_mask,
+                                    const gridff_train_params* tp, float* loss_out, int flags) {
+  if (!m || !x || !targets || !tp || n_targets < 1 || K < 1)
+    return set_err(m ? m->ctx : nullptr, GRIDFF_EINVAL, "bad argument");
+  gridff_ctx* ctx = m->ctx;
+  GRIDFF_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int rows = n_targets * K;
+  gridff_status st = ensure_batch(m, std::max(rows, n_targets));
+  if (st != GRIDFF_OK) return st;
+  cudaStream_t s = ctx->stream;
+  const int Mp = pad16(rows), n_in = m->sizes[0], L = m->L;
+  GRIDFF_CUDA(ctx, cudaMemcpyAsync(m->Xs, x, (size_t)rows * n_in * sizeof(float), cudaMemcpyHostToDevice, s));
+  GRIDFF_CUDA(ctx, cudaMemcpyAsync(m->Ts, targets, (size_t)n_targets * kOut * sizeof(float), cudaMemcpyHostToDevice, s));
+  if (tors_mask)
+    GRIDFF_CUDA(ctx, cudaMemcpyAsync(m->Ms, tors_mask, (size_t)n_targets * kTors * sizeof(float),
+                                     cudaMemcpyHostToDevice, s));
+  input_kernel<<<grid1((long long)Mp * m->pads[0]), 256, 0, s>>>(m->Xs, rows, n_in, Mp, m->pads[0], m->H[0], m->HT[0]);
+  forward_rows(m, rows);
+  // loss and dL/dY (written into G with the last layer's padded stride)
+  const int op_last = m->pads[L];
+  GRIDFF_CUDA(ctx, cudaMemsetAsync(m->G, 0, (size_t)Mp * op_last * sizeof(float), s));
+  wta_kernel<<<grid1(n_targets, 128), 128, 0, s>>>(m->Y, m->Ts, tors_mask ? m->Ms : nullptr, n_targets, K, op_last,
+                                                  tp->w_q, tp->w_t, (float)tp->tile[0], (float)tp->tile[1], m->G,
+                                                  m->loss, m->winner);
+  // backward
+  float* Gcur = m->G;
+  float* Gnext = m->G2;
+  for (int l = L - 1; l >= 0; --l) {
+    const int ip = m->pads[l], op = m->pads[l + 1];
+    grad_prep_kernel<<<grid1((long long)Mp * op), 256, 0, s>>>(Gcur, l == L - 1 ? nullptr : m->Apre[l], rows,
+                                                               m->sizes[l + 1], Mp, op, m->Gb, m->GbT);
+    colsum_kernel<<<grid1(m->sizes[l + 1], 128), 128, 0, s>>>(Gcur, Mp, op, m->sizes[l + 1], m->Gr + m->boff[l]);
+    // dW [out][in] = G^T X: A = GbT [op][Mp], Bt = HT [ip][Mp]
+    gemm(s, m->GbT, Mp, m->HT[l], Mp, m->C, ip, op, ip, Mp);
+    // copy the live block of C into the flat gradient array
+    GRIDFF_CUDA(ctx, cudaMemcpy2DAsync(m->Gr + m->woff[l], m->sizes[l] * sizeof(float), m->C, ip * sizeof(float),
+                                       m->sizes[l] * sizeof(float), m->sizes[l + 1], cudaMemcpyDeviceToDevice, s));
+    if (l > 0) {
+      // dL/d(input) = G W: A = Gb [Mp][op], Bt = WbT [ip][op]
+      gemm(s, m->Gb, op, m->WbT[l], op, Gnext, ip, Mp, ip, op);
+      std::swap(Gcur, Gnext);
+    }
+  }
+  GRIDFF_CUDA(ctx, cudaGetLastError());
+  if (!(flags & GRIDFF_MLP_NO_UPDATE)) {
+    m->t += 1;
+    const double b1 = tp->beta1, b2 = tp->beta2;
+    const float c1 = (float)(tp->lr / (1.0 - pow(b1, (double)m->t)));
+    const float c2 = (float)(1.0 / (1.0 - pow(b2, (double)m->t)));
+    adam_kernel<<<grid1((long long)m->n_params), 256, 0, s>>>(m->P, m->Gr, m->Am, m->Av, (int)m->n_params,
+                                                              tp->beta1, tp->beta2, tp->eps, c1, c2);
+    refresh_bf16(m);
+  }
+  if (loss_out) {
+    std::vector<float> l(n_targets);
+    GRIDFF_CUDA(ctx, cudaMemcpyAsync(l.data(), m->loss, n_targets * sizeof(float), cudaMemcpyDeviceToHost, s));
+    GRIDFF_CUDA(ctx, cudaStreamSynchronize(s));
+    double sum = 0;
+    for (float v : l) sum += v;
+    *loss_out = (float)(sum / n_targets);
+  } else {
+    GRIDFF_CUDA(ctx, cudaStreamSynchronize(s));
+  }
+  GRIDFF_CUDA(ctx, cudaGetLastError());
+  return GRIDFF_OK;
+}
+
+gridff_status gridff_mlp_propose(gridff_mlp* m, gridff_replicas* R, const float* descriptor, int32_t n_desc,
+                                 uint64_t seed, const double origin_xy[2], const double tile_xy[2]) {
+  if (!m || !R || !descriptor || !origin_xy || !tile_xy) return set_err(m ? m->ctx : nullptr, GRIDFF_EINVAL, "null argument");
+  gridff_ctx* ctx = m->ctx;
+  if (!R->rigid) return set_err(ctx, GRIDFF_ENOTSUP, "proposals are written for rigid replicas");
+  if (n_desc < 0 || n_desc > m->sizes[0]) return set_err(ctx, GRIDFF_EINVAL, "descriptor longer than the input");
+  if (m->sizes[0] - n_desc > 64) return set_err(ctx, GRIDFF_EINVAL, "at most 64 noise inputs per row");
+  GRIDFF_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int rows = R->n_rep;
+  gridff_status st = ensure_batch(m, rows);
+  if (st != GRIDFF_OK) return st;
+  cudaStream_t s = ctx->stream;
+  const int Mp = pad16(rows);
+  GRIDFF_CUDA(ctx, cudaMemcpyAsync(m->desc, descriptor, n_desc * sizeof(float), cudaMemcpyHostToDevice, s));
+  propose_input_kernel<<<grid1((long long)Mp * m->pads[0]), 256, 0, s>>>(m->desc, n_desc, m->sizes[0] - n_desc, rows,
+                                                                         (unsigned long long)seed, Mp, m->pads[0],
+                                                                         m->H[0], m->HT[0]);
+  forward_rows(m, rows);
+  pose_kernel<<<grid1(rows, 128), 128, 0, s>>>(m->Y, rows, (float)origin_xy[0], (float)origin_xy[1],
+                                               (float)tile_xy[0], (float)tile_xy[1], R->x);
+  GRIDFF_CUDA(ctx, cudaMemsetAsync(R->v, 0, 6 * (size_t)rows * sizeof(float), s));
+  GRIDFF_CUDA(ctx, cudaGetLastError());
+  GRIDFF_CUDA(ctx, cudaStreamSynchronize(s));
+  return GRIDFF_OK;
+}
+
+// Descriptor of a molecule template (host computation, 64 floats): atom
+// count, composition by mass class, charge moments, principal moments of
+// inertia, size and the number of torsion terms; zero padding.
+gridff_status gridff_molecule_descriptor(const gridff_molecule* mol, float* out) {
+  if (!mol || !out || mol->n_atoms < 1 || !mol->xyz || !mol->mass || !mol->q) return GRIDFF_EINVAL;
+  const int n = mol->n_atoms;
+  for (int i = 0; i < 64; ++i) out[i] = 0.f;
+  double M = 0, c[3] = {0, 0, 0};
+  for (int i = 0; i < n; ++i) {
+    M += mol->mass[i];
+    for (int a = 0; a < 3; ++a) c[a] += mol->mass[i] * mol->xyz[3 * i + a];
+  }
+  for (int a = 0; a < 3; ++a) c[a] /= M;
+  int cls[5] = {0, 0, 0, 0, 0};   // <4 amu, 10-13, 13-15, 15-17, other
+  double Q = 0, dip[3] = {0, 0, 0}, I[3][3] = {{0}}, rg = 0, rmax = 0;
+  for (int i = 0; i < n; ++i) {
+    const double m = mol->mass[i];
+    cls[m < 4 ? 0 : m < 13 ? 1 : m < 15 ? 2 : m < 17 ? 3 : 4]++;
+    double r[3] = {mol->xyz[3 * i] - c[0], mol->xyz[3 * i + 1] - c[1], mol->xyz[3 * i + 2] - c[2]};
+    const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+    Q += mol->q[i];
+    for (int a = 0; a < 3; ++a) dip[a] += mol->q[i] * r[a];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) I[a][b] += m * ((a == b ? r2 : 0.0) - r[a] * r[b]);
+    rg += m * r2;
+    rmax = std::max(rmax, sqrt(r2));
+  }
+  // eigenvalues of the symmetric 3x3 inertia tensor (trigonometric method)
+  double p1 = I[0][1] * I[0][1] + I[0][2] * I[0][2] + I[1][2] * I[1][2];
+  double ev[3];
+  double tr = I[0][0] + I[1][1] + I[2][2];
+  if (p1 < 1e-18) {
+    ev[0] = I[0][0]; ev[1] = I[1][1]; ev[2] = I[2][2];
+  } else {
+    double qm = tr / 3;
+    double p2 = (I[0][0] - qm) * (I[0][0] - qm) + (I[1][1] - qm) * (I[1][1] - qm) + (I[2][2] - qm) * (I[2][2] - qm) + 2 * p1;
+    double p = sqrt(p2 / 6);
+    double Bm[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) Bm[a][b] = (I[a][b] - (a == b ? qm : 0.0)) / p;
+    double detB = Bm[0][0] * (Bm[1][1] * Bm[2][2] - Bm[1][2] * Bm[2][1]) -
+                  Bm[0][1] * (Bm[1][0] * Bm[2][2] - Bm[1][2] * Bm[2][0]) +
+                  Bm[0][2] * (Bm[1][0] * Bm[2][1] - Bm[1][1] * Bm[2][0]);
+    double r = std::min(1.0, std::max(-1.0, detB / 2));
+    double phi = acos(r) / 3;
+    ev[0] = qm + 2 * p * cos(phi);
+    ev[2] = qm + 2 * p * cos(phi + 2.0943951023931953);
+    ev[1] = 3 * qm - ev[0] - ev[2];
+  }
+  std::sort(ev, ev + 3);
+  int k = 0;
+  out[k++] = n / 128.f;
+  for (int j = 0; j < 5; ++j) out[k++] = (float)cls[j] / n;
+  out[k++] = (float)Q;
+  out[k++] = (float)sqrt(dip[0] * dip[0] + dip[1] * dip[1] + dip[2] * dip[2]) / 10.f;
+  for (int j = 0; j < 3; ++j) out[k++] = (float)sqrt(ev[j] / M) / 5.f;
+  out[k++] = (float)sqrt(rg / M) / 5.f;
+  out[k++] = (float)rmax / 10.f;
+  out[k++] = mol->n_torsions / 12.f;
+  return GRIDFF_OK;
+}
+
+}  // extern "C"

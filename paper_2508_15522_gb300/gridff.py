@@ -72,6 +72,11 @@ class MDParams(C.Structure):
     _fields_ = [("dt", C.c_float), ("record_every", C.c_int32), ("clock_budget_s", C.c_double)]
 
 
+class TrainParams(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("w_q", C.c_float), ("w_t", C.c_float), ("tile", C.c_double * 2)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with "
@@ -108,6 +113,16 @@ def _load():
         "gridff_run": (I32, [P, P, P, I32, C.POINTER(MDParams), C.c_int, P]),
         "gridff_probe_read_bandwidth": (I32, [P, P, C.c_size_t, I32, C.POINTER(C.c_double)]),
         "gridff_last_kernel_ms": (F64, [P]),
+        "gridff_mlp_create": (I32, [P, I32, C.POINTER(C.c_int32), C.POINTER(P)]),
+        "gridff_mlp_destroy": (None, [P]),
+        "gridff_mlp_num_params": (C.c_int64, [P]),
+        "gridff_mlp_set_params": (I32, [P, P]),
+        "gridff_mlp_get_params": (I32, [P, P, P]),
+        "gridff_mlp_forward": (I32, [P, I32, P, P]),
+        "gridff_mlp_train_step": (I32, [P, I32, I32, P, P, P, C.POINTER(TrainParams), C.POINTER(C.c_float),
+                                        C.c_int]),
+        "gridff_mlp_propose": (I32, [P, P, P, I32, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "gridff_molecule_descriptor": (I32, [C.POINTER(Molecule), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -125,6 +140,9 @@ EXPORTED = (
     "gridff_replicas_destroy", "gridff_replicas_info", "gridff_set_state", "gridff_get_state",
     "gridff_get_positions", "gridff_get_fire_state", "gridff_eval", "gridff_fire_params_default",
     "gridff_relax", "gridff_run", "gridff_probe_read_bandwidth", "gridff_last_kernel_ms",
+    "gridff_mlp_create", "gridff_mlp_destroy", "gridff_mlp_num_params", "gridff_mlp_set_params",
+    "gridff_mlp_get_params", "gridff_mlp_forward", "gridff_mlp_train_step", "gridff_mlp_propose",
+    "gridff_molecule_descriptor",
 )
 
 
@@ -399,3 +417,101 @@ def run(ctx: Context, grid, reps: Replicas, nsteps: int, dt: float, record_every
     if check and st != OK:
         ctx.check(st)
     return st, trace
+
+
+MLP_OUT = 19
+MLP_NO_UPDATE = 1
+
+
+def train_params(lr=1e-3, tile=(1.0, 1.0), **kw) -> TrainParams:
+    """gridff_train_params with the library defaults (Adam 0.9/0.999/1e-8,
+    w_q = 1, w_t = 0.25) and the given learning rate and tile."""
+    p = TrainParams(lr, 0.9, 0.999, 1e-8, 1.0, 0.25, (C.c_double * 2)(*tile))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def molecule_descriptor(mol) -> np.ndarray:
+    """64-float descriptor of a molecule template (gridff_molecule_descriptor)."""
+    keep = []
+    m = _mol_struct(mol, keep)
+    out = np.zeros(64, np.float32)
+    st = lib.gridff_molecule_descriptor(C.byref(m), out.ctypes.data_as(C.c_void_p))
+    if st != 0:
+        raise GridffError(st, "gridff_molecule_descriptor: bad molecule")
+    return out
+
+
+class MLP:
+    """gridff_mlp: the pose-proposal network (FP32 master parameters,
+    bfloat16 tensor-core GEMMs)."""
+
+    def __init__(self, ctx: Context, sizes):
+        sz = np.ascontiguousarray(sizes, np.int32)
+        h = C.c_void_p()
+        ctx.check(lib.gridff_mlp_create(ctx.h, len(sz) - 1, sz.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(h)))
+        self.ctx, self.h, self.sizes = ctx, h, tuple(int(s) for s in sz)
+        self.n_params = int(lib.gridff_mlp_num_params(h))
+
+    @staticmethod
+    def flatten(Ws, bs) -> np.ndarray:
+        return np.concatenate([np.concatenate([np.ravel(W), np.ravel(b)]) for W, b in zip(Ws, bs)]).astype(np.float32)
+
+    def unflatten(self, flat):
+        Ws, bs, o = [], [], 0
+        for i, j in zip(self.sizes[:-1], self.sizes[1:]):
+            Ws.append(flat[o:o + i * j].reshape(j, i)); o += i * j
+            bs.append(flat[o:o + j]); o += j
+        return Ws, bs
+
+    def set_params(self, Ws, bs):
+        flat = self.flatten(Ws, bs)
+        if flat.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters, got {flat.size}")
+        self.ctx.check(lib.gridff_mlp_set_params(self.h, flat.ctypes.data_as(C.c_void_p)))
+
+    def get_params(self):
+        p = np.empty(self.n_params, np.float32); g = np.empty(self.n_params, np.float32)
+        self.ctx.check(lib.gridff_mlp_get_params(self.h, p.ctypes.data_as(C.c_void_p), g.ctypes.data_as(C.c_void_p)))
+        return p, g
+
+    def forward(self, x):
+        x = np.ascontiguousarray(x, np.float32)
+        if x.ndim != 2 or x.shape[1] != self.sizes[0]:
+            raise ValueError(f"x must be (rows, {self.sizes[0]})")
+        y = np.empty((x.shape[0], MLP_OUT), np.float32)
+        self.ctx.check(lib.gridff_mlp_forward(self.h, x.shape[0], x.ctypes.data_as(C.c_void_p),
+                                              y.ctypes.data_as(C.c_void_p)))
+        return y
+
+    def train_step(self, x, targets, K, params: TrainParams, tors_mask=None, update=True):
+        x = np.ascontiguousarray(x, np.float32)
+        t = np.ascontiguousarray(targets, np.float32)
+        B = t.shape[0]
+        if x.shape != (B * K, self.sizes[0]) or t.shape != (B, MLP_OUT):
+            raise ValueError("x must be (n_targets*K, n_in) and targets (n_targets, 19)")
+        m = None if tors_mask is None else np.ascontiguousarray(tors_mask, np.float32)
+        loss = C.c_float()
+        self.ctx.check(lib.gridff_mlp_train_step(
+            self.h, B, K, x.ctypes.data_as(C.c_void_p), t.ctypes.data_as(C.c_void_p),
+            None if m is None else m.ctypes.data_as(C.c_void_p), C.byref(params), C.byref(loss),
+            0 if update else MLP_NO_UPDATE))
+        return loss.value
+
+    def propose(self, reps: Replicas, descriptor, seed, origin_xy, tile_xy):
+        d = np.ascontiguousarray(descriptor, np.float32)
+        o = (C.c_double * 2)(*origin_xy); t = (C.c_double * 2)(*tile_xy)
+        self.ctx.check(lib.gridff_mlp_propose(self.h, reps.h, d.ctypes.data_as(C.c_void_p), d.size,
+                                              C.c_uint64(seed), o, t))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.gridff_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

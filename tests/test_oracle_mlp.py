@@ -85,3 +85,18 @@ def test_wta_gradient_only_on_the_winner():
     assert win.tolist() == [1, 0]
     assert np.count_nonzero(np.abs(g).sum(1)) == 2
     assert L == pytest.approx((0.01 + 0.04) / 2)
+
+
+def test_splitmix64_published_sequence():
+    # SplitMix64 seeded with 0 (state advances by the golden gamma each call)
+    # starts 0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F.
+    gamma = 0x9E3779B97F4A7C15
+    outs = [mlp.splitmix64((k * gamma) & ((1 << 64) - 1)) for k in range(3)]
+    assert outs == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_counter_normal_moments():
+    z = mlp.counter_normal(12345, 200, 16).ravel()
+    assert abs(z.mean()) < 4 / np.sqrt(z.size)
+    assert abs(z.var() - 1) < 6 * np.sqrt(2 / z.size)
+    assert abs(np.mean(z ** 4) - 3) < 0.3
