@@ -322,6 +322,33 @@ gridff_status gridff_run(gridff_ctx* ctx, const gridff_grid* grid, gridff_replic
                          int32_t nsteps, const gridff_md_params* params, int flags,
                          double* energy_trace);
 
+/* --------------------------------------------------------------- sampling */
+
+/* Random starting poses of a rigid replica set (Sec. 7: molecules start
+ * from random placements over the surface).  Replica r draws six uniforms
+ * u_j = (splitmix64(seed XOR splitmix64(64 r + j)) >> 40) / 2^24, j = 0..5
+ * (the generator of gridff_mlp_propose): orientation by Shoemake's method,
+ *   a = sqrt(1 - u0), b = sqrt(u0),
+ *   q = (w, x, y, z) = (b cos 2pi u2, a sin 2pi u1, a cos 2pi u1, b sin 2pi u2),
+ * centre of mass (origin_x + u3 Lx, origin_y + u4 Ly, z_lo + u5 (z_hi - z_lo)),
+ * then raised, if needed, until the lowest atom is at z_floor.  Velocities
+ * are zeroed.  Errors: EINVAL, ENOTSUP (flexible replicas), ECUDA. */
+gridff_status gridff_random_poses(gridff_replicas* reps, uint64_t seed, const double origin_xy[2],
+                                  const double tile_xy[2], double z_lo, double z_hi,
+                                  double z_floor);
+
+/* RMSD uniqueness filter of relaxed rigid poses (Sec. 7).  poses [n][7]
+ * (centre of mass, quaternion; normalised here) are poses of template
+ * `tmpl` of reps, ordered by the caller (e.g. by energy).  RMSD between
+ * two poses = sqrt(mean over atoms |r_i - r'_i|^2), the centres compared
+ * by the minimum image on the tile in x and y.  dup_of[i] receives the
+ * smallest j < i whose RMSD to pose i is below `threshold`, else -1; a
+ * pose with dup_of = -1 is a new structure.  Host arrays unless
+ * GRIDFF_DEVICE_PTRS.  Errors: EINVAL, ECUDA. */
+gridff_status gridff_rmsd_unique(gridff_replicas* reps, int32_t tmpl, int32_t n, const float* poses,
+                                 const double tile_xy[2], double threshold, int32_t* dup_of,
+                                 int flags);
+
 /* --------------------------------------------------------- pose proposal */
 
 /* Learned proposal of starting poses for relaxations.  The paper has no

@@ -335,18 +335,6 @@ __device__ void intra_quad(const TemplateView& tv, int ab, int n, int i, int q, 
   E += e + 0.5f * enb;
 }
 
-__device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float R[9]) {
-  R[0] = w * w + x * x - y * y - z * z;
-  R[1] = 2.f * (x * y - w * z);
-  R[2] = 2.f * (x * z + w * y);
-  R[3] = 2.f * (x * y + w * z);
-  R[4] = w * w - x * x + y * y - z * z;
-  R[5] = 2.f * (y * z - w * x);
-  R[6] = 2.f * (x * z - w * y);
-  R[7] = 2.f * (y * z + w * x);
-  R[8] = w * w - x * x - y * y + z * z;
-}
-
 // q <- q (x) (cos(a/2), sin(a/2) u), normalised.
 __device__ __forceinline__ void quat_advance(float q[4], float ux, float uy, float uz, float ang) {
   float s, c;

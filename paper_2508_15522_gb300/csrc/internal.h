@@ -14,6 +14,21 @@
 #define GRIDFF_KE 14.399645f          // eV*A/e^2
 #define GRIDFF_ACC 9.648533e-3f       // A/fs^2 per eV/(A*amu)
 
+#ifdef __CUDACC__
+// Rotation matrix (row-major) of a unit quaternion (w, x, y, z).
+__device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float R[9]) {
+  R[0] = w * w + x * x - y * y - z * z;
+  R[1] = 2.f * (x * y - w * z);
+  R[2] = 2.f * (x * z + w * y);
+  R[3] = 2.f * (x * y + w * z);
+  R[4] = w * w - x * x + y * y - z * z;
+  R[5] = 2.f * (y * z - w * x);
+  R[6] = 2.f * (x * z - w * y);
+  R[7] = 2.f * (y * z + w * x);
+  R[8] = w * w - x * x - y * y + z * z;
+}
+#endif
+
 struct gridff_ctx {
   int device = 0;
   int n_sm = 0;

@@ -35,18 +35,6 @@ gridff_status finish(gridff_ctx* ctx, int flags) {
   return GRIDFF_OK;
 }
 
-__device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float R[9]) {
-  R[0] = w * w + x * x - y * y - z * z;
-  R[1] = 2.f * (x * y - w * z);
-  R[2] = 2.f * (x * z + w * y);
-  R[3] = 2.f * (x * y + w * z);
-  R[4] = w * w - x * x + y * y - z * z;
-  R[5] = 2.f * (y * z - w * x);
-  R[6] = 2.f * (x * z - w * y);
-  R[7] = 2.f * (y * z + w * x);
-  R[8] = w * w - x * x - y * y + z * z;
-}
-
 // Lab-frame atom positions of rigid replicas: r_i = R(q) b_i + com.
 __global__ void rigid_positions_kernel(TemplateView tv, const int* rep_tmpl, const int* rep_off,
                                        const float* pose, int n_rep, float* out) {

@@ -123,6 +123,9 @@ def _load():
                                         C.c_int]),
         "gridff_mlp_propose": (I32, [P, P, P, I32, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "gridff_molecule_descriptor": (I32, [C.POINTER(Molecule), P]),
+        "gridff_random_poses": (I32, [P, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double), F64, F64,
+                                      F64]),
+        "gridff_rmsd_unique": (I32, [P, I32, I32, P, C.POINTER(C.c_double), F64, P, C.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -142,7 +145,7 @@ EXPORTED = (
     "gridff_relax", "gridff_run", "gridff_probe_read_bandwidth", "gridff_last_kernel_ms",
     "gridff_mlp_create", "gridff_mlp_destroy", "gridff_mlp_num_params", "gridff_mlp_set_params",
     "gridff_mlp_get_params", "gridff_mlp_forward", "gridff_mlp_train_step", "gridff_mlp_propose",
-    "gridff_molecule_descriptor",
+    "gridff_molecule_descriptor", "gridff_random_poses", "gridff_rmsd_unique",
 )
 
 
@@ -352,6 +355,21 @@ class Replicas:
         p = {k: v.ctypes.data_as(C.c_void_p) for k, v in out.items()}
         self.ctx.check(lib.gridff_get_fire_state(self.h, p["dt"], p["alpha"], p["nplus"], p["status"],
                                                  p["steps"], p["energy"], 0))
+        return out
+
+    def random_poses(self, seed, origin_xy, tile_xy, z_lo, z_hi, z_floor):
+        """Random rigid starting poses drawn on the device (gridff_random_poses)."""
+        o = (C.c_double * 2)(*origin_xy); t = (C.c_double * 2)(*tile_xy)
+        self.ctx.check(lib.gridff_random_poses(self.h, C.c_uint64(seed), o, t, float(z_lo), float(z_hi),
+                                               float(z_floor)))
+
+    def rmsd_unique(self, poses, tile_xy, threshold=0.1, tmpl=0):
+        """dup_of[i]: first earlier pose within `threshold` RMSD, else -1."""
+        p = np.ascontiguousarray(poses, np.float32).reshape(-1, 7)
+        out = np.empty(len(p), np.int32)
+        t = (C.c_double * 2)(*tile_xy)
+        self.ctx.check(lib.gridff_rmsd_unique(self.h, tmpl, len(p), p.ctypes.data_as(C.c_void_p), t,
+                                              float(threshold), out.ctypes.data_as(C.c_void_p), 0))
         return out
 
     def close(self):
