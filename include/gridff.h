@@ -307,6 +307,79 @@ gridff_status gridff_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_repl
                            int32_t nsteps, const gridff_fire_params* params, int flags,
                            gridff_relax_result* result);
 
+/* ------------------------------------------- launch configuration, tuning */
+
+/* How gridff_relax lays a relaxation out on the GPU.  The paper runs one
+ * work-group per replica (Sec. 7); these are the GB300 layouts this
+ * library offers for the same computation (every layout gives the same
+ * result up to FP32 summation order). */
+#define GRIDFF_KERNEL_RIGID_SUBWARP 0  /* rigid: lanes_per_replica lanes per replica, lane per atom,
+                                          every atom's stencil cached (cache_slots >= atoms) */
+#define GRIDFF_KERNEL_RIGID_QUAD 1     /* rigid: warp per replica, 4 lanes per atom */
+#define GRIDFF_KERNEL_FLEX_QUAD 2      /* flexible: warp per replica, 4 lanes per atom for the grid
+                                          and for that atom's intramolecular terms */
+#define GRIDFF_KERNEL_FLEX_TERMS 3     /* flexible: warp per replica, grid by 4 lanes per atom, then
+                                          each intramolecular term once (lane per term) with
+                                          shared-memory force scatter */
+
+typedef struct {
+  int32_t kernel;             /* GRIDFF_KERNEL_* */
+  int32_t lanes_per_replica;  /* RIGID_SUBWARP: 8, 16 or 32 */
+  int32_t warps_per_block;    /* SUBWARP, QUAD kernels: 4; FLEX_TERMS: 2, 4 or 8 */
+  int32_t cache_slots;        /* stencil staging: shared-memory stencil-cache slots per replica
+                                 (the first cache_slots atoms keep their 4x4x4 stencil between
+                                 steps); 0 = no staging, every gather from L2/HBM */
+  int32_t queue;              /* FLEX_TERMS: 1 = replicas handed out by an atomic work queue in
+                                 decreasing cost order (uneven sizes), 0 = static round robin */
+  int32_t l2_window;          /* 1 = the grid is put in an L2 persisting access-policy window
+                                 (reserves persisting L2 for the context until gridff_destroy) */
+} gridff_launch_config;
+
+/* Fix the launch configuration of relaxations of `reps` (NULL: back to the
+ * library's heuristic).  Errors: EINVAL when the configuration does not
+ * apply to the replica set (checked here and at launch). */
+gridff_status gridff_set_launch_config(gridff_replicas* reps, const gridff_launch_config* cfg);
+/* The configuration gridff_relax would use now (heuristic if none set);
+ * use_grid = 0 for relaxations with GRIDFF_NO_GRID. */
+gridff_status gridff_get_launch_config(const gridff_replicas* reps, int use_grid, gridff_launch_config* cfg);
+
+typedef struct {
+  gridff_launch_config cfg;
+  double atom_evals_per_s;    /* measured rate of the trial (0 = did not fit) */
+  double ms;                  /* kernel time of the trial */
+} gridff_tune_trial;
+
+/* Autotuner: times short relaxations (trial_steps FIRE iterations from the
+ * current state, FIRE scalars reset, force threshold as in params) of
+ * candidate configurations by coordinate descent over the kernel (and warps
+ * per block), the stencil staging (cache slots), the work queue and the L2
+ * window, picks the fastest in atom evaluations per second and makes it the
+ * replica set's configuration.  The state (positions, velocities, FIRE
+ * scalars, status, counters, energies) is restored afterwards.  Allocates
+ * scratch for one copy of the state.  trials (may be NULL) receives up to
+ * max_trials records; n_trials the number run.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+gridff_status gridff_tune(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* reps,
+                          const gridff_fire_params* params, int32_t trial_steps, int flags,
+                          gridff_launch_config* best, gridff_tune_trial* trials,
+                          int32_t max_trials, int32_t* n_trials);
+
+/* One relaxation captured in a CUDA graph: FIRE reset (unless
+ * GRIDFF_CONTINUE), result reset and the persistent relaxation kernel of
+ * the replica set's configuration at the time of capture, all on the
+ * context stream.  Each gridff_graph_launch replays it (one graph launch);
+ * the replica set, grid, nsteps and params are fixed at capture.
+ * Capture needs a context stream that is not the legacy default stream.
+ * Errors: EINVAL, ECUDA. */
+typedef struct gridff_graph gridff_graph;
+gridff_status gridff_relax_graph_create(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* reps,
+                                        int32_t nsteps, const gridff_fire_params* params, int flags,
+                                        gridff_graph** out);
+/* Replay.  result != NULL: wait for it and fill result (as gridff_relax,
+ * including EABORTED/ESTEPLIMIT); result == NULL: return after enqueueing. */
+gridff_status gridff_graph_launch(gridff_graph* graph, gridff_relax_result* result);
+void gridff_graph_destroy(gridff_graph* graph);
+
 typedef struct {
   float dt;               /* fs */
   int32_t record_every;   /* energy trace cadence in steps (0 = no trace) */

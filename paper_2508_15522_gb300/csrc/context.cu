@@ -58,6 +58,12 @@ void gridff_destroy(gridff_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->l2_limit_set) {
+    // give back the persisting-L2 set-aside taken by L2-window launches
+    cudaCtxResetPersistingL2Cache();
+    cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, ctx->l2_prev_limit);
+    cudaGetLastError();
+  }
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   if (ctx->result_dev) cudaFree(ctx->result_dev);

@@ -416,6 +416,148 @@ __device__ __forceinline__ Acc flex_forces(const GridView& g, bool use_grid, boo
   return e;
 }
 
+// Intramolecular forces of one flexible replica from its template's
+// unique-term lists: the lanes take terms round-robin, evaluate each term
+// once and scatter its forces to its atoms with shared-memory atomics
+// (adds into s_f).  Returns this lane's share of the energy.  Same terms as
+// intra_quad (reduced UFF-like form; nonbonded on pairs more than two bonds
+// apart), without the per-atom repetition.
+__device__ float intra_terms(const TemplateView& tv, int t, int lane, const float* s_x, float* s_f) {
+  float e = 0.f;
+  const float alpha = tv.alpha;
+  const int p1 = tv.pair_off[t + 1];
+  for (int p = tv.pair_off[t] + lane; p < p1; p += 32) {
+    const PairRec pr = tv.pairs[p];
+    const int i = pr.ij & 0xffff, j = pr.ij >> 16;
+    const float3 d = sub3(ld3(s_x, i), ld3(s_x, j));
+    const float r2 = dot3(d, d);
+    const float ir = rsqrtf(r2);
+    const float r = r2 * ir;
+    const float e1 = expf(-alpha * (r - pr.R));
+    const float em = pr.ee * e1 * (e1 - 2.f);
+    const float dEdr = 2.f * alpha * pr.ee * e1 * (1.f - e1) - pr.qq * ir * ir;
+    const float c = -dEdr * ir;
+    atomicAdd(&s_f[3 * i], c * d.x);
+    atomicAdd(&s_f[3 * i + 1], c * d.y);
+    atomicAdd(&s_f[3 * i + 2], c * d.z);
+    atomicAdd(&s_f[3 * j], -c * d.x);
+    atomicAdd(&s_f[3 * j + 1], -c * d.y);
+    atomicAdd(&s_f[3 * j + 2], -c * d.z);
+    e += em + pr.qq * ir;
+  }
+  for (int b = tv.ub_off[t] + lane; b < tv.ub_off[t + 1]; b += 32) {
+    const BondTerm B = tv.ub[b];
+    const float3 d = sub3(ld3(s_x, B.i), ld3(s_x, B.j));
+    const float r = sqrtf(dot3(d, d));
+    const float dr = r - B.r0;
+    const float c = r > 0.f ? -2.f * B.k * dr / r : 0.f;
+    atomicAdd(&s_f[3 * B.i], c * d.x);
+    atomicAdd(&s_f[3 * B.i + 1], c * d.y);
+    atomicAdd(&s_f[3 * B.i + 2], c * d.z);
+    atomicAdd(&s_f[3 * B.j], -c * d.x);
+    atomicAdd(&s_f[3 * B.j + 1], -c * d.y);
+    atomicAdd(&s_f[3 * B.j + 2], -c * d.z);
+    e += B.k * dr * dr;
+  }
+  for (int a = tv.ua_off[t] + lane; a < tv.ua_off[t + 1]; a += 32) {
+    const AngleRec A = tv.ua[a];
+    const float3 u = sub3(ld3(s_x, A.a), ld3(s_x, A.b)), w = sub3(ld3(s_x, A.c), ld3(s_x, A.b));
+    const float lu2 = dot3(u, u), lw2 = dot3(w, w);
+    const float inv = rsqrtf(lu2 * lw2);
+    const float c = dot3(u, w) * inv;
+    const float dEdc = 2.f * A.k * (c - A.cos0);
+    const float3 ga = make_float3(w.x * inv - c * u.x / lu2, w.y * inv - c * u.y / lu2, w.z * inv - c * u.z / lu2);
+    const float3 gc = make_float3(u.x * inv - c * w.x / lw2, u.y * inv - c * w.y / lw2, u.z * inv - c * w.z / lw2);
+    atomicAdd(&s_f[3 * A.a], -dEdc * ga.x);
+    atomicAdd(&s_f[3 * A.a + 1], -dEdc * ga.y);
+    atomicAdd(&s_f[3 * A.a + 2], -dEdc * ga.z);
+    atomicAdd(&s_f[3 * A.c], -dEdc * gc.x);
+    atomicAdd(&s_f[3 * A.c + 1], -dEdc * gc.y);
+    atomicAdd(&s_f[3 * A.c + 2], -dEdc * gc.z);
+    atomicAdd(&s_f[3 * A.b], dEdc * (ga.x + gc.x));
+    atomicAdd(&s_f[3 * A.b + 1], dEdc * (ga.y + gc.y));
+    atomicAdd(&s_f[3 * A.b + 2], dEdc * (ga.z + gc.z));
+    e += A.k * (c - A.cos0) * (c - A.cos0);
+  }
+  for (int k = tv.ut_off[t] + lane; k < tv.ut_off[t + 1]; k += 32) {
+    const TorsionRec T = tv.ut[k];
+    const float3 xa = ld3(s_x, T.a), xb = ld3(s_x, T.b), xc = ld3(s_x, T.c), xd = ld3(s_x, T.d);
+    const float3 F = sub3(xa, xb), G = sub3(xb, xc), H = sub3(xd, xc);
+    const float3 A = cross3(F, G), B = cross3(H, G);
+    const float A2 = dot3(A, A), B2 = dot3(B, B), G2 = dot3(G, G);
+    if (A2 < 1e-12f || B2 < 1e-12f || G2 < 1e-12f) continue;   // collinear: no torque
+    const float Gn = sqrtf(G2);
+    const float iAB = rsqrtf(A2 * B2);
+    const float cphi = dot3(A, B) * iAB;
+    const float sphi = dot3(cross3(B, A), G) * iAB / Gn;
+    const float phi = atan2f(sphi, cphi);
+    float sn, cn;
+    sincosf(T.n * phi, &sn, &cn);
+    const float dEdphi = 0.5f * T.V * T.cn0 * T.n * sn;
+    const float FG = dot3(F, G) / (A2 * Gn), HG = dot3(H, G) / (B2 * Gn);
+    const float ca = -Gn / A2, cd = Gn / B2;
+    const float a1 = -ca + FG, b1 = -cd + HG;
+    // gradients of phi with respect to the four atoms
+    const float3 g0 = make_float3(ca * A.x, ca * A.y, ca * A.z);
+    const float3 g3 = make_float3(cd * B.x, cd * B.y, cd * B.z);
+    const float3 g1 = make_float3(a1 * A.x - HG * B.x, a1 * A.y - HG * B.y, a1 * A.z - HG * B.z);
+    const float3 g2 = make_float3(b1 * B.x - FG * A.x, b1 * B.y - FG * A.y, b1 * B.z - FG * A.z);
+    atomicAdd(&s_f[3 * T.a], -dEdphi * g0.x);
+    atomicAdd(&s_f[3 * T.a + 1], -dEdphi * g0.y);
+    atomicAdd(&s_f[3 * T.a + 2], -dEdphi * g0.z);
+    atomicAdd(&s_f[3 * T.b], -dEdphi * g1.x);
+    atomicAdd(&s_f[3 * T.b + 1], -dEdphi * g1.y);
+    atomicAdd(&s_f[3 * T.b + 2], -dEdphi * g1.z);
+    atomicAdd(&s_f[3 * T.c], -dEdphi * g2.x);
+    atomicAdd(&s_f[3 * T.c + 1], -dEdphi * g2.y);
+    atomicAdd(&s_f[3 * T.c + 2], -dEdphi * g2.z);
+    atomicAdd(&s_f[3 * T.d], -dEdphi * g3.x);
+    atomicAdd(&s_f[3 * T.d + 1], -dEdphi * g3.y);
+    atomicAdd(&s_f[3 * T.d + 2], -dEdphi * g3.z);
+    e += 0.5f * T.V * (1.f - T.cn0 * cn);
+  }
+  return e;
+}
+
+// Forces of one flexible replica (positions in s.x) with the grid term by
+// quads (stored per atom) followed by the unique-term intramolecular pass
+// (added with shared-memory atomics).  Writes s.f, s.eg; returns this
+// lane's share of the energy.
+template <class Acc = double>
+__device__ __forceinline__ Acc flex_forces_terms(const GridView& g, bool use_grid, bool use_intra,
+                                                 const TemplateView& tv, int t, int ab, int n, int lane,
+                                                 WarpState& s, int& flags, const StencilCache& sc) {
+  __syncwarp();
+  const int quad = lane >> 2, q = lane & 3;
+  Acc e = Acc(0);
+  for (int base = 0; base < n; base += kQuads) {
+    const int i = base + quad;
+    const bool act = i < n;
+    float x = 0.f, y = 0.f, z = 0.f;
+    float4 par = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (act) {
+      x = s.x[3 * i];
+      y = s.x[3 * i + 1];
+      z = s.x[3 * i + 2];
+      par = __ldg(&tv.par[ab + i]);
+      if (!finite3(x, y, z)) flags |= GRIDFF_REP_NONFINITE;
+    }
+    float eg = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+    if (use_grid) grid_quad(g, q, act, x, y, z, par, eg, fx, fy, fz, flags, sc, i);
+    if (act && q == 0) {
+      s.f[3 * i] = fx;
+      s.f[3 * i + 1] = fy;
+      s.f[3 * i + 2] = fz;
+      s.eg[i] = eg;
+      e += (Acc)eg;
+    }
+  }
+  __syncwarp();
+  if (use_intra) e += (Acc)intra_terms(tv, t, lane, s.x, s.f);
+  __syncwarp();
+  return e;
+}
+
 // Grid forces of a rigid replica: total force (lab) and body-frame torque
 // (warp-reduced), and this lane's share of the energy (not reduced),
 // accumulated per atom in Acc (double for the NVE energy trace, float for
@@ -991,6 +1133,127 @@ relax_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
 }
 
 // ---------------------------------------------------------------------------
+// FIRE, flexible replicas of uneven size: unique-term intramolecular pass,
+// WPB warps per block, replicas handed out by a work queue in decreasing
+// cost order (order != nullptr) or statically (order == nullptr).  Same
+// iteration as relax_flex_kernel.
+// ---------------------------------------------------------------------------
+template <int WPB>
+__global__ void __launch_bounds__(32 * WPB, 16 / WPB)
+relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
+                        const int* __restrict__ rep_off, const int* __restrict__ order, int n_rep, float* xs,
+                        float* vs, float* fdt, float* falpha, int* fnp, int* status, int* steps, double* energy,
+                        int nsteps, FireP fp, Control ctl, int use_grid, int use_intra, int S) {
+  __shared__ WarpState s_all[WPB];
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  WarpState& s = s_all[wib];
+  const StencilCache sc = warp_cache(dyn_smem, S, wib);
+  const int warp = blockIdx.x * WPB + wib;
+  const int n_warps = gridDim.x * WPB;
+  const unsigned long long t0 = gtimer();
+  for (int k = warp;; k += n_warps) {
+    if (order) {
+      int next = 0;
+      if (lane == 0) next = atomicAdd(&ctl.res->next, 1);
+      k = __shfl_sync(kFull, next, 0);
+    }
+    if (k >= n_rep) break;
+    const int r = order ? order[k] : k;
+    const int t = rep_tmpl[r], n = tv.natoms[t], ab = tv.atom_off[t], off = rep_off[r];
+    __syncwarp();
+    cache_reset(sc, lane);
+    for (int m = lane; m < 3 * n; m += 32) {
+      s.x[m] = xs[3 * (size_t)off + m];
+      s.v[m] = vs[3 * (size_t)off + m];
+    }
+    float dt = fdt[r], al = falpha[r];
+    int np = fnp[r], st = status[r], evals = 0;
+    float elane = 0.f;
+    for (int it = 0; it < nsteps; ++it) {
+      if (st & (GRIDFF_REP_CONVERGED | GRIDFF_REP_NONFINITE)) break;
+      if ((it & 31) == 0) {
+        int sb = stop_bits(ctl, t0, lane);
+        if (sb) {
+          st |= sb;
+          break;
+        }
+      }
+      int flags = 0;
+      const float e = flex_forces_terms<float>(g, use_grid, use_intra, tv, t, ab, n, lane, s, flags, sc);
+      float f2 = 0.f, P = 0.f, v2 = 0.f;
+      for (int m = lane; m < 3 * n; m += 32) {
+        float f = s.f[m], v = s.v[m];
+        f2 = fmaf(f, f, f2);
+        P = fmaf(f, v, P);
+        v2 = fmaf(v, v, v2);
+      }
+      f2 = wsum(f2);
+      P = wsum(P);
+      v2 = wsum(v2);
+      st |= __reduce_or_sync(kFull, flags);
+      ++evals;
+      elane = e;
+      if ((st & GRIDFF_REP_NONFINITE) || !isfinite(f2)) {
+        st |= GRIDFF_REP_NONFINITE;
+        break;
+      }
+      if (f2 < fp.f_conv2) {
+        st |= GRIDFF_REP_CONVERGED;
+        break;
+      }
+      float keep, mixf;
+      if (P > 0.f) {
+        keep = 1.f - al;
+        mixf = f2 > 0.f ? al * sqrtf(v2 / f2) : 0.f;
+        if (np > fp.n_min) {
+          dt = fminf(dt * fp.f_inc, fp.dt_max);
+          al *= fp.f_alpha;
+        }
+        ++np;
+      } else {
+        keep = 0.f;
+        mixf = 0.f;
+        dt *= fp.f_dec;
+        al = fp.alpha_start;
+        np = 0;
+      }
+      for (int i = lane; i < n; i += 32) {
+        const float im = 1.f / __ldg(&tv.body[ab + i]).w;
+        float d[3];
+        for (int a = 0; a < 3; ++a) {
+          float f = s.f[3 * i + a];
+          float vv = keep * s.v[3 * i + a] + mixf * f;
+          vv += GRIDFF_ACC * f * im * dt;
+          s.v[3 * i + a] = vv;
+          d[a] = vv * dt;
+        }
+        float dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        float scl = dn > fp.d_max ? fp.d_max / dn : 1.f;
+        for (int a = 0; a < 3; ++a) s.x[3 * i + a] += d[a] * scl;
+      }
+    }
+    __syncwarp();
+    for (int m = lane; m < 3 * n; m += 32) {
+      xs[3 * (size_t)off + m] = s.x[m];
+      vs[3 * (size_t)off + m] = s.v[m];
+    }
+    const double Etot = evals > 0 ? wsum((double)elane) : energy[r];
+    if (evals > 0 && !isfinite(Etot)) st |= GRIDFF_REP_NONFINITE;
+    if (lane == 0) {
+      fdt[r] = dt;
+      falpha[r] = al;
+      fnp[r] = np;
+      status[r] = st;
+      int total = steps[r] + evals;
+      steps[r] = total;
+      energy[r] = Etot;
+      report(ctl, n, evals, st, total);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // NVE, flexible replicas: velocity Verlet
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads, kMinBlocksPerSM)
@@ -1258,8 +1521,9 @@ int rigid_subwarp_width(const gridff_replicas* R) {
   return cache_bytes(n) * kSwWarps * (32 / W) <= 200 * 1024 ? W : 0;
 }
 
+// Allow `bytes` of dynamic shared memory (needed whenever static plus
+// dynamic shared memory exceeds 48 KB).
 cudaError_t set_dyn_smem(const void* kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 int persistent_blocks(gridff_ctx* ctx, const void* kernel, int n_rep, size_t dyn_smem = 0) {
@@ -1286,6 +1550,55 @@ gridff_status check_common(gridff_ctx* ctx, const gridff_grid* grid, gridff_repl
   return GRIDFF_OK;
 }
 
+__global__ void fire_reset_kernel(int n, float dt0, float a0, float* dt, float* al, int* np, int* st, int* steps) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  dt[r] = dt0;
+  al[r] = a0;
+  np[r] = 0;
+  st[r] = 0;
+  steps[r] = 0;
+}
+
+const void* rigid_sw_ptr(int W) {
+  return W == 8 ? (const void*)relax_rigid_sw_kernel<8, kSwWarps, kSwMinBlocks>
+       : W == 16 ? (const void*)relax_rigid_sw_kernel<16, kSwWarps, kSwMinBlocks>
+                 : (const void*)relax_rigid_sw_kernel<32, kSwWarps, kSwMinBlocks>;
+}
+const void* flex_terms_ptr(int wpb) {
+  return wpb == 2 ? (const void*)relax_flex_terms_kernel<2>
+       : wpb == 8 ? (const void*)relax_flex_terms_kernel<8> : (const void*)relax_flex_terms_kernel<4>;
+}
+
+struct KernelShape {
+  const void* fn;
+  int threads;
+  int units_per_block;   // replicas resident per block
+  size_t dyn;            // dynamic shared memory
+};
+
+// Kernel, block shape and dynamic shared memory of configuration c, or
+// fn == nullptr when c does not apply to R.
+KernelShape shape_of(const gridff_replicas* R, const LaunchCfg& c) {
+  KernelShape k{nullptr, 0, 0, 0};
+  switch (c.kernel) {
+    case GRIDFF_KERNEL_RIGID_SUBWARP:
+      if (!R->rigid || (c.W != 8 && c.W != 16 && c.W != 32) || c.S < R->max_natoms) return k;
+      return {rigid_sw_ptr(c.W), 32 * kSwWarps, kSwWarps * (32 / c.W), cache_bytes(c.S) * kSwWarps * (32 / c.W)};
+    case GRIDFF_KERNEL_RIGID_QUAD:
+      if (!R->rigid || c.wpb != kWarpsPerBlock) return k;
+      return {(const void*)relax_rigid_kernel, kThreads, kWarpsPerBlock, cache_bytes(c.S) * kWarpsPerBlock};
+    case GRIDFF_KERNEL_FLEX_QUAD:
+      if (R->rigid || c.wpb != kWarpsPerBlock) return k;
+      return {(const void*)relax_flex_kernel, kThreads, kWarpsPerBlock, cache_bytes(c.S) * kWarpsPerBlock};
+    case GRIDFF_KERNEL_FLEX_TERMS:
+      if (R->rigid || (c.wpb != 2 && c.wpb != 4 && c.wpb != 8)) return k;
+      return {flex_terms_ptr(c.wpb), 32 * c.wpb, c.wpb, cache_bytes(c.S) * c.wpb};
+    default:
+      return k;
+  }
+}
+
 gridff_status finish_launch(gridff_ctx* ctx, DevResult* hres) {
   GRIDFF_CUDA(ctx, cudaGetLastError());
   GRIDFF_CUDA(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
@@ -1302,6 +1615,173 @@ gridff_status finish_launch(gridff_ctx* ctx, DevResult* hres) {
 }
 
 }  // namespace
+
+LaunchCfg default_launch_cfg(const gridff_replicas* R, bool use_grid) {
+  LaunchCfg c;
+  if (R->rigid) {
+    const int W = rigid_subwarp_width(R);
+    if (use_grid && W > 0) {
+      c.kernel = GRIDFF_KERNEL_RIGID_SUBWARP;
+      c.W = W;
+      c.wpb = kSwWarps;
+      c.S = R->max_natoms;
+    } else {
+      c.kernel = GRIDFF_KERNEL_RIGID_QUAD;
+      c.wpb = kWarpsPerBlock;
+      c.S = cache_slots(R, true);
+    }
+  } else {
+    c.kernel = GRIDFF_KERNEL_FLEX_QUAD;
+    c.wpb = kWarpsPerBlock;
+    c.S = cache_slots(R, false);
+  }
+  return c;
+}
+
+gridff_status check_fire_params(gridff_ctx* ctx, const gridff_fire_params& P) {
+  if (!(P.dt_start > 0) || !(P.dt_max > 0) || !(P.d_max > 0) || P.f_conv < 0)
+    return set_err(ctx, GRIDFF_EINVAL, "bad FIRE parameters");
+  return GRIDFF_OK;
+}
+
+gridff_status prepare_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* R, const LaunchCfg& c,
+                            int flags, int* blocks_out) {
+  const KernelShape k = shape_of(R, c);
+  if (!k.fn) return set_err(ctx, GRIDFF_EINVAL, "launch configuration (kernel %d) does not apply", c.kernel);
+  if (c.S < 0 || c.S > GRIDFF_MAX_ATOMS) return set_err(ctx, GRIDFF_EINVAL, "cache slots %d", c.S);
+  if (c.kernel == GRIDFF_KERNEL_RIGID_SUBWARP && (flags & GRIDFF_NO_GRID))
+    return set_err(ctx, GRIDFF_EINVAL, "the sub-warp rigid kernel needs the grid term");
+  GRIDFF_CUDA(ctx, set_dyn_smem(k.fn, k.dyn));
+  int per_sm = 0;
+  GRIDFF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, k.threads, k.dyn));
+  if (per_sm < 1) return set_err(ctx, GRIDFF_EINVAL, "launch configuration does not fit on an SM");
+  if (GRIDFF_BLOCK_CAP > 0 && per_sm > GRIDFF_BLOCK_CAP) per_sm = GRIDFF_BLOCK_CAP;
+  const int need = (R->n_rep + k.units_per_block - 1) / k.units_per_block;
+  *blocks_out = need < per_sm * ctx->n_sm ? need : per_sm * ctx->n_sm;
+  if (c.l2win) {
+    if (!grid || (flags & GRIDFF_NO_GRID)) return set_err(ctx, GRIDFF_EINVAL, "L2 window without a grid");
+    int max_persist = 0, max_win = 0;
+    GRIDFF_CUDA(ctx, cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, ctx->device));
+    GRIDFF_CUDA(ctx, cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, ctx->device));
+    if (max_persist <= 0 || max_win <= 0) return set_err(ctx, GRIDFF_ENOTSUP, "no persisting L2 on this device");
+    if (!ctx->l2_limit_set) {
+      GRIDFF_CUDA(ctx, cudaDeviceGetLimit(&ctx->l2_prev_limit, cudaLimitPersistingL2CacheSize));
+      ctx->l2_limit_set = 1;
+    }
+    const size_t want = grid->rec_bytes < (size_t)max_persist ? grid->rec_bytes : (size_t)max_persist;
+    size_t cur = 0;
+    GRIDFF_CUDA(ctx, cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize));
+    if (cur < want) GRIDFF_CUDA(ctx, cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want));
+  }
+  return GRIDFF_OK;
+}
+
+namespace {
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_ex(void (*fn)(KArgs...), int blocks, int threads, size_t dyn, cudaStream_t s,
+                      const cudaAccessPolicyWindow* win, Args... args) {
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3(blocks);
+  lc.blockDim = dim3(threads);
+  lc.dynamicSmemBytes = dyn;
+  lc.stream = s;
+  cudaLaunchAttribute attr[1];
+  if (win) {
+    attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[0].val.accessPolicyWindow = *win;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&lc, fn, args...);
+}
+
+}  // namespace
+
+gridff_status enqueue_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* R, const LaunchCfg& c,
+                            int blocks, int nsteps, const gridff_fire_params& P, int flags) {
+  cudaStream_t s = ctx->stream;
+  if (!(flags & GRIDFF_CONTINUE)) {
+    fire_reset_kernel<<<(R->n_rep + 255) / 256, 256, 0, s>>>(R->n_rep, P.dt_start, P.alpha_start, R->fire_dt,
+                                                             R->fire_alpha, R->fire_nplus, R->status, R->steps);
+    GRIDFF_CUDA(ctx, cudaGetLastError());
+  }
+  // without CONTINUE the FIRE scalars, status and counters start afresh; a
+  // continued relaxation keeps them (converged/non-finite replicas stay
+  // frozen, stop bits of the previous call stay visible)
+  GRIDFF_CUDA(ctx, cudaMemsetAsync(ctx->result_dev, 0, sizeof(DevResult), s));
+  FireP fp{P.dt_start, P.dt_max, P.f_inc, P.f_dec, P.alpha_start, P.f_alpha, P.d_max,
+           P.f_conv * P.f_conv, P.n_min};
+  Control ctl{ctx->ctrl_dev, (unsigned long long)(P.clock_budget_s > 0 ? P.clock_budget_s * 1e9 : 0),
+              (DevResult*)ctx->result_dev};
+  GridView gv = grid ? grid->view() : empty_view();
+  const int use_grid = !(flags & GRIDFF_NO_GRID), use_intra = !(flags & GRIDFF_NO_INTRA);
+  const KernelShape k = shape_of(R, c);
+  cudaAccessPolicyWindow win{};
+  const cudaAccessPolicyWindow* wp = nullptr;
+  if (c.l2win && grid) {
+    int max_win = 0;
+    size_t lim = 0;
+    cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, ctx->device);
+    cudaDeviceGetLimit(&lim, cudaLimitPersistingL2CacheSize);
+    win.base_ptr = (void*)grid->rec;
+    win.num_bytes = grid->rec_bytes < (size_t)max_win ? grid->rec_bytes : (size_t)max_win;
+    win.hitRatio = win.num_bytes > 0 && lim < win.num_bytes ? (float)lim / (float)win.num_bytes : 1.f;
+    win.hitProp = cudaAccessPropertyPersisting;
+    win.missProp = cudaAccessPropertyStreaming;
+    wp = &win;
+  }
+  cudaError_t e = cudaSuccess;
+  switch (c.kernel) {
+    case GRIDFF_KERNEL_RIGID_SUBWARP:
+      if (c.W == 8)
+        e = launch_ex(relax_rigid_sw_kernel<8, kSwWarps, kSwMinBlocks>, blocks, k.threads, k.dyn, s, wp, gv, R->tv,
+                      (const int*)R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha, R->fire_nplus,
+                      R->status, R->steps, R->energy, nsteps, fp, ctl, c.S);
+      else if (c.W == 16)
+        e = launch_ex(relax_rigid_sw_kernel<16, kSwWarps, kSwMinBlocks>, blocks, k.threads, k.dyn, s, wp, gv,
+                      R->tv, (const int*)R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha,
+                      R->fire_nplus, R->status, R->steps, R->energy, nsteps, fp, ctl, c.S);
+      else
+        e = launch_ex(relax_rigid_sw_kernel<32, kSwWarps, kSwMinBlocks>, blocks, k.threads, k.dyn, s, wp, gv,
+                      R->tv, (const int*)R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha,
+                      R->fire_nplus, R->status, R->steps, R->energy, nsteps, fp, ctl, c.S);
+      break;
+    case GRIDFF_KERNEL_RIGID_QUAD:
+      e = launch_ex(relax_rigid_kernel, blocks, k.threads, k.dyn, s, wp, gv, R->tv, (const int*)R->rep_tmpl,
+                    R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha, R->fire_nplus, R->status, R->steps, R->energy,
+                    nsteps, fp, ctl, use_grid, c.S);
+      break;
+    case GRIDFF_KERNEL_FLEX_QUAD:
+      e = launch_ex(relax_flex_kernel, blocks, k.threads, k.dyn, s, wp, gv, R->tv, (const int*)R->rep_tmpl,
+                    (const int*)R->rep_off, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha, R->fire_nplus,
+                    R->status, R->steps, R->energy, nsteps, fp, ctl, use_grid, use_intra, c.S);
+      break;
+    case GRIDFF_KERNEL_FLEX_TERMS: {
+      const int* ord = c.queue ? (const int*)R->order : nullptr;
+      if (c.wpb == 2)
+        e = launch_ex(relax_flex_terms_kernel<2>, blocks, k.threads, k.dyn, s, wp, gv, R->tv,
+                      (const int*)R->rep_tmpl, (const int*)R->rep_off, ord, R->n_rep, R->x, R->v, R->fire_dt,
+                      R->fire_alpha, R->fire_nplus, R->status, R->steps, R->energy, nsteps, fp, ctl, use_grid,
+                      use_intra, c.S);
+      else if (c.wpb == 8)
+        e = launch_ex(relax_flex_terms_kernel<8>, blocks, k.threads, k.dyn, s, wp, gv, R->tv,
+                      (const int*)R->rep_tmpl, (const int*)R->rep_off, ord, R->n_rep, R->x, R->v, R->fire_dt,
+                      R->fire_alpha, R->fire_nplus, R->status, R->steps, R->energy, nsteps, fp, ctl, use_grid,
+                      use_intra, c.S);
+      else
+        e = launch_ex(relax_flex_terms_kernel<4>, blocks, k.threads, k.dyn, s, wp, gv, R->tv,
+                      (const int*)R->rep_tmpl, (const int*)R->rep_off, ord, R->n_rep, R->x, R->v, R->fire_dt,
+                      R->fire_alpha, R->fire_nplus, R->status, R->steps, R->energy, nsteps, fp, ctl, use_grid,
+                      use_intra, c.S);
+      break;
+    }
+    default:
+      return set_err(ctx, GRIDFF_EINVAL, "unknown kernel %d", c.kernel);
+  }
+  if (e != cudaSuccess) return set_err(ctx, GRIDFF_ECUDA, "relaxation launch: %s", cudaGetErrorString(e));
+  return GRIDFF_OK;
+}
 
 extern "C" {
 
@@ -1352,86 +1832,20 @@ gridff_status gridff_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_repl
   gridff_fire_params def;
   gridff_fire_params_default(&def);
   const gridff_fire_params& P = prm ? *prm : def;
-  if (!(P.dt_start > 0) || !(P.dt_max > 0) || !(P.d_max > 0) || P.f_conv < 0)
-    return set_err(ctx, GRIDFF_EINVAL, "bad FIRE parameters");
+  if ((st = check_fire_params(ctx, P)) != GRIDFF_OK) return st;
   GRIDFF_CUDA(ctx, cudaSetDevice(ctx->device));
-  cudaStream_t s = ctx->stream;
-  if (!(flags & GRIDFF_CONTINUE)) {
-    // reset FIRE scalars, status and counters (fill on the device)
-    std::vector<float> dt(R->n_rep, P.dt_start), al(R->n_rep, P.alpha_start);
-    GRIDFF_CUDA(ctx, cudaMemcpyAsync(R->fire_dt, dt.data(), R->n_rep * sizeof(float), cudaMemcpyHostToDevice, s));
-    GRIDFF_CUDA(ctx, cudaMemcpyAsync(R->fire_alpha, al.data(), R->n_rep * sizeof(float), cudaMemcpyHostToDevice, s));
-    GRIDFF_CUDA(ctx, cudaMemsetAsync(R->fire_nplus, 0, R->n_rep * sizeof(int), s));
-    GRIDFF_CUDA(ctx, cudaMemsetAsync(R->status, 0, R->n_rep * sizeof(int), s));
-    GRIDFF_CUDA(ctx, cudaMemsetAsync(R->steps, 0, R->n_rep * sizeof(int), s));
-    GRIDFF_CUDA(ctx, cudaStreamSynchronize(s));
-  } else {
-    // a continued relaxation clears only the stop bits of the previous call
-    // (kept in the status words; converged/non-finite replicas stay frozen)
-  }
-  GRIDFF_CUDA(ctx, cudaMemsetAsync(ctx->result_dev, 0, sizeof(DevResult), s));
-  FireP fp{P.dt_start, P.dt_max, P.f_inc, P.f_dec, P.alpha_start, P.f_alpha, P.d_max,
-           P.f_conv * P.f_conv, P.n_min};
-  Control ctl{ctx->ctrl_dev, (unsigned long long)(P.clock_budget_s > 0 ? P.clock_budget_s * 1e9 : 0),
-              (DevResult*)ctx->result_dev};
-  GridView gv = grid ? grid->view() : empty_view();
-  int use_grid = !(flags & GRIDFF_NO_GRID), use_intra = !(flags & GRIDFF_NO_INTRA);
-  GRIDFF_CUDA(ctx, cudaEventRecord(ctx->ev0, s));
-  if (R->rigid) {
-    const int W = rigid_subwarp_width(R);
-    if (use_grid && W > 0) {
-      // one sub-warp of W lanes per replica, every atom cached
-      const int S = R->max_natoms;
-      const size_t dyn = cache_bytes(S) * kSwWarps * (32 / W);
-      const void* k = W == 8 ? (const void*)relax_rigid_sw_kernel<8, kSwWarps, kSwMinBlocks>
-                    : W == 16 ? (const void*)relax_rigid_sw_kernel<16, kSwWarps, kSwMinBlocks>
-                              : (const void*)relax_rigid_sw_kernel<32, kSwWarps, kSwMinBlocks>;
-      GRIDFF_CUDA(ctx, set_dyn_smem(k, dyn));
-      const int per_block = kSwWarps * (32 / W);
-      int per_sm = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * kSwWarps, dyn);
-      if (per_sm < 1) per_sm = 1;
-      int need = (R->n_rep + per_block - 1) / per_block;
-      int blocks = need < per_sm * ctx->n_sm ? need : per_sm * ctx->n_sm;
-      if (W == 8)
-        relax_rigid_sw_kernel<8, kSwWarps, kSwMinBlocks><<<blocks, 32 * kSwWarps, dyn, s>>>(gv, R->tv,
-            R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha, R->fire_nplus, R->status, R->steps,
-            R->energy, nsteps, fp, ctl, S);
-      else if (W == 16)
-        relax_rigid_sw_kernel<16, kSwWarps, kSwMinBlocks><<<blocks, 32 * kSwWarps, dyn, s>>>(gv, R->tv,
-            R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha, R->fire_nplus, R->status, R->steps,
-            R->energy, nsteps, fp, ctl, S);
-      else
-        relax_rigid_sw_kernel<32, kSwWarps, kSwMinBlocks><<<blocks, 32 * kSwWarps, dyn, s>>>(gv, R->tv,
-            R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha, R->fire_nplus, R->status, R->steps,
-            R->energy, nsteps, fp, ctl, S);
-    } else {
-      const int S = cache_slots(R, true);
-      const size_t dyn = cache_bytes(S) * kWarpsPerBlock;
-      GRIDFF_CUDA(ctx, set_dyn_smem((const void*)relax_rigid_kernel, dyn));
-      int blocks = persistent_blocks(ctx, (const void*)relax_rigid_kernel, R->n_rep, dyn);
-      relax_rigid_kernel<<<blocks, kThreads, dyn, s>>>(gv, R->tv, R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt,
-                                                       R->fire_alpha, R->fire_nplus, R->status, R->steps,
-                                                       R->energy, nsteps, fp, ctl, use_grid, S);
-    }
-  } else {
-    const int S = cache_slots(R, false);
-    const size_t dyn = cache_bytes(S) * kWarpsPerBlock;
-    GRIDFF_CUDA(ctx, set_dyn_smem((const void*)relax_flex_kernel, dyn));
-    int blocks = persistent_blocks(ctx, (const void*)relax_flex_kernel, R->n_rep, dyn);
-    relax_flex_kernel<<<blocks, kThreads, dyn, s>>>(gv, R->tv, R->rep_tmpl, R->rep_off, R->n_rep, R->x, R->v,
-                                                    R->fire_dt, R->fire_alpha, R->fire_nplus, R->status,
-                                                    R->steps, R->energy, nsteps, fp, ctl, use_grid, use_intra, S);
-  }
+  const bool use_grid = !(flags & GRIDFF_NO_GRID);
+  const LaunchCfg c = R->cfg.kernel >= 0 ? R->cfg : default_launch_cfg(R, use_grid);
+  int blocks = 0;
+  if ((st = prepare_relax(ctx, grid, R, c, flags, &blocks)) != GRIDFF_OK) return st;
+  GRIDFF_CUDA(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
+  if ((st = enqueue_relax(ctx, grid, R, c, blocks, nsteps, P, flags)) != GRIDFF_OK) return st;
   DevResult h{};
   gridff_status rs = finish_launch(ctx, &h);
   if (result) {
     result->atom_evals = (int64_t)h.atom_evals;
     result->n_converged = h.n_converged;
     result->max_steps = h.max_steps;
-  }
-  if (flags & GRIDFF_CONTINUE) {
-    // nothing else: stop bits stay visible in the status words
   }
   return rs;
 }

@@ -37,6 +37,8 @@ struct gridff_ctx {
   volatile int* ctrl_host = nullptr;  // host-mapped: [0] abort flag
   int* ctrl_dev = nullptr;            // device alias of ctrl_host
   int* result_dev = nullptr;          // device word: OR of per-replica stop bits
+  size_t l2_prev_limit = 0;           // persisting-L2 limit before the first L2-window launch
+  int l2_limit_set = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double last_ms = 0.0;
   std::string err;
@@ -80,6 +82,13 @@ struct BondRec { int j; int own; float k; float r0; };   // own: count the energ
 struct AngleRec { int a, b, c, role; float k, cos0, pad0, pad1; };
 struct TorsionRec { int a, b, c, d; int role; int n; float V, cn0; };
 
+// Unique-term lists (each term once; forces scattered with shared-memory
+// atomics).  Nonbonded pairs i < j more than two bonds apart, ordered by
+// j - i then i (consecutive lanes touch distinct atoms), with the pair's
+// mixed parameters precomputed.
+struct PairRec { uint32_t ij; float R; float ee; float qq; };   // ij = i | j << 16; R = R_i + R_j
+struct BondTerm { int i, j; float k, r0; };
+
 // Molecule templates as the kernels see them (all device pointers).
 struct TemplateView {
   const int* natoms;        // [T]
@@ -94,6 +103,14 @@ struct TemplateView {
   const AngleRec* angles;
   const int* tors_off;      // [A+1]
   const TorsionRec* tors;
+  const int* pair_off;      // [T+1] nonbonded pair list per template
+  const PairRec* pairs;
+  const int* ub_off;        // [T+1] unique bonds
+  const BondTerm* ub;
+  const int* ua_off;        // [T+1] unique angles (AngleRec, role unused)
+  const AngleRec* ua;
+  const int* ut_off;        // [T+1] unique torsions (TorsionRec, role unused)
+  const TorsionRec* ut;
   const float4* rigid;      // [T] {M, I1, I2, I3}
   const float* rmax;        // [T]
   float alpha;
@@ -105,7 +122,18 @@ struct DevResult {
   int stop_bits;      // OR of GRIDFF_REP_ABORTED / GRIDFF_REP_STEPLIMIT over replicas
   int n_converged;
   int max_steps;
-  int pad[3];
+  int next;           // work-queue position (replicas handed out so far)
+  int pad[2];
+};
+
+// Launch configuration of a relaxation (mirrors gridff_launch_config).
+struct LaunchCfg {
+  int kernel = -1;   // GRIDFF_KERNEL_*; -1 = not chosen (heuristic default)
+  int W = 32;        // rigid sub-warp: lanes per replica
+  int wpb = 4;       // warps per block
+  int S = 0;         // stencil-cache slots per replica (0 = no staging)
+  int queue = 0;     // work queue in decreasing cost order
+  int l2win = 0;     // grid in an L2 persisting access-policy window
 };
 
 struct gridff_replicas {
@@ -122,6 +150,7 @@ struct gridff_replicas {
   TemplateView tv{};
   int* rep_tmpl = nullptr;     // [n_rep]
   int* rep_off = nullptr;      // [n_rep+1]
+  int* order = nullptr;        // [n_rep] replicas by decreasing estimated cost (work-queue order)
   float* x = nullptr;          // flexible [3N]; rigid [7 n_rep]
   float* v = nullptr;          // flexible [3N]; rigid [6 n_rep]
   float* fire_dt = nullptr;
@@ -132,10 +161,23 @@ struct gridff_replicas {
   double* energy = nullptr;
   // host copy of offsets
   int* h_rep_off = nullptr;
+  LaunchCfg cfg;               // set by gridff_tune / gridff_set_launch_config
 };
 
 // error helpers -------------------------------------------------------------
 gridff_status set_err(gridff_ctx* ctx, gridff_status st, const char* fmt, ...);
+
+// Relaxation launch shared by gridff_relax, the autotuner and graph capture
+// (dynamics.cu).  prepare_relax validates cfg for R and sets kernel
+// attributes (not capturable); enqueue_relax puts the FIRE reset (unless
+// CONTINUE), the result reset and the relaxation kernel on the context
+// stream (capturable; no synchronisation).
+LaunchCfg default_launch_cfg(const gridff_replicas* R, bool use_grid);
+gridff_status prepare_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* R, const LaunchCfg& c,
+                            int flags, int* blocks_out);
+gridff_status enqueue_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* R, const LaunchCfg& c,
+                            int blocks, int nsteps, const gridff_fire_params& P, int flags);
+gridff_status check_fire_params(gridff_ctx* ctx, const gridff_fire_params& P);
 #define GRIDFF_CUDA(ctx, call)                                                     \
   do {                                                                             \
     cudaError_t e_ = (call);                                                       \

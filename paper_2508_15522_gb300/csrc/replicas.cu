@@ -76,6 +76,12 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
   std::vector<BondRec> bonds;
   std::vector<AngleRec> angles;
   std::vector<TorsionRec> tors;
+  std::vector<int> pair_off(1, 0), ub_off(1, 0), ua_off(1, 0), ut_off(1, 0);
+  std::vector<PairRec> pairs;
+  std::vector<BondTerm> ub;
+  std::vector<AngleRec> ua;
+  std::vector<TorsionRec> ut;
+  std::vector<double> tmpl_cost(n_templates);
   int max_n = 0;
   for (int t = 0; t < n_templates; ++t) {
     const gridff_molecule& m = T[t];
@@ -113,7 +119,10 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
           return set_err(ctx, GRIDFF_EINVAL, "template %d: angle %d repeats an atom", t, a);
         for (int role = 0; role < 3; ++role)
           pa[A[role]].push_back(AngleRec{A[0], A[1], A[2], role, m.angle_k[a], m.angle_cos0[a], 0, 0});
+        ua.push_back(AngleRec{A[0], A[1], A[2], 0, m.angle_k[a], m.angle_cos0[a], 0, 0});
       }
+      for (int b = 0; b < m.n_bonds; ++b)
+        ub.push_back(BondTerm{m.bonds[2 * b], m.bonds[2 * b + 1], m.bond_k[b], m.bond_r0[b]});
       for (int a = 0; a < m.n_torsions; ++a) {
         const int* A = m.torsions + 4 * a;
         for (int k = 0; k < 4; ++k)
@@ -121,8 +130,13 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
         for (int role = 0; role < 4; ++role)
           pt[A[role]].push_back(TorsionRec{A[0], A[1], A[2], A[3], role, m.torsion_n[a],
                                            m.torsion_V[a], m.torsion_cos_nphi0[a]});
+        ut.push_back(TorsionRec{A[0], A[1], A[2], A[3], 0, m.torsion_n[a], m.torsion_V[a],
+                                m.torsion_cos_nphi0[a]});
       }
     }
+    ub_off.push_back((int)ub.size());
+    ua_off.push_back((int)ua.size());
+    ut_off.push_back((int)ut.size());
     double M = 0, cx = 0, cy = 0, cz = 0;
     for (int i = 0; i < n; ++i) {
       if (!(m.mass[i] > 0)) return set_err(ctx, GRIDFF_EINVAL, "template %d: mass of atom %d", t, i);
@@ -174,6 +188,21 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
         if (depth[j] >= 0) w[j >> 5] |= 1u << (j & 31);
       for (int k = 0; k < 4; ++k) excl.push_back(w[k]);
     }
+    // nonbonded pair list (flexible only), diagonal order
+    const size_t ex0 = excl.size() - 4 * (size_t)n;
+    if (!rigid)
+      for (int d = 1; d < n; ++d)
+        for (int i = 0; i + d < n; ++i) {
+          const int j = i + d;
+          if ((excl[ex0 + 4 * i + (j >> 5)] >> (j & 31)) & 1u) continue;
+          pairs.push_back(PairRec{(uint32_t)i | ((uint32_t)j << 16), m.R[i] + m.R[j], m.eps[i] * m.eps[j],
+                                  GRIDFF_KE * m.q[i] * m.q[j]});
+        }
+    pair_off.push_back((int)pairs.size());
+    // relative cost of one force evaluation (work-queue order): grid per
+    // atom plus intramolecular terms
+    tmpl_cost[t] = 8.0 * n + (pair_off[t + 1] - pair_off[t]) + 2.0 * (ub_off[t + 1] - ub_off[t]) +
+                   3.0 * (ua_off[t + 1] - ua_off[t]) + 6.0 * (ut_off[t + 1] - ut_off[t]);
     for (int i = 0; i < n; ++i) {
       double R = m.R[i], eps = m.eps[i];
       body.push_back(make_float4(m.xyz[3 * i], m.xyz[3 * i + 1], m.xyz[3 * i + 2], m.mass[i]));
@@ -196,13 +225,19 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
     rep_tmpl[r] = t;
     rep_off[r + 1] = rep_off[r] + natoms[t];
   }
+  std::vector<int> order(n_rep);
+  for (int r = 0; r < n_rep; ++r) order[r] = r;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return tmpl_cost[rep_tmpl[a]] > tmpl_cost[rep_tmpl[b]]; });
   // one device blob for the templates
   std::vector<unsigned char> blob;
   size_t o_nat = push(blob, natoms), o_aoff = push(blob, atom_off), o_body = push(blob, body),
          o_par = push(blob, par), o_nb = push(blob, nb), o_ex = push(blob, excl),
          o_boff = push(blob, bond_off), o_b = push(blob, bonds), o_aof = push(blob, angle_off),
          o_a = push(blob, angles), o_tof = push(blob, tors_off), o_t = push(blob, tors),
-         o_rig = push(blob, rig), o_rmax = push(blob, rmax);
+         o_rig = push(blob, rig), o_rmax = push(blob, rmax), o_poff = push(blob, pair_off),
+         o_p = push(blob, pairs), o_ubo = push(blob, ub_off), o_ub = push(blob, ub), o_uao = push(blob, ua_off),
+         o_ua = push(blob, ua), o_uto = push(blob, ut_off), o_ut = push(blob, ut), o_ord = push(blob, order);
   gridff_replicas* R = new gridff_replicas();
   R->ctx = ctx;
   R->device = ctx->device;
@@ -234,6 +269,15 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
   R->tv.tors = (const TorsionRec*)(B + o_t);
   R->tv.rigid = (const float4*)(B + o_rig);
   R->tv.rmax = (const float*)(B + o_rmax);
+  R->tv.pair_off = (const int*)(B + o_poff);
+  R->tv.pairs = (const PairRec*)(B + o_p);
+  R->tv.ub_off = (const int*)(B + o_ubo);
+  R->tv.ub = (const BondTerm*)(B + o_ub);
+  R->tv.ua_off = (const int*)(B + o_uao);
+  R->tv.ua = (const AngleRec*)(B + o_ua);
+  R->tv.ut_off = (const int*)(B + o_uto);
+  R->tv.ut = (const TorsionRec*)(B + o_ut);
+  R->order = (int*)(B + o_ord);
   R->tv.alpha = (float)alpha;
   size_t nx = rigid ? 7 * (size_t)n_rep : 3 * (size_t)R->n_atoms;
   size_t nv = rigid ? 6 * (size_t)n_rep : 3 * (size_t)R->n_atoms;

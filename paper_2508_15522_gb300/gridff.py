@@ -72,6 +72,18 @@ class MDParams(C.Structure):
     _fields_ = [("dt", C.c_float), ("record_every", C.c_int32), ("clock_budget_s", C.c_double)]
 
 
+class LaunchConfig(C.Structure):
+    _fields_ = [("kernel", C.c_int32), ("lanes_per_replica", C.c_int32), ("warps_per_block", C.c_int32),
+                ("cache_slots", C.c_int32), ("queue", C.c_int32), ("l2_window", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TuneTrial(C.Structure):
+    _fields_ = [("cfg", LaunchConfig), ("atom_evals_per_s", C.c_double), ("ms", C.c_double)]
+
+
 class TrainParams(C.Structure):
     _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
                 ("w_q", C.c_float), ("w_t", C.c_float), ("tile", C.c_double * 2)]
@@ -126,6 +138,13 @@ def _load():
         "gridff_random_poses": (I32, [P, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_double), F64, F64,
                                       F64]),
         "gridff_rmsd_unique": (I32, [P, I32, I32, P, C.POINTER(C.c_double), F64, P, C.c_int]),
+        "gridff_set_launch_config": (I32, [P, C.POINTER(LaunchConfig)]),
+        "gridff_get_launch_config": (I32, [P, C.c_int, C.POINTER(LaunchConfig)]),
+        "gridff_tune": (I32, [P, P, P, C.POINTER(FireParams), I32, C.c_int, C.POINTER(LaunchConfig),
+                              C.POINTER(TuneTrial), I32, C.POINTER(C.c_int32)]),
+        "gridff_relax_graph_create": (I32, [P, P, P, I32, C.POINTER(FireParams), C.c_int, C.POINTER(P)]),
+        "gridff_graph_launch": (I32, [P, C.POINTER(RelaxResult)]),
+        "gridff_graph_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -146,7 +165,11 @@ EXPORTED = (
     "gridff_mlp_create", "gridff_mlp_destroy", "gridff_mlp_num_params", "gridff_mlp_set_params",
     "gridff_mlp_get_params", "gridff_mlp_forward", "gridff_mlp_train_step", "gridff_mlp_propose",
     "gridff_molecule_descriptor", "gridff_random_poses", "gridff_rmsd_unique",
+    "gridff_set_launch_config", "gridff_get_launch_config", "gridff_tune", "gridff_relax_graph_create",
+    "gridff_graph_launch", "gridff_graph_destroy",
 )
+
+KERNEL_RIGID_SUBWARP, KERNEL_RIGID_QUAD, KERNEL_FLEX_QUAD, KERNEL_FLEX_TERMS = 0, 1, 2, 3
 
 
 def _is_torch(a):
@@ -357,6 +380,21 @@ class Replicas:
                                                  p["steps"], p["energy"], 0))
         return out
 
+    def set_launch_config(self, cfg=None, **kw):
+        """Fix the relaxation layout (None: the library's heuristic)."""
+        if cfg is None and not kw:
+            self.ctx.check(lib.gridff_set_launch_config(self.h, None))
+            return
+        c = self.launch_config() if cfg is None else cfg
+        for k, v in kw.items():
+            setattr(c, k, v)
+        self.ctx.check(lib.gridff_set_launch_config(self.h, C.byref(c)))
+
+    def launch_config(self, use_grid=True) -> LaunchConfig:
+        c = LaunchConfig()
+        self.ctx.check(lib.gridff_get_launch_config(self.h, int(bool(use_grid)), C.byref(c)))
+        return c
+
     def random_poses(self, seed, origin_xy, tile_xy, z_lo, z_hi, z_floor):
         """Random rigid starting poses drawn on the device (gridff_random_poses)."""
         o = (C.c_double * 2)(*origin_xy); t = (C.c_double * 2)(*tile_xy)
@@ -526,6 +564,53 @@ class MLP:
     def close(self):
         if getattr(self, "h", None):
             lib.gridff_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tune(ctx: Context, grid, reps: Replicas, params: FireParams | None = None, trial_steps: int = 20,
+         flags: int = 0, max_trials: int = 64):
+    """gridff_tune -> (best LaunchConfig, [trial dicts])."""
+    best = LaunchConfig()
+    trials = (TuneTrial * max_trials)()
+    n = C.c_int32()
+    ctx.check(lib.gridff_tune(ctx.h, grid.h if grid else None, reps.h,
+                              C.byref(params) if params is not None else None, int(trial_steps), flags,
+                              C.byref(best), trials, max_trials, C.byref(n)))
+    log = [dict(t.cfg.as_dict(), atom_evals_per_s=t.atom_evals_per_s, ms=t.ms)
+           for t in trials[:min(n.value, max_trials)]]
+    return best, log
+
+
+class RelaxGraph:
+    """gridff_relax_graph_create: one relaxation captured in a CUDA graph."""
+
+    def __init__(self, ctx: Context, grid, reps: Replicas, nsteps: int, params: FireParams | None = None,
+                 flags: int = 0):
+        h = C.c_void_p()
+        ctx.check(lib.gridff_relax_graph_create(ctx.h, grid.h if grid else None, reps.h, int(nsteps),
+                                                C.byref(params) if params is not None else None, flags,
+                                                C.byref(h)))
+        self.ctx, self.h = ctx, h
+
+    def launch(self, wait: bool = True, check: bool = True):
+        if not wait:
+            self.ctx.check(lib.gridff_graph_launch(self.h, None))
+            return OK, None
+        res = RelaxResult()
+        st = lib.gridff_graph_launch(self.h, C.byref(res))
+        if check and st != OK:
+            self.ctx.check(st)
+        return st, res
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.gridff_graph_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -359,29 +359,31 @@ def random_flexible_molecule(n_atoms: int, n_torsions: int, seed: int) -> Molecu
     n_h = n_atoms - n_heavy
     elements = list(g.choice(["C", "C", "C", "O"], size=n_heavy))
     parent = [-1] + [int(g.integers(max(0, k - 2), k)) for k in range(1, n_heavy)]
-    pos = [np.zeros(3)]
+    pos = np.zeros((n_atoms, 3))
     for k in range(1, n_heavy):
         p = pos[parent[k]]
+        others = np.delete(pos[:k], parent[k], axis=0)
         for _ in range(200):
             d = g.normal(size=3)
             d /= np.linalg.norm(d)
             cand = p + 1.50 * d
-            if all(np.linalg.norm(cand - x) > 2.2 for i, x in enumerate(pos) if i != parent[k]):
+            if np.all(np.linalg.norm(others - cand, axis=1) > 2.2):
                 break
-        pos.append(cand)
+        pos[k] = cand
     bonds = [(parent[k], k) for k in range(1, n_heavy)]
     for h in range(n_h):
         host = int(g.integers(0, n_heavy))
+        others = np.delete(pos[:n_heavy + h], host, axis=0)
         for _ in range(200):
             d = g.normal(size=3)
             d /= np.linalg.norm(d)
             cand = pos[host] + 1.09 * d
-            if all(np.linalg.norm(cand - x) > 1.6 for i, x in enumerate(pos) if i != host):
+            if np.all(np.linalg.norm(others - cand, axis=1) > 1.6):
                 break
-        pos.append(cand)
+        pos[n_heavy + h] = cand
         elements.append("H")
         bonds.append((host, n_heavy + h))
-    xyz = np.array(pos)
+    xyz = pos.copy()
     xyz -= xyz.mean(0)
     q = _zero_sum(g.uniform(-0.3, 0.3, n_atoms))
     mol = _finish(elements, xyz, q, bonds)
@@ -406,6 +408,18 @@ def uneven_sizes(n_rep: int, seed: int, lo: int = 10, hi: int = 120) -> np.ndarr
     """Log-uniform molecule sizes in [lo, hi]."""
     g = rng(seed)
     return np.clip(np.round(np.exp(g.uniform(math.log(lo), math.log(hi), n_rep))), lo, hi).astype(int)
+
+
+def uneven_batch(n_rep: int, n_templates: int, seed: int, lo: int = 10, hi: int = 120):
+    """A batch of flexible replicas of uneven size: ``n_templates`` random
+    molecules with log-uniform sizes in [lo, hi] and 0-12 torsion bonds
+    (uniform), and the template of every replica (uniform).  Returns
+    (templates, template_of)."""
+    g = rng(seed)
+    sizes = uneven_sizes(n_templates, seed + 1, lo, hi)
+    tors = g.integers(0, 13, n_templates)
+    mols = [random_flexible_molecule(int(n), int(t), seed + 100 + k) for k, (n, t) in enumerate(zip(sizes, tors))]
+    return mols, g.integers(0, n_templates, n_rep).astype(np.int32)
 
 
 # ---------------------------------------------------------------------------

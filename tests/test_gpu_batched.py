@@ -1,0 +1,215 @@
+"""GPU parity of the batched relaxation layouts (unique-term flexible kernel
+with warps-per-block, stencil-staging and work-queue variants), the
+autotuner and CUDA-graph replay, against the oracle's FIRE."""
+import numpy as np
+import pytest
+
+from oracle import dynamics as odyn
+from oracle import grid as ogrid
+from paper_2508_15522_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2508_15522_gb300 import gridff
+    return gridff
+
+
+@pytest.fixture(scope="module")
+def ctx(G):
+    return G.Context(0)
+
+
+@pytest.fixture(scope="module")
+def field(G, ctx):
+    sub = synth.rocksalt_slab(ncell=2)
+    box = synth.grid_box_for(sub, 0.25, height=8.0)
+    n, h = ogrid.grid_dims(box.length, box.spacing)
+    coefs = synth.random_coefficients(n, 3, seed=71, scale=(0.02, 0.01, 0.03))
+    grid = G.grid_from_coefs(ctx, coefs, box.origin, h, 7)
+    return sub, box, h, coefs.astype(np.float32).astype(np.float64), grid
+
+
+@pytest.fixture(scope="module")
+def uneven():
+    """Templates of 10, 47 and 70 atoms with torsions, and an uneven replica
+    list (the 128-atom maximum is covered by its own one-step case)."""
+    mols = [synth.chain_molecule(), synth.random_flexible_molecule(47, 8, 3),
+            synth.random_flexible_molecule(70, 10, 5)]
+    tof = np.array([0, 2, 1, 1, 0, 2, 0, 1, 0], np.int32)
+    return mols, tof
+
+
+def _start(sub, mols, tof, seed):
+    xs = []
+    for r, t in enumerate(tof):
+        xs.append(synth.flexible_positions(mols[t], sub, 1, seed=seed + r)[0])
+    return [x.astype(np.float32) for x in xs]
+
+
+CHECKPOINTS = (1, 5, 20)
+
+
+def _oracle(field, mols, tof, x0, checkpoints=CHECKPOINTS):
+    """Oracle FIRE positions of every replica after each checkpoint's number
+    of steps (one trajectory per template, continued between checkpoints)."""
+    sub, box, h, c32, grid = field
+    out = {k: [None] * len(tof) for k in checkpoints}
+    for t, mol in enumerate(mols):
+        rows = [r for r in range(len(tof)) if tof[r] == t]
+        if not rows:
+            continue
+        fn = odyn.make_force_fn(c32, ("C", "P", "L"), box.origin, h, mol)
+        x = np.stack([x0[r] for r in rows]).astype(np.float64)
+        v = np.zeros_like(x)
+        state, done = None, 0
+        for k in checkpoints:
+            ref = odyn.fire_flexible(x, v, mol.mass, fn, k - done, odyn.FireParams(f_conv=0.0), state=state)
+            x, v, done = ref["x"], ref["v"], k
+            state = {key: ref[key] for key in ("dt", "alpha", "nplus", "status", "steps")}
+            for j, r in enumerate(rows):
+                out[k][r] = x[j]
+    return out
+
+
+@pytest.fixture(scope="module")
+def refs(field, uneven):
+    mols, tof = uneven
+    x0 = _start(field[0], mols, tof, 81)
+    return x0, _oracle(field, mols, tof, x0)
+
+
+LAYOUTS = [dict(kernel=3, warps_per_block=w, cache_slots=S, queue=q)
+           for w, S, q in ((2, 0, 1), (4, 32, 1), (8, 64, 0), (4, 70, 0), (8, 16, 1))]
+TOL = {1: 2e-6, 5: 2e-5, 20: 2e-4}
+
+
+def _relax_and_compare(G, ctx, grid, mols, tof, x0, ref, configure):
+    for nsteps in CHECKPOINTS:
+        reps = G.Replicas(ctx, mols, tof)
+        configure(reps)
+        reps.set_state(np.concatenate([x.ravel() for x in x0]))
+        st, res = G.relax(ctx, grid, reps, nsteps, G.fire_params(f_conv=0.0))
+        assert res.atom_evals == sum(mols[t].n for t in tof) * nsteps
+        x, _ = reps.get_state()
+        off = reps.atom_offset
+        for r in range(len(tof)):
+            xr = x[3 * off[r]:3 * off[r + 1]].reshape(-1, 3)
+            assert np.abs(xr - ref[nsteps][r]).max() <= TOL[nsteps], (nsteps, r)
+        assert (reps.fire_state()["steps"] == nsteps).all()
+        reps.close()
+
+
+@pytest.mark.parametrize("layout", LAYOUTS, ids=lambda d: "w{warps_per_block}-S{cache_slots}-q{queue}".format(**d))
+def test_flex_terms_layouts_match_oracle(G, ctx, field, uneven, refs, layout):
+    mols, tof = uneven
+    x0, ref = refs
+    _relax_and_compare(G, ctx, field[4], mols, tof, x0, ref,
+                       lambda reps: reps.set_launch_config(G.LaunchConfig(lanes_per_replica=32, l2_window=0,
+                                                                          **layout)))
+
+
+def test_flex_terms_largest_molecule_one_step(G, ctx, field):
+    mol = synth.random_flexible_molecule(128, 12, 4)
+    x0 = [synth.flexible_positions(mol, field[0], 1, seed=131)[0].astype(np.float32)]
+    ref = _oracle(field, [mol], np.array([0]), x0, checkpoints=(1,))
+    reps = G.Replicas(ctx, [mol], [0])
+    reps.set_launch_config(kernel=G.KERNEL_FLEX_TERMS, warps_per_block=4, cache_slots=128, queue=1)
+    reps.set_state(x0[0].ravel())
+    G.relax(ctx, field[4], reps, 1, G.fire_params(f_conv=0.0))
+    x, _ = reps.get_state()
+    assert np.abs(x.reshape(-1, 3) - ref[1][0]).max() <= TOL[1]
+    reps.close()
+
+
+def test_flex_terms_energy_matches_eval(G, ctx, field, uneven):
+    """The energy a relaxation reports equals gridff_eval at the final state."""
+    sub, box, h, c32, grid = field
+    mols, tof = uneven
+    reps = G.Replicas(ctx, mols, tof)
+    reps.set_launch_config(kernel=G.KERNEL_FLEX_TERMS, warps_per_block=4, cache_slots=32, queue=1)
+    reps.set_state(np.concatenate([x.ravel() for x in _start(sub, mols, tof, 91)]))
+    G.relax(ctx, grid, reps, 1, G.fire_params(f_conv=0.0))      # energy of the evaluated (start) state
+    e_relax = reps.fire_state()["energy"]
+    reps.set_state(np.concatenate([x.ravel() for x in _start(sub, mols, tof, 91)]))
+    E, F, _ = G.eval(ctx, grid, reps)[:3]
+    assert np.allclose(e_relax, E, atol=1e-5 * 128, rtol=1e-5)
+
+
+def test_tuner_restores_state_and_picks_a_valid_layout(G, ctx, field, uneven, refs):
+    sub, box, h, c32, grid = field
+    mols, tof = uneven
+    reps = G.Replicas(ctx, mols, tof)
+    x0 = np.concatenate([x.ravel() for x in refs[0]])
+    reps.set_state(x0)
+    before = reps.get_state()
+    best, log = G.tune(ctx, grid, reps, G.fire_params(f_conv=0.0), trial_steps=5)
+    after = reps.get_state()
+    assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+    assert len(log) >= 4 and max(t["atom_evals_per_s"] for t in log) > 0
+    cfg = reps.launch_config()
+    assert cfg.kernel == best.kernel and cfg.cache_slots == best.cache_slots
+    reps.close()
+    # relaxing with the tuned layout gives the oracle's trajectory
+    _relax_and_compare(G, ctx, grid, mols, tof, refs[0], refs[1],
+                       lambda r: r.set_launch_config(best))
+
+
+def test_rigid_tuner_and_graph_replay_bitwise(G, ctx, field):
+    """Rigid kernels are deterministic: a graph replay equals a direct call
+    bit for bit, for the tuned layout."""
+    sub, box, h, c32, grid = field
+    mol = synth.c24h8o6_core()
+    n_rep = 300
+    com, quat = synth.rigid_poses(mol, sub, n_rep, seed=111)
+    pose = np.concatenate([com, quat], 1).astype(np.float32).ravel()
+    reps = G.Replicas(ctx, [mol], [0] * n_rep, rigid=True)
+    reps.set_state(pose)
+    best, log = G.tune(ctx, grid, reps, G.fire_params(f_conv=0.0), trial_steps=10)
+    assert best.kernel in (G.KERNEL_RIGID_SUBWARP, G.KERNEL_RIGID_QUAD)
+    G.relax(ctx, grid, reps, 50, G.fire_params(f_conv=0.0))
+    x_direct, _ = reps.get_state()
+    graph = G.RelaxGraph(ctx, grid, reps, 50, G.fire_params(f_conv=0.0))
+    for _ in range(2):
+        reps.set_state(pose)
+        st, res = graph.launch()
+        assert res.atom_evals == n_rep * mol.n * 50
+        x_graph, _ = reps.get_state()
+        assert np.array_equal(x_graph, x_direct)
+    graph.close()
+    reps.close()
+
+
+def test_flex_graph_replay_matches_direct(G, ctx, field, uneven):
+    sub, box, h, c32, grid = field
+    mols, tof = uneven
+    x0 = np.concatenate([x.ravel() for x in _start(sub, mols, tof, 121)])
+    reps = G.Replicas(ctx, mols, tof)
+    reps.set_launch_config(kernel=G.KERNEL_FLEX_TERMS, warps_per_block=4, cache_slots=32, queue=1)
+    reps.set_state(x0)
+    G.relax(ctx, grid, reps, 30, G.fire_params(f_conv=0.0))
+    x_direct, _ = reps.get_state()
+    graph = G.RelaxGraph(ctx, grid, reps, 30, G.fire_params(f_conv=0.0))
+    reps.set_state(x0)
+    graph.launch()
+    x_graph, _ = reps.get_state()
+    # shared-memory atomics sum in a run-dependent order: FP32 rounding only
+    assert np.abs(x_graph - x_direct).max() < 1e-4
+    graph.close()
+    reps.close()
+
+
+def test_bad_launch_configs_are_rejected(G, ctx, uneven):
+    mols, tof = uneven
+    reps = G.Replicas(ctx, mols, tof)
+    with pytest.raises(G.GridffError):
+        reps.set_launch_config(kernel=G.KERNEL_RIGID_SUBWARP)        # flexible replicas
+    with pytest.raises(G.GridffError):
+        reps.set_launch_config(kernel=G.KERNEL_FLEX_TERMS, warps_per_block=3)
+    with pytest.raises(G.GridffError):
+        reps.set_launch_config(kernel=G.KERNEL_FLEX_TERMS, warps_per_block=4, cache_slots=500)
+    reps.close()
