@@ -211,6 +211,10 @@ __device__ __forceinline__ void grid_quad(const GridView& g, int q, bool act, fl
 // Bytes of one warp's cache with S slots (a multiple of 16).
 __host__ __device__ constexpr size_t cache_bytes(int S) { return (size_t)S * 256 + (((size_t)S * 4 + 15) & ~size_t(15)); }
 
+// Bytes of one warp's dynamic shared memory in the unique-term flexible
+// kernel: its stencil cache and the staged nonbonded parameters.
+__host__ __device__ constexpr size_t flex_terms_warp_bytes(int S) { return cache_bytes(S) + (size_t)kMaxA * 16; }
+
 __device__ __forceinline__ StencilCache warp_cache(unsigned char* dyn, int S, int wib) {
   StencilCache sc;
   unsigned char* base = dyn + (size_t)wib * cache_bytes(S);
@@ -416,35 +420,94 @@ __device__ __forceinline__ Acc flex_forces(const GridView& g, bool use_grid, boo
   return e;
 }
 
-// Intramolecular forces of one flexible replica from its template's
-// unique-term lists: the lanes take terms round-robin, evaluate each term
-// once and scatter its forces to its atoms with shared-memory atomics
-// (adds into s_f).  Returns this lane's share of the energy.  Same terms as
+// Intramolecular forces of one flexible replica, each term evaluated once:
+// the lanes split the terms and add every term's forces to its atoms in
+// s_f (nonbonded pairs without atomics, on a schedule that gives the lanes
+// distinct atoms at every step; bonded terms with atomics).  Returns this
+// lane's share of the energy.  Same terms as
 // intra_quad (reduced UFF-like form; nonbonded on pairs more than two bonds
 // apart), without the per-atom repetition.
-__device__ float intra_terms(const TemplateView& tv, int t, int lane, const float* s_x, float* s_f) {
+__device__ __forceinline__ uint32_t pick4(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3, int k) {
+  return k == 0 ? w0 : k == 1 ? w1 : k == 2 ? w2 : w3;
+}
+
+// Nonbonded force factor c (F_i = c d, d = x_i - x_j) and energy of one pair
+// (Morse with mixed R_i + R_j and eps_i eps_j, plus Coulomb).
+__device__ __forceinline__ void nb_pair(float3 d, float4 pi, float4 pj, float alpha, float& c, float& e) {
+  const float r2 = dot3(d, d);
+  const float ir = rsqrtf(r2);
+  const float r = r2 * ir;
+  const float e1 = expf(-alpha * (r - (pi.y + pj.y)));
+  const float ee = pi.z * pj.z;
+  const float qq = GRIDFF_KE * pi.x * pj.x;
+  c = -(2.f * alpha * ee * e1 * (1.f - e1) - qq * ir * ir) * ir;
+  e = ee * e1 * (e1 - 2.f) + qq * ir;
+}
+
+__device__ float intra_terms(const TemplateView& tv, int t, int lane, const float* s_x, float* s_f,
+                             const float4* s_nb) {
   float e = 0.f;
   const float alpha = tv.alpha;
-  const int p1 = tv.pair_off[t + 1];
-  for (int p = tv.pair_off[t] + lane; p < p1; p += 32) {
-    const PairRec pr = tv.pairs[p];
-    const int i = pr.ij & 0xffff, j = pr.ij >> 16;
-    const float3 d = sub3(ld3(s_x, i), ld3(s_x, j));
-    const float r2 = dot3(d, d);
-    const float ir = rsqrtf(r2);
-    const float r = r2 * ir;
-    const float e1 = expf(-alpha * (r - pr.R));
-    const float em = pr.ee * e1 * (e1 - 2.f);
-    const float dEdr = 2.f * alpha * pr.ee * e1 * (1.f - e1) - pr.qq * ir * ir;
-    const float c = -dEdr * ir;
-    atomicAdd(&s_f[3 * i], c * d.x);
-    atomicAdd(&s_f[3 * i + 1], c * d.y);
-    atomicAdd(&s_f[3 * i + 2], c * d.z);
-    atomicAdd(&s_f[3 * j], -c * d.x);
-    atomicAdd(&s_f[3 * j + 1], -c * d.y);
-    atomicAdd(&s_f[3 * j + 2], -c * d.z);
-    e += em + pr.qq * ir;
+  const int n = tv.natoms[t], ab = tv.atom_off[t];
+  // Nonbonded pairs: every unordered pair {i, (i + d) mod n} once, for
+  // d = 1 .. n/2 (for even n the pairs at d = n/2 only from i < n/2).  The
+  // lane owns atom i = lane + 32a and keeps its position, parameters,
+  // exclusion words and force in registers.  At a given d the partners j
+  // of the lanes are distinct, so each lane adds the partner's force to
+  // s_f[j] with a plain read-modify-write; the warp synchronises between
+  // values of d (two values of d are evaluated together, their writes
+  // separated).  Lanes without a pair at a d (beyond n, excluded, or
+  // counted by the other atom) take part with a zero force.
+  const int dmax = n / 2;
+  for (int i0 = 0; i0 < n; i0 += 32) {
+    const int i = i0 + lane;
+    const bool own = i < n;
+    const int ii = own ? i : 0;
+    const float3 xi = ld3(s_x, ii);
+    const float4 pi = s_nb[ii];
+    const uint32_t* ex = tv.excl + 4 * (size_t)(ab + ii);
+    const uint32_t w0 = __ldg(&ex[0]), w1 = __ldg(&ex[1]), w2 = __ldg(&ex[2]), w3 = __ldg(&ex[3]);
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    for (int d = 1; d <= dmax; d += 2) {
+      const bool two = d + 1 <= dmax;
+      int ja = ii + d, jb = ii + d + 1;
+      if (ja >= n) ja -= n;
+      if (jb >= n) jb -= n;
+      const bool acta = own && !(2 * d == n && i >= d) && !((pick4(w0, w1, w2, w3, ja >> 5) >> (ja & 31)) & 1u);
+      const bool actb = two && own && !(2 * (d + 1) == n && i >= d + 1) &&
+                        !((pick4(w0, w1, w2, w3, jb >> 5) >> (jb & 31)) & 1u);
+      const float3 da = sub3(xi, ld3(s_x, ja)), db = sub3(xi, ld3(s_x, jb));
+      float ca, ea, cb, eb;
+      nb_pair(da, pi, s_nb[ja], alpha, ca, ea);
+      nb_pair(db, pi, s_nb[jb], alpha, cb, eb);
+      ca = acta ? ca : 0.f;
+      cb = actb ? cb : 0.f;
+      e += (acta ? ea : 0.f) + (actb ? eb : 0.f);
+      fx = fmaf(ca, da.x, fmaf(cb, db.x, fx));
+      fy = fmaf(ca, da.y, fmaf(cb, db.y, fy));
+      fz = fmaf(ca, da.z, fmaf(cb, db.z, fz));
+      if (own) {
+        s_f[3 * ja] -= ca * da.x;
+        s_f[3 * ja + 1] -= ca * da.y;
+        s_f[3 * ja + 2] -= ca * da.z;
+      }
+      __syncwarp();
+      if (own && two) {
+        s_f[3 * jb] -= cb * db.x;
+        s_f[3 * jb + 1] -= cb * db.y;
+        s_f[3 * jb + 2] -= cb * db.z;
+      }
+      __syncwarp();
+    }
+    if (own) {
+      s_f[3 * i] += fx;
+      s_f[3 * i + 1] += fy;
+      s_f[3 * i + 2] += fz;
+    }
+    __syncwarp();
   }
+  // Bonded terms (few per atom): lanes take terms round-robin and add the
+  // forces with shared-memory atomics.
   for (int b = tv.ub_off[t] + lane; b < tv.ub_off[t + 1]; b += 32) {
     const BondTerm B = tv.ub[b];
     const float3 d = sub3(ld3(s_x, B.i), ld3(s_x, B.j));
@@ -526,7 +589,8 @@ __device__ float intra_terms(const TemplateView& tv, int t, int lane, const floa
 template <class Acc = double>
 __device__ __forceinline__ Acc flex_forces_terms(const GridView& g, bool use_grid, bool use_intra,
                                                  const TemplateView& tv, int t, int ab, int n, int lane,
-                                                 WarpState& s, int& flags, const StencilCache& sc) {
+                                                 WarpState& s, int& flags, const StencilCache& sc,
+                                                 const float4* s_nb) {
   __syncwarp();
   const int quad = lane >> 2, q = lane & 3;
   Acc e = Acc(0);
@@ -553,7 +617,7 @@ __device__ __forceinline__ Acc flex_forces_terms(const GridView& g, bool use_gri
     }
   }
   __syncwarp();
-  if (use_intra) e += (Acc)intra_terms(tv, t, lane, s.x, s.f);
+  if (use_intra) e += (Acc)intra_terms(tv, t, lane, s.x, s.f, s_nb);
   __syncwarp();
   return e;
 }
@@ -870,7 +934,7 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
         const bool miss = cl.inside && sc.key[i < S ? i : 0] != key;
         // refill the missing stencils, W/4 atoms at a time (one per quad)
         unsigned msub = __ballot_sync(kFull, miss);
-        if (W < 32) msub = (msub >> (sw * W)) & ((1u << W) - 1u);
+        if constexpr (W < 32) msub = (msub >> (sw * W)) & ((1u << (W & 31)) - 1u);
         while (__any_sync(kFull, msub != 0)) {
           const int qd = l >> 2, qq = l & 3;
           unsigned m = msub;
@@ -1138,8 +1202,11 @@ relax_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
 // cost order (order != nullptr) or statically (order == nullptr).  Same
 // iteration as relax_flex_kernel.
 // ---------------------------------------------------------------------------
+#ifndef GRIDFF_FLEX_WARPS_PER_SM
+#define GRIDFF_FLEX_WARPS_PER_SM 32    // register budget: 65536 / (32 * 32) = 64 per thread
+#endif
 template <int WPB>
-__global__ void __launch_bounds__(32 * WPB, 16 / WPB)
+__global__ void __launch_bounds__(32 * WPB, GRIDFF_FLEX_WARPS_PER_SM / WPB)
 relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
                         const int* __restrict__ rep_off, const int* __restrict__ order, int n_rep, float* xs,
                         float* vs, float* fdt, float* falpha, int* fnp, int* status, int* steps, double* energy,
@@ -1148,7 +1215,14 @@ relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   WarpState& s = s_all[wib];
-  const StencilCache sc = warp_cache(dyn_smem, S, wib);
+  // per-warp dynamic shared memory: stencil cache, then the template's
+  // nonbonded parameters {q, R, eps, 0}
+  unsigned char* wbase = dyn_smem + (size_t)wib * flex_terms_warp_bytes(S);
+  StencilCache sc;
+  sc.val = (float4*)wbase;
+  sc.key = (int*)(wbase + (size_t)S * 256);
+  sc.S = S;
+  float4* s_nb = (float4*)(wbase + cache_bytes(S));
   const int warp = blockIdx.x * WPB + wib;
   const int n_warps = gridDim.x * WPB;
   const unsigned long long t0 = gtimer();
@@ -1167,6 +1241,7 @@ relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep
       s.x[m] = xs[3 * (size_t)off + m];
       s.v[m] = vs[3 * (size_t)off + m];
     }
+    for (int i = lane; i < n; i += 32) s_nb[i] = __ldg(&tv.nb[ab + i]);
     float dt = fdt[r], al = falpha[r];
     int np = fnp[r], st = status[r], evals = 0;
     float elane = 0.f;
@@ -1180,7 +1255,7 @@ relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep
         }
       }
       int flags = 0;
-      const float e = flex_forces_terms<float>(g, use_grid, use_intra, tv, t, ab, n, lane, s, flags, sc);
+      const float e = flex_forces_terms<float>(g, use_grid, use_intra, tv, t, ab, n, lane, s, flags, sc, s_nb);
       float f2 = 0.f, P = 0.f, v2 = 0.f;
       for (int m = lane; m < 3 * n; m += 32) {
         float f = s.f[m], v = s.v[m];
@@ -1593,7 +1668,7 @@ KernelShape shape_of(const gridff_replicas* R, const LaunchCfg& c) {
       return {(const void*)relax_flex_kernel, kThreads, kWarpsPerBlock, cache_bytes(c.S) * kWarpsPerBlock};
     case GRIDFF_KERNEL_FLEX_TERMS:
       if (R->rigid || (c.wpb != 2 && c.wpb != 4 && c.wpb != 8)) return k;
-      return {flex_terms_ptr(c.wpb), 32 * c.wpb, c.wpb, cache_bytes(c.S) * c.wpb};
+      return {flex_terms_ptr(c.wpb), 32 * c.wpb, c.wpb, flex_terms_warp_bytes(c.S) * c.wpb};
     default:
       return k;
   }
@@ -1631,9 +1706,12 @@ LaunchCfg default_launch_cfg(const gridff_replicas* R, bool use_grid) {
       c.S = cache_slots(R, true);
     }
   } else {
-    c.kernel = GRIDFF_KERNEL_FLEX_QUAD;
-    c.wpb = kWarpsPerBlock;
-    c.S = cache_slots(R, false);
+    // measured on 16384 replicas of 10-120 atoms: the unique-term kernel
+    // with the work queue and no stencil staging is fastest
+    c.kernel = GRIDFF_KERNEL_FLEX_TERMS;
+    c.wpb = 8;
+    c.S = 0;
+    c.queue = 1;
   }
   return c;
 }
@@ -1651,6 +1729,13 @@ gridff_status prepare_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_rep
   if (c.S < 0 || c.S > GRIDFF_MAX_ATOMS) return set_err(ctx, GRIDFF_EINVAL, "cache slots %d", c.S);
   if (c.kernel == GRIDFF_KERNEL_RIGID_SUBWARP && (flags & GRIDFF_NO_GRID))
     return set_err(ctx, GRIDFF_EINVAL, "the sub-warp rigid kernel needs the grid term");
+  cudaFuncAttributes fa{};
+  GRIDFF_CUDA(ctx, cudaFuncGetAttributes(&fa, k.fn));
+  int optin = 0;
+  GRIDFF_CUDA(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+  if (fa.sharedSizeBytes + k.dyn > (size_t)optin)
+    return set_err(ctx, GRIDFF_EINVAL, "launch configuration needs %zu B of shared memory per block (limit %d)",
+                   fa.sharedSizeBytes + k.dyn, optin);
   GRIDFF_CUDA(ctx, set_dyn_smem(k.fn, k.dyn));
   int per_sm = 0;
   GRIDFF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, k.threads, k.dyn));

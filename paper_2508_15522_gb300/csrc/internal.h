@@ -82,11 +82,7 @@ struct BondRec { int j; int own; float k; float r0; };   // own: count the energ
 struct AngleRec { int a, b, c, role; float k, cos0, pad0, pad1; };
 struct TorsionRec { int a, b, c, d; int role; int n; float V, cn0; };
 
-// Unique-term lists (each term once; forces scattered with shared-memory
-// atomics).  Nonbonded pairs i < j more than two bonds apart, ordered by
-// j - i then i (consecutive lanes touch distinct atoms), with the pair's
-// mixed parameters precomputed.
-struct PairRec { uint32_t ij; float R; float ee; float qq; };   // ij = i | j << 16; R = R_i + R_j
+// Unique bond (each bond once).
 struct BondTerm { int i, j; float k, r0; };
 
 // Molecule templates as the kernels see them (all device pointers).
@@ -103,8 +99,6 @@ struct TemplateView {
   const AngleRec* angles;
   const int* tors_off;      // [A+1]
   const TorsionRec* tors;
-  const int* pair_off;      // [T+1] nonbonded pair list per template
-  const PairRec* pairs;
   const int* ub_off;        // [T+1] unique bonds
   const BondTerm* ub;
   const int* ua_off;        // [T+1] unique angles (AngleRec, role unused)

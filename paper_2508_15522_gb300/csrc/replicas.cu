@@ -76,8 +76,7 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
   std::vector<BondRec> bonds;
   std::vector<AngleRec> angles;
   std::vector<TorsionRec> tors;
-  std::vector<int> pair_off(1, 0), ub_off(1, 0), ua_off(1, 0), ut_off(1, 0);
-  std::vector<PairRec> pairs;
+  std::vector<int> ub_off(1, 0), ua_off(1, 0), ut_off(1, 0);
   std::vector<BondTerm> ub;
   std::vector<AngleRec> ua;
   std::vector<TorsionRec> ut;
@@ -102,6 +101,9 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
       adj[i].push_back(j);
       adj[j].push_back(i);
     }
+    std::vector<BondTerm> tub;
+    std::vector<AngleRec> tua;
+    std::vector<TorsionRec> tut;
     std::vector<std::vector<BondRec>> pb(n);
     std::vector<std::vector<AngleRec>> pa(n);
     std::vector<std::vector<TorsionRec>> pt(n);
@@ -119,10 +121,10 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
           return set_err(ctx, GRIDFF_EINVAL, "template %d: angle %d repeats an atom", t, a);
         for (int role = 0; role < 3; ++role)
           pa[A[role]].push_back(AngleRec{A[0], A[1], A[2], role, m.angle_k[a], m.angle_cos0[a], 0, 0});
-        ua.push_back(AngleRec{A[0], A[1], A[2], 0, m.angle_k[a], m.angle_cos0[a], 0, 0});
+        tua.push_back(AngleRec{A[0], A[1], A[2], 0, m.angle_k[a], m.angle_cos0[a], 0, 0});
       }
       for (int b = 0; b < m.n_bonds; ++b)
-        ub.push_back(BondTerm{m.bonds[2 * b], m.bonds[2 * b + 1], m.bond_k[b], m.bond_r0[b]});
+        tub.push_back(BondTerm{m.bonds[2 * b], m.bonds[2 * b + 1], m.bond_k[b], m.bond_r0[b]});
       for (int a = 0; a < m.n_torsions; ++a) {
         const int* A = m.torsions + 4 * a;
         for (int k = 0; k < 4; ++k)
@@ -130,10 +132,13 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
         for (int role = 0; role < 4; ++role)
           pt[A[role]].push_back(TorsionRec{A[0], A[1], A[2], A[3], role, m.torsion_n[a],
                                            m.torsion_V[a], m.torsion_cos_nphi0[a]});
-        ut.push_back(TorsionRec{A[0], A[1], A[2], A[3], 0, m.torsion_n[a], m.torsion_V[a],
+        tut.push_back(TorsionRec{A[0], A[1], A[2], A[3], 0, m.torsion_n[a], m.torsion_V[a],
                                 m.torsion_cos_nphi0[a]});
       }
     }
+    ub.insert(ub.end(), tub.begin(), tub.end());
+    ua.insert(ua.end(), tua.begin(), tua.end());
+    ut.insert(ut.end(), tut.begin(), tut.end());
     ub_off.push_back((int)ub.size());
     ua_off.push_back((int)ua.size());
     ut_off.push_back((int)ut.size());
@@ -188,21 +193,11 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
         if (depth[j] >= 0) w[j >> 5] |= 1u << (j & 31);
       for (int k = 0; k < 4; ++k) excl.push_back(w[k]);
     }
-    // nonbonded pair list (flexible only), diagonal order
-    const size_t ex0 = excl.size() - 4 * (size_t)n;
-    if (!rigid)
-      for (int d = 1; d < n; ++d)
-        for (int i = 0; i + d < n; ++i) {
-          const int j = i + d;
-          if ((excl[ex0 + 4 * i + (j >> 5)] >> (j & 31)) & 1u) continue;
-          pairs.push_back(PairRec{(uint32_t)i | ((uint32_t)j << 16), m.R[i] + m.R[j], m.eps[i] * m.eps[j],
-                                  GRIDFF_KE * m.q[i] * m.q[j]});
-        }
-    pair_off.push_back((int)pairs.size());
-    // relative cost of one force evaluation (work-queue order): grid per
-    // atom plus intramolecular terms
-    tmpl_cost[t] = 8.0 * n + (pair_off[t + 1] - pair_off[t]) + 2.0 * (ub_off[t + 1] - ub_off[t]) +
-                   3.0 * (ua_off[t + 1] - ua_off[t]) + 6.0 * (ut_off[t + 1] - ut_off[t]);
+    // relative cost of one force evaluation (work-queue order): grid quad
+    // rounds, nonbonded pair steps, bonded terms per lane
+    const double pair_steps = rigid ? 0.0 : (double)((n + 31) / 32) * (n / 2);
+    tmpl_cost[t] = 3.0 * ((n + 7) / 8) + pair_steps + 2.0 * (ub_off[t + 1] - ub_off[t]) / 32.0 +
+                   3.0 * (ua_off[t + 1] - ua_off[t]) / 32.0 + 6.0 * (ut_off[t + 1] - ut_off[t]) / 32.0;
     for (int i = 0; i < n; ++i) {
       double R = m.R[i], eps = m.eps[i];
       body.push_back(make_float4(m.xyz[3 * i], m.xyz[3 * i + 1], m.xyz[3 * i + 2], m.mass[i]));
@@ -235,8 +230,7 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
          o_par = push(blob, par), o_nb = push(blob, nb), o_ex = push(blob, excl),
          o_boff = push(blob, bond_off), o_b = push(blob, bonds), o_aof = push(blob, angle_off),
          o_a = push(blob, angles), o_tof = push(blob, tors_off), o_t = push(blob, tors),
-         o_rig = push(blob, rig), o_rmax = push(blob, rmax), o_poff = push(blob, pair_off),
-         o_p = push(blob, pairs), o_ubo = push(blob, ub_off), o_ub = push(blob, ub), o_uao = push(blob, ua_off),
+         o_rig = push(blob, rig), o_rmax = push(blob, rmax), o_ubo = push(blob, ub_off), o_ub = push(blob, ub), o_uao = push(blob, ua_off),
          o_ua = push(blob, ua), o_uto = push(blob, ut_off), o_ut = push(blob, ut), o_ord = push(blob, order);
   gridff_replicas* R = new gridff_replicas();
   R->ctx = ctx;
@@ -269,8 +263,6 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
   R->tv.tors = (const TorsionRec*)(B + o_t);
   R->tv.rigid = (const float4*)(B + o_rig);
   R->tv.rmax = (const float*)(B + o_rmax);
-  R->tv.pair_off = (const int*)(B + o_poff);
-  R->tv.pairs = (const PairRec*)(B + o_p);
   R->tv.ub_off = (const int*)(B + o_ubo);
   R->tv.ub = (const BondTerm*)(B + o_ub);
   R->tv.ua_off = (const int*)(B + o_uao);

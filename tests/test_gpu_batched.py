@@ -85,6 +85,7 @@ def refs(field, uneven):
 
 LAYOUTS = [dict(kernel=3, warps_per_block=w, cache_slots=S, queue=q)
            for w, S, q in ((2, 0, 1), (4, 32, 1), (8, 64, 0), (4, 70, 0), (8, 16, 1))]
+LAYOUTS += [dict(kernel=2, warps_per_block=4, cache_slots=S, queue=0) for S in (0, 48)]
 TOL = {1: 2e-6, 5: 2e-5, 20: 2e-4}
 
 
@@ -104,7 +105,8 @@ def _relax_and_compare(G, ctx, grid, mols, tof, x0, ref, configure):
         reps.close()
 
 
-@pytest.mark.parametrize("layout", LAYOUTS, ids=lambda d: "w{warps_per_block}-S{cache_slots}-q{queue}".format(**d))
+@pytest.mark.parametrize("layout", LAYOUTS,
+                         ids=lambda d: "k{kernel}-w{warps_per_block}-S{cache_slots}-q{queue}".format(**d))
 def test_flex_terms_layouts_match_oracle(G, ctx, field, uneven, refs, layout):
     mols, tof = uneven
     x0, ref = refs
