@@ -849,10 +849,12 @@ relax_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl
 // of each run, and store the channel-combined node values); then every lane
 // contracts its own atom's 64 cached values (16 z passes, 4 y, 1 x) with
 // no work repeated across lanes.  Cache layout of a replica (S >= atoms
-// slots): float4 m = 4a + b (the (x, y) run a, b) holds the run's 4 z-nodes
-// and sits at index m * S + i.
+// slots): the 16 (x, y) runs (a, b) form 8 pairs p = 2a + (b >> 1); float4
+// 2p + h of atom i (index (2p + h) * S + i) holds z-nodes 2h and 2h + 1 of
+// the pair's two runs interleaved, (A_2h, B_2h, A_2h+1, B_2h+1), so the
+// contraction runs on paired FP32 FMAs.
 // ---------------------------------------------------------------------------
-template <int W, int WPB, int MINB>
+template <int W, int R, int WPB, int MINB>
 __global__ void __launch_bounds__(32 * WPB, MINB)
 relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, int n_rep,
                       float* pose, float* vel, float* fdt, float* falpha, int* fnp, int* status,
@@ -892,9 +894,20 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
       np = fnp[r];
       st = status[r];
     }
+    // this lane's atoms i = k W + l, k < R (R W >= atoms): body coordinates
+    // and grid factors stay in registers for the whole relaxation
+    float4 bk[R], pk[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int i = k * W + l;
+      bk[k] = pk[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (valid && i < n) {
+        bk[k] = __ldg(&tv.body[ab + i]);
+        pk[k] = __ldg(&tv.par[ab + i]);
+      }
+    }
     for (int i = l; i < S; i += W) sc.key[i] = -1;
     __syncwarp();
-    const int rounds = __reduce_max_sync(kFull, (n + W - 1) / W);
     float elane = 0.f;
     bool done = !valid;
     for (int it = 0; it < nsteps; ++it) {
@@ -918,21 +931,20 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
       float Ft[3] = {0.f, 0.f, 0.f}, tq[3] = {0.f, 0.f, 0.f};
       float e = 0.f;
       int flags = 0;
-      for (int k = 0; k < rounds; ++k) {
+      // locate every atom of the lane and refill the stencils that changed
+      // cell, W/4 atoms at a time (one per quad)
+      Cell cl[R];
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
         const int i = k * W + l;
         const bool act = run && i < n;
-        float4 b = make_float4(0.f, 0.f, 0.f, 0.f), par = b;
-        if (act) {
-          b = __ldg(&tv.body[ab + i]);
-          par = __ldg(&tv.par[ab + i]);
-        }
+        const float4 b = bk[k];
         const float px = Rm[0] * b.x + Rm[1] * b.y + Rm[2] * b.z + c[0];
         const float py = Rm[3] * b.x + Rm[4] * b.y + Rm[5] * b.z + c[1];
         const float pz = Rm[6] * b.x + Rm[7] * b.y + Rm[8] * b.z + c[2];
-        const Cell cl = locate(g, act, px, py, pz, flags);
-        const int key = (cl.ix * g.ny + cl.iy) * g.nz + cl.iz;
-        const bool miss = cl.inside && sc.key[i < S ? i : 0] != key;
-        // refill the missing stencils, W/4 atoms at a time (one per quad)
+        cl[k] = locate(g, act, px, py, pz, flags);
+        const int key = (cl[k].ix * g.ny + cl[k].iy) * g.nz + cl[k].iz;
+        const bool miss = cl[k].inside && sc.key[i < S ? i : 0] != key;
         unsigned msub = __ballot_sync(kFull, miss);
         if constexpr (W < 32) msub = (msub >> (sw * W)) & ((1u << (W & 31)) - 1u);
         while (__any_sync(kFull, msub != 0)) {
@@ -941,47 +953,79 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
           for (int j = 0; j < qd && m; ++j) m &= m - 1;
           const int owner = m ? __ffs(m) - 1 : -1;
           const int src = sw * W + (owner < 0 ? 0 : owner);
-          const int oix = __shfl_sync(kFull, cl.ix, src), oiy = __shfl_sync(kFull, cl.iy, src);
-          const int oiz = __shfl_sync(kFull, cl.iz, src), okey = __shfl_sync(kFull, key, src);
-          const float oQ = __shfl_sync(kFull, par.x, src), oP = __shfl_sync(kFull, par.y, src);
-          const float oL = __shfl_sync(kFull, par.z, src);
+          const int oix = __shfl_sync(kFull, cl[k].ix, src), oiy = __shfl_sync(kFull, cl[k].iy, src);
+          const int oiz = __shfl_sync(kFull, cl[k].iz, src), okey = __shfl_sync(kFull, key, src);
+          const float oQ = __shfl_sync(kFull, pk[k].x, src), oP = __shfl_sync(kFull, pk[k].y, src);
+          const float oL = __shfl_sync(kFull, pk[k].z, src);
           if (owner >= 0) {
             const int slot = k * W + owner;
             const float4* p0 = g.rec + ((long long)oix * g.nyp + oiy) * g.nzp + oiz + qq;
             float4 rr[16];
 #pragma unroll
             for (int mm = 0; mm < 16; ++mm) rr[mm] = __ldg(p0 + (mm >> 2) * g.sx + (mm & 3) * g.nzp);
+            // run mm = 4a + b, z-node qq goes to float4 2p + (qq >> 1) of
+            // run pair p = 2a + (b >> 1), component 2 (qq & 1) + (b & 1)
 #pragma unroll
-            for (int mm = 0; mm < 16; ++mm)
-              cval[((size_t)mm * S + slot) * 4 + qq] = fmaf(oQ, rr[mm].x, fmaf(oP, rr[mm].y, oL * rr[mm].z));
+            for (int mm = 0; mm < 16; ++mm) {
+              const int a = mm >> 2, bq = mm & 3;
+              const int f4 = 2 * (2 * a + (bq >> 1)) + (qq >> 1);
+              cval[((size_t)f4 * S + slot) * 4 + 2 * (qq & 1) + (bq & 1)] =
+                  fmaf(oQ, rr[mm].x, fmaf(oP, rr[mm].y, oL * rr[mm].z));
+            }
             if (qq == 0) sc.key[slot] = okey;
           }
           for (int j = 0; j < W / 4 && msub; ++j) msub &= msub - 1;
         }
-        __syncwarp();
-        if (cl.inside) {
+      }
+      __syncwarp();
+      // contract every atom of the lane (independent chains)
+#pragma unroll
+      for (int k = 0; k < R; ++k) {
+        const int i = k * W + l;
+        if (cl[k].inside) {
           float wx[4], dwx[4], wy[4], dwy[4], wz[4], dwz[4];
-          bspline_weights(cl.tx, wx, dwx);
-          bspline_weights(cl.ty, wy, dwy);
-          bspline_weights(cl.tz, wz, dwz);
+          bspline_weights(cl[k].tx, wx, dwx);
+          bspline_weights(cl[k].ty, wy, dwy);
+          bspline_weights(cl[k].tz, wz, dwz);
+          // two (x, y) runs at a time with paired FP32 FMAs: the cache
+          // holds run pairs interleaved, so (run A, run B) values of one
+          // z-node form an operand pair
+          float2 WZ[4], DZ[4];
+#pragma unroll
+          for (int cz = 0; cz < 4; ++cz) {
+            WZ[cz] = make_float2(wz[cz], wz[cz]);
+            DZ[cz] = make_float2(dwz[cz], dwz[cz]);
+          }
           float ev = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
-            float sv = 0.f, sy = 0.f, sz = 0.f;
+            float2 yv = make_float2(0.f, 0.f), yy = yv, yz = yv;
 #pragma unroll
-            for (int bb = 0; bb < 4; ++bb) {
-              const float4 rr = sc.val[(4 * a + bb) * S + i];
-              const float zv = fmaf(wz[0], rr.x, fmaf(wz[1], rr.y, fmaf(wz[2], rr.z, wz[3] * rr.w)));
-              const float zd = fmaf(dwz[0], rr.x, fmaf(dwz[1], rr.y, fmaf(dwz[2], rr.z, dwz[3] * rr.w)));
-              sv = fmaf(wy[bb], zv, sv);
-              sy = fmaf(dwy[bb], zv, sy);
-              sz = fmaf(wy[bb], zd, sz);
+            for (int pb = 0; pb < 2; ++pb) {
+              const int pr = 2 * a + pb;
+              const float4 F0 = sc.val[(2 * pr) * S + i], F1 = sc.val[(2 * pr + 1) * S + i];
+              const float2 z0 = make_float2(F0.x, F0.y), z1 = make_float2(F0.z, F0.w);
+              const float2 z2 = make_float2(F1.x, F1.y), z3 = make_float2(F1.z, F1.w);
+              float2 zv = __fmul2_rn(WZ[3], z3), zd = __fmul2_rn(DZ[3], z3);
+              zv = __ffma2_rn(WZ[2], z2, zv);
+              zd = __ffma2_rn(DZ[2], z2, zd);
+              zv = __ffma2_rn(WZ[1], z1, zv);
+              zd = __ffma2_rn(DZ[1], z1, zd);
+              zv = __ffma2_rn(WZ[0], z0, zv);
+              zd = __ffma2_rn(DZ[0], z0, zd);
+              const float2 WY = make_float2(wy[2 * pb], wy[2 * pb + 1]);
+              const float2 DY = make_float2(dwy[2 * pb], dwy[2 * pb + 1]);
+              yv = __ffma2_rn(WY, zv, yv);
+              yy = __ffma2_rn(DY, zv, yy);
+              yz = __ffma2_rn(WY, zd, yz);
             }
+            const float sv = yv.x + yv.y, sy = yy.x + yy.y, sz = yz.x + yz.y;
             ev = fmaf(wx[a], sv, ev);
             gx = fmaf(dwx[a], sv, gx);
             gy = fmaf(wx[a], sy, gy);
             gz = fmaf(wx[a], sz, gz);
           }
+          const float4 b = bk[k];
           const float fx = -gx * g.inv_dx, fy = -gy * g.inv_dy, fz = -gz * g.inv_dz;
           e += ev;
           Ft[0] += fx;
@@ -1593,7 +1637,7 @@ int rigid_subwarp_width(const gridff_replicas* R) {
   if (GRIDFF_RIGID_SUBWARP >= 0) return GRIDFF_RIGID_SUBWARP;
   const int n = R->max_natoms;
   const int W = n <= 12 ? 8 : n <= 48 ? 16 : 32;
-  return cache_bytes(n) * kSwWarps * (32 / W) <= 200 * 1024 ? W : 0;
+  return cache_bytes(n) * kSwWarps * (32 / W) <= 200 * 1024 && (n + W - 1) / W <= 4 ? W : 0;
 }
 
 // Allow `bytes` of dynamic shared memory (needed whenever static plus
@@ -1635,11 +1679,20 @@ __global__ void fire_reset_kernel(int n, float dt0, float a0, float* dt, float* 
   steps[r] = 0;
 }
 
-const void* rigid_sw_ptr(int W) {
-  return W == 8 ? (const void*)relax_rigid_sw_kernel<8, kSwWarps, kSwMinBlocks>
-       : W == 16 ? (const void*)relax_rigid_sw_kernel<16, kSwWarps, kSwMinBlocks>
-                 : (const void*)relax_rigid_sw_kernel<32, kSwWarps, kSwMinBlocks>;
+using SwFn = void (*)(GridView, TemplateView, const int*, int, float*, float*, float*, float*, int*, int*, int*,
+                     double*, int, FireP, Control, int);
+
+// Sub-warp rigid kernel for W lanes per replica and R atoms per lane.
+SwFn rigid_sw_fn(int W, int R) {
+#define GRIDFF_SW(w, r) \
+  if (W == w && R == r) return relax_rigid_sw_kernel<w, r, kSwWarps, kSwMinBlocks>;
+  GRIDFF_SW(8, 1) GRIDFF_SW(8, 2) GRIDFF_SW(8, 3) GRIDFF_SW(8, 4)
+  GRIDFF_SW(16, 1) GRIDFF_SW(16, 2) GRIDFF_SW(16, 3) GRIDFF_SW(16, 4)
+  GRIDFF_SW(32, 1) GRIDFF_SW(32, 2) GRIDFF_SW(32, 3) GRIDFF_SW(32, 4)
+#undef GRIDFF_SW
+  return nullptr;
 }
+int sw_rounds(const gridff_replicas* R, int W) { return (R->max_natoms + W - 1) / W; }
 const void* flex_terms_ptr(int wpb) {
   return wpb == 2 ? (const void*)relax_flex_terms_kernel<2>
        : wpb == 8 ? (const void*)relax_flex_terms_kernel<8> : (const void*)relax_flex_terms_kernel<4>;
@@ -1657,9 +1710,12 @@ struct KernelShape {
 KernelShape shape_of(const gridff_replicas* R, const LaunchCfg& c) {
   KernelShape k{nullptr, 0, 0, 0};
   switch (c.kernel) {
-    case GRIDFF_KERNEL_RIGID_SUBWARP:
+    case GRIDFF_KERNEL_RIGID_SUBWARP: {
       if (!R->rigid || (c.W != 8 && c.W != 16 && c.W != 32) || c.S < R->max_natoms) return k;
-      return {rigid_sw_ptr(c.W), 32 * kSwWarps, kSwWarps * (32 / c.W), cache_bytes(c.S) * kSwWarps * (32 / c.W)};
+      const SwFn fn = rigid_sw_fn(c.W, sw_rounds(R, c.W));
+      if (!fn) return k;
+      return {(const void*)fn, 32 * kSwWarps, kSwWarps * (32 / c.W), cache_bytes(c.S) * kSwWarps * (32 / c.W)};
+    }
     case GRIDFF_KERNEL_RIGID_QUAD:
       if (!R->rigid || c.wpb != kWarpsPerBlock) return k;
       return {(const void*)relax_rigid_kernel, kThreads, kWarpsPerBlock, cache_bytes(c.S) * kWarpsPerBlock};
@@ -1819,18 +1875,9 @@ gridff_status enqueue_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_rep
   cudaError_t e = cudaSuccess;
   switch (c.kernel) {
     case GRIDFF_KERNEL_RIGID_SUBWARP:
-      if (c.W == 8)
-        e = launch_ex(relax_rigid_sw_kernel<8, kSwWarps, kSwMinBlocks>, blocks, k.threads, k.dyn, s, wp, gv, R->tv,
-                      (const int*)R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha, R->fire_nplus,
-                      R->status, R->steps, R->energy, nsteps, fp, ctl, c.S);
-      else if (c.W == 16)
-        e = launch_ex(relax_rigid_sw_kernel<16, kSwWarps, kSwMinBlocks>, blocks, k.threads, k.dyn, s, wp, gv,
-                      R->tv, (const int*)R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha,
-                      R->fire_nplus, R->status, R->steps, R->energy, nsteps, fp, ctl, c.S);
-      else
-        e = launch_ex(relax_rigid_sw_kernel<32, kSwWarps, kSwMinBlocks>, blocks, k.threads, k.dyn, s, wp, gv,
-                      R->tv, (const int*)R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha,
-                      R->fire_nplus, R->status, R->steps, R->energy, nsteps, fp, ctl, c.S);
+      e = launch_ex(rigid_sw_fn(c.W, sw_rounds(R, c.W)), blocks, k.threads, k.dyn, s, wp, gv, R->tv,
+                    (const int*)R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha, R->fire_nplus,
+                    R->status, R->steps, R->energy, nsteps, fp, ctl, c.S);
       break;
     case GRIDFF_KERNEL_RIGID_QUAD:
       e = launch_ex(relax_rigid_kernel, blocks, k.threads, k.dyn, s, wp, gv, R->tv, (const int*)R->rep_tmpl,
