@@ -84,8 +84,16 @@ typedef enum {
 #define GRIDFF_CH_P 2            /* Pauli V^P */
 #define GRIDFF_CH_L 4            /* London V^L */
 
-/* coefficient storage */
-#define GRIDFF_STORE_F32 0       /* float32, one 16-byte record {C, P, L, 0} per node */
+/* coefficient storage (precision tiers).  A grid with the Coulomb channel
+ * stores 4 slots {C, P, L, 0} per node, a grid without it 2 slots {P, L}.
+ * FP16 / BF16 hold coefficient / s_ch, s_ch = 2^(e - 15) with
+ * max |coefficient of the channel| < 2^e (so |value| < 2^15), rounded to
+ * the nearest FP16 / BF16 number (ties to even) from the FP64 coefficient;
+ * the kernels multiply by s_ch in FP32.  Interpolation, forces and the
+ * channel combination stay FP32 for every tier. */
+#define GRIDFF_STORE_F32 0       /* float32: 16 (4 slots) or 8 (2 slots) bytes per node */
+#define GRIDFF_STORE_F16 1       /* IEEE half: 8 or 4 bytes per node, per-channel scale */
+#define GRIDFF_STORE_BF16 2      /* bfloat16: 8 or 4 bytes per node, per-channel scale */
 
 typedef struct gridff_ctx gridff_ctx;
 typedef struct gridff_grid gridff_grid;
@@ -186,6 +194,10 @@ gridff_status gridff_fit_coefs_noalloc(gridff_ctx* ctx, const double* values, do
 /* Grid metadata; any output pointer may be NULL. */
 gridff_status gridff_grid_info(const gridff_grid* grid, int32_t dims[3], double origin[3],
                                double spacing[3], int32_t* channels, size_t* device_bytes);
+
+/* Storage tier of the grid and its channel scales s_C, s_P, s_L (1 for
+ * FP32 and for absent channels). */
+gridff_status gridff_grid_storage(const gridff_grid* grid, int32_t* storage, float scales[3]);
 
 /* Copy FP64 node values (what = 0) or coefficients (what = 1), layout
  * [channel][ix][iy][iz], to a host array.  Needs keep_f64 at build time.

@@ -13,6 +13,9 @@
 
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "internal.h"
 
 namespace {
@@ -129,6 +132,70 @@ __device__ __forceinline__ Cell locate(const GridView& g, bool act, float x, flo
   return c;
 }
 
+// Channel-combined values c = Q C + P P + L L of the 16 (x, y) runs at one
+// z-node: records base + a sx + b nzp, run m = 4a + b, for the grid's record
+// kind (channel scales folded into the atom's factors; the branch is
+// uniform over the warp).
+// KIND >= 0: the record kind is known at compile time (no other code is
+// generated); KIND < 0: dispatch on g.kind.
+template <int KIND = -1>
+__device__ __forceinline__ void gather_runs(const GridView& g, long long base, float4 par, float cv[16]) {
+  const float fc = par.x * g.sC, fp = par.y * g.sP, fl = par.z * g.sL;
+  switch (KIND >= 0 ? KIND : g.kind) {
+    case REC_F32x4: {
+      const float4* p = (const float4*)g.rec + base;
+      float4 r[16];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) r[m] = __ldg(p + (m >> 2) * g.sx + (m & 3) * g.nzp);
+#pragma unroll
+      for (int m = 0; m < 16; ++m) cv[m] = fmaf(fc, r[m].x, fmaf(fp, r[m].y, fl * r[m].z));
+      break;
+    }
+    case REC_F32x2: {
+      const float2* p = (const float2*)g.rec + base;
+      float2 r[16];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) r[m] = __ldg(p + (m >> 2) * g.sx + (m & 3) * g.nzp);
+#pragma unroll
+      for (int m = 0; m < 16; ++m) cv[m] = fmaf(fp, r[m].x, fl * r[m].y);
+      break;
+    }
+    case REC_F16x4:
+    case REC_BF16x4: {
+      const uint2* p = (const uint2*)g.rec + base;
+      uint2 r[16];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) r[m] = __ldg(p + (m >> 2) * g.sx + (m & 3) * g.nzp);
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        float2 a, b;
+        if (g.kind == REC_F16x4) {
+          a = __half22float2(*reinterpret_cast<const __half2*>(&r[m].x));
+          b = __half22float2(*reinterpret_cast<const __half2*>(&r[m].y));
+        } else {
+          a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r[m].x));
+          b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r[m].y));
+        }
+        cv[m] = fmaf(fc, a.x, fmaf(fp, a.y, fl * b.x));
+      }
+      break;
+    }
+    default: {   // REC_F16x2, REC_BF16x2
+      const unsigned* p = (const unsigned*)g.rec + base;
+      unsigned r[16];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) r[m] = __ldg(p + (m >> 2) * g.sx + (m & 3) * g.nzp);
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const float2 a = g.kind == REC_F16x2 ? __half22float2(*reinterpret_cast<const __half2*>(&r[m]))
+                                             : __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r[m]));
+        cv[m] = fmaf(fp, a.x, fl * a.y);
+      }
+      break;
+    }
+  }
+}
+
 // Energy and force of one atom in the substrate field (Eqs. E, E_Coulomb,
 // E_Morse), evaluated by the 4 lanes of a quad (q = lane & 3); every lane of
 // the quad returns the full result.  Lane q gathers record q of each of
@@ -165,14 +232,7 @@ __device__ __forceinline__ void grid_quad(const GridView& g, int q, bool act, fl
         cv[4 * j + 3] = v.w;
       }
     } else {
-      const float4* p0 = g.rec + ((long long)cl.ix * g.nyp + cl.iy) * g.nzp + cl.iz + q;
-      float4 r[16];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) r[4 * a + b] = __ldg(p0 + a * g.sx + b * g.nzp);
-#pragma unroll
-      for (int j = 0; j < 16; ++j) cv[j] = fmaf(par.x, r[j].x, fmaf(par.y, r[j].y, par.z * r[j].z));
+      gather_runs(g, ((long long)cl.ix * g.nyp + cl.iy) * g.nzp + cl.iz + q, par, cv);
       if (cached) {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
@@ -854,7 +914,26 @@ relax_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl
 // the pair's two runs interleaved, (A_2h, B_2h, A_2h+1, B_2h+1), so the
 // contraction runs on paired FP32 FMAs.
 // ---------------------------------------------------------------------------
-template <int W, int R, int WPB, int MINB>
+// Element k (runtime, k < R) of a register array, by selects (no local
+// memory).
+template <int R, class T>
+__device__ __forceinline__ T pick_r(const T (&a)[R], int k) {
+  T v = a[0];
+#pragma unroll
+  for (int j = 1; j < R; ++j)
+    if (k == j) v = a[j];
+  return v;
+}
+template <int R>
+__device__ __forceinline__ int pick_cell(const Cell (&c)[R], int k, int axis) {
+  int v = axis == 0 ? c[0].ix : axis == 1 ? c[0].iy : c[0].iz;
+#pragma unroll
+  for (int j = 1; j < R; ++j)
+    if (k == j) v = axis == 0 ? c[j].ix : axis == 1 ? c[j].iy : c[j].iz;
+  return v;
+}
+
+template <int W, int R, int WPB, int MINB, int KIND>
 __global__ void __launch_bounds__(32 * WPB, MINB)
 relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, int n_rep,
                       float* pose, float* vel, float* fdt, float* falpha, int* fnp, int* status,
@@ -931,9 +1010,10 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
       float Ft[3] = {0.f, 0.f, 0.f}, tq[3] = {0.f, 0.f, 0.f};
       float e = 0.f;
       int flags = 0;
-      // locate every atom of the lane and refill the stencils that changed
-      // cell, W/4 atoms at a time (one per quad)
+      // locate every atom of the lane
       Cell cl[R];
+      int key[R];
+      unsigned miss_mask[R];
 #pragma unroll
       for (int k = 0; k < R; ++k) {
         const int i = k * W + l;
@@ -943,34 +1023,42 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
         const float py = Rm[3] * b.x + Rm[4] * b.y + Rm[5] * b.z + c[1];
         const float pz = Rm[6] * b.x + Rm[7] * b.y + Rm[8] * b.z + c[2];
         cl[k] = locate(g, act, px, py, pz, flags);
-        const int key = (cl[k].ix * g.ny + cl[k].iy) * g.nz + cl[k].iz;
-        const bool miss = cl[k].inside && sc.key[i < S ? i : 0] != key;
+        key[k] = (cl[k].ix * g.ny + cl[k].iy) * g.nz + cl[k].iz;
+        const bool miss = cl[k].inside && sc.key[i < S ? i : 0] != key[k];
         unsigned msub = __ballot_sync(kFull, miss);
         if constexpr (W < 32) msub = (msub >> (sw * W)) & ((1u << (W & 31)) - 1u);
+        miss_mask[k] = msub;
+      }
+      // refill the stencils that changed cell, W/4 atoms at a time (one per
+      // quad); one copy of the gather code for all rounds
+#pragma unroll 1
+      for (int k = 0; k < R; ++k) {
+        unsigned msub = pick_r<R>(miss_mask, k);
         while (__any_sync(kFull, msub != 0)) {
           const int qd = l >> 2, qq = l & 3;
           unsigned m = msub;
           for (int j = 0; j < qd && m; ++j) m &= m - 1;
           const int owner = m ? __ffs(m) - 1 : -1;
           const int src = sw * W + (owner < 0 ? 0 : owner);
-          const int oix = __shfl_sync(kFull, cl[k].ix, src), oiy = __shfl_sync(kFull, cl[k].iy, src);
-          const int oiz = __shfl_sync(kFull, cl[k].iz, src), okey = __shfl_sync(kFull, key, src);
-          const float oQ = __shfl_sync(kFull, pk[k].x, src), oP = __shfl_sync(kFull, pk[k].y, src);
-          const float oL = __shfl_sync(kFull, pk[k].z, src);
+          const int oix = __shfl_sync(kFull, pick_cell<R>(cl, k, 0), src);
+          const int oiy = __shfl_sync(kFull, pick_cell<R>(cl, k, 1), src);
+          const int oiz = __shfl_sync(kFull, pick_cell<R>(cl, k, 2), src);
+          const int okey = __shfl_sync(kFull, pick_r<R>(key, k), src);
+          const float4 pkk = pick_r<R>(pk, k);
+          const float oQ = __shfl_sync(kFull, pkk.x, src), oP = __shfl_sync(kFull, pkk.y, src);
+          const float oL = __shfl_sync(kFull, pkk.z, src);
           if (owner >= 0) {
             const int slot = k * W + owner;
-            const float4* p0 = g.rec + ((long long)oix * g.nyp + oiy) * g.nzp + oiz + qq;
-            float4 rr[16];
-#pragma unroll
-            for (int mm = 0; mm < 16; ++mm) rr[mm] = __ldg(p0 + (mm >> 2) * g.sx + (mm & 3) * g.nzp);
+            float cv[16];
+            gather_runs<KIND>(g, ((long long)oix * g.nyp + oiy) * g.nzp + oiz + qq, make_float4(oQ, oP, oL, 0.f),
+                              cv);
             // run mm = 4a + b, z-node qq goes to float4 2p + (qq >> 1) of
             // run pair p = 2a + (b >> 1), component 2 (qq & 1) + (b & 1)
 #pragma unroll
             for (int mm = 0; mm < 16; ++mm) {
               const int a = mm >> 2, bq = mm & 3;
               const int f4 = 2 * (2 * a + (bq >> 1)) + (qq >> 1);
-              cval[((size_t)f4 * S + slot) * 4 + 2 * (qq & 1) + (bq & 1)] =
-                  fmaf(oQ, rr[mm].x, fmaf(oP, rr[mm].y, oL * rr[mm].z));
+              cval[((size_t)f4 * S + slot) * 4 + 2 * (qq & 1) + (bq & 1)] = cv[mm];
             }
             if (qq == 0) sc.key[slot] = okey;
           }
@@ -1682,10 +1770,13 @@ __global__ void fire_reset_kernel(int n, float dt0, float a0, float* dt, float* 
 using SwFn = void (*)(GridView, TemplateView, const int*, int, float*, float*, float*, float*, int*, int*, int*,
                      double*, int, FireP, Control, int);
 
-// Sub-warp rigid kernel for W lanes per replica and R atoms per lane.
-SwFn rigid_sw_fn(int W, int R) {
-#define GRIDFF_SW(w, r) \
-  if (W == w && R == r) return relax_rigid_sw_kernel<w, r, kSwWarps, kSwMinBlocks>;
+// Sub-warp rigid kernel for W lanes per replica and R atoms per lane; FP32
+// four-slot grids get a build without the other record kinds' code.
+SwFn rigid_sw_fn(int W, int R, int kind) {
+#define GRIDFF_SW(w, r)                                                                     \
+  if (W == w && R == r)                                                                     \
+    return kind == REC_F32x4 ? relax_rigid_sw_kernel<w, r, kSwWarps, kSwMinBlocks, REC_F32x4> \
+                             : relax_rigid_sw_kernel<w, r, kSwWarps, kSwMinBlocks, -1>;
   GRIDFF_SW(8, 1) GRIDFF_SW(8, 2) GRIDFF_SW(8, 3) GRIDFF_SW(8, 4)
   GRIDFF_SW(16, 1) GRIDFF_SW(16, 2) GRIDFF_SW(16, 3) GRIDFF_SW(16, 4)
   GRIDFF_SW(32, 1) GRIDFF_SW(32, 2) GRIDFF_SW(32, 3) GRIDFF_SW(32, 4)
@@ -1707,12 +1798,12 @@ struct KernelShape {
 
 // Kernel, block shape and dynamic shared memory of configuration c, or
 // fn == nullptr when c does not apply to R.
-KernelShape shape_of(const gridff_replicas* R, const LaunchCfg& c) {
+KernelShape shape_of(const gridff_replicas* R, const LaunchCfg& c, int kind) {
   KernelShape k{nullptr, 0, 0, 0};
   switch (c.kernel) {
     case GRIDFF_KERNEL_RIGID_SUBWARP: {
       if (!R->rigid || (c.W != 8 && c.W != 16 && c.W != 32) || c.S < R->max_natoms) return k;
-      const SwFn fn = rigid_sw_fn(c.W, sw_rounds(R, c.W));
+      const SwFn fn = rigid_sw_fn(c.W, sw_rounds(R, c.W), kind);
       if (!fn) return k;
       return {(const void*)fn, 32 * kSwWarps, kSwWarps * (32 / c.W), cache_bytes(c.S) * kSwWarps * (32 / c.W)};
     }
@@ -1780,7 +1871,7 @@ gridff_status check_fire_params(gridff_ctx* ctx, const gridff_fire_params& P) {
 
 gridff_status prepare_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* R, const LaunchCfg& c,
                             int flags, int* blocks_out) {
-  const KernelShape k = shape_of(R, c);
+  const KernelShape k = shape_of(R, c, grid ? grid->kind : REC_F32x4);
   if (!k.fn) return set_err(ctx, GRIDFF_EINVAL, "launch configuration (kernel %d) does not apply", c.kernel);
   if (c.S < 0 || c.S > GRIDFF_MAX_ATOMS) return set_err(ctx, GRIDFF_EINVAL, "cache slots %d", c.S);
   if (c.kernel == GRIDFF_KERNEL_RIGID_SUBWARP && (flags & GRIDFF_NO_GRID))
@@ -1857,7 +1948,8 @@ gridff_status enqueue_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_rep
               (DevResult*)ctx->result_dev};
   GridView gv = grid ? grid->view() : empty_view();
   const int use_grid = !(flags & GRIDFF_NO_GRID), use_intra = !(flags & GRIDFF_NO_INTRA);
-  const KernelShape k = shape_of(R, c);
+  const int kind = grid ? grid->kind : REC_F32x4;
+  const KernelShape k = shape_of(R, c, kind);
   cudaAccessPolicyWindow win{};
   const cudaAccessPolicyWindow* wp = nullptr;
   if (c.l2win && grid) {
@@ -1875,7 +1967,7 @@ gridff_status enqueue_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_rep
   cudaError_t e = cudaSuccess;
   switch (c.kernel) {
     case GRIDFF_KERNEL_RIGID_SUBWARP:
-      e = launch_ex(rigid_sw_fn(c.W, sw_rounds(R, c.W)), blocks, k.threads, k.dyn, s, wp, gv, R->tv,
+      e = launch_ex(rigid_sw_fn(c.W, sw_rounds(R, c.W), kind), blocks, k.threads, k.dyn, s, wp, gv, R->tv,
                     (const int*)R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha, R->fire_nplus,
                     R->status, R->steps, R->energy, nsteps, fp, ctl, c.S);
       break;

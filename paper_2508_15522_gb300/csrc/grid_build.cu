@@ -3,9 +3,12 @@
 //   -> exact cubic B-spline coefficients (separable 1D line solves)
 //   -> padded float4 records read by the interpolation kernels.
 // Everything before the final packing runs in FP64.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -260,11 +263,25 @@ void host_tables(int n, bool cyclic, std::vector<double>& out, double& fac, doub
 }
 
 // --------------------------------------------------------------------------
-// packing into padded float4 records
+// packing into padded records
 // --------------------------------------------------------------------------
-__global__ void pack_kernel(const double* __restrict__ coefs, int nx, int ny, int nz, int nyp,
-                            int nzp, long long n_rec, int slotC, int slotP, int slotL,
-                            float4* __restrict__ rec) {
+// Round x to the nearest value with `bits` significant bits (ties to even),
+// quantum at least 2^min_exp: the value an FP16 (11, -24) or BF16 (8, -133)
+// number nearest to x has; computed exactly in FP64 (x / q is exact for a
+// power of two q, rint rounds to even).
+__device__ double round_sig(double x, int bits, int min_exp) {
+  if (x == 0.0 || !isfinite(x)) return x;
+  int e;
+  frexp(x, &e);
+  const int qe = e - bits > min_exp ? e - bits : min_exp;
+  const double q = ldexp(1.0, qe);
+  return rint(x / q) * q;
+}
+
+template <int KIND>
+__global__ void pack_kernel(const double* __restrict__ coefs, int nx, int ny, int nz, int nyp, int nzp,
+                            long long n_rec, int slotC, int slotP, int slotL, double iC, double iP, double iL,
+                            void* __restrict__ out) {
   long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_rec) return;
   int pz = (int)(r % nzp);
@@ -274,11 +291,46 @@ __global__ void pack_kernel(const double* __restrict__ coefs, int nx, int ny, in
   int iz = min(max(pz - 1, 0), nz - 1);
   size_t n_nodes = (size_t)nx * ny * nz;
   size_t node = ((size_t)ix * ny + iy) * nz + iz;
-  float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (slotC >= 0) o.x = (float)coefs[(size_t)slotC * n_nodes + node];
-  if (slotP >= 0) o.y = (float)coefs[(size_t)slotP * n_nodes + node];
-  if (slotL >= 0) o.z = (float)coefs[(size_t)slotL * n_nodes + node];
-  rec[r] = o;
+  // coefficient / scale (the scales are powers of two: exact)
+  const double c = slotC >= 0 ? coefs[(size_t)slotC * n_nodes + node] * iC : 0.0;
+  const double p = slotP >= 0 ? coefs[(size_t)slotP * n_nodes + node] * iP : 0.0;
+  const double l = slotL >= 0 ? coefs[(size_t)slotL * n_nodes + node] * iL : 0.0;
+  if (KIND == REC_F32x4) {
+    ((float4*)out)[r] = make_float4((float)c, (float)p, (float)l, 0.f);
+  } else if (KIND == REC_F32x2) {
+    ((float2*)out)[r] = make_float2((float)p, (float)l);
+  } else if (KIND == REC_F16x4 || KIND == REC_F16x2) {
+    const __half hc = __double2half(round_sig(c, 11, -24)), hp = __double2half(round_sig(p, 11, -24));
+    const __half hl = __double2half(round_sig(l, 11, -24));
+    if (KIND == REC_F16x4) {
+      ((__half2*)out)[2 * r] = __halves2half2(hc, hp);
+      ((__half2*)out)[2 * r + 1] = __halves2half2(hl, __double2half(0.0));
+    } else {
+      ((__half2*)out)[r] = __halves2half2(hp, hl);
+    }
+  } else {
+    const __nv_bfloat16 bc = __double2bfloat16(round_sig(c, 8, -133));
+    const __nv_bfloat16 bp = __double2bfloat16(round_sig(p, 8, -133));
+    const __nv_bfloat16 bl = __double2bfloat16(round_sig(l, 8, -133));
+    if (KIND == REC_BF16x4) {
+      ((__nv_bfloat162*)out)[2 * r] = __halves2bfloat162(bc, bp);
+      ((__nv_bfloat162*)out)[2 * r + 1] = __halves2bfloat162(bl, __double2bfloat16(0.0));
+    } else {
+      ((__nv_bfloat162*)out)[r] = __halves2bfloat162(bp, bl);
+    }
+  }
+}
+
+// max |coefficient| of each channel (bit patterns of non-negative doubles
+// order like the values)
+__global__ void absmax_kernel(const double* __restrict__ coefs, size_t n_nodes, int n_ch,
+                              unsigned long long* __restrict__ out) {
+  for (int ch = 0; ch < n_ch; ++ch) {
+    double m = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += (size_t)gridDim.x * blockDim.x)
+      m = fmax(m, fabs(coefs[(size_t)ch * n_nodes + i]));
+    if (m > 0.0) atomicMax(&out[ch], (unsigned long long)__double_as_longlong(m));
+  }
 }
 
 struct DevFree {
@@ -304,7 +356,8 @@ void channel_slots(int channels, int& sC, int& sP, int& sL, int& n_ch) {
 }
 
 // Allocate grid->rec for the grid's storage layout and pack FP64
-// coefficients ([C][nx][ny][nz], device) into it.
+// coefficients ([C][nx][ny][nz], device) into it.  FP16/BF16: per-channel
+// scale 2^(e - 15) with max |coef| < 2^e, so that |coef| / scale < 2^15.
 gridff_status pack_records(gridff_ctx* ctx, gridff_grid* g, const double* data) {
   int nx = g->dims[0], ny = g->dims[1], nz = g->dims[2];
   cudaStream_t s = ctx->stream;
@@ -313,16 +366,59 @@ gridff_status pack_records(gridff_ctx* ctx, gridff_grid* g, const double* data) 
   g->nzp = nz + 2;
   int sC, sP, sL, nch;
   channel_slots(g->channels, sC, sP, sL, nch);
+  const bool two = sC < 0;     // no Coulomb channel: {P, L} records
+  g->kind = g->storage == GRIDFF_STORE_F16 ? (two ? REC_F16x2 : REC_F16x4)
+          : g->storage == GRIDFF_STORE_BF16 ? (two ? REC_BF16x2 : REC_BF16x4)
+                                            : (two ? REC_F32x2 : REC_F32x4);
+  double inv[3] = {1.0, 1.0, 1.0};
+  g->scale[0] = g->scale[1] = g->scale[2] = 1.f;
+  if (g->storage != GRIDFF_STORE_F32) {
+    unsigned long long* mx = nullptr;
+    GRIDFF_CUDA(ctx, cudaMallocAsync((void**)&mx, 3 * sizeof(unsigned long long), s));
+    cudaError_t e = cudaMemsetAsync(mx, 0, 3 * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) {
+      absmax_kernel<<<4 * ctx->n_sm, 256, 0, s>>>(data, (size_t)nx * ny * nz, nch, mx);
+      e = cudaGetLastError();
+    }
+    unsigned long long h[3] = {0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, mx, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(mx, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return set_err(ctx, GRIDFF_ECUDA, "channel maxima: %s", cudaGetErrorString(e));
+    const int slot_of[3] = {sC, sP, sL};
+    for (int c = 0; c < 3; ++c) {
+      if (slot_of[c] < 0) continue;
+      double m;
+      memcpy(&m, &h[slot_of[c]], sizeof(double));
+      int ex = 0;
+      if (m > 0.0) frexp(m, &ex);
+      g->scale[c] = (float)ldexp(1.0, ex - 15);
+      inv[c] = ldexp(1.0, 15 - ex);
+    }
+  }
   long long n_rec = (long long)g->nxp * g->nyp * g->nzp;
-  g->rec_bytes = (size_t)n_rec * sizeof(float4);
+  g->rec_bytes = (size_t)n_rec * rec_bytes_of(g->kind);
   GRIDFF_CUDA(ctx, cudaMalloc(&g->rec, g->rec_bytes));
-  pack_kernel<<<(unsigned)((n_rec + 255) / 256), 256, 0, s>>>(data, nx, ny, nz, g->nyp, g->nzp, n_rec,
-                                                                sC, sP, sL, g->rec);
+  const unsigned blocks = (unsigned)((n_rec + 255) / 256);
+#define GRIDFF_PACK(K)                                                                                \
+  pack_kernel<K><<<blocks, 256, 0, s>>>(data, nx, ny, nz, g->nyp, g->nzp, n_rec, sC, sP, sL, inv[0], \
+                                         inv[1], inv[2], g->rec)
+  switch (g->kind) {
+    case REC_F32x4: GRIDFF_PACK(REC_F32x4); break;
+    case REC_F32x2: GRIDFF_PACK(REC_F32x2); break;
+    case REC_F16x4: GRIDFF_PACK(REC_F16x4); break;
+    case REC_F16x2: GRIDFF_PACK(REC_F16x2); break;
+    case REC_BF16x4: GRIDFF_PACK(REC_BF16x4); break;
+    default: GRIDFF_PACK(REC_BF16x2); break;
+  }
+#undef GRIDFF_PACK
   GRIDFF_CUDA(ctx, cudaGetLastError());
   return GRIDFF_OK;
 }
 
-bool storage_ok(int st) { return st == GRIDFF_STORE_F32; }
+bool storage_ok(int st) {
+  return st == GRIDFF_STORE_F32 || st == GRIDFF_STORE_F16 || st == GRIDFF_STORE_BF16;
+}
 
 // Fit coefficients in place (3 passes) and pack them into grid->rec.
 gridff_status fit_and_pack(gridff_ctx* ctx, gridff_grid* g, double* data, DevFree& df) {
@@ -476,6 +572,10 @@ double* noalloc_tables_address(int device, cudaError_t* err) {
 GridView gridff_grid::view() const {
   GridView v;
   v.rec = rec;
+  v.kind = kind;
+  v.sC = scale[0];
+  v.sP = scale[1];
+  v.sL = scale[2];
   v.nx = dims[0];
   v.ny = dims[1];
   v.nz = dims[2];
@@ -792,6 +892,14 @@ gridff_status gridff_fit_coefs_noalloc(gridff_ctx* ctx, const double* values, do
       coefs, nx, (long long)ny * nz, lines, ny * nz, 1, N, tab, 1);
   GRIDFF_CUDA(ctx, cudaGetLastError());
   if (!(flags & GRIDFF_ASYNC)) GRIDFF_CUDA(ctx, cudaStreamSynchronize(s));
+  return GRIDFF_OK;
+}
+
+gridff_status gridff_grid_storage(const gridff_grid* g, int32_t* storage, float scales[3]) {
+  if (!g) return GRIDFF_EINVAL;
+  if (storage) *storage = g->storage;
+  if (scales)
+    for (int c = 0; c < 3; ++c) scales[c] = g->scale[c];
   return GRIDFF_OK;
 }
 

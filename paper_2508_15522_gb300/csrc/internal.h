@@ -44,14 +44,24 @@ struct gridff_ctx {
   std::string err;
 };
 
+// Record kinds: 4 slots {C, P, L, 0}, or 2 slots {P, L} for grids without
+// the Coulomb channel; FP32, or FP16 / BF16 holding coefficient / scale
+// with a power-of-two scale per channel.
+enum RecKind { REC_F32x4 = 0, REC_F32x2 = 1, REC_F16x4 = 2, REC_F16x2 = 3, REC_BF16x4 = 4, REC_BF16x2 = 5 };
+inline int rec_bytes_of(int kind) {
+  return kind == REC_F32x4 ? 16 : (kind == REC_F32x2 || kind == REC_F16x4 || kind == REC_BF16x4) ? 8 : 4;
+}
+
 // Coefficient grid as the kernels see it (passed by value).
-// Node records are float4 {C, P, L, 0}; the record array is padded so that
-// every 4x4x4 stencil is a set of 16 contiguous runs of 4 records:
+// The record array is padded so that every 4x4x4 stencil is a set of 16
+// contiguous runs of 4 records:
 //   padded x index p <-> logical (p - 1) mod nx, p in [0, nx + 3)
 //   padded y index    likewise
 //   padded z index p <-> logical clamp(p - 1, 0, nz - 1), p in [0, nz + 2)
 struct GridView {
-  const float4* rec;
+  const void* rec;
+  int kind;              // RecKind
+  float sC, sP, sL;      // channel scales (1 for FP32)
   int nx, ny, nz;
   int nyp, nzp;
   long long sx;          // record stride between x planes = nyp * nzp
@@ -68,7 +78,9 @@ struct gridff_grid {
   double spacing[3] = {0, 0, 0};
   int channels = 0;
   int storage = 0;
-  float4* rec = nullptr;
+  int kind = REC_F32x4;
+  float scale[3] = {1.f, 1.f, 1.f};   // C, P, L
+  void* rec = nullptr;
   size_t rec_bytes = 0;
   int nxp = 0, nyp = 0, nzp = 0;
   double* f64_values = nullptr;   // [C][nx][ny][nz] if kept

@@ -23,7 +23,7 @@ OK, EINVAL, ENOMEM, ECUDA, EABORTED, ESTEPLIMIT, ENOTSUP = range(7)
 REP_CONVERGED, REP_BELOW, REP_NONFINITE, REP_ABORTED, REP_STEPLIMIT = 1, 2, 4, 8, 16
 DEVICE_PTRS, ASYNC, CONTINUE, NO_GRID, NO_INTRA = 1, 2, 4, 8, 16
 CH_C, CH_P, CH_L = 1, 2, 4
-STORE_F32 = 0
+STORE_F32, STORE_F16, STORE_BF16 = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EABORTED", 5: "ESTEPLIMIT",
                 6: "ENOTSUP"}
 
@@ -110,6 +110,7 @@ def _load():
         "gridff_grid_info": (I32, [P, C.POINTER(C.c_int32), C.POINTER(C.c_double),
                                    C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_size_t)]),
         "gridff_grid_download_f64": (I32, [P, C.c_int, C.POINTER(C.c_double)]),
+        "gridff_grid_storage": (I32, [P, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
         "gridff_grid_destroy": (None, [P]),
         "gridff_replicas_create": (I32, [P, I32, C.POINTER(Molecule), I32, C.POINTER(C.c_int32), I32,
                                          F64, C.POINTER(P)]),
@@ -166,6 +167,7 @@ EXPORTED = (
     "gridff_mlp_get_params", "gridff_mlp_forward", "gridff_mlp_train_step", "gridff_mlp_propose",
     "gridff_molecule_descriptor", "gridff_random_poses", "gridff_rmsd_unique",
     "gridff_set_launch_config", "gridff_get_launch_config", "gridff_tune", "gridff_relax_graph_create",
+    "gridff_grid_storage",
     "gridff_graph_launch", "gridff_graph_destroy",
 )
 
@@ -242,6 +244,9 @@ class Grid:
         ctx.check(lib.gridff_grid_info(handle, dims, org, sp, C.byref(ch), C.byref(nb)))
         self.dims, self.origin, self.spacing = tuple(dims), tuple(org), tuple(sp)
         self.channels, self.device_bytes = ch.value, nb.value
+        st = C.c_int32(); sc = (C.c_float * 3)()
+        ctx.check(lib.gridff_grid_storage(handle, C.byref(st), sc))
+        self.storage, self.scales = st.value, tuple(sc)
 
     @property
     def n_channels(self):

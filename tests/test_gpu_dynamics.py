@@ -57,10 +57,12 @@ def test_fire_flexible_first_steps_match_oracle(G, ctx, small_field):
         assert (fs["steps"] == nsteps).all()
 
 
-@pytest.mark.parametrize("storage", [0])
+@pytest.mark.parametrize("storage", [0, 1, 2])
 def test_fire_rigid_first_steps_match_oracle(G, ctx, small_field, storage):
+    from oracle import precision as oprec
     sub, box, h, c32, grid0 = small_field
     grid = G.grid_from_coefs(ctx, c32, box.origin, h, 7, storage=storage)
+    c32 = oprec.quantize(c32, {0: "f32", 1: "f16", 2: "bf16"}[storage])[0]
     mol = synth.c24h8o6_core()
     n_rep = 33
     com, quat = synth.rigid_poses(mol, sub, n_rep, seed=33)

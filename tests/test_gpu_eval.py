@@ -11,6 +11,7 @@ from oracle import bspline as obs
 from oracle import dynamics as odyn
 from oracle import grid as ogrid
 from oracle import intra as ointra
+from oracle import precision as oprec
 from oracle import substrate as osub
 from paper_2508_15522_gb300 import synth
 
@@ -46,7 +47,22 @@ def _oracle_grid(coefs, chans, origin, h, pts, mol_q, mol_R, mol_eps, dtype):
     return ogrid.grid_energy_forces(coefs, chans, origin, h, pts, mol_q, mol_R, mol_eps, dtype=dtype)
 
 
-@pytest.mark.parametrize("storage", [0])
+TIER = {0: "f32", 1: "f16", 2: "bf16"}
+
+
+def _check_storage(grid, coefs, storage, n_slots):
+    """Tier bookkeeping: the grid's channel scales are the oracle's and its
+    records have the tier's width; returns the coefficients the kernels see."""
+    cq, scales = oprec.quantize(coefs, TIER[storage])
+    present = [s for s, on in zip(grid.scales, (grid.channels & 1, grid.channels & 2, grid.channels & 4)) if on]
+    assert np.array_equal(np.array(present, np.float64), scales)
+    n_rec = (grid.dims[0] + 3) * (grid.dims[1] + 3) * (grid.dims[2] + 2)
+    width = {0: 4, 1: 2, 2: 2}[storage] * n_slots
+    assert grid.device_bytes == n_rec * width
+    return cq
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2])
 @pytest.mark.parametrize("shape", [(17, 13, 21), (8, 9, 6), (9, 7, 5)])
 def test_eval_random_field_matches_fp32_oracle(G, ctx, shape, storage):
     """Random coefficients, points spanning periodic wraps, the clamped z
@@ -66,7 +82,8 @@ def test_eval_random_field_matches_fp32_oracle(G, ctx, shape, storage):
     reps.set_state(pts.ravel())
     E, F, Ea, S = G.eval(ctx, grid, reps, flags=G.NO_INTRA)
     Q = np.tile(mol.q, n_rep); R = np.tile(mol.R, n_rep); eps = np.tile(mol.eps, n_rep)
-    E32, F32, below = _oracle_grid(coefs, ("C", "P", "L"), origin, h, pts, Q, R, eps, np.float32)
+    cq = _check_storage(grid, coefs, storage, 4)
+    E32, F32, below = _oracle_grid(cq, ("C", "P", "L"), origin, h, pts, Q, R, eps, np.float32)
     scale = max(1.0, np.abs(F32).max())
     assert np.abs(F - F32).max() <= TOL_F * scale
     assert np.abs(Ea - E32).max() <= TOL_E * max(1.0, np.abs(E32).max())
@@ -76,7 +93,7 @@ def test_eval_random_field_matches_fp32_oracle(G, ctx, shape, storage):
     assert np.array_equal((S & G.REP_BELOW) != 0, below_rep)
 
 
-@pytest.mark.parametrize("storage", [0])
+@pytest.mark.parametrize("storage", [0, 1, 2])
 def test_eval_two_channel_grid(G, ctx, storage):
     shape, h, origin = (12, 10, 16), (0.25, 0.3, 0.2), (0.0, 0.0, 1.0)
     coefs = synth.random_coefficients(shape, 2, seed=15, scale=(1.0, 0.5))
@@ -86,7 +103,8 @@ def test_eval_two_channel_grid(G, ctx, storage):
     reps = G.Replicas(ctx, [mol], [0] * 4)
     reps.set_state(pts.astype(np.float32).ravel())
     E, F, Ea, S = G.eval(ctx, grid, reps, flags=G.NO_INTRA)
-    E32, F32, _ = _oracle_grid(coefs, ("P", "L"), origin, h, pts.astype(np.float32), np.tile(mol.q, 4),
+    cq = _check_storage(grid, coefs, storage, 2)
+    E32, F32, _ = _oracle_grid(cq, ("P", "L"), origin, h, pts.astype(np.float32), np.tile(mol.q, 4),
                                np.tile(mol.R, 4), np.tile(mol.eps, 4), np.float32)
     assert np.abs(F - F32).max() <= TOL_F * max(1, np.abs(F32).max())
     assert np.abs(Ea - E32).max() <= TOL_E * max(1, np.abs(E32).max())
