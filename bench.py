@@ -381,6 +381,69 @@ def uneven_batch_comparison(G, ctx, grid, sub):
     return out
 
 
+def precision_comparison(G, ctx):
+    """Coefficient precision tiers on the neutral fcc(111) workload: a=4.08 A
+    slab, 12 x 12 surface cells, 4 layers (576 atoms), Pauli and London
+    channels only, 0.05 A grid over the 11.5 x 10.0 A tile and 20 A height;
+    65536 rigid 24-atom molecules at random poses, 200 FIRE iterations per
+    tier (f_conv = 0).  Error per tier: per-atom energy and force of 64
+    replicas (1536 atoms) at their starting poses against the FP64 pairwise
+    reference (direct Morse sums over the periodic slab)."""
+    from oracle import substrate as osub
+    from paper_2508_15522_gb300 import synth
+    sub = synth.fcc111_slab(a=4.08, ncell=12, layers=4)
+    box = synth.grid_box_for(sub, 0.05, height=20.0)
+    mol = synth.rigid_molecule(24, 2024)
+    n_rep = 65536
+    com, quat = synth.rigid_poses(mol, sub, n_rep, seed=2025)
+    pose = np.concatenate([com, quat], 1).astype(np.float32).ravel()
+    sample = 64
+    pts = None
+    out = {"grid": None, "replicas": n_rep, "atoms_per_replica": mol.n, "fire_iterations": 200}
+    errs = {}
+    t0 = time.perf_counter()
+    grid32 = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, channels=G.CH_P | G.CH_L,
+                          keep_f64=True)
+    out["build_s"] = time.perf_counter() - t0
+    coefs = grid32.download_f64("coefs")
+    out["grid"] = list(grid32.dims)
+    for tier, st in (("f32", G.STORE_F32), ("f16", G.STORE_F16), ("bf16", G.STORE_BF16)):
+        # every tier packs the same FP64 coefficients
+        grid = grid32 if st == G.STORE_F32 else G.grid_from_coefs(ctx, coefs, grid32.origin, grid32.spacing,
+                                                                  G.CH_P | G.CH_L, storage=st)
+        reps = G.Replicas(ctx, [mol], [0] * n_rep, rigid=True)
+        reps.set_state(pose)
+        G.relax(ctx, grid, reps, 20, G.fire_params(f_conv=0.0))         # warm-up
+        reps.set_state(pose)
+        st_, res = G.relax(ctx, grid, reps, 200, G.fire_params(f_conv=0.0))
+        ms = ctx.last_kernel_ms()
+        # errors at the starting poses of the first `sample` replicas
+        probe = G.Replicas(ctx, [mol], [0] * sample, rigid=True)
+        probe.set_state(pose[:7 * sample])
+        if pts is None:
+            pts = probe.positions().astype(np.float64)
+            Q = np.tile(mol.q, sample); R = np.tile(mol.R, sample); eps = np.tile(mol.eps, sample)
+            E_ref, F_ref = osub.pairwise_reference(pts, Q, R, eps, sub)
+        # per-atom grid energies and forces at those positions (flexible view)
+        flex = G.Replicas(ctx, [mol], [0] * sample)
+        flex.set_state(pts.astype(np.float32).ravel())
+        E, F, Ea, S = G.eval(ctx, grid, flex, flags=G.NO_INTRA)
+        errs[tier] = {"max_abs_dE_per_atom_eV": float(np.abs(Ea - E_ref).max()),
+                      "rms_dE_per_atom_eV": float(np.sqrt(np.mean((Ea - E_ref) ** 2))),
+                      "max_abs_dF_eV_per_A": float(np.abs(F - F_ref).max()),
+                      "max_abs_dE_per_molecule_eV": float(np.abs(E - E_ref.reshape(sample, -1).sum(1)).max())}
+        out[tier] = {"grid_bytes": grid.device_bytes, "kernel_ms": ms,
+                     "atom_evals_per_s": res.atom_evals / (ms * 1e-3),
+                     "replica_steps_per_s": n_rep * 200 / (ms * 1e-3), "error_vs_fp64_pairwise": errs[tier],
+                     "scales": list(grid.scales)}
+        for h in (flex, probe, reps):
+            h.close()
+        if grid is not grid32:
+            grid.close()
+    grid32.close()
+    return out
+
+
 def run_gpu(args):
     import torch
     import __graft_entry__ as ge
@@ -475,7 +538,7 @@ def run_gpu(args):
         "replica_steps_per_s": value / mol.n,
         "roofline": {"bound": "l2", "achieved": achieved, "peak": l2_peak, "unit": "GB/s",
                      "frac": (achieved / l2_peak) if l2_peak else None, "traffic": tpe,
-                     "kernel": "relax_rigid_sw_kernel<16>", "bytes_per_unit": BYTES_PER_EVAL,
+                     "kernel": "relax_rigid_sw_kernel<W=16, R=3, F32x4>", "bytes_per_unit": BYTES_PER_EVAL,
                      "units_per_launch": per_launch_evals, "kernel_ms": k_ms,
                      "peak_source": "measured in this run: streaming read of a 48 MB L2-resident buffer "
                                     "(gridff_probe_read_bandwidth, best of 3 launch shapes)",
@@ -491,6 +554,7 @@ def run_gpu(args):
         line["nve_drift"] = nve_drift(G, ctx, grid, reps, mol, pose)
         line["minima"] = minima_comparison(G, ctx, grid, mol, sub)
         line["uneven_batch"] = uneven_batch_comparison(G, ctx, grid, sub)
+        line["precision_tiers"] = precision_comparison(G, ctx)
     if rank == 0 and world == 1 and not args.quick:
         cv, cdt, cdesc = oracle_sample()
         line["cpu_baseline"] = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cdesc}

@@ -404,6 +404,15 @@ def random_flexible_molecule(n_atoms: int, n_torsions: int, seed: int) -> Molecu
     return mol
 
 
+def rigid_molecule(n_atoms: int, seed: int) -> Molecule:
+    """A generated molecule of ``n_atoms`` atoms (random tree geometry) used
+    as a rigid body: coordinates in its principal-axes frame centred at the
+    centre of mass, no intramolecular terms."""
+    m = random_flexible_molecule(n_atoms, 0, seed)
+    body, _ = _principal_frame(m.xyz, m.mass)
+    return Molecule(m.elements, body, m.q, m.R, m.eps, m.mass)
+
+
 def uneven_sizes(n_rep: int, seed: int, lo: int = 10, hi: int = 120) -> np.ndarray:
     """Log-uniform molecule sizes in [lo, hi]."""
     g = rng(seed)
