@@ -521,6 +521,43 @@ gridff_status gridff_mlp_propose(gridff_mlp* mlp, gridff_replicas* reps, const f
  * torsion count / 12; zero padding.  Errors: EINVAL. */
 gridff_status gridff_molecule_descriptor(const gridff_molecule* mol, float* out);
 
+/* ----------------------------------------------------------------- Langevin */
+
+typedef struct {
+  float dt;               /* fs */
+  float temperature;      /* K */
+  float gamma;            /* friction (1/fs) */
+  uint64_t seed;          /* noise stream */
+  int64_t step0;          /* global index of the first step of this call (noise counter) */
+  double clock_budget_s;  /* as in gridff_fire_params */
+} gridff_langevin_params;
+
+/* Langevin dynamics of flexible replicas for nsteps (the thermalisation
+ * step of the paper's minima hopping, Sec. 7), BAOAB splitting with
+ * c1 = exp(-gamma dt), c2 = sqrt(1 - c1^2):
+ *   v += dt/2 a;  x += dt/2 v;  v = c1 v + c2 sqrt(kB T / m) xi;
+ *   x += dt/2 v;  forces;  v += dt/2 a      (kB = 8.617333262e-5 eV/K).
+ * xi of replica r, global step s = step0 + k, component m = 3 i + a is
+ *   z(splitmix64(splitmix64(seed XOR splitmix64(r)) XOR (512 s + m)))
+ * with z(.) the Box-Muller normal of gridff_mlp_propose's generator.
+ * The replicas' energies receive the energy of the final state; status
+ * bits ABORTED / STEPLIMIT / NONFINITE as for gridff_run.  Uses the
+ * replica set's unique-term launch configuration if one is set.
+ * Errors: EINVAL, ENOTSUP (rigid replicas), ECUDA, EABORTED, ESTEPLIMIT. */
+gridff_status gridff_langevin(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* reps,
+                              int32_t nsteps, const gridff_langevin_params* params, int flags);
+
+/* RMSD uniqueness filter for flexible structures (Sec. 7): xyz holds n
+ * structures of one molecule of n_atoms atoms ([n][n_atoms][3], ordered by
+ * the caller, e.g. by energy).  RMSD of structures A, B = sqrt(mean over
+ * atoms |a_i - b_i - t|^2) where t shifts B by whole tile periods in x, y
+ * so that the atoms' mean positions are closest (minimum image); no
+ * alignment (adsorption site and orientation count).  dup_of[i] = smallest
+ * j < i within `threshold`, else -1.  Host arrays unless GRIDFF_DEVICE_PTRS.
+ * Errors: EINVAL (n_atoms outside 1..128), ECUDA. */
+gridff_status gridff_rmsd_unique_xyz(gridff_ctx* ctx, int32_t n_atoms, int32_t n, const float* xyz,
+                                     const double tile_xy[2], double threshold, int32_t* dup_of, int flags);
+
 /* ------------------------------------------------------------ measurement */
 
 /* Read `bytes` of a device buffer `iters` times with a streaming kernel and

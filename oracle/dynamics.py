@@ -351,3 +351,45 @@ def nve_rigid(com, quat, vel, omega, body, mass, force_fn, nsteps, dt, record_ev
         if (s + 1) % record_every == 0:
             trace.append(E + rigid_kinetic(vel, omega_of(q, pq), M, I))
     return com, q, vel, omega_of(q, pq), np.array(trace)
+
+
+KB = 8.617333262e-5   # eV/K
+
+
+def langevin_noise(seed, replicas, step, n_comp):
+    """xi[r, m] of the library's Langevin noise stream for global step
+    `step`: the SplitMix64 output of splitmix64(seed ^ splitmix64(r)) ^
+    (512 step + m), turned into a normal by Box-Muller (float64 here)."""
+    from .mlp import splitmix64
+    out = np.empty((len(replicas), n_comp))
+    for k, r in enumerate(replicas):
+        key = splitmix64(seed ^ splitmix64(int(r)))
+        for m in range(n_comp):
+            s = splitmix64(key ^ (512 * step + m))
+            u1 = ((s >> 40) + 1) / 2.0 ** 24
+            u2 = ((s >> 16) & 0xFFFFFF) / 2.0 ** 24
+            out[k, m] = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    return out
+
+
+def langevin_baoab(x, v, mass, force_fn, nsteps, dt, T, gamma, noise):
+    """Langevin dynamics by the BAOAB splitting (Leimkuhler and Matthews):
+    half kick, half drift, exact Ornstein-Uhlenbeck step
+    v <- c1 v + c2 sqrt(kB T / m) xi (c1 = exp(-gamma dt), c2 = sqrt(1 - c1^2)),
+    half drift, half kick.  noise(step) -> xi (R, n*3).  Returns (x, v, E)
+    with E the energy of the final state."""
+    x = np.array(x, np.float64); v = np.array(v, np.float64)
+    R, n, _ = x.shape
+    m = np.asarray(mass, np.float64)[None, :, None]
+    c1 = np.exp(-gamma * dt)
+    c2 = np.sqrt(1.0 - c1 * c1)
+    sig = np.sqrt(KB * T * ACC / m)
+    E, F, _ = force_fn(x)
+    for s in range(nsteps):
+        v = v + 0.5 * dt * ACC * F / m
+        x = x + 0.5 * dt * v
+        v = c1 * v + c2 * sig * noise(s).reshape(R, n, 3)
+        x = x + 0.5 * dt * v
+        E, F, _ = force_fn(x)
+        v = v + 0.5 * dt * ACC * F / m
+    return x, v, E

@@ -69,3 +69,25 @@ def dup_of(body, poses, tile_xy, threshold):
                 break
         out.append(found)
     return np.array(out, np.int32)
+
+
+def rmsd_xyz(a, b, tile_xy):
+    """RMSD of two structures (n, 3) of one molecule after shifting b by
+    whole tile periods in x, y toward a's mean position; no alignment."""
+    a = np.asarray(a, np.float64); b = np.array(b, np.float64)
+    d = a[:, :2].mean(0) - b[:, :2].mean(0)
+    for k in range(2):
+        b[:, k] += tile_xy[k] * np.round(d[k] / tile_xy[k])
+    return float(np.sqrt(np.mean(np.sum((a - b) ** 2, 1))))
+
+
+def dup_of_xyz(structs, tile_xy, threshold):
+    out = []
+    for i in range(len(structs)):
+        found = -1
+        for j in range(i):
+            if rmsd_xyz(structs[i], structs[j], tile_xy) < threshold:
+                found = j
+                break
+        out.append(found)
+    return np.array(out, np.int32)

@@ -1461,6 +1461,101 @@ relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep
 }
 
 // ---------------------------------------------------------------------------
+// Langevin dynamics of flexible replicas (the thermalisation of minima
+// hopping, Sec. 7), BAOAB splitting: half kick, half drift, exact
+// Ornstein-Uhlenbeck velocity update v <- c1 v + c2 sqrt(kT/m) xi, half
+// drift, forces, half kick; c1 = exp(-gamma dt), c2 = sqrt(1 - c1^2).
+// xi of replica r, global step s, component m = 3 i + a:
+//   normal_of(splitmix64(splitmix64(seed ^ splitmix64(r)) ^ (512 s + m))).
+// Layout as relax_flex_terms_kernel (warp per replica, work queue).
+// ---------------------------------------------------------------------------
+template <int WPB>
+__global__ void __launch_bounds__(32 * WPB, GRIDFF_FLEX_WARPS_PER_SM / WPB)
+langevin_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
+                     const int* __restrict__ rep_off, const int* __restrict__ order, int n_rep, float* xs,
+                     float* vs, int* status, double* energy, int nsteps, float dt, float c1, float c2,
+                     float kT_acc, unsigned long long seed, long long step0, Control ctl, int use_grid,
+                     int use_intra, int S) {
+  __shared__ WarpState s_all[WPB];
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  WarpState& s = s_all[wib];
+  unsigned char* wbase = dyn_smem + (size_t)wib * flex_terms_warp_bytes(S);
+  StencilCache sc;
+  sc.val = (float4*)wbase;
+  sc.key = (int*)(wbase + (size_t)S * 256);
+  sc.S = S;
+  float4* s_nb = (float4*)(wbase + cache_bytes(S));
+  const int warp = blockIdx.x * WPB + wib;
+  const int n_warps = gridDim.x * WPB;
+  const unsigned long long t0 = gtimer();
+  const float hdt = 0.5f * dt;
+  for (int k = warp;; k += n_warps) {
+    if (order) {
+      int next = 0;
+      if (lane == 0) next = atomicAdd(&ctl.res->next, 1);
+      k = __shfl_sync(kFull, next, 0);
+    }
+    if (k >= n_rep) break;
+    const int r = order ? order[k] : k;
+    const int t = rep_tmpl[r], n = tv.natoms[t], ab = tv.atom_off[t], off = rep_off[r];
+    const unsigned long long key = splitmix64(seed ^ splitmix64((unsigned long long)r));
+    __syncwarp();
+    cache_reset(sc, lane);
+    for (int m = lane; m < 3 * n; m += 32) {
+      s.x[m] = xs[3 * (size_t)off + m];
+      s.v[m] = vs[3 * (size_t)off + m];
+    }
+    for (int i = lane; i < n; i += 32) s_nb[i] = __ldg(&tv.nb[ab + i]);
+    int st = status[r] & ~(GRIDFF_REP_CONVERGED | GRIDFF_REP_ABORTED | GRIDFF_REP_STEPLIMIT);
+    int flags = 0, steps_done = 0;
+    float elane = flex_forces_terms<float>(g, use_grid, use_intra, tv, t, ab, n, lane, s, flags, sc, s_nb);
+    for (int it = 0; it < nsteps && !(st & GRIDFF_REP_NONFINITE); ++it) {
+      if ((it & 31) == 0) {
+        const int sb = stop_bits(ctl, t0, lane);
+        if (sb) {
+          st |= sb;
+          break;
+        }
+      }
+      const unsigned long long sstep = (unsigned long long)(step0 + it) * 512ull;
+      for (int m = lane; m < 3 * n; m += 32) {
+        const float im = 1.f / __ldg(&tv.body[ab + m / 3]).w;
+        float v = s.v[m] + hdt * GRIDFF_ACC * s.f[m] * im;
+        float x = s.x[m] + hdt * v;
+        const float xi = normal_of(splitmix64(key ^ (sstep + (unsigned long long)m)));
+        v = c1 * v + c2 * sqrtf(kT_acc * im) * xi;
+        s.x[m] = x + hdt * v;
+        s.v[m] = v;
+      }
+      elane = flex_forces_terms<float>(g, use_grid, use_intra, tv, t, ab, n, lane, s, flags, sc, s_nb);
+      float f2 = 0.f;
+      for (int m = lane; m < 3 * n; m += 32) {
+        const float im = 1.f / __ldg(&tv.body[ab + m / 3]).w;
+        s.v[m] += hdt * GRIDFF_ACC * s.f[m] * im;
+        f2 = fmaf(s.f[m], s.f[m], f2);
+      }
+      f2 = wsum(f2);
+      st |= __reduce_or_sync(kFull, flags);
+      ++steps_done;
+      if (!isfinite(f2)) st |= GRIDFF_REP_NONFINITE;
+    }
+    __syncwarp();
+    for (int m = lane; m < 3 * n; m += 32) {
+      xs[3 * (size_t)off + m] = s.x[m];
+      vs[3 * (size_t)off + m] = s.v[m];
+    }
+    const double Etot = wsum((double)elane);
+    if (!isfinite(Etot)) st |= GRIDFF_REP_NONFINITE;
+    if (lane == 0) {
+      status[r] = st;
+      energy[r] = Etot;
+      report(ctl, n, steps_done + 1, st, steps_done);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // NVE, flexible replicas: velocity Verlet
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads, kMinBlocksPerSM)
@@ -2072,6 +2167,52 @@ gridff_status gridff_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_repl
     result->max_steps = h.max_steps;
   }
   return rs;
+}
+
+gridff_status gridff_langevin(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* R, int32_t nsteps,
+                              const gridff_langevin_params* prm, int flags) {
+  gridff_status st = check_common(ctx, grid, R, flags);
+  if (st != GRIDFF_OK) return st;
+  if (!prm || !(prm->dt > 0) || !(prm->temperature >= 0) || !(prm->gamma >= 0) || nsteps < 0 || prm->step0 < 0)
+    return set_err(ctx, GRIDFF_EINVAL, "bad Langevin parameters");
+  if (R->rigid) return set_err(ctx, GRIDFF_ENOTSUP, "Langevin dynamics is implemented for flexible replicas");
+  GRIDFF_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  GRIDFF_CUDA(ctx, cudaMemsetAsync(ctx->result_dev, 0, sizeof(DevResult), s));
+  Control ctl{ctx->ctrl_dev, (unsigned long long)(prm->clock_budget_s > 0 ? prm->clock_budget_s * 1e9 : 0),
+              (DevResult*)ctx->result_dev};
+  GridView gv = grid ? grid->view() : empty_view();
+  const int use_grid = !(flags & GRIDFF_NO_GRID), use_intra = !(flags & GRIDFF_NO_INTRA);
+  const double c1 = exp(-(double)prm->gamma * prm->dt);
+  const double c2 = sqrt(1.0 - c1 * c1);
+  const double kB = 8.617333262e-5;   // eV/K
+  const float kT_acc = (float)(kB * prm->temperature * GRIDFF_ACC);
+  // layout: the replica set's unique-term configuration if it has one
+  const LaunchCfg c = R->cfg.kernel == GRIDFF_KERNEL_FLEX_TERMS ? R->cfg : default_launch_cfg(R, true);
+  const int wpb = c.kernel == GRIDFF_KERNEL_FLEX_TERMS ? c.wpb : 8;
+  const int S = c.kernel == GRIDFF_KERNEL_FLEX_TERMS ? c.S : 0;
+  const void* fn = wpb == 2 ? (const void*)langevin_flex_kernel<2>
+                 : wpb == 4 ? (const void*)langevin_flex_kernel<4> : (const void*)langevin_flex_kernel<8>;
+  const size_t dyn = flex_terms_warp_bytes(S) * wpb;
+  GRIDFF_CUDA(ctx, set_dyn_smem(fn, dyn));
+  int per_sm = 0;
+  GRIDFF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * wpb, dyn));
+  if (per_sm < 1) return set_err(ctx, GRIDFF_EINVAL, "Langevin launch does not fit on an SM");
+  const int need = (R->n_rep + wpb - 1) / wpb;
+  const int blocks = need < per_sm * ctx->n_sm ? need : per_sm * ctx->n_sm;
+  GRIDFF_CUDA(ctx, cudaEventRecord(ctx->ev0, s));
+#define GRIDFF_LANGEVIN(W)                                                                                 \
+  langevin_flex_kernel<W><<<blocks, 32 * W, dyn, s>>>(gv, R->tv, R->rep_tmpl, R->rep_off, R->order, R->n_rep, \
+                                                      R->x, R->v, R->status, R->energy, nsteps, prm->dt,     \
+                                                      (float)c1, (float)c2, kT_acc,                         \
+                                                      (unsigned long long)prm->seed, (long long)prm->step0,  \
+                                                      ctl, use_grid, use_intra, S)
+  if (wpb == 2) GRIDFF_LANGEVIN(2);
+  else if (wpb == 4) GRIDFF_LANGEVIN(4);
+  else GRIDFF_LANGEVIN(8);
+#undef GRIDFF_LANGEVIN
+  DevResult h{};
+  return finish_launch(ctx, &h);
 }
 
 gridff_status gridff_run(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* R, int32_t nsteps,

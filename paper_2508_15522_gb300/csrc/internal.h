@@ -15,6 +15,26 @@
 #define GRIDFF_ACC 9.648533e-3f       // A/fs^2 per eV/(A*amu)
 
 #ifdef __CUDACC__
+// SplitMix64 (Steele, Lea and Flood, 2014): the output for state x
+// (advance by the golden gamma, then the variant-13 mix).
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+// Uniform [0, 1) from the top 24 bits of a 64-bit draw.
+__device__ __forceinline__ float uniform_of(unsigned long long s) {
+  return (float)(s >> 40) * (1.0f / 16777216.0f);
+}
+// Standard normal from one 64-bit draw by Box-Muller:
+// u1 = ((s >> 40) + 1) / 2^24 in (0, 1], u2 = ((s >> 16) mod 2^24) / 2^24.
+__device__ __forceinline__ float normal_of(unsigned long long s) {
+  const float u1 = (float)((s >> 40) + 1) * (1.0f / 16777216.0f);
+  const float u2 = (float)((s >> 16) & 0xFFFFFF) * (1.0f / 16777216.0f);
+  return sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
+}
+
 // Rotation matrix (row-major) of a unit quaternion (w, x, y, z).
 __device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float R[9]) {
   R[0] = w * w + x * x - y * y - z * z;

@@ -194,17 +194,8 @@ __global__ void weights_bf16_kernel(const float* __restrict__ W, int n_out, int 
 }
 
 // Counter-based standard normal: splitmix64 of (seed, counter), Box-Muller.
-__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
-  x += 0x9E3779B97F4A7C15ull;
-  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-  return x ^ (x >> 31);
-}
 __device__ __forceinline__ float normal01(unsigned long long seed, unsigned long long counter) {
-  const unsigned long long r = splitmix64(seed ^ splitmix64(counter));
-  const float u1 = (float)((r >> 40) + 1) * (1.0f / 16777216.0f);    // (0, 1]
-  const float u2 = (float)((r >> 16) & 0xFFFFFF) * (1.0f / 16777216.0f);  // [0, 1)
-  return sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
+  return normal_of(splitmix64(seed ^ splitmix64(counter)));
 }
 
 // Proposal inputs: row r = [descriptor (n_desc), noise (n_noise)].

@@ -9,17 +9,9 @@
 
 namespace {
 
-__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
-  x += 0x9E3779B97F4A7C15ull;
-  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
-  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
-  return x ^ (x >> 31);
-}
-
 // Uniform [0, 1) draw j of row r (24 bits).
 __device__ __forceinline__ float uniform01(unsigned long long seed, int r, int j) {
-  const unsigned long long s = mix64(seed ^ mix64((unsigned long long)r * 64 + j));
-  return (float)(s >> 40) * (1.0f / 16777216.0f);
+  return uniform_of(splitmix64(seed ^ splitmix64((unsigned long long)r * 64 + j)));
 }
 
 // One warp per replica: centre of mass uniform over the tile and over
@@ -137,6 +129,52 @@ __global__ void dedupe_kernel(const Moments* __restrict__ mom, const float* __re
   if (lane == 0) dup_of[i] = found;
 }
 
+// Mean x, y of each structure (for the minimum-image shift).
+__global__ void centers_kernel(const float* __restrict__ xyz, int na, int n, float2* __restrict__ cen) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float* p = xyz + (size_t)i * na * 3;
+  float sx = 0.f, sy = 0.f;
+  for (int a = 0; a < na; ++a) {
+    sx += p[3 * a];
+    sy += p[3 * a + 1];
+  }
+  cen[i] = make_float2(sx / na, sy / na);
+}
+
+// dup_of[i] = smallest j < i whose mean squared atom displacement from i,
+// after shifting j by whole tile periods toward i's mean position, is below
+// thr2; else -1.  One warp per i; lane l tests j = j0 + l over all atoms.
+__global__ void dedupe_xyz_kernel(const float* __restrict__ xyz, const float2* __restrict__ cen, int na, int n,
+                                  float Lx, float Ly, float thr2, int* __restrict__ dup_of) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  const float* pi = xyz + (size_t)i * na * 3;
+  const float2 ci = cen[i];
+  const float lim = thr2 * na;
+  int found = -1;
+  for (int j0 = 0; j0 < i && found < 0; j0 += 32) {
+    const int j = j0 + lane;
+    bool hit = false;
+    if (j < i) {
+      const float2 cj = cen[j];
+      const float tx = Lx * rintf((ci.x - cj.x) / Lx), ty = Ly * rintf((ci.y - cj.y) / Ly);
+      const float* pj = xyz + (size_t)j * na * 3;
+      float ss = 0.f;
+      for (int a = 0; a < na && ss < lim; ++a) {
+        const float dx = pi[3 * a] - pj[3 * a] - tx, dy = pi[3 * a + 1] - pj[3 * a + 1] - ty;
+        const float dz = pi[3 * a + 2] - pj[3 * a + 2];
+        ss += dx * dx + dy * dy + dz * dz;
+      }
+      hit = ss < lim;
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, hit);
+    if (b) found = j0 + __ffs(b) - 1;
+  }
+  if (lane == 0) dup_of[i] = found;
+}
+
 }  // namespace
 
 extern "C" {
@@ -195,3 +233,37 @@ gridff_status gridff_rmsd_unique(gridff_replicas* R, int32_t tmpl, int32_t n, co
 }
 
 }  // extern "C"
+
+extern "C" gridff_status gridff_rmsd_unique_xyz(gridff_ctx* ctx, int32_t na, int32_t n, const float* xyz,
+                                                const double tile_xy[2], double threshold, int32_t* dup_of,
+                                                int flags) {
+  if (!ctx || !tile_xy || n < 0 || (n > 0 && (!xyz || !dup_of))) return set_err(ctx, GRIDFF_EINVAL, "null argument");
+  if (na < 1 || na > GRIDFF_MAX_ATOMS) return set_err(ctx, GRIDFF_EINVAL, "n_atoms %d outside 1..%d", na, GRIDFF_MAX_ATOMS);
+  if (!(threshold > 0) || !(tile_xy[0] > 0 && tile_xy[1] > 0))
+    return set_err(ctx, GRIDFF_EINVAL, "threshold and tile must be positive");
+  if (n == 0) return GRIDFF_OK;
+  GRIDFF_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  const bool dev = flags & GRIDFF_DEVICE_PTRS;
+  const size_t xyz_bytes = (size_t)n * na * 3 * sizeof(float), dup_bytes = (size_t)n * sizeof(int32_t);
+  const size_t cen_off = 0, xyz_off = ((size_t)n * sizeof(float2) + 255) & ~(size_t)255;
+  const size_t dup_off = xyz_off + ((xyz_bytes + 255) & ~(size_t)255);
+  char* buf = nullptr;
+  GRIDFF_CUDA(ctx, cudaMallocAsync((void**)&buf, dup_off + dup_bytes, s));
+  const float* p = dev ? xyz : (const float*)(buf + xyz_off);
+  int* d = dev ? dup_of : (int*)(buf + dup_off);
+  float2* cen = (float2*)(buf + cen_off);
+  cudaError_t e = cudaSuccess;
+  if (!dev) e = cudaMemcpyAsync(buf + xyz_off, xyz, xyz_bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    centers_kernel<<<(n + 127) / 128, 128, 0, s>>>(p, na, n, cen);
+    dedupe_xyz_kernel<<<(unsigned)(((long long)n * 32 + 127) / 128), 128, 0, s>>>(
+        p, cen, na, n, (float)tile_xy[0], (float)tile_xy[1], (float)(threshold * threshold), d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(dup_of, d, dup_bytes, cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(buf, s);
+  if (e == cudaSuccess && !(dev && (flags & GRIDFF_ASYNC))) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return set_err(ctx, GRIDFF_ECUDA, "rmsd_unique_xyz: %s", cudaGetErrorString(e));
+  return GRIDFF_OK;
+}

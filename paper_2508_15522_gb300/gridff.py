@@ -72,6 +72,11 @@ class MDParams(C.Structure):
     _fields_ = [("dt", C.c_float), ("record_every", C.c_int32), ("clock_budget_s", C.c_double)]
 
 
+class LangevinParams(C.Structure):
+    _fields_ = [("dt", C.c_float), ("temperature", C.c_float), ("gamma", C.c_float), ("seed", C.c_uint64),
+                ("step0", C.c_int64), ("clock_budget_s", C.c_double)]
+
+
 class LaunchConfig(C.Structure):
     _fields_ = [("kernel", C.c_int32), ("lanes_per_replica", C.c_int32), ("warps_per_block", C.c_int32),
                 ("cache_slots", C.c_int32), ("queue", C.c_int32), ("l2_window", C.c_int32)]
@@ -111,6 +116,8 @@ def _load():
                                    C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_size_t)]),
         "gridff_grid_download_f64": (I32, [P, C.c_int, C.POINTER(C.c_double)]),
         "gridff_grid_storage": (I32, [P, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
+        "gridff_langevin": (I32, [P, P, P, I32, C.POINTER(LangevinParams), C.c_int]),
+        "gridff_rmsd_unique_xyz": (I32, [P, I32, I32, P, C.POINTER(C.c_double), F64, P, C.c_int]),
         "gridff_grid_destroy": (None, [P]),
         "gridff_replicas_create": (I32, [P, I32, C.POINTER(Molecule), I32, C.POINTER(C.c_int32), I32,
                                          F64, C.POINTER(P)]),
@@ -167,7 +174,7 @@ EXPORTED = (
     "gridff_mlp_get_params", "gridff_mlp_forward", "gridff_mlp_train_step", "gridff_mlp_propose",
     "gridff_molecule_descriptor", "gridff_random_poses", "gridff_rmsd_unique",
     "gridff_set_launch_config", "gridff_get_launch_config", "gridff_tune", "gridff_relax_graph_create",
-    "gridff_grid_storage",
+    "gridff_grid_storage", "gridff_langevin", "gridff_rmsd_unique_xyz",
     "gridff_graph_launch", "gridff_graph_destroy",
 )
 
@@ -623,3 +630,24 @@ class RelaxGraph:
             self.close()
         except Exception:
             pass
+
+
+def langevin(ctx: Context, grid, reps: Replicas, nsteps: int, dt: float, temperature: float, gamma: float,
+             seed: int, step0: int = 0, flags: int = 0, clock_budget_s: float = 0.0, check: bool = True):
+    """gridff_langevin (BAOAB) -> status."""
+    p = LangevinParams(dt, temperature, gamma, C.c_uint64(seed), step0, clock_budget_s)
+    st = lib.gridff_langevin(ctx.h, grid.h if grid else None, reps.h, int(nsteps), C.byref(p), flags)
+    if check and st != OK:
+        ctx.check(st)
+    return st
+
+
+def rmsd_unique_xyz(ctx: Context, xyz, tile_xy, threshold=0.1):
+    """dup_of for n structures of one molecule, xyz (n, n_atoms, 3)."""
+    x = np.ascontiguousarray(xyz, np.float32)
+    n, na = x.shape[0], x.shape[1]
+    out = np.empty(n, np.int32)
+    t = (C.c_double * 2)(*tile_xy)
+    ctx.check(lib.gridff_rmsd_unique_xyz(ctx.h, na, n, x.ctypes.data_as(C.c_void_p), t, float(threshold),
+                                         out.ctypes.data_as(C.c_void_p), 0))
+    return out

@@ -1,6 +1,10 @@
-"""Sampling of adsorption minima of a rigid molecule over a substrate grid.
+"""Sampling of adsorption minima over a substrate grid.
 
-Two ways to choose where FIRE relaxations start, both on the device:
+Minima hopping of flexible molecules (Sec. 7): Langevin thermalisation,
+FIRE relaxation and the RMSD uniqueness filter, repeated (`MinimaHopping`).
+
+For rigid molecules, two ways to choose where FIRE relaxations start, both
+on the device:
 
 * random starts (Sec. 7: random placements over the surface), drawn by
   ``gridff_random_poses``;
@@ -149,3 +153,53 @@ def new_network(ctx: G.Context, targets: np.ndarray, seed: int = 0) -> G.MLP:
     Ws, bs = init_params(net.sizes, seed, out_bias)
     net.set_params(Ws, bs)
     return net
+
+
+class MinimaHopping:
+    """Minima hopping of flexible replicas adsorbed on the substrate (Sec. 7):
+    every hop thermalises all replicas by Langevin dynamics at T for
+    `md_steps` steps (BAOAB, `gridff_langevin`), relaxes them by FIRE until
+    |F| < f_conv (0.1 meV/A in the paper), and compares every converged
+    structure with all minima found so far by the RMSD criterion
+    (`gridff_rmsd_unique_xyz`, 0.1 A), lowest energy first.  The next hop
+    starts from the relaxed structures.  `curve` records (seconds of
+    sampling, unique minima, converged relaxations) after each hop."""
+
+    def __init__(self, ctx: G.Context, grid: G.Grid, mol, x0: np.ndarray, tile_xy, temperature=300.0,
+                 md_steps=1000, dt=1.0, gamma=0.01, f_conv=1e-4, relax_steps=5000, rmsd=0.1, seed=1):
+        self.ctx, self.grid, self.mol, self.tile = ctx, grid, mol, tuple(tile_xy)
+        n_rep = len(x0)
+        self.reps = G.Replicas(ctx, [mol], [0] * n_rep)
+        self.reps.set_state(np.ascontiguousarray(x0, np.float32).ravel())
+        self.T, self.md_steps, self.dt, self.gamma = temperature, md_steps, dt, gamma
+        self.fire = G.fire_params(f_conv=f_conv)
+        self.relax_steps, self.rmsd, self.seed = relax_steps, rmsd, seed
+        self.step = 0
+        self.db_x = np.zeros((0, mol.n, 3), np.float32)
+        self.db_E = np.zeros(0)
+        self.elapsed = 0.0
+        self.curve = []
+
+    def hop(self):
+        t0 = time.perf_counter()
+        G.langevin(self.ctx, self.grid, self.reps, self.md_steps, self.dt, self.T, self.gamma, self.seed,
+                   step0=self.step)
+        self.step += self.md_steps
+        G.relax(self.ctx, self.grid, self.reps, self.relax_steps, self.fire, check=False)
+        fs = self.reps.fire_state()
+        conv = (fs["status"] & G.REP_CONVERGED) != 0
+        x = self.reps.positions().reshape(len(conv), self.mol.n, 3)
+        cand_x, cand_E = x[conv], fs["energy"][conv]
+        order = np.argsort(cand_E, kind="stable")
+        cand_x, cand_E = cand_x[order], cand_E[order]
+        S = np.concatenate([self.db_x, cand_x])
+        dup = G.rmsd_unique_xyz(self.ctx, S, self.tile, self.rmsd) if len(S) else np.zeros(0, np.int32)
+        new = dup[len(self.db_x):] < 0
+        self.db_x = np.concatenate([self.db_x, cand_x[new]])
+        self.db_E = np.concatenate([self.db_E, cand_E[new]])
+        self.elapsed += time.perf_counter() - t0
+        self.curve.append((self.elapsed, len(self.db_x), int(conv.sum())))
+        return self.curve[-1]
+
+    def close(self):
+        self.reps.close()

@@ -108,6 +108,24 @@ def rocksalt_slab(a: float = 5.64, ncell: int = 4, layers: int = 2,
     return Substrate(xyz, np.array(q), R, eps, el, cell, z_top, (2 * a, 2 * a))
 
 
+def with_top_vacancy(sub: Substrate, element: str = "Cl") -> Substrate:
+    """The slab with one ``element`` atom of the top layer removed (the one
+    nearest the centre of the supercell).  The defect repeats with the
+    supercell, so the grid tile becomes the orthogonal period of the
+    supercell lattice, A1 + A2 and A1 - A2 for the rock-salt supercell."""
+    top = np.where((np.abs(sub.xyz[:, 2] - sub.z_top) < 1e-6) &
+                   (np.array(sub.elements) == element))[0]
+    centre = 0.5 * (sub.cell[0] + sub.cell[1])
+    k = top[np.argmin(np.linalg.norm(sub.xyz[top, :2] - centre[:2], axis=1))]
+    keep = np.ones(sub.n, bool)
+    keep[k] = False
+    ex = sub.cell[0] + sub.cell[1]
+    ey = sub.cell[0] - sub.cell[1]
+    return Substrate(sub.xyz[keep], sub.q[keep], sub.R[keep], sub.eps[keep],
+                     [e for e, kk in zip(sub.elements, keep) if kk], sub.cell, sub.z_top,
+                     (float(abs(ex[0])), float(abs(ey[1]))))
+
+
 def fcc111_slab(a: float = 4.08, ncell: int = 12, layers: int = 4,
                 grid_height: float = 20.0, z_gap: float = 1.0,
                 vacuum_factor: float = 3.0) -> Substrate:

@@ -149,3 +149,46 @@ def test_no_squish_energy_error_second_order():
                                mol.xyz, mol.mass, fn, int(round(400 / dt)), dt)
         errs.append(np.abs(tr[:, 0] - tr[0, 0]).max())
     assert 3.0 < errs[0] / errs[1] < 5.0
+
+
+def test_langevin_without_friction_is_velocity_verlet():
+    g = np.random.default_rng(41)
+    k = 0.7
+    x0 = g.standard_normal((3, 4, 3)); v0 = 0.01 * g.standard_normal((3, 4, 3)); mass = np.full(4, 12.0)
+    fn = lambda x: (0.5 * k * np.sum(x * x, (1, 2)), -k * x, np.zeros(len(x), int))
+    xl, vl, _ = dyn.langevin_baoab(x0, v0, mass, fn, 50, 0.7, 300.0, 0.0, lambda s: g.standard_normal((3, 12)))
+    xv, vv, _ = dyn.nve_flexible(x0, v0, mass, fn, 50, 0.7)
+    assert np.allclose(xl, xv, atol=1e-12) and np.allclose(vl, vv, atol=1e-12)
+
+
+def test_langevin_free_particles_reach_maxwell_boltzmann():
+    g = np.random.default_rng(42)
+    R, n, T, m = 50, 20, 300.0, 12.0
+    fn = lambda x: (np.zeros(len(x)), np.zeros_like(x), np.zeros(len(x), int))
+    x, v, _ = dyn.langevin_baoab(np.zeros((R, n, 3)), np.zeros((R, n, 3)), np.full(n, m), fn, 30, 1.0, T, 1.0,
+                                  lambda s: g.standard_normal((R, 3 * n)))
+    var = dyn.KB * T * dyn.ACC / m
+    N = v.size
+    assert abs(np.mean(v * v) / var - 1.0) < 5 * np.sqrt(2.0 / N)
+
+
+def test_langevin_harmonic_configurational_temperature():
+    """BAOAB samples the harmonic oscillator's positions exactly:
+    <x^2> = kB T / k."""
+    g = np.random.default_rng(43)
+    R, n, T, k = 40, 10, 300.0, 1.0
+    fn = lambda x: (0.5 * k * np.sum(x * x, (1, 2)), -k * x, np.zeros(len(x), int))
+    x = np.zeros((R, n, 3)); v = np.zeros((R, n, 3))
+    acc = []
+    for block in range(40):
+        x, v, _ = dyn.langevin_baoab(x, v, np.full(n, 12.0), fn, 50, 2.0, T, 0.05,
+                                      lambda s: g.standard_normal((R, 3 * n)))
+        if block >= 10:
+            acc.append(np.mean(x * x))
+    assert abs(np.mean(acc) / (dyn.KB * T / k) - 1.0) < 0.05
+
+
+def test_langevin_noise_stream_is_standard_normal():
+    z = dyn.langevin_noise(99, range(20), 7, 60).ravel()
+    assert abs(z.mean()) < 4 / np.sqrt(z.size) and abs(z.var() - 1) < 6 * np.sqrt(2 / z.size)
+    assert not np.array_equal(dyn.langevin_noise(99, [0], 7, 5), dyn.langevin_noise(99, [0], 8, 5))

@@ -56,3 +56,22 @@ def test_random_poses_ranges_and_uniform_orientation(body):
     R = quat_matrix(P[:, 3:])
     assert np.abs(R.mean(0)).max() < 4 / np.sqrt(n)
     assert np.mean(P[:, 3] ** 2) == pytest.approx(0.25, abs=4 * 0.15 / np.sqrt(n))
+
+
+def test_rmsd_xyz_translation_tile_image_and_conformation():
+    g = np.random.default_rng(12)
+    a = g.standard_normal((9, 3)) + [3.0, 4.0, 8.0]
+    b = a + [0.3, 0.0, -0.4]
+    assert sampling.rmsd_xyz(a, b, TILE) == pytest.approx(0.5)
+    assert sampling.rmsd_xyz(a, a + [2 * TILE[0], -TILE[1], 0.0], TILE) == pytest.approx(0.0, abs=1e-12)
+    c = a.copy(); c[0] += [0.0, 0.0, 0.9]                       # one atom moved: conformation counts
+    assert sampling.rmsd_xyz(a, c, TILE) == pytest.approx(0.3)
+    # a rotation about the mean position is not aligned away
+    ang = 0.2
+    Rz = np.array([[np.cos(ang), -np.sin(ang), 0], [np.sin(ang), np.cos(ang), 0], [0, 0, 1.0]])
+    m = a.mean(0)
+    r = (a - m) @ Rz.T + m
+    ref = np.sqrt(np.mean(np.sum((a - r) ** 2, 1)))
+    assert sampling.rmsd_xyz(a, r, TILE) == pytest.approx(ref) and ref > 0.1
+    assert sampling.dup_of_xyz([a, b, a + [TILE[0], 0, 0], c, b + [0.01, 0, 0]], TILE, 0.1).tolist() == \
+        [-1, -1, 0, -1, 1]
