@@ -444,6 +444,64 @@ def precision_comparison(G, ctx):
     return out
 
 
+def c2_accuracy(G, ctx, grid, sub, mol, pose, n_sample=8):
+    """Error of the GPU energies and forces against the FP64 pairwise
+    reference (direct Morse sums over the periodic slab and the EW3DC
+    Ewald potential) for the first n_sample replicas at their start poses."""
+    from oracle import dynamics as odyn
+    from oracle import substrate as osub
+    reps = G.Replicas(ctx, [mol], [0] * n_sample, rigid=True)
+    reps.set_state(pose[:n_sample].ravel())
+    E, F, Ea, S = G.eval(ctx, grid, reps)
+    body = mol.xyz.astype(np.float32).astype(np.float64)
+    x = odyn.rigid_positions(pose[:n_sample, :3].astype(np.float64), pose[:n_sample, 3:].astype(np.float64), body)
+    Er, Fr = osub.pairwise_reference(x.reshape(-1, 3), np.tile(mol.q, n_sample), np.tile(mol.R, n_sample),
+                                     np.tile(mol.eps, n_sample), sub)
+    reps.close()
+    return {"replicas": n_sample, "max_abs_dE_per_molecule_eV": float(np.abs(E - Er.reshape(n_sample, -1).sum(1)).max()),
+            "max_abs_dE_per_atom_eV": float(np.abs(Ea - Er).max()),
+            "max_abs_dF_eV_per_A": float(np.abs(F - Fr).max()),
+            "reference": "FP64 pairwise (Morse direct sums within 17 A + EW3DC Ewald)"}
+
+
+def interpolation_roofline(G, ctx, grid, box, torch, dev, stream, l2_peak):
+    """Grid interpolation alone (gridff_eval, no intramolecular terms, no
+    stencil reuse) at uniform random points over the tile and the z band
+    [z0 + 2, z0 + 8] A: 65536 x 38 = 2.49 M points per launch, 20 launches
+    back to back on the stream (the grid stays L2-resident)."""
+    from paper_2508_15522_gb300 import synth
+    n_rep, n_at = 65536, 38
+    g = synth.rng(3003)
+    els = list(g.choice(["C", "H", "O"], n_at))
+    R = np.array([synth.ELEMENTS[e][0] for e in els]); eps = np.array([synth.ELEMENTS[e][1] for e in els])
+    pm = synth.Molecule(els, np.zeros((n_at, 3)), g.uniform(-0.3, 0.3, n_at), R, eps, np.full(n_at, 12.0))
+    reps = G.Replicas(ctx, [pm], [0] * n_rep)
+    pts = synth.uniform_points(n_rep * n_at, box, 3004, zband=(2.0, 8.0)).astype(np.float32)
+    reps.set_state(torch.from_numpy(pts.ravel()).to(dev))
+    E = torch.empty(n_rep, dtype=torch.float64, device=dev)
+    F = torch.empty(3 * n_rep * n_at, dtype=torch.float32, device=dev)
+    Ea = torch.empty(n_rep * n_at, dtype=torch.float32, device=dev)
+    St = torch.empty(n_rep, dtype=torch.int32, device=dev)
+    for _ in range(3):
+        G.eval(ctx, grid, reps, flags=G.NO_INTRA | G.ASYNC, out=(E, F, Ea, St))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    iters = 20
+    for _ in range(iters):
+        G.eval(ctx, grid, reps, flags=G.NO_INTRA | G.ASYNC, out=(E, F, Ea, St))
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / iters
+    evals = n_rep * n_at
+    achieved = BYTES_PER_EVAL * evals / (ms * 1e-3) / 1e9
+    reps.close()
+    return {"kernel": "eval_kernel (quad gather, no stencil cache)", "atom_evals_per_s": evals / (ms * 1e-3),
+            "ms_per_launch": ms, "points_per_launch": evals, "points": "uniform over the tile, z0 + [2, 8] A",
+            "roofline": {"bound": "l2", "achieved": achieved, "peak": l2_peak, "unit": "GB/s",
+                         "frac": achieved / l2_peak if l2_peak else None}}
+
+
 def minima_hopping_curve(G, ctx):
     """Minima hopping (Sec. 7) of a flexible 22-atom molecule on a NaCl(001)
     slab with a Cl vacancy (4 x 4 primitive cells, 3 layers, 95 atoms; grid
@@ -582,6 +640,8 @@ def run_gpu(args):
         line["uneven_batch"] = uneven_batch_comparison(G, ctx, grid, sub)
         line["precision_tiers"] = precision_comparison(G, ctx)
         line["minima_hopping"] = minima_hopping_curve(G, ctx)
+        line["interpolation_only"] = interpolation_roofline(G, ctx, grid, box, torch, dev, stream, l2_peak)
+        line["accuracy_vs_fp64_pairwise"] = c2_accuracy(G, ctx, grid, sub, mol, pose)
     if rank == 0 and world == 1 and not args.quick:
         cv, cdt, cdesc = oracle_sample()
         line["cpu_baseline"] = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cdesc}
