@@ -146,6 +146,44 @@ def oracle_sample(iters=ORACLE_SAMPLE_ITERS):
     return evals / dt, dt, desc
 
 
+def _oracle_worker(args):
+    """One process of the all-cores oracle sample: rigid FIRE of replicas
+    [lo, hi) (single-threaded numpy)."""
+    lo, hi, iters = args
+    from oracle import dynamics as odyn
+    from oracle import grid as ogrid
+    from paper_2508_15522_gb300 import synth
+    sub, box, mol, pose = workload()
+    n, h = ogrid.grid_dims(box.length, box.spacing)
+    coefs = synth.random_coefficients(n, 3, seed=SEED, scale=(0.01, 0.01, 0.01))
+    fn = odyn.make_force_fn(coefs, ("C", "P", "L"), box.origin, h, mol, intra=False)
+    t0 = time.perf_counter()
+    odyn.fire_rigid(pose[lo:hi, :3].astype(np.float64), pose[lo:hi, 3:].astype(np.float64), np.zeros((hi - lo, 3)),
+                    np.zeros((hi - lo, 3)), mol.xyz, mol.mass, fn, iters, odyn.FireParams(f_conv=0.0))
+    return (hi - lo) * mol.n * iters, time.perf_counter() - t0
+
+
+def oracle_sample_all_cores(iters=ORACLE_SAMPLE_ITERS, per_proc=16):
+    """The oracle sample spread over every host core: one spawned process per
+    core, each relaxing `per_proc` replicas (numpy pinned to one thread per
+    process).  Returns (atom-evals/s over the wall time of the parallel
+    section, seconds, cores, description)."""
+    import multiprocessing as mp
+    cores = max(1, min(os.cpu_count() or 1, 64))
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    jobs = [(k * per_proc, (k + 1) * per_proc, iters) for k in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_worker, [(0, 1, 1)] * cores)          # start-up and imports, untimed
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_worker, jobs)
+        wall = time.perf_counter() - t0
+    evals = sum(e for e, _ in res)
+    desc = (f"{cores * per_proc} of the {N_REP} replicas x {iters} FIRE iterations on a full-size "
+            f"113x113x200 coefficient grid (numpy FP64), {cores} processes x {per_proc} replicas, one per core")
+    return evals / wall, wall, cores, desc
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -154,7 +192,7 @@ def run_reference(args):
         pass   # the oracle has no warm-up state; warm-up steps are not timed
     vals = []
     for _ in range(args.steps):
-        v, dt, desc = oracle_sample(REFERENCE_STEP_ITERS)
+        v, dt, cores, desc = oracle_sample_all_cores(REFERENCE_STEP_ITERS)
         vals.append((v, dt))
     value = statistics.mean(v for v, _ in vals)
     ms = statistics.mean(dt for _, dt in vals) * 1e3
@@ -162,7 +200,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config({"sample": desc}),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -643,13 +681,54 @@ def run_gpu(args):
         line["interpolation_only"] = interpolation_roofline(G, ctx, grid, box, torch, dev, stream, l2_peak)
         line["accuracy_vs_fp64_pairwise"] = c2_accuracy(G, ctx, grid, sub, mol, pose)
     if rank == 0 and world == 1 and not args.quick:
-        cv, cdt, cdesc = oracle_sample()
-        line["cpu_baseline"] = {"value": cv, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cdesc}
+        cv, cdt, ccores, cdesc = oracle_sample_all_cores()
+        line["cpu_baseline"] = {"value": cv, "unit": UNIT, "cores": ccores, "kind": "oracle", "sample": cdesc}
+        cv1, cdt1, cdesc1 = oracle_sample()
+        line["cpu_baseline_1core"] = {"value": cv1, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cdesc1}
     if rank == 0:
         print(json.dumps(line))
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def profile_case(args):
+    """A small, self-contained launch of one kernel family for ncu captures
+    (no JSON line): `uneven` relaxes 4096 of the uneven flexible replicas
+    for 20 FIRE iterations; `langevin` runs 20 Langevin steps on them;
+    `mlp` runs 20 training steps of the proposal network.  Each runs its
+    launch twice (the second is the one to capture with -s)."""
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2508_15522_gb300 import gridff as G
+    from paper_2508_15522_gb300 import synth
+    ctx = G.Context(0)
+    if args.profile_case in ("uneven", "langevin"):
+        sub, box, _, _ = workload()
+        grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing)
+        mols, tof = synth.uneven_batch(16384, 256, 77)
+        tof = tof[:4096]
+        reps = G.Replicas(ctx, mols, tof)
+        x0 = uneven_positions(G, reps, mols, tof, sub, 5000)
+        for _ in range(2):
+            reps.set_state(x0)
+            if args.profile_case == "uneven":
+                G.relax(ctx, grid, reps, 20, G.fire_params(f_conv=0.0))
+            else:
+                G.langevin(ctx, grid, reps, 20, 1.0, 300.0, 0.01, 11)
+        print(args.profile_case, "kernel ms", ctx.last_kernel_ms())
+    elif args.profile_case == "mlp":
+        from paper_2508_15522_gb300 import sampling as S
+        g = np.random.default_rng(5)
+        T = np.zeros((4096, G.MLP_OUT), np.float32)
+        T[:, :3] = g.uniform(0, 5.64, (4096, 3))
+        q = g.standard_normal((4096, 4))
+        T[:, 3:7] = q / np.linalg.norm(q, axis=1, keepdims=True)
+        net = S.new_network(ctx, T, seed=1)
+        surf = S.Surface((0.0, 0.0), (5.64, 5.64), 0.0, 1.0, 0.0)
+        for _ in range(2):
+            S.train(net, np.zeros(S.N_DESC, np.float32), T, surf, 20, batch=256, K=8)
+        print("mlp trained")
 
 
 def main():
@@ -662,8 +741,12 @@ def main():
                     help="FIRE iterations per step (profiling runs use a short step)")
     ap.add_argument("--quick", action="store_true",
                     help="skip the e2e leg, the bandwidth probes and the CPU baseline (profiling runs)")
+    ap.add_argument("--profile-case", choices=["uneven", "langevin", "mlp"], default=None,
+                    help="run one small kernel case for an ncu capture and exit (no JSON line)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_case:
+        profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)
