@@ -304,7 +304,7 @@ def minima_comparison(G, ctx, grid, mol, sub):
     T = S.pose_targets(P[h], surf)
     net = S.new_network(ctx, T, seed=1)
     t0 = time.perf_counter()
-    losses = S.train(net, sp.desc, T, surf, 3000, batch=256, K=8, lr=1e-3, seed=7)
+    losses = S.train_on_device(net, sp.desc, T, surf, 3000, batch=256, K=8, lr=1e-3, seed=7)
     train_s = time.perf_counter() - t0
     out = {"surface_tile_A": [a, a], "relaxations_for_training": 64 * n_rep, "converged_minima": int(sum(C)),
            "training_targets": int(h.sum()), "generation_s": gen_s, "best_known_eV": e_best,
@@ -727,7 +727,7 @@ def profile_case(args):
         net = S.new_network(ctx, T, seed=1)
         surf = S.Surface((0.0, 0.0), (5.64, 5.64), 0.0, 1.0, 0.0)
         for _ in range(2):
-            S.train(net, np.zeros(S.N_DESC, np.float32), T, surf, 20, batch=256, K=8)
+            S.train_on_device(net, np.zeros(S.N_DESC, np.float32), T, surf, 20, batch=256, K=8)
         print("mlp trained")
 
 

@@ -497,6 +497,28 @@ gridff_status gridff_mlp_train_step(gridff_mlp* mlp, int32_t n_targets, int32_t 
                                     const float* targets, const float* tors_mask,
                                     const gridff_train_params* params, float* loss_out, int flags);
 
+/* Upload a training set of n target poses ([n][19], unit quaternions) and
+ * optional torsion masks ([n][12], NULL = no torsions) into device memory
+ * owned by the network (replaces the previous set).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+gridff_status gridff_mlp_set_targets(gridff_mlp* mlp, int32_t n, const float* targets,
+                                     const float* tors_mask);
+
+/* `steps` training steps on the device with no host round trip between
+ * them.  Step s (a counter kept by the network across calls) draws its
+ * n_targets targets from the training set, target b being row
+ * splitmix64(seed XOR splitmix64(2^20 s + b)) mod n, and K input rows per
+ * target: the descriptor (n_desc floats, host) followed by
+ * sizes[0] - n_desc <= 64 normal draws, draw j of row m from the counter
+ * 64 (2^20 s + m) + j (the generator of gridff_mlp_propose); then the
+ * winner-takes-all loss, backward pass and Adam step of
+ * gridff_mlp_train_step.  losses (host, may be NULL) receives the mean loss
+ * of every step.  n_targets K < 2^20.  Errors: EINVAL (no training set),
+ * ENOMEM, ECUDA. */
+gridff_status gridff_mlp_train(gridff_mlp* mlp, int32_t steps, int32_t n_targets, int32_t K,
+                               const float* descriptor, int32_t n_desc, uint64_t seed,
+                               const gridff_train_params* params, float* losses);
+
 /* Propose one pose per replica of a rigid replica set: inputs are the
  * descriptor (n_desc <= sizes[0] floats, host) followed by
  * sizes[0] - n_desc <= 64 standard normal draws from a counter-based

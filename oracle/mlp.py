@@ -132,3 +132,20 @@ def counter_normal(seed: int, rows: int, dim: int) -> np.ndarray:
             u2 = ((s >> 16) & 0xFFFFFF) / 2.0 ** 24
             out[r, j] = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
     return out
+
+
+def train_batch(seed: int, step: int, n_all: int, B: int, K: int, desc, n_noise: int):
+    """The library's device-side training batch of step `step`: target rows
+    splitmix64(seed ^ splitmix64(2^20 step + b)) mod n_all, and inputs
+    [descriptor, noise] with noise j of row m from the counter
+    64 (2^20 step + m) + j (Box-Muller in float64 here)."""
+    rows = [splitmix64(seed ^ splitmix64((step << 20) + b)) % n_all for b in range(B)]
+    X = np.zeros((B * K, len(desc) + n_noise))
+    X[:, :len(desc)] = np.asarray(desc, np.float64)
+    for m in range(B * K):
+        for j in range(n_noise):
+            s = splitmix64(seed ^ splitmix64((((step << 20) + m) << 6) + j))
+            u1 = ((s >> 40) + 1) / 2.0 ** 24
+            u2 = ((s >> 16) & 0xFFFFFF) / 2.0 ** 24
+            X[m, len(desc) + j] = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    return np.array(rows), X

@@ -17,6 +17,7 @@ namespace {
 
 constexpr int kOut = 19;      // 3 position + 4 quaternion + 12 torsions
 constexpr int kTors = 12;
+constexpr int kMaxSplit = 8;  // split-K parts of the weight-gradient GEMM
 
 inline int pad16(int n) { return (n + 15) & ~15; }
 
@@ -26,13 +27,22 @@ inline int pad16(int n) { return (n + 15) & ~15; }
 // N % 8 == 0, K % 16 == 0.  One warp per 16 x 8 output tile, K in steps of
 // 16 with one tensor-core mma per step.
 // ---------------------------------------------------------------------------
+// C[M][N] (FP32) = A[M][K] * B, A row-major bf16 (lda), B given as Bt[N][K]
+// row-major bf16 (ldb), i.e. B is K x N column-major.  M % 16 == 0,
+// N % 8 == 0, K % 16 == 0.  One warp per 16 x 8 output tile, K in steps of
+// 16 with one tensor-core mma per step.  Split K: block row y handles
+// K range [y K, (y + 1) K) and writes its partial product to C + y * cstride.
 __global__ void gemm_bf16_kernel(const __nv_bfloat16* __restrict__ A, int lda,
                                  const __nv_bfloat16* __restrict__ Bt, int ldb, float* __restrict__ C,
-                                 int ldc, int M, int N, int K, int accumulate) {
+                                 int ldc, int M, int N, int K, long long cstride) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const int tiles_n = N / 8;
   if (warp >= (M / 16) * tiles_n) return;
+  const int ks = blockIdx.y;
+  A += (size_t)ks * K;
+  Bt += (size_t)ks * K;
+  C += (size_t)ks * cstride;
   const int tm = warp / tiles_n, tn = warp % tiles_n;
   const int g = lane >> 2, t = lane & 3;
   float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
@@ -54,11 +64,18 @@ __global__ void gemm_bf16_kernel(const __nv_bfloat16* __restrict__ A, int lda,
   }
   float* r0 = C + (size_t)(tm * 16 + g) * ldc + tn * 8 + 2 * t;
   float* r1 = r0 + (size_t)8 * ldc;
-  if (accumulate) {
-    r0[0] += c0; r0[1] += c1; r1[0] += c2; r1[1] += c3;
-  } else {
-    r0[0] = c0; r0[1] = c1; r1[0] = c2; r1[1] = c3;
-  }
+  r0[0] = c0; r0[1] = c1; r1[0] = c2; r1[1] = c3;
+}
+
+// C = sum over the S partial products (fixed order: deterministic).
+__global__ void splitk_sum_kernel(const float* __restrict__ part, long long cstride, int S, int M, int N, int ldc,
+                                  float* __restrict__ C) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)M * N) return;
+  const long long off = (idx / N) * ldc + idx % N;
+  float v = 0.f;
+  for (int k = 0; k < S; ++k) v += part[k * cstride + off];
+  C[off] = v;
 }
 
 // Input rows (FP32 [rows][n_in]) -> bf16 layer input, row-major [Mp][in_p]
@@ -158,13 +175,32 @@ __global__ void grad_prep_kernel(float* __restrict__ G, const float* __restrict_
   GbT[(size_t)j * Mp + m] = b;
 }
 
-// db[j] = sum_m G[m][j]
-__global__ void colsum_kernel(const float* __restrict__ G, int Mp, int out_p, int n_out, float* __restrict__ db) {
+// db[j] = sum_m G[m][j] in two passes (deterministic): block (x, y) sums
+// rows [y R, (y + 1) R) of 32 columns (8 row groups, coalesced across the
+// columns) into part[y][j]; then colsum_final adds the chunks in order.
+__global__ void colsum_kernel(const float* __restrict__ G, int Mp, int out_p, int n_out, int rows_per_chunk,
+                              float* __restrict__ part) {
+  __shared__ float sh[8][33];
+  const int j = blockIdx.x * 32 + threadIdx.x;
+  const int m0 = blockIdx.y * rows_per_chunk, m1 = min(Mp, m0 + rows_per_chunk);
+  float s = 0.f;
+  if (j < n_out)
+    for (int m = m0 + threadIdx.y; m < m1; m += 8) s += G[(size_t)m * out_p + j];
+  sh[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && j < n_out) {
+    float t = 0.f;
+    for (int y = 0; y < 8; ++y) t += sh[y][threadIdx.x];
+    part[(size_t)blockIdx.y * n_out + j] = t;
+  }
+}
+
+__global__ void colsum_final_kernel(const float* __restrict__ part, int chunks, int n_out, float* __restrict__ db) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n_out) return;
-  float s = 0.f;
-  for (int m = 0; m < Mp; ++m) s += G[(size_t)m * out_p + j];
-  db[j] = s;
+  float t = 0.f;
+  for (int c = 0; c < chunks; ++c) t += part[(size_t)c * n_out + j];
+  db[j] = t;
 }
 
 // Adam on FP32 master parameters; c1 = lr / (1 - b1^t), c2 = 1 / (1 - b2^t).
@@ -237,6 +273,55 @@ __global__ void pose_kernel(const float* __restrict__ Y, int rows, float ox, flo
   }
 }
 
+// Training batch drawn on the device: target b of step `step` is row
+// splitmix64(seed ^ splitmix64(2^20 step + b)) mod n_all of the training set.
+__global__ void sample_targets_kernel(const float* __restrict__ T_all, const float* __restrict__ M_all, int n_all,
+                                      int B, unsigned long long seed, long long step, float* __restrict__ Ts,
+                                      float* __restrict__ Ms) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const unsigned long long h = splitmix64(seed ^ splitmix64(((unsigned long long)step << 20) + b));
+  const int row = (int)(h % (unsigned long long)n_all);
+  for (int j = 0; j < kOut; ++j) Ts[(size_t)b * kOut + j] = T_all[(size_t)row * kOut + j];
+  for (int j = 0; j < kTors; ++j) Ms[(size_t)b * kTors + j] = M_all ? M_all[(size_t)row * kTors + j] : 0.f;
+}
+
+// Training inputs: row m = [descriptor, N(0,1) noise], noise j of row m of
+// step `step` from the counter 64 (2^20 step + m) + j.
+__global__ void train_inputs_kernel(const float* __restrict__ desc, int n_desc, int n_noise, int rows,
+                                    unsigned long long seed, long long step, int Mp, int in_p,
+                                    __nv_bfloat16* __restrict__ H, __nv_bfloat16* __restrict__ HT) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= Mp * in_p) return;
+  const int m = idx / in_p, k = idx % in_p;
+  float v = 0.f;
+  if (m < rows) {
+    if (k < n_desc) {
+      v = desc[k];
+    } else if (k < n_desc + n_noise) {
+      const unsigned long long c = ((((unsigned long long)step << 20) + m) << 6) + (k - n_desc);
+      v = normal_of(splitmix64(seed ^ splitmix64(c)));
+    }
+  }
+  const __nv_bfloat16 b = __float2bfloat16(v);
+  H[idx] = b;
+  HT[(size_t)k * Mp + m] = b;
+}
+
+// out[0] = mean of loss[0..n) (one block).
+__global__ void loss_mean_kernel(const float* __restrict__ loss, int n, float* __restrict__ out) {
+  __shared__ float part[256];
+  float s = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += loss[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = part[0] / n;
+}
+
 inline unsigned grid1(long long n, int b = 256) { return (unsigned)((n + b - 1) / b); }
 
 }  // namespace
@@ -259,6 +344,7 @@ struct gridff_mlp {
   std::vector<__nv_bfloat16*> H, HT;   // layer inputs (L)
   std::vector<float*> Apre;             // pre-activations (L)
   float* C = nullptr;              // GEMM output scratch [cap][max_pad]
+  float* Cpart = nullptr;          // split-K partial products [8][max_pad][max_pad]
   float* G = nullptr;              // gradient scratch [cap][max_pad]
   float* G2 = nullptr;
   __nv_bfloat16* Gb = nullptr;
@@ -271,6 +357,13 @@ struct gridff_mlp {
   int* winner = nullptr;           // [cap]
   float* desc = nullptr;           // [n_in]
   std::vector<void*> owned;
+  // device-resident training set and loss history (gridff_mlp_train)
+  float* T_all = nullptr;
+  float* M_all = nullptr;
+  int n_all = 0;
+  float* loss_hist = nullptr;
+  int loss_cap = 0;
+  long long rng_step = 0;
 };
 
 namespace {
@@ -292,7 +385,7 @@ gridff_status ensure_batch(gridff_mlp* m, int rows) {
     for (auto* h : m->H) if (p == h) return true;
     for (auto* h : m->HT) if (p == h) return true;
     for (auto* a : m->Apre) if (p == a) return true;
-    return p == m->C || p == m->G || p == m->G2 || p == m->Gb || p == m->GbT || p == m->Y || p == m->Xs ||
+    return p == m->C || p == m->Cpart || p == m->G || p == m->G2 || p == m->Gb || p == m->GbT || p == m->Y || p == m->Xs ||
            p == m->Ts || p == m->Ms || p == m->loss || p == m->winner;
   };
   cudaStreamSynchronize(ctx->stream);
@@ -313,6 +406,7 @@ gridff_status ensure_batch(gridff_mlp* m, int rows) {
   }
   // C also holds a weight gradient [out_p][in_p], which can exceed Mp rows
   ok &= dalloc(m, &m->C, (size_t)std::max(Mp, maxp) * maxp) == cudaSuccess;
+  ok &= dalloc(m, &m->Cpart, (size_t)kMaxSplit * maxp * maxp) == cudaSuccess;
   ok &= dalloc(m, &m->G, (size_t)Mp * maxp) == cudaSuccess;
   ok &= dalloc(m, &m->G2, (size_t)Mp * maxp) == cudaSuccess;
   ok &= dalloc(m, &m->Gb, (size_t)Mp * maxp) == cudaSuccess;
@@ -328,10 +422,25 @@ gridff_status ensure_batch(gridff_mlp* m, int rows) {
   return GRIDFF_OK;
 }
 
+// C = A B^T-layout product; with `part` (scratch of kMaxSplit * M * ldc
+// floats) a long-K product with few output tiles is split over K.
 void gemm(cudaStream_t s, const __nv_bfloat16* A, int lda, const __nv_bfloat16* Bt, int ldb, float* C, int ldc,
-          int M, int N, int K) {
+          int M, int N, int K, float* part = nullptr) {
   const long long warps = (long long)(M / 16) * (N / 8);
-  gemm_bf16_kernel<<<grid1(warps * 32, 128), 128, 0, s>>>(A, lda, Bt, ldb, C, ldc, M, N, K, 0);
+  int S = 1;
+  if (part && warps < 2048)
+    for (int cand = kMaxSplit; cand > 1; cand >>= 1)
+      if ((K / 16) % cand == 0 && K / cand >= 128) {
+        S = cand;
+        break;
+      }
+  if (S == 1) {
+    gemm_bf16_kernel<<<grid1(warps * 32, 128), 128, 0, s>>>(A, lda, Bt, ldb, C, ldc, M, N, K, 0);
+    return;
+  }
+  const long long cstride = (long long)M * ldc;
+  gemm_bf16_kernel<<<dim3(grid1(warps * 32, 128), S), 128, 0, s>>>(A, lda, Bt, ldb, part, ldc, M, N, K / S, cstride);
+  splitk_sum_kernel<<<grid1((long long)M * N), 256, 0, s>>>(part, cstride, S, M, N, ldc, C);
 }
 
 void refresh_bf16(gridff_mlp* m) {
@@ -354,6 +463,60 @@ void forward_rows(gridff_mlp* m, int rows) {
         m->C, m->P + m->boff[l], rows, m->sizes[l + 1], Mp, op, m->Apre[l], last ? nullptr : m->H[l + 1],
         last ? nullptr : m->HT[l + 1], m->Y);
   }
+}
+
+// One training step on inputs already in H[0]/HT[0] and targets in Ts/Ms:
+// forward, winner-takes-all loss, backward, Adam (unless NO_UPDATE).
+// Enqueued on the context stream, no synchronisation.
+gridff_status enqueue_train(gridff_mlp* m, int n_targets, int K, bool mask_on, const gridff_train_params* tp,
+                            int flags) {
+  gridff_ctx* ctx = m->ctx;
+  cudaStream_t s = ctx->stream;
+  const int rows = n_targets * K;
+  const int Mp = pad16(rows), L = m->L;
+  forward_rows(m, rows);
+  // loss and dL/dY (written into G with the last layer's padded stride)
+  const int op_last = m->pads[L];
+  GRIDFF_CUDA(ctx, cudaMemsetAsync(m->G, 0, (size_t)Mp * op_last * sizeof(float), s));
+  wta_kernel<<<grid1(n_targets, 128), 128, 0, s>>>(m->Y, m->Ts, mask_on ? m->Ms : nullptr, n_targets, K, op_last,
+                                                  tp->w_q, tp->w_t, (float)tp->tile[0], (float)tp->tile[1], m->G,
+                                                  m->loss, m->winner);
+  // backward
+  float* Gcur = m->G;
+  float* Gnext = m->G2;
+  for (int l = L - 1; l >= 0; --l) {
+    const int ip = m->pads[l], op = m->pads[l + 1];
+    grad_prep_kernel<<<grid1((long long)Mp * op), 256, 0, s>>>(Gcur, l == L - 1 ? nullptr : m->Apre[l], rows,
+                                                               m->sizes[l + 1], Mp, op, m->Gb, m->GbT);
+    {
+      const int n_out = m->sizes[l + 1];
+      const int rpc = std::max(256, (Mp + 63) / 64);
+      const int chunks = (Mp + rpc - 1) / rpc;
+      colsum_kernel<<<dim3((n_out + 31) / 32, chunks), dim3(32, 8), 0, s>>>(Gcur, Mp, op, n_out, rpc, m->Cpart);
+      colsum_final_kernel<<<grid1(n_out, 128), 128, 0, s>>>(m->Cpart, chunks, n_out, m->Gr + m->boff[l]);
+    }
+    // dW [out][in] = G^T X: A = GbT [op][Mp], Bt = HT [ip][Mp]
+    gemm(s, m->GbT, Mp, m->HT[l], Mp, m->C, ip, op, ip, Mp, m->Cpart);
+    // copy the live block of C into the flat gradient array
+    GRIDFF_CUDA(ctx, cudaMemcpy2DAsync(m->Gr + m->woff[l], m->sizes[l] * sizeof(float), m->C, ip * sizeof(float),
+                                       m->sizes[l] * sizeof(float), m->sizes[l + 1], cudaMemcpyDeviceToDevice, s));
+    if (l > 0) {
+      // dL/d(input) = G W: A = Gb [Mp][op], Bt = WbT [ip][op]
+      gemm(s, m->Gb, op, m->WbT[l], op, Gnext, ip, Mp, ip, op);
+      std::swap(Gcur, Gnext);
+    }
+  }
+  GRIDFF_CUDA(ctx, cudaGetLastError());
+  if (!(flags & GRIDFF_MLP_NO_UPDATE)) {
+    m->t += 1;
+    const double b1 = tp->beta1, b2 = tp->beta2;
+    const float c1 = (float)(tp->lr / (1.0 - pow(b1, (double)m->t)));
+    const float c2 = (float)(1.0 / (1.0 - pow(b2, (double)m->t)));
+    adam_kernel<<<grid1((long long)m->n_params), 256, 0, s>>>(m->P, m->Gr, m->Am, m->Av, (int)m->n_params,
+                                                              tp->beta1, tp->beta2, tp->eps, c1, c2);
+    refresh_bf16(m);
+  }
+  return GRIDFF_OK;
 }
 
 }  // namespace
@@ -475,49 +638,14 @@ gridff_status gridff_mlp_train_step(gridff_mlp* m, int32_t n_targets, int32_t K,
   gridff_status st = ensure_batch(m, std::max(rows, n_targets));
   if (st != GRIDFF_OK) return st;
   cudaStream_t s = ctx->stream;
-  const int Mp = pad16(rows), n_in = m->sizes[0], L = m->L;
+  const int Mp = pad16(rows), n_in = m->sizes[0];
   GRIDFF_CUDA(ctx, cudaMemcpyAsync(m->Xs, x, (size_t)rows * n_in * sizeof(float), cudaMemcpyHostToDevice, s));
   GRIDFF_CUDA(ctx, cudaMemcpyAsync(m->Ts, targets, (size_t)n_targets * kOut * sizeof(float), cudaMemcpyHostToDevice, s));
   if (tors_mask)
     GRIDFF_CUDA(ctx, cudaMemcpyAsync(m->Ms, tors_mask, (size_t)n_targets * kTors * sizeof(float),
                                      cudaMemcpyHostToDevice, s));
   input_kernel<<<grid1((long long)Mp * m->pads[0]), 256, 0, s>>>(m->Xs, rows, n_in, Mp, m->pads[0], m->H[0], m->HT[0]);
-  forward_rows(m, rows);
-  // loss and dL/dY (written into G with the last layer's padded stride)
-  const int op_last = m->pads[L];
-  GRIDFF_CUDA(ctx, cudaMemsetAsync(m->G, 0, (size_t)Mp * op_last * sizeof(float), s));
-  wta_kernel<<<grid1(n_targets, 128), 128, 0, s>>>(m->Y, m->Ts, tors_mask ? m->Ms : nullptr, n_targets, K, op_last,
-                                                  tp->w_q, tp->w_t, (float)tp->tile[0], (float)tp->tile[1], m->G,
-                                                  m->loss, m->winner);
-  // backward
-  float* Gcur = m->G;
-  float* Gnext = m->G2;
-  for (int l = L - 1; l >= 0; --l) {
-    const int ip = m->pads[l], op = m->pads[l + 1];
-    grad_prep_kernel<<<grid1((long long)Mp * op), 256, 0, s>>>(Gcur, l == L - 1 ? nullptr : m->Apre[l], rows,
-                                                               m->sizes[l + 1], Mp, op, m->Gb, m->GbT);
-    colsum_kernel<<<grid1(m->sizes[l + 1], 128), 128, 0, s>>>(Gcur, Mp, op, m->sizes[l + 1], m->Gr + m->boff[l]);
-    // dW [out][in] = G^T X: A = GbT [op][Mp], Bt = HT [ip][Mp]
-    gemm(s, m->GbT, Mp, m->HT[l], Mp, m->C, ip, op, ip, Mp);
-    // copy the live block of C into the flat gradient array
-    GRIDFF_CUDA(ctx, cudaMemcpy2DAsync(m->Gr + m->woff[l], m->sizes[l] * sizeof(float), m->C, ip * sizeof(float),
-                                       m->sizes[l] * sizeof(float), m->sizes[l + 1], cudaMemcpyDeviceToDevice, s));
-    if (l > 0) {
-      // dL/d(input) = G W: A = Gb [Mp][op], Bt = WbT [ip][op]
-      gemm(s, m->Gb, op, m->WbT[l], op, Gnext, ip, Mp, ip, op);
-      std::swap(Gcur, Gnext);
-    }
-  }
-  GRIDFF_CUDA(ctx, cudaGetLastError());
-  if (!(flags & GRIDFF_MLP_NO_UPDATE)) {
-    m->t += 1;
-    const double b1 = tp->beta1, b2 = tp->beta2;
-    const float c1 = (float)(tp->lr / (1.0 - pow(b1, (double)m->t)));
-    const float c2 = (float)(1.0 / (1.0 - pow(b2, (double)m->t)));
-    adam_kernel<<<grid1((long long)m->n_params), 256, 0, s>>>(m->P, m->Gr, m->Am, m->Av, (int)m->n_params,
-                                                              tp->beta1, tp->beta2, tp->eps, c1, c2);
-    refresh_bf16(m);
-  }
+  if ((st = enqueue_train(m, n_targets, K, tors_mask != nullptr, tp, flags)) != GRIDFF_OK) return st;
   if (loss_out) {
     std::vector<float> l(n_targets);
     GRIDFF_CUDA(ctx, cudaMemcpyAsync(l.data(), m->loss, n_targets * sizeof(float), cudaMemcpyDeviceToHost, s));
@@ -529,6 +657,75 @@ gridff_status gridff_mlp_train_step(gridff_mlp* m, int32_t n_targets, int32_t K,
     GRIDFF_CUDA(ctx, cudaStreamSynchronize(s));
   }
   GRIDFF_CUDA(ctx, cudaGetLastError());
+  return GRIDFF_OK;
+}
+
+gridff_status gridff_mlp_set_targets(gridff_mlp* m, int32_t n, const float* targets, const float* tors_mask) {
+  if (!m || n < 1 || !targets) return set_err(m ? m->ctx : nullptr, GRIDFF_EINVAL, "bad argument");
+  gridff_ctx* ctx = m->ctx;
+  GRIDFF_CUDA(ctx, cudaSetDevice(ctx->device));
+  GRIDFF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  for (void* p : {(void*)m->T_all, (void*)m->M_all}) {
+    if (!p) continue;
+    cudaFree(p);
+    m->owned.erase(std::remove(m->owned.begin(), m->owned.end(), p), m->owned.end());
+  }
+  m->T_all = m->M_all = nullptr;
+  m->n_all = 0;
+  if (dalloc(m, &m->T_all, (size_t)n * kOut) != cudaSuccess ||
+      (tors_mask && dalloc(m, &m->M_all, (size_t)n * kTors) != cudaSuccess))
+    return set_err(ctx, GRIDFF_ENOMEM, "training set of %d rows", n);
+  GRIDFF_CUDA(ctx, cudaMemcpyAsync(m->T_all, targets, (size_t)n * kOut * sizeof(float), cudaMemcpyHostToDevice,
+                                   ctx->stream));
+  if (tors_mask)
+    GRIDFF_CUDA(ctx, cudaMemcpyAsync(m->M_all, tors_mask, (size_t)n * kTors * sizeof(float), cudaMemcpyHostToDevice,
+                                     ctx->stream));
+  GRIDFF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  m->n_all = n;
+  return GRIDFF_OK;
+}
+
+gridff_status gridff_mlp_train(gridff_mlp* m, int32_t steps, int32_t n_targets, int32_t K, const float* descriptor,
+                               int32_t n_desc, uint64_t seed, const gridff_train_params* tp, float* losses) {
+  if (!m || !tp || steps < 0 || n_targets < 1 || K < 1 || n_desc < 0 || (n_desc > 0 && !descriptor))
+    return set_err(m ? m->ctx : nullptr, GRIDFF_EINVAL, "bad argument");
+  gridff_ctx* ctx = m->ctx;
+  if (m->n_all < 1) return set_err(ctx, GRIDFF_EINVAL, "no training set (gridff_mlp_set_targets)");
+  if (n_desc > m->sizes[0] || m->sizes[0] - n_desc > 64)
+    return set_err(ctx, GRIDFF_EINVAL, "descriptor of %d floats for %d inputs", n_desc, m->sizes[0]);
+  if ((long long)n_targets * K >= (1 << 20)) return set_err(ctx, GRIDFF_EINVAL, "batch rows must be below 2^20");
+  GRIDFF_CUDA(ctx, cudaSetDevice(ctx->device));
+  const int rows = n_targets * K;
+  gridff_status st = ensure_batch(m, rows);
+  if (st != GRIDFF_OK) return st;
+  if (steps > m->loss_cap) {
+    if (m->loss_hist) {
+      cudaStreamSynchronize(ctx->stream);
+      cudaFree(m->loss_hist);
+      m->owned.erase(std::remove(m->owned.begin(), m->owned.end(), (void*)m->loss_hist), m->owned.end());
+      m->loss_hist = nullptr;
+    }
+    if (dalloc(m, &m->loss_hist, (size_t)steps) != cudaSuccess) return set_err(ctx, GRIDFF_ENOMEM, "loss history");
+    m->loss_cap = steps;
+  }
+  cudaStream_t s = ctx->stream;
+  const int Mp = pad16(rows);
+  if (n_desc > 0)
+    GRIDFF_CUDA(ctx, cudaMemcpyAsync(m->desc, descriptor, n_desc * sizeof(float), cudaMemcpyHostToDevice, s));
+  for (int k = 0; k < steps; ++k) {
+    const long long step = m->rng_step++;
+    sample_targets_kernel<<<grid1(n_targets, 128), 128, 0, s>>>(m->T_all, m->M_all, m->n_all, n_targets,
+                                                                (unsigned long long)seed, step, m->Ts, m->Ms);
+    train_inputs_kernel<<<grid1((long long)Mp * m->pads[0]), 256, 0, s>>>(
+        m->desc, n_desc, m->sizes[0] - n_desc, rows, (unsigned long long)seed, step, Mp, m->pads[0], m->H[0],
+        m->HT[0]);
+    if ((st = enqueue_train(m, n_targets, K, m->M_all != nullptr, tp, 0)) != GRIDFF_OK) return st;
+    loss_mean_kernel<<<1, 256, 0, s>>>(m->loss, n_targets, m->loss_hist + k);
+  }
+  GRIDFF_CUDA(ctx, cudaGetLastError());
+  if (losses && steps > 0)
+    GRIDFF_CUDA(ctx, cudaMemcpyAsync(losses, m->loss_hist, steps * sizeof(float), cudaMemcpyDeviceToHost, s));
+  GRIDFF_CUDA(ctx, cudaStreamSynchronize(s));
   return GRIDFF_OK;
 }
 

@@ -117,6 +117,8 @@ def _load():
         "gridff_grid_download_f64": (I32, [P, C.c_int, C.POINTER(C.c_double)]),
         "gridff_grid_storage": (I32, [P, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
         "gridff_langevin": (I32, [P, P, P, I32, C.POINTER(LangevinParams), C.c_int]),
+        "gridff_mlp_set_targets": (I32, [P, I32, P, P]),
+        "gridff_mlp_train": (I32, [P, I32, I32, I32, P, I32, C.c_uint64, C.POINTER(TrainParams), P]),
         "gridff_rmsd_unique_xyz": (I32, [P, I32, I32, P, C.POINTER(C.c_double), F64, P, C.c_int]),
         "gridff_grid_destroy": (None, [P]),
         "gridff_replicas_create": (I32, [P, I32, C.POINTER(Molecule), I32, C.POINTER(C.c_int32), I32,
@@ -174,7 +176,8 @@ EXPORTED = (
     "gridff_mlp_get_params", "gridff_mlp_forward", "gridff_mlp_train_step", "gridff_mlp_propose",
     "gridff_molecule_descriptor", "gridff_random_poses", "gridff_rmsd_unique",
     "gridff_set_launch_config", "gridff_get_launch_config", "gridff_tune", "gridff_relax_graph_create",
-    "gridff_grid_storage", "gridff_langevin", "gridff_rmsd_unique_xyz",
+    "gridff_grid_storage", "gridff_langevin", "gridff_rmsd_unique_xyz", "gridff_mlp_set_targets",
+    "gridff_mlp_train",
     "gridff_graph_launch", "gridff_graph_destroy",
 )
 
@@ -566,6 +569,23 @@ class MLP:
             None if m is None else m.ctypes.data_as(C.c_void_p), C.byref(params), C.byref(loss),
             0 if update else MLP_NO_UPDATE))
         return loss.value
+
+    def set_targets(self, targets, tors_mask=None):
+        t = np.ascontiguousarray(targets, np.float32)
+        if t.ndim != 2 or t.shape[1] != MLP_OUT:
+            raise ValueError("targets must be (n, 19)")
+        m = None if tors_mask is None else np.ascontiguousarray(tors_mask, np.float32)
+        self.ctx.check(lib.gridff_mlp_set_targets(self.h, len(t), t.ctypes.data_as(C.c_void_p),
+                                                  None if m is None else m.ctypes.data_as(C.c_void_p)))
+
+    def train(self, steps, n_targets, K, descriptor, seed, params: TrainParams):
+        """gridff_mlp_train: `steps` device-side steps; returns the losses."""
+        d = np.ascontiguousarray(descriptor, np.float32)
+        out = np.empty(steps, np.float32)
+        self.ctx.check(lib.gridff_mlp_train(self.h, int(steps), int(n_targets), int(K), d.ctypes.data_as(C.c_void_p),
+                                            d.size, C.c_uint64(seed), C.byref(params),
+                                            out.ctypes.data_as(C.c_void_p)))
+        return out
 
     def propose(self, reps: Replicas, descriptor, seed, origin_xy, tile_xy):
         d = np.ascontiguousarray(descriptor, np.float32)

@@ -145,6 +145,14 @@ def train(net: G.MLP, desc: np.ndarray, targets: np.ndarray, surface: Surface, s
     return np.array(losses)
 
 
+def train_on_device(net: G.MLP, desc: np.ndarray, targets: np.ndarray, surface: Surface, steps: int,
+                    batch: int = 256, K: int = 8, lr: float = 1e-3, seed: int = 0):
+    """The same training, with the batches drawn on the device and no host
+    round trip between steps (gridff_mlp_train); returns the losses."""
+    net.set_targets(targets)
+    return net.train(steps, batch, K, desc, seed, G.train_params(lr=lr, tile=surface.tile_xy))
+
+
 def new_network(ctx: G.Context, targets: np.ndarray, seed: int = 0) -> G.MLP:
     net = G.MLP(ctx, (N_DESC + N_NOISE,) + HIDDEN + (G.MLP_OUT,))
     out_bias = np.zeros(G.MLP_OUT, np.float32)

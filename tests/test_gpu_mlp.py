@@ -201,3 +201,36 @@ def test_bad_arguments_are_rejected(gf, ctx):
     with pytest.raises(gf.GridffError):
         net.propose(flex, np.zeros(136, np.float32), 1, (0, 0), TILE)
     net.close(); reps.close(); flex.close()
+
+
+def test_device_training_step_matches_oracle(gf, ctx):
+    """gridff_mlp_train draws its batch on the device; the oracle rebuilds the
+    same batch from the counters and takes the same Adam step."""
+    Ws, bs = synth.mlp_weights(SIZES, 71)
+    Ws = [W.astype(np.float32).astype(np.float64) for W in Ws]
+    net = gf.MLP(ctx, SIZES)
+    net.set_params(Ws, bs)
+    T_all, mask_all = _targets(500, 72)
+    net.set_targets(T_all, mask_all)
+    desc = (synth.rng(73).random(64) * 0.5).astype(np.float32)
+    B, K, seed, lr = 48, 3, 0x5EED, 1e-3
+    losses = net.train(1, B, K, desc, seed, gf.train_params(lr=lr, tile=TILE))
+    p, _ = net.get_params()
+    rows, X = omlp.train_batch(seed, 0, len(T_all), B, K, desc.astype(np.float64), 16)
+    T = T_all[rows].astype(np.float64); M = mask_all[rows].astype(np.float64)
+    out, cache = omlp.forward(Ws, bs, X, mirror=True)
+    L, dout, _ = omlp.wta_loss(out, T, M, K, TILE)
+    assert losses[0] == pytest.approx(L, rel=2e-3)
+    dWs, dbs = omlp.backward(Ws, cache, dout, mirror=True)
+    params = [a.copy() for pair in zip(Ws, bs) for a in pair]
+    grads = [a for pair in zip(dWs, dbs) for a in pair]
+    omlp.adam(params, grads, {}, lr=lr, t=1)
+    ref = np.concatenate([a.ravel() for a in params])
+    g = np.concatenate([a.ravel() for a in grads])
+    scale = np.concatenate([np.full(a.size, np.max(np.abs(a))) for a in grads])
+    sure = np.abs(g) > 0.05 * scale
+    assert sure.sum() > 1000 and np.max(np.abs(p[sure] - ref[sure])) < 1e-6
+    # further steps continue the counter stream and lower the loss
+    more = net.train(300, 256, 4, desc, seed, gf.train_params(lr=1e-3, tile=TILE))
+    assert np.all(np.isfinite(more)) and more[-20:].mean() < more[:20].mean()
+    net.close()

@@ -88,7 +88,7 @@ def test_mlp_proposals_beat_random_starts(gf, ctx):
     h = C & (E <= e_best + 0.01)
     n_unique = len(sp.unique(P[h], E[h]))
     net = S.new_network(ctx, S.pose_targets(P[h], surf), seed=3)
-    S.train(net, sp.desc, S.pose_targets(P[h], surf), surf, 1500, batch=256, K=8, lr=1e-3, seed=4)
+    S.train_on_device(net, sp.desc, S.pose_targets(P[h], surf), surf, 3000, batch=256, K=8, lr=1e-3, seed=4)
     rnd = [sp.random_batch(200 + k) for k in range(2)]
     mlp = [sp.proposal_batch(net, 300 + k) for k in range(2)]
     frac_r = np.mean([S.hits(b, e_best).mean() for b in rnd])
