@@ -1014,14 +1014,15 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
       Cell cl[R];
       int key[R];
       unsigned miss_mask[R];
+      float3 arm[R];   // R(q) b_i: the atom's lab-frame offset from the centre of mass
 #pragma unroll
       for (int k = 0; k < R; ++k) {
         const int i = k * W + l;
         const bool act = run && i < n;
         const float4 b = bk[k];
-        const float px = Rm[0] * b.x + Rm[1] * b.y + Rm[2] * b.z + c[0];
-        const float py = Rm[3] * b.x + Rm[4] * b.y + Rm[5] * b.z + c[1];
-        const float pz = Rm[6] * b.x + Rm[7] * b.y + Rm[8] * b.z + c[2];
+        arm[k] = make_float3(Rm[0] * b.x + Rm[1] * b.y + Rm[2] * b.z, Rm[3] * b.x + Rm[4] * b.y + Rm[5] * b.z,
+                             Rm[6] * b.x + Rm[7] * b.y + Rm[8] * b.z);
+        const float px = arm[k].x + c[0], py = arm[k].y + c[1], pz = arm[k].z + c[2];
         cl[k] = locate(g, act, px, py, pz, flags);
         key[k] = (cl[k].ix * g.ny + cl[k].iy) * g.nz + cl[k].iz;
         const bool miss = cl[k].inside && sc.key[i < S ? i : 0] != key[k];
@@ -1113,19 +1114,25 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
             gy = fmaf(wx[a], sy, gy);
             gz = fmaf(wx[a], sz, gz);
           }
-          const float4 b = bk[k];
           const float fx = -gx * g.inv_dx, fy = -gy * g.inv_dy, fz = -gz * g.inv_dz;
           e += ev;
           Ft[0] += fx;
           Ft[1] += fy;
           Ft[2] += fz;
-          const float hx = Rm[0] * fx + Rm[3] * fy + Rm[6] * fz;
-          const float hy = Rm[1] * fx + Rm[4] * fy + Rm[7] * fz;
-          const float hz = Rm[2] * fx + Rm[5] * fy + Rm[8] * fz;
-          tq[0] += b.y * hz - b.z * hy;
-          tq[1] += b.z * hx - b.x * hz;
-          tq[2] += b.x * hy - b.y * hx;
+          // lab-frame torque (R b) x f; turned into the body frame once per step
+          const float3 a = arm[k];
+          tq[0] += a.y * fz - a.z * fy;
+          tq[1] += a.z * fx - a.x * fz;
+          tq[2] += a.x * fy - a.y * fx;
         }
+      }
+      {
+        // body-frame torque R^T tau_lab (linear: the per-lane partial sums
+        // may be rotated before the sub-warp sum)
+        const float t0 = tq[0], t1 = tq[1], t2 = tq[2];
+        tq[0] = Rm[0] * t0 + Rm[3] * t1 + Rm[6] * t2;
+        tq[1] = Rm[1] * t0 + Rm[4] * t1 + Rm[7] * t2;
+        tq[2] = Rm[2] * t0 + Rm[5] * t1 + Rm[8] * t2;
       }
       // sums over the sub-warp (xor offsets below W stay inside it)
 #pragma unroll
