@@ -402,7 +402,16 @@ __device__ void intra_quad(const TemplateView& tv, int ab, int n, int i, int q, 
 // q <- q (x) (cos(a/2), sin(a/2) u), normalised.
 __device__ __forceinline__ void quat_advance(float q[4], float ux, float uy, float uz, float ang) {
   float s, c;
-  sincosf(0.5f * ang, &s, &c);
+  const float h = 0.5f * ang;
+  if (fabsf(h) < 0.05f) {
+    // Taylor series of sin and cos to h^5 and h^6: truncation below
+    // h^7 / 5040 < 2e-13 (relative 4e-12) for |h| < 0.05
+    const float h2 = h * h;
+    s = h * (1.f - h2 * (1.f / 6.f) * (1.f - h2 * (1.f / 20.f)));
+    c = 1.f - h2 * 0.5f * (1.f - h2 * (1.f / 12.f) * (1.f - h2 * (1.f / 30.f)));
+  } else {
+    sincosf(h, &s, &c);
+  }
   float bx = s * ux, by = s * uy, bz = s * uz;
   float w = q[0] * c - q[1] * bx - q[2] * by - q[3] * bz;
   float x = q[0] * bx + q[1] * c + q[2] * bz - q[3] * by;
@@ -987,6 +996,9 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
     }
     for (int i = l; i < S; i += W) sc.key[i] = -1;
     __syncwarp();
+    const float inv_m = 1.f / rig.x;
+    const float3 inv_I = make_float3(1.f / rig.y, 1.f / rig.z, 1.f / rig.w);
+    const float ang_cap = fp.d_max / rmax;
     float elane = 0.f;
     bool done = !valid;
     for (int it = 0; it < nsteps; ++it) {
@@ -1158,14 +1170,18 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
         st |= GRIDFF_REP_CONVERGED;
         continue;
       }
-      // FIRE decision (identical in every lane of the sub-warp)
+      // FIRE decision (identical in every lane of the sub-warp).  The
+      // serial part of each iteration: norms by reciprocal square roots,
+      // reciprocal masses and moments precomputed, no divisions.
       const float P = Ft[0] * v[0] + Ft[1] * v[1] + Ft[2] * v[2] + tq[0] * w[0] + tq[1] * w[1] + tq[2] * w[2];
       if (P > 0.f) {
-        const float fn = sqrtf(Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2]);
-        const float tn = sqrtf(tq[0] * tq[0] + tq[1] * tq[1] + tq[2] * tq[2]);
-        const float vn = sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-        const float wn = sqrtf(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-        const float sf = fn > 0.f ? al * vn / fn : 0.f, sw_ = tn > 0.f ? al * wn / tn : 0.f;
+        const float F2 = Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2];
+        const float T2 = tq[0] * tq[0] + tq[1] * tq[1] + tq[2] * tq[2];
+        const float V2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        const float W2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+        // al |v| / |F| and al |w| / |tau|
+        const float sf = F2 > 0.f && V2 > 0.f ? al * V2 * rsqrtf(V2) * rsqrtf(F2) : 0.f;
+        const float sw_ = T2 > 0.f && W2 > 0.f ? al * W2 * rsqrtf(W2) * rsqrtf(T2) : 0.f;
         for (int a = 0; a < 3; ++a) {
           v[a] = (1.f - al) * v[a] + sf * Ft[a];
           w[a] = (1.f - al) * w[a] + sw_ * tq[a];
@@ -1181,21 +1197,22 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
         al = fp.alpha_start;
         np = 0;
       }
-      const float aM = GRIDFF_ACC * dt / rig.x;
-      v[0] += aM * Ft[0];
-      v[1] += aM * Ft[1];
-      v[2] += aM * Ft[2];
-      w[0] += GRIDFF_ACC * dt * tq[0] / rig.y;
-      w[1] += GRIDFF_ACC * dt * tq[1] / rig.z;
-      w[2] += GRIDFF_ACC * dt * tq[2] / rig.w;
+      const float adt = GRIDFF_ACC * dt;
+      v[0] += adt * inv_m * Ft[0];
+      v[1] += adt * inv_m * Ft[1];
+      v[2] += adt * inv_m * Ft[2];
+      w[0] += adt * inv_I.x * tq[0];
+      w[1] += adt * inv_I.y * tq[1];
+      w[2] += adt * inv_I.z * tq[2];
       const float dr[3] = {v[0] * dt, v[1] * dt, v[2] * dt};
-      const float dn = sqrtf(dr[0] * dr[0] + dr[1] * dr[1] + dr[2] * dr[2]);
-      const float scl = dn > fp.d_max ? fp.d_max / dn : 1.f;
+      const float dn2 = dr[0] * dr[0] + dr[1] * dr[1] + dr[2] * dr[2];
+      const float scl = dn2 > fp.d_max * fp.d_max ? fp.d_max * rsqrtf(dn2) : 1.f;
       for (int a = 0; a < 3; ++a) c[a] += dr[a] * scl;
-      const float wn = sqrtf(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-      if (wn > 0.f) {
-        const float ang = fminf(wn * dt, fp.d_max / rmax);
-        quat_advance(q, w[0] / wn, w[1] / wn, w[2] / wn, ang);
+      const float wn2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+      if (wn2 > 0.f) {
+        const float iw = rsqrtf(wn2);
+        const float ang = fminf(wn2 * iw * dt, ang_cap);
+        quat_advance(q, w[0] * iw, w[1] * iw, w[2] * iw, ang);
       }
     }
     // energy of the last evaluation: sum over the sub-warp in FP64
