@@ -1146,7 +1146,8 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
         tq[1] = Rm[1] * t0 + Rm[4] * t1 + Rm[7] * t2;
         tq[2] = Rm[2] * t0 + Rm[5] * t1 + Rm[8] * t2;
       }
-      // sums over the sub-warp (xor offsets below W stay inside it)
+      // sums over the sub-warp (xor offsets below W stay inside it); the
+      // only flag locate() raises is BELOW: one ballot instead of a sum
 #pragma unroll
       for (int o = W / 2; o > 0; o >>= 1) {
 #pragma unroll
@@ -1154,18 +1155,23 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
           Ft[a] += __shfl_xor_sync(kFull, Ft[a], o);
           tq[a] += __shfl_xor_sync(kFull, tq[a], o);
         }
-        flags |= __shfl_xor_sync(kFull, flags, o);
+      }
+      {
+        unsigned bb = __ballot_sync(kFull, (flags & GRIDFF_REP_BELOW) != 0);
+        if constexpr (W < 32) bb = (bb >> (sw * W)) & ((1u << (W & 31)) - 1u);
+        flags = bb ? GRIDFF_REP_BELOW : 0;
       }
       if (!run) continue;
       st |= flags;
       ++evals;
       elane = e;
-      if (!(finite3(Ft[0], Ft[1], Ft[2]) && finite3(tq[0], tq[1], tq[2]) && finite3(c[0], c[1], c[2]))) {
+      const float f2 = Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2] + tq[0] * tq[0] + tq[1] * tq[1] +
+                       tq[2] * tq[2];
+      // a NaN or infinity in any force or torque component reaches f2
+      if (!isfinite(f2) || !isfinite(c[0] + c[1] + c[2])) {
         st |= GRIDFF_REP_NONFINITE;
         continue;
       }
-      const float f2 = Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2] + tq[0] * tq[0] + tq[1] * tq[1] +
-                       tq[2] * tq[2];
       if (f2 < fp.f_conv2) {
         st |= GRIDFF_REP_CONVERGED;
         continue;
@@ -1397,7 +1403,12 @@ relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep
       s.x[m] = xs[3 * (size_t)off + m];
       s.v[m] = vs[3 * (size_t)off + m];
     }
-    for (int i = lane; i < n; i += 32) s_nb[i] = __ldg(&tv.nb[ab + i]);
+    // nonbonded parameters, and the inverse mass in the free fourth slot
+    for (int i = lane; i < n; i += 32) {
+      float4 p = __ldg(&tv.nb[ab + i]);
+      p.w = 1.f / __ldg(&tv.body[ab + i]).w;
+      s_nb[i] = p;
+    }
     float dt = fdt[r], al = falpha[r];
     int np = fnp[r], st = status[r], evals = 0;
     float elane = 0.f;
@@ -1436,7 +1447,7 @@ relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep
       float keep, mixf;
       if (P > 0.f) {
         keep = 1.f - al;
-        mixf = f2 > 0.f ? al * sqrtf(v2 / f2) : 0.f;
+        mixf = f2 > 0.f && v2 > 0.f ? al * v2 * rsqrtf(v2) * rsqrtf(f2) : 0.f;   // al |v| / |F|
         if (np > fp.n_min) {
           dt = fminf(dt * fp.f_inc, fp.dt_max);
           al *= fp.f_alpha;
@@ -1449,18 +1460,19 @@ relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep
         al = fp.alpha_start;
         np = 0;
       }
+      const float adt = GRIDFF_ACC * dt, dmax2 = fp.d_max * fp.d_max;
       for (int i = lane; i < n; i += 32) {
-        const float im = 1.f / __ldg(&tv.body[ab + i]).w;
+        const float im = s_nb[i].w;
         float d[3];
         for (int a = 0; a < 3; ++a) {
           float f = s.f[3 * i + a];
           float vv = keep * s.v[3 * i + a] + mixf * f;
-          vv += GRIDFF_ACC * f * im * dt;
+          vv += adt * im * f;
           s.v[3 * i + a] = vv;
           d[a] = vv * dt;
         }
-        float dn = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-        float scl = dn > fp.d_max ? fp.d_max / dn : 1.f;
+        const float dn2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        const float scl = dn2 > dmax2 ? fp.d_max * rsqrtf(dn2) : 1.f;
         for (int a = 0; a < 3; ++a) s.x[3 * i + a] += d[a] * scl;
       }
     }
@@ -1514,6 +1526,7 @@ langevin_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tm
   const int n_warps = gridDim.x * WPB;
   const unsigned long long t0 = gtimer();
   const float hdt = 0.5f * dt;
+  const float sq_kT = sqrtf(kT_acc);
   for (int k = warp;; k += n_warps) {
     if (order) {
       int next = 0;
@@ -1530,7 +1543,12 @@ langevin_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tm
       s.x[m] = xs[3 * (size_t)off + m];
       s.v[m] = vs[3 * (size_t)off + m];
     }
-    for (int i = lane; i < n; i += 32) s_nb[i] = __ldg(&tv.nb[ab + i]);
+    // nonbonded parameters, and 1/sqrt(m) in the free fourth slot
+    for (int i = lane; i < n; i += 32) {
+      float4 p = __ldg(&tv.nb[ab + i]);
+      p.w = rsqrtf(__ldg(&tv.body[ab + i]).w);
+      s_nb[i] = p;
+    }
     int st = status[r] & ~(GRIDFF_REP_CONVERGED | GRIDFF_REP_ABORTED | GRIDFF_REP_STEPLIMIT);
     int flags = 0, steps_done = 0;
     float elane = flex_forces_terms<float>(g, use_grid, use_intra, tv, t, ab, n, lane, s, flags, sc, s_nb);
@@ -1544,19 +1562,19 @@ langevin_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tm
       }
       const unsigned long long sstep = (unsigned long long)(step0 + it) * 512ull;
       for (int m = lane; m < 3 * n; m += 32) {
-        const float im = 1.f / __ldg(&tv.body[ab + m / 3]).w;
-        float v = s.v[m] + hdt * GRIDFF_ACC * s.f[m] * im;
+        const float rsm = s_nb[m / 3].w;   // 1 / sqrt(m_i)
+        float v = s.v[m] + hdt * GRIDFF_ACC * s.f[m] * (rsm * rsm);
         float x = s.x[m] + hdt * v;
         const float xi = normal_of(splitmix64(key ^ (sstep + (unsigned long long)m)));
-        v = c1 * v + c2 * sqrtf(kT_acc * im) * xi;
+        v = c1 * v + c2 * sq_kT * rsm * xi;
         s.x[m] = x + hdt * v;
         s.v[m] = v;
       }
       elane = flex_forces_terms<float>(g, use_grid, use_intra, tv, t, ab, n, lane, s, flags, sc, s_nb);
       float f2 = 0.f;
       for (int m = lane; m < 3 * n; m += 32) {
-        const float im = 1.f / __ldg(&tv.body[ab + m / 3]).w;
-        s.v[m] += hdt * GRIDFF_ACC * s.f[m] * im;
+        const float rsm = s_nb[m / 3].w;
+        s.v[m] += hdt * GRIDFF_ACC * s.f[m] * (rsm * rsm);
         f2 = fmaf(s.f[m], s.f[m], f2);
       }
       f2 = wsum(f2);
