@@ -581,8 +581,13 @@ def run_gpu(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
+    # one explicit stream for torch and the library: the legacy default
+    # stream (handle 0) would make the context create its own stream, and
+    # events recorded on the default stream would not bracket its kernels
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
     ctx = G.Context(local, stream=stream.cuda_stream)
+    assert ctx.stream == stream.cuda_stream
 
     sub, box, mol, pose = workload()
     grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing)
