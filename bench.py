@@ -493,10 +493,15 @@ def c2_accuracy(G, ctx, grid, sub, mol, pose, n_sample=8):
     E, F, Ea, S = G.eval(ctx, grid, reps)
     body = mol.xyz.astype(np.float32).astype(np.float64)
     x = odyn.rigid_positions(pose[:n_sample, :3].astype(np.float64), pose[:n_sample, 3:].astype(np.float64), body)
+    t0 = time.perf_counter()
     Er, Fr = osub.pairwise_reference(x.reshape(-1, 3), np.tile(mol.q, n_sample), np.tile(mol.R, n_sample),
                                      np.tile(mol.eps, n_sample), sub)
+    pair_s = time.perf_counter() - t0
     reps.close()
-    return {"replicas": n_sample, "max_abs_dE_per_molecule_eV": float(np.abs(E - Er.reshape(n_sample, -1).sum(1)).max()),
+    return {"replicas": n_sample,
+            "cpu_pairwise_fp64": {"value": n_sample * mol.n / pair_s, "unit": UNIT, "cores": 1,
+                                  "sample": f"{n_sample} replicas x {mol.n} atoms, one evaluation each"},
+            "max_abs_dE_per_molecule_eV": float(np.abs(E - Er.reshape(n_sample, -1).sum(1)).max()),
             "max_abs_dE_per_atom_eV": float(np.abs(Ea - Er).max()),
             "max_abs_dF_eV_per_A": float(np.abs(F - Fr).max()),
             "reference": "FP64 pairwise (Morse direct sums within 17 A + EW3DC Ewald)"}
