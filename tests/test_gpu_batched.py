@@ -215,3 +215,56 @@ def test_bad_launch_configs_are_rejected(G, ctx, uneven):
     with pytest.raises(G.GridffError):
         reps.set_launch_config(kernel=G.KERNEL_FLEX_TERMS, warps_per_block=4, cache_slots=500)
     reps.close()
+
+
+def test_edge_sizes_flexible_one_and_two_atoms(G, ctx, field):
+    """Molecules of one and two atoms (no nonbonded pair, one excluded pair)
+    in the unique-term kernel, against the oracle."""
+    sub, box, h, c32, grid = field
+    g = synth.rng(171)
+    mols = []
+    for n in (1, 2):
+        els = ["C", "O"][:n]
+        R = np.array([synth.ELEMENTS[e][0] for e in els]); eps = np.array([synth.ELEMENTS[e][1] for e in els])
+        xyz = np.array([[0.0, 0.0, 0.0], [1.2, 0.0, 0.0]])[:n]
+        bonds = np.array([[0, 1]], np.int32) if n == 2 else np.zeros((0, 2), np.int32)
+        m = synth.Molecule(els, xyz, np.zeros(n), R, eps, np.array([12.0, 16.0])[:n], bonds=bonds,
+                           bond_k=np.array([20.0])[:len(bonds)], bond_r0=np.array([1.25])[:len(bonds)])
+        mols.append(m)
+    tof = np.array([0, 1, 0, 1], np.int32)
+    x0 = [(mols[t].xyz + [g.uniform(0, 5), g.uniform(0, 5), box.origin[2] + 3.0]).astype(np.float32) for t in tof]
+    reps = G.Replicas(ctx, mols, tof)
+    reps.set_launch_config(kernel=G.KERNEL_FLEX_TERMS, warps_per_block=8, cache_slots=0, queue=1)
+    reps.set_state(np.concatenate([x.ravel() for x in x0]))
+    G.relax(ctx, grid, reps, 5, G.fire_params(f_conv=0.0))
+    x, _ = reps.get_state()
+    off = reps.atom_offset
+    for r, t in enumerate(tof):
+        fn = odyn.make_force_fn(c32, ("C", "P", "L"), box.origin, h, mols[t])
+        ref = odyn.fire_flexible(x0[r][None].astype(np.float64), np.zeros((1,) + x0[r].shape), mols[t].mass, fn, 5,
+                                 odyn.FireParams(f_conv=0.0))
+        assert np.abs(x[3 * off[r]:3 * off[r + 1]].reshape(-1, 3) - ref["x"][0]).max() < 2e-5
+    reps.close()
+
+
+def test_rigid_largest_molecule_subwarp(G, ctx, field):
+    """A 128-atom rigid body (the template maximum) takes the 32-lane,
+    4-atoms-per-lane instance of the sub-warp kernel."""
+    sub, box, h, c32, grid = field
+    mol = synth.rigid_molecule(128, 181)
+    com, quat = synth.rigid_poses(mol, sub, 5, seed=182)
+    pose = np.concatenate([com, quat], 1).astype(np.float32)
+    reps = G.Replicas(ctx, [mol], [0] * 5, rigid=True)
+    cfg = reps.launch_config()
+    assert cfg.kernel == G.KERNEL_RIGID_SUBWARP and cfg.lanes_per_replica == 32
+    reps.set_state(pose.ravel())
+    G.relax(ctx, grid, reps, 3, G.fire_params(f_conv=0.0))
+    x, _ = reps.get_state()
+    body = mol.xyz.astype(np.float32).astype(np.float64)
+    fn = odyn.make_force_fn(c32, ("C", "P", "L"), box.origin, h, mol, intra=False)
+    ref = odyn.fire_rigid(pose[:, :3].astype(np.float64), pose[:, 3:].astype(np.float64), np.zeros((5, 3)),
+                          np.zeros((5, 3)), body, mol.mass, fn, 3, odyn.FireParams(f_conv=0.0))
+    xg = odyn.rigid_positions(x.reshape(5, 7)[:, :3].astype(np.float64), x.reshape(5, 7)[:, 3:].astype(np.float64),
+                              body)
+    assert np.abs(xg - odyn.rigid_positions(ref["com"], ref["quat"], body)).max() < 5e-5
+    reps.close()
