@@ -942,6 +942,159 @@ __device__ __forceinline__ int pick_cell(const Cell (&c)[R], int k, int axis) {
   return v;
 }
 
+// Grid forces of the replica served by this sub-warp at pose (c, Rm): every
+// lane locates its R atoms, the stencils that changed cell are refilled by
+// the quads, every lane contracts its atoms; returns the total force and the
+// body-frame torque summed over the sub-warp, this lane's share of the
+// energy (Acc: float for relaxations, double for NVE) and the BELOW flag.
+template <int W, int R, int KIND, class Acc>
+__device__ __forceinline__ void sw_forces(const GridView& g, const StencilCache& sc, float* cval, int S, int sw, int l,
+                                          int n, bool run, const float c[3], const float Rm[9],
+                                          const float4 (&bk)[R], const float4 (&pk)[R], float Ft[3], float tq[3],
+                                          Acc& e, int& flags) {
+  for (int a = 0; a < 3; ++a) Ft[a] = tq[a] = 0.f;
+  e = Acc(0);
+  // locate every atom of the lane
+  Cell cl[R];
+  int key[R];
+  unsigned miss_mask[R];
+  float3 arm[R];   // R(q) b_i: the atom's lab-frame offset from the centre of mass
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    const int i = k * W + l;
+    const bool act = run && i < n;
+    const float4 b = bk[k];
+    arm[k] = make_float3(Rm[0] * b.x + Rm[1] * b.y + Rm[2] * b.z, Rm[3] * b.x + Rm[4] * b.y + Rm[5] * b.z,
+                         Rm[6] * b.x + Rm[7] * b.y + Rm[8] * b.z);
+    const float px = arm[k].x + c[0], py = arm[k].y + c[1], pz = arm[k].z + c[2];
+    cl[k] = locate(g, act, px, py, pz, flags);
+    key[k] = (cl[k].ix * g.ny + cl[k].iy) * g.nz + cl[k].iz;
+    const bool miss = cl[k].inside && sc.key[i < S ? i : 0] != key[k];
+    unsigned msub = __ballot_sync(kFull, miss);
+    if constexpr (W < 32) msub = (msub >> (sw * W)) & ((1u << (W & 31)) - 1u);
+    miss_mask[k] = msub;
+  }
+  // refill the stencils that changed cell, W/4 atoms at a time (one per
+  // quad); one copy of the gather code for all rounds
+#pragma unroll 1
+  for (int k = 0; k < R; ++k) {
+    unsigned msub = pick_r<R>(miss_mask, k);
+    while (__any_sync(kFull, msub != 0)) {
+      const int qd = l >> 2, qq = l & 3;
+      unsigned m = msub;
+      for (int j = 0; j < qd && m; ++j) m &= m - 1;
+      const int owner = m ? __ffs(m) - 1 : -1;
+      const int src = sw * W + (owner < 0 ? 0 : owner);
+      const int oix = __shfl_sync(kFull, pick_cell<R>(cl, k, 0), src);
+      const int oiy = __shfl_sync(kFull, pick_cell<R>(cl, k, 1), src);
+      const int oiz = __shfl_sync(kFull, pick_cell<R>(cl, k, 2), src);
+      const int okey = __shfl_sync(kFull, pick_r<R>(key, k), src);
+      const float4 pkk = pick_r<R>(pk, k);
+      const float oQ = __shfl_sync(kFull, pkk.x, src), oP = __shfl_sync(kFull, pkk.y, src);
+      const float oL = __shfl_sync(kFull, pkk.z, src);
+      if (owner >= 0) {
+        const int slot = k * W + owner;
+        float cv[16];
+        gather_runs<KIND>(g, ((long long)oix * g.nyp + oiy) * g.nzp + oiz + qq, make_float4(oQ, oP, oL, 0.f),
+                          cv);
+        // run mm = 4a + b, z-node qq goes to float4 2p + (qq >> 1) of
+        // run pair p = 2a + (b >> 1), component 2 (qq & 1) + (b & 1)
+#pragma unroll
+        for (int mm = 0; mm < 16; ++mm) {
+          const int a = mm >> 2, bq = mm & 3;
+          const int f4 = 2 * (2 * a + (bq >> 1)) + (qq >> 1);
+          cval[((size_t)f4 * S + slot) * 4 + 2 * (qq & 1) + (bq & 1)] = cv[mm];
+        }
+        if (qq == 0) sc.key[slot] = okey;
+      }
+      for (int j = 0; j < W / 4 && msub; ++j) msub &= msub - 1;
+    }
+  }
+  __syncwarp();
+  // contract every atom of the lane (independent chains)
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    const int i = k * W + l;
+    if (cl[k].inside) {
+      float wx[4], dwx[4], wy[4], dwy[4], wz[4], dwz[4];
+      bspline_weights(cl[k].tx, wx, dwx);
+      bspline_weights(cl[k].ty, wy, dwy);
+      bspline_weights(cl[k].tz, wz, dwz);
+      // two (x, y) runs at a time with paired FP32 FMAs: the cache
+      // holds run pairs interleaved, so (run A, run B) values of one
+      // z-node form an operand pair
+      float2 WZ[4], DZ[4];
+#pragma unroll
+      for (int cz = 0; cz < 4; ++cz) {
+        WZ[cz] = make_float2(wz[cz], wz[cz]);
+        DZ[cz] = make_float2(dwz[cz], dwz[cz]);
+      }
+      float ev = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        float2 yv = make_float2(0.f, 0.f), yy = yv, yz = yv;
+#pragma unroll
+        for (int pb = 0; pb < 2; ++pb) {
+          const int pr = 2 * a + pb;
+          const float4 F0 = sc.val[(2 * pr) * S + i], F1 = sc.val[(2 * pr + 1) * S + i];
+          const float2 z0 = make_float2(F0.x, F0.y), z1 = make_float2(F0.z, F0.w);
+          const float2 z2 = make_float2(F1.x, F1.y), z3 = make_float2(F1.z, F1.w);
+          float2 zv = __fmul2_rn(WZ[3], z3), zd = __fmul2_rn(DZ[3], z3);
+          zv = __ffma2_rn(WZ[2], z2, zv);
+          zd = __ffma2_rn(DZ[2], z2, zd);
+          zv = __ffma2_rn(WZ[1], z1, zv);
+          zd = __ffma2_rn(DZ[1], z1, zd);
+          zv = __ffma2_rn(WZ[0], z0, zv);
+          zd = __ffma2_rn(DZ[0], z0, zd);
+          const float2 WY = make_float2(wy[2 * pb], wy[2 * pb + 1]);
+          const float2 DY = make_float2(dwy[2 * pb], dwy[2 * pb + 1]);
+          yv = __ffma2_rn(WY, zv, yv);
+          yy = __ffma2_rn(DY, zv, yy);
+          yz = __ffma2_rn(WY, zd, yz);
+        }
+        const float sv = yv.x + yv.y, sy = yy.x + yy.y, sz = yz.x + yz.y;
+        ev = fmaf(wx[a], sv, ev);
+        gx = fmaf(dwx[a], sv, gx);
+        gy = fmaf(wx[a], sy, gy);
+        gz = fmaf(wx[a], sz, gz);
+      }
+      const float fx = -gx * g.inv_dx, fy = -gy * g.inv_dy, fz = -gz * g.inv_dz;
+      e += ev;
+      Ft[0] += fx;
+      Ft[1] += fy;
+      Ft[2] += fz;
+      // lab-frame torque (R b) x f; turned into the body frame once per step
+      const float3 a = arm[k];
+      tq[0] += a.y * fz - a.z * fy;
+      tq[1] += a.z * fx - a.x * fz;
+      tq[2] += a.x * fy - a.y * fx;
+    }
+  }
+  {
+    // body-frame torque R^T tau_lab (linear: the per-lane partial sums
+    // may be rotated before the sub-warp sum)
+    const float t0 = tq[0], t1 = tq[1], t2 = tq[2];
+    tq[0] = Rm[0] * t0 + Rm[3] * t1 + Rm[6] * t2;
+    tq[1] = Rm[1] * t0 + Rm[4] * t1 + Rm[7] * t2;
+    tq[2] = Rm[2] * t0 + Rm[5] * t1 + Rm[8] * t2;
+  }
+  // sums over the sub-warp (xor offsets below W stay inside it); the
+  // only flag locate() raises is BELOW: one ballot instead of a sum
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      Ft[a] += __shfl_xor_sync(kFull, Ft[a], o);
+      tq[a] += __shfl_xor_sync(kFull, tq[a], o);
+    }
+  }
+  {
+    unsigned bb = __ballot_sync(kFull, (flags & GRIDFF_REP_BELOW) != 0);
+    if constexpr (W < 32) bb = (bb >> (sw * W)) & ((1u << (W & 31)) - 1u);
+    flags = bb ? GRIDFF_REP_BELOW : 0;
+  }
+}
+
 template <int W, int R, int WPB, int MINB, int KIND>
 __global__ void __launch_bounds__(32 * WPB, MINB)
 relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, int n_rep,
@@ -1019,148 +1172,10 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
       const bool run = !done;
       float Rm[9];
       quat_rot(q[0], q[1], q[2], q[3], Rm);
-      float Ft[3] = {0.f, 0.f, 0.f}, tq[3] = {0.f, 0.f, 0.f};
+      float Ft[3], tq[3];
       float e = 0.f;
       int flags = 0;
-      // locate every atom of the lane
-      Cell cl[R];
-      int key[R];
-      unsigned miss_mask[R];
-      float3 arm[R];   // R(q) b_i: the atom's lab-frame offset from the centre of mass
-#pragma unroll
-      for (int k = 0; k < R; ++k) {
-        const int i = k * W + l;
-        const bool act = run && i < n;
-        const float4 b = bk[k];
-        arm[k] = make_float3(Rm[0] * b.x + Rm[1] * b.y + Rm[2] * b.z, Rm[3] * b.x + Rm[4] * b.y + Rm[5] * b.z,
-                             Rm[6] * b.x + Rm[7] * b.y + Rm[8] * b.z);
-        const float px = arm[k].x + c[0], py = arm[k].y + c[1], pz = arm[k].z + c[2];
-        cl[k] = locate(g, act, px, py, pz, flags);
-        key[k] = (cl[k].ix * g.ny + cl[k].iy) * g.nz + cl[k].iz;
-        const bool miss = cl[k].inside && sc.key[i < S ? i : 0] != key[k];
-        unsigned msub = __ballot_sync(kFull, miss);
-        if constexpr (W < 32) msub = (msub >> (sw * W)) & ((1u << (W & 31)) - 1u);
-        miss_mask[k] = msub;
-      }
-      // refill the stencils that changed cell, W/4 atoms at a time (one per
-      // quad); one copy of the gather code for all rounds
-#pragma unroll 1
-      for (int k = 0; k < R; ++k) {
-        unsigned msub = pick_r<R>(miss_mask, k);
-        while (__any_sync(kFull, msub != 0)) {
-          const int qd = l >> 2, qq = l & 3;
-          unsigned m = msub;
-          for (int j = 0; j < qd && m; ++j) m &= m - 1;
-          const int owner = m ? __ffs(m) - 1 : -1;
-          const int src = sw * W + (owner < 0 ? 0 : owner);
-          const int oix = __shfl_sync(kFull, pick_cell<R>(cl, k, 0), src);
-          const int oiy = __shfl_sync(kFull, pick_cell<R>(cl, k, 1), src);
-          const int oiz = __shfl_sync(kFull, pick_cell<R>(cl, k, 2), src);
-          const int okey = __shfl_sync(kFull, pick_r<R>(key, k), src);
-          const float4 pkk = pick_r<R>(pk, k);
-          const float oQ = __shfl_sync(kFull, pkk.x, src), oP = __shfl_sync(kFull, pkk.y, src);
-          const float oL = __shfl_sync(kFull, pkk.z, src);
-          if (owner >= 0) {
-            const int slot = k * W + owner;
-            float cv[16];
-            gather_runs<KIND>(g, ((long long)oix * g.nyp + oiy) * g.nzp + oiz + qq, make_float4(oQ, oP, oL, 0.f),
-                              cv);
-            // run mm = 4a + b, z-node qq goes to float4 2p + (qq >> 1) of
-            // run pair p = 2a + (b >> 1), component 2 (qq & 1) + (b & 1)
-#pragma unroll
-            for (int mm = 0; mm < 16; ++mm) {
-              const int a = mm >> 2, bq = mm & 3;
-              const int f4 = 2 * (2 * a + (bq >> 1)) + (qq >> 1);
-              cval[((size_t)f4 * S + slot) * 4 + 2 * (qq & 1) + (bq & 1)] = cv[mm];
-            }
-            if (qq == 0) sc.key[slot] = okey;
-          }
-          for (int j = 0; j < W / 4 && msub; ++j) msub &= msub - 1;
-        }
-      }
-      __syncwarp();
-      // contract every atom of the lane (independent chains)
-#pragma unroll
-      for (int k = 0; k < R; ++k) {
-        const int i = k * W + l;
-        if (cl[k].inside) {
-          float wx[4], dwx[4], wy[4], dwy[4], wz[4], dwz[4];
-          bspline_weights(cl[k].tx, wx, dwx);
-          bspline_weights(cl[k].ty, wy, dwy);
-          bspline_weights(cl[k].tz, wz, dwz);
-          // two (x, y) runs at a time with paired FP32 FMAs: the cache
-          // holds run pairs interleaved, so (run A, run B) values of one
-          // z-node form an operand pair
-          float2 WZ[4], DZ[4];
-#pragma unroll
-          for (int cz = 0; cz < 4; ++cz) {
-            WZ[cz] = make_float2(wz[cz], wz[cz]);
-            DZ[cz] = make_float2(dwz[cz], dwz[cz]);
-          }
-          float ev = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            float2 yv = make_float2(0.f, 0.f), yy = yv, yz = yv;
-#pragma unroll
-            for (int pb = 0; pb < 2; ++pb) {
-              const int pr = 2 * a + pb;
-              const float4 F0 = sc.val[(2 * pr) * S + i], F1 = sc.val[(2 * pr + 1) * S + i];
-              const float2 z0 = make_float2(F0.x, F0.y), z1 = make_float2(F0.z, F0.w);
-              const float2 z2 = make_float2(F1.x, F1.y), z3 = make_float2(F1.z, F1.w);
-              float2 zv = __fmul2_rn(WZ[3], z3), zd = __fmul2_rn(DZ[3], z3);
-              zv = __ffma2_rn(WZ[2], z2, zv);
-              zd = __ffma2_rn(DZ[2], z2, zd);
-              zv = __ffma2_rn(WZ[1], z1, zv);
-              zd = __ffma2_rn(DZ[1], z1, zd);
-              zv = __ffma2_rn(WZ[0], z0, zv);
-              zd = __ffma2_rn(DZ[0], z0, zd);
-              const float2 WY = make_float2(wy[2 * pb], wy[2 * pb + 1]);
-              const float2 DY = make_float2(dwy[2 * pb], dwy[2 * pb + 1]);
-              yv = __ffma2_rn(WY, zv, yv);
-              yy = __ffma2_rn(DY, zv, yy);
-              yz = __ffma2_rn(WY, zd, yz);
-            }
-            const float sv = yv.x + yv.y, sy = yy.x + yy.y, sz = yz.x + yz.y;
-            ev = fmaf(wx[a], sv, ev);
-            gx = fmaf(dwx[a], sv, gx);
-            gy = fmaf(wx[a], sy, gy);
-            gz = fmaf(wx[a], sz, gz);
-          }
-          const float fx = -gx * g.inv_dx, fy = -gy * g.inv_dy, fz = -gz * g.inv_dz;
-          e += ev;
-          Ft[0] += fx;
-          Ft[1] += fy;
-          Ft[2] += fz;
-          // lab-frame torque (R b) x f; turned into the body frame once per step
-          const float3 a = arm[k];
-          tq[0] += a.y * fz - a.z * fy;
-          tq[1] += a.z * fx - a.x * fz;
-          tq[2] += a.x * fy - a.y * fx;
-        }
-      }
-      {
-        // body-frame torque R^T tau_lab (linear: the per-lane partial sums
-        // may be rotated before the sub-warp sum)
-        const float t0 = tq[0], t1 = tq[1], t2 = tq[2];
-        tq[0] = Rm[0] * t0 + Rm[3] * t1 + Rm[6] * t2;
-        tq[1] = Rm[1] * t0 + Rm[4] * t1 + Rm[7] * t2;
-        tq[2] = Rm[2] * t0 + Rm[5] * t1 + Rm[8] * t2;
-      }
-      // sums over the sub-warp (xor offsets below W stay inside it); the
-      // only flag locate() raises is BELOW: one ballot instead of a sum
-#pragma unroll
-      for (int o = W / 2; o > 0; o >>= 1) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          Ft[a] += __shfl_xor_sync(kFull, Ft[a], o);
-          tq[a] += __shfl_xor_sync(kFull, tq[a], o);
-        }
-      }
-      {
-        unsigned bb = __ballot_sync(kFull, (flags & GRIDFF_REP_BELOW) != 0);
-        if constexpr (W < 32) bb = (bb >> (sw * W)) & ((1u << (W & 31)) - 1u);
-        flags = bb ? GRIDFF_REP_BELOW : 0;
-      }
+      sw_forces<W, R, KIND, float>(g, sc, cval, S, sw, l, n, run, c, Rm, bk, pk, Ft, tq, e, flags);
       if (!run) continue;
       st |= flags;
       ++evals;
@@ -1817,6 +1832,149 @@ run_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, 
   }
 }
 
+// NVE of rigid replicas with the sub-warp layout of relax_rigid_sw_kernel
+// (W lanes per replica, R atoms per lane, the stencil cache, sw_forces) and
+// the NO_SQUISH splitting of run_rigid_kernel.  The energy is accumulated
+// per lane in FP64 and summed over the sub-warp only when it is recorded.
+template <int W, int R, int WPB, int MINB, int KIND>
+__global__ void __launch_bounds__(32 * WPB, MINB)
+run_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, int n_rep, float* pose, float* vel,
+                    int* status, double* energy, int nsteps, float dt, int rec_every, double* trace, Control ctl,
+                    int S) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  constexpr int RPW = 32 / W;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int sw = lane / W, l = lane % W;
+  const StencilCache sc = warp_cache(dyn_smem, S, wib * RPW + sw);
+  float* const cval = (float*)sc.val;
+  const int warp = blockIdx.x * WPB + wib;
+  const int n_warps = gridDim.x * WPB;
+  const unsigned long long t0 = gtimer();
+  for (int r0 = warp * RPW; r0 < n_rep; r0 += n_warps * RPW) {      // uniform over the warp
+    const int r = r0 + sw;
+    const bool valid = r < n_rep;
+    int n = 0, ab = 0;
+    float4 rig = make_float4(1.f, 1.f, 1.f, 1.f);
+    float c[3] = {0.f, 0.f, 0.f}, q[4] = {1.f, 0.f, 0.f, 0.f}, v[3] = {0.f, 0.f, 0.f}, p[4] = {0.f, 0.f, 0.f, 0.f};
+    int st = 0;
+    if (valid) {
+      const int t = rep_tmpl[r];
+      n = tv.natoms[t];
+      ab = tv.atom_off[t];
+      rig = tv.rigid[t];
+      for (int a = 0; a < 3; ++a) {
+        c[a] = pose[7 * (size_t)r + a];
+        v[a] = vel[6 * (size_t)r + a];
+      }
+      for (int a = 0; a < 4; ++a) q[a] = pose[7 * (size_t)r + 3 + a];
+      const float L[3] = {rig.y * vel[6 * (size_t)r + 3], rig.z * vel[6 * (size_t)r + 4],
+                          rig.w * vel[6 * (size_t)r + 5]};
+      p[0] = 2.f * (-q[1] * L[0] - q[2] * L[1] - q[3] * L[2]);
+      p[1] = 2.f * (q[0] * L[0] - q[3] * L[1] + q[2] * L[2]);
+      p[2] = 2.f * (q[3] * L[0] + q[0] * L[1] - q[1] * L[2]);
+      p[3] = 2.f * (-q[2] * L[0] + q[1] * L[1] + q[0] * L[2]);
+      st = status[r] & ~(GRIDFF_REP_ABORTED | GRIDFF_REP_STEPLIMIT);
+    }
+    const float I[3] = {rig.y, rig.z, rig.w};
+    float4 bk[R], pk[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const int i = k * W + l;
+      bk[k] = pk[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (valid && i < n) {
+        bk[k] = __ldg(&tv.body[ab + i]);
+        pk[k] = __ldg(&tv.par[ab + i]);
+      }
+    }
+    for (int i = l; i < S; i += W) sc.key[i] = -1;
+    __syncwarp();
+    const float ham = 0.5f * dt * GRIDFF_ACC / rig.x;
+    auto sub_sum = [&](double x) {
+#pragma unroll
+      for (int o = W / 2; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+      return x;
+    };
+    auto total = [&](double epot) {
+      float L[3];
+      body_L(q, p, L);
+      double ke = 0.5 * rig.x * (double)(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+      for (int a = 0; a < 3; ++a) ke += 0.5 * (double)L[a] * (double)L[a] / (double)I[a];
+      return epot + ke / (double)GRIDFF_ACC;
+    };
+    float Rm[9];
+    quat_rot(q[0], q[1], q[2], q[3], Rm);
+    float Ft[3], tq[3];
+    double e = 0.0;
+    int flags = 0, evals = 0;
+    bool run = valid;
+    sw_forces<W, R, KIND, double>(g, sc, cval, S, sw, l, n, run, c, Rm, bk, pk, Ft, tq, e, flags);
+    {
+      const double e0 = sub_sum(e);
+      if (trace && valid && l == 0) trace[r] = total(e0);
+    }
+    int rec = 1;
+    for (int it = 0; it < nsteps; ++it) {
+      if ((it & 31) == 0) {
+        int sb = 0;
+        if (l == 0 && run) {
+          if (*ctl.abort_flag) sb |= GRIDFF_REP_ABORTED;
+          if (ctl.budget_ns && gtimer() - t0 > ctl.budget_ns) sb |= GRIDFF_REP_STEPLIMIT;
+        }
+        sb = __shfl_sync(kFull, sb, sw * W);
+        if (sb) {
+          st |= sb;
+          run = false;
+        }
+      }
+      if (!__any_sync(kFull, run)) break;
+      if (run) {
+        const float h = 0.5f * dt;
+        for (int a = 0; a < 3; ++a) v[a] += ham * Ft[a];
+        const float tb[3] = {GRIDFF_ACC * tq[0], GRIDFF_ACC * tq[1], GRIDFF_ACC * tq[2]};
+        kick_rot(p, q, tb, h);
+        for (int a = 0; a < 3; ++a) c[a] += dt * v[a];
+        free_rot(3, h, I[2], q, p);
+        free_rot(2, h, I[1], q, p);
+        free_rot(1, dt, I[0], q, p);
+        free_rot(2, h, I[1], q, p);
+        free_rot(3, h, I[2], q, p);
+      }
+      quat_rot(q[0], q[1], q[2], q[3], Rm);
+      int f2 = 0;
+      sw_forces<W, R, KIND, double>(g, sc, cval, S, sw, l, n, run, c, Rm, bk, pk, Ft, tq, e, f2);
+      if (run) {
+        flags |= f2;
+        ++evals;
+        for (int a = 0; a < 3; ++a) v[a] += ham * Ft[a];
+        const float tb[3] = {GRIDFF_ACC * tq[0], GRIDFF_ACC * tq[1], GRIDFF_ACC * tq[2]};
+        kick_rot(p, q, tb, 0.5f * dt);
+      }
+      if (rec_every > 0 && (it + 1) % rec_every == 0) {
+        const double et = sub_sum(e);
+        if (trace && valid && run && l == 0) trace[(size_t)rec * n_rep + r] = total(et);
+        ++rec;
+      }
+    }
+    const double et = sub_sum(e);
+    if (valid && l == 0) {
+      st |= flags;
+      if (!isfinite(et)) st |= GRIDFF_REP_NONFINITE;
+      float L[3];
+      body_L(q, p, L);
+      for (int a = 0; a < 3; ++a) {
+        pose[7 * (size_t)r + a] = c[a];
+        vel[6 * (size_t)r + a] = v[a];
+        vel[6 * (size_t)r + 3 + a] = L[a] / I[a];
+      }
+      for (int a = 0; a < 4; ++a) pose[7 * (size_t)r + 3 + a] = q[a];
+      status[r] = st;
+      energy[r] = et;
+      report(ctl, n, evals, st & ~GRIDFF_REP_CONVERGED, evals);
+    }
+    __syncwarp();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -1934,6 +2092,21 @@ SwFn rigid_sw_fn(int W, int R, int kind) {
   return nullptr;
 }
 int sw_rounds(const gridff_replicas* R, int W) { return (R->max_natoms + W - 1) / W; }
+
+using RunSwFn = void (*)(GridView, TemplateView, const int*, int, float*, float*, int*, double*, int, float, int,
+                         double*, Control, int);
+// NVE sub-warp kernel for W lanes per replica and R atoms per lane.
+RunSwFn run_sw_fn(int W, int R, int kind) {
+#define GRIDFF_RSW(w, r)                                                                  \
+  if (W == w && R == r)                                                                   \
+    return kind == REC_F32x4 ? run_rigid_sw_kernel<w, r, kSwWarps, kSwMinBlocks, REC_F32x4> \
+                             : run_rigid_sw_kernel<w, r, kSwWarps, kSwMinBlocks, -1>;
+  GRIDFF_RSW(8, 1) GRIDFF_RSW(8, 2) GRIDFF_RSW(8, 3) GRIDFF_RSW(8, 4)
+  GRIDFF_RSW(16, 1) GRIDFF_RSW(16, 2) GRIDFF_RSW(16, 3) GRIDFF_RSW(16, 4)
+  GRIDFF_RSW(32, 1) GRIDFF_RSW(32, 2) GRIDFF_RSW(32, 3) GRIDFF_RSW(32, 4)
+#undef GRIDFF_RSW
+  return nullptr;
+}
 const void* flex_terms_ptr(int wpb) {
   return wpb == 2 ? (const void*)relax_flex_terms_kernel<2>
        : wpb == 8 ? (const void*)relax_flex_terms_kernel<8> : (const void*)relax_flex_terms_kernel<4>;
@@ -2300,6 +2473,29 @@ gridff_status gridff_run(gridff_ctx* ctx, const gridff_grid* grid, gridff_replic
   GRIDFF_CUDA(ctx, cudaEventRecord(ctx->ev0, s));
   if (R->rigid) {
     if (!use_grid) return set_err(ctx, GRIDFF_EINVAL, "rigid replicas need the grid term");
+    const int W = rigid_subwarp_width(R);
+    const RunSwFn fn = W > 0 ? run_sw_fn(W, sw_rounds(R, W), grid->kind) : nullptr;
+    if (fn) {
+      // the sub-warp layout of the relaxation, every atom cached
+      const int S = R->max_natoms;
+      const size_t dyn = cache_bytes(S) * kSwWarps * (32 / W);
+      GRIDFF_CUDA(ctx, set_dyn_smem((const void*)fn, dyn));
+      const int per_block = kSwWarps * (32 / W);
+      int per_sm = 0;
+      GRIDFF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, 32 * kSwWarps, dyn));
+      if (per_sm < 1) per_sm = 1;
+      const int need = (R->n_rep + per_block - 1) / per_block;
+      const int blocks = need < per_sm * ctx->n_sm ? need : per_sm * ctx->n_sm;
+      fn<<<blocks, 32 * kSwWarps, dyn, s>>>(gv, R->tv, R->rep_tmpl, R->n_rep, R->x, R->v, R->status, R->energy,
+                                            nsteps, prm->dt, rec_every, dtrace, ctl, S);
+      DevResult h{};
+      gridff_status rs = finish_launch(ctx, &h);
+      if (energy_trace && !dev) {
+        GRIDFF_CUDA(ctx, cudaMemcpyAsync(energy_trace, dtrace, tbytes, cudaMemcpyDeviceToHost, s));
+        GRIDFF_CUDA(ctx, cudaStreamSynchronize(s));
+      }
+      return rs;
+    }
     const int S = cache_slots(R, true);
     const size_t dyn = cache_bytes(S) * kWarpsPerBlock;
     GRIDFF_CUDA(ctx, set_dyn_smem((const void*)run_rigid_kernel, dyn));
