@@ -62,7 +62,10 @@ typedef enum {
   GRIDFF_ECUDA = 3,       /* CUDA runtime error (message has cudaGetErrorString) */
   GRIDFF_EABORTED = 4,    /* the host abort flag stopped a relax/run call */
   GRIDFF_ESTEPLIMIT = 5,  /* the clock budget of a relax/run call ran out */
-  GRIDFF_ENOTSUP = 6      /* combination not supported by this build */
+  GRIDFF_ENOTSUP = 6,     /* combination not supported by this build */
+  GRIDFF_ETIMEOUT = 7     /* a bounded wait inside a kernel ran out (a relaxation split across
+                             two warps did not receive its first part in time); the replicas
+                             concerned keep the state of that first part */
 } gridff_status;
 
 /* per-replica status bits (status_out arrays, gridff_get_fire_state) */
@@ -345,6 +348,8 @@ typedef struct {
                                  decreasing cost order (uneven sizes), 0 = static round robin */
   int32_t l2_window;          /* 1 = the grid is put in an L2 persisting access-policy window
                                  (reserves persisting L2 for the context until gridff_destroy) */
+  int32_t blocks;             /* 0 = as many blocks as are resident on the GPU at once; > 0 = at
+                                 most this many (the kernels are persistent and loop over work) */
 } gridff_launch_config;
 
 /* Fix the launch configuration of relaxations of `reps` (NULL: back to the

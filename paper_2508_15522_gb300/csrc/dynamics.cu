@@ -1095,11 +1095,69 @@ __device__ __forceinline__ void sw_forces(const GridView& g, const StencilCache&
   }
 }
 
+// Time-sliced schedule of the sub-warp relaxation.  A warp task is the
+// 32 / W replicas one warp relaxes together; all run the same iteration
+// count, so when the tasks outnumber the resident warps by a non-integer
+// factor, whole tasks per warp leave the last round partly idle (4096
+// replicas on 1216 warps: 1.68 rounds take 2).  Instead the P x nsteps grid
+// of (task, iteration) is cut into equal contiguous ranges, one per warp
+// (McNaughton's wrap-around rule for preemptive scheduling).  A range starts
+// inside task p0 and ends inside task p1; the warp runs first the head of p1
+// (iterations from 0), then the whole tasks between, and last the tail of p0,
+// whose head the previous warp ran first.  A task's two parts never overlap
+// in time when every range holds at least nsteps iterations, which the
+// 5/4 condition below guarantees with a margin of a quarter of a task.  The
+// head's final state goes through global memory (the same arrays a call
+// reads and writes) and a per-task flag; the tail's wait is bounded.
+struct SwSchedule {
+  bool sliced;
+  bool has_head, has_tail;
+  int p_head, it_head;   // head part: task p_head, iterations [0, it_head)
+  int p_tail, it_tail;   // tail part: task p_tail, iterations [it_tail, nsteps)
+  int p_first;           // first whole task
+  int n_parts;
+};
+
+__device__ __forceinline__ SwSchedule sw_schedule(int warp, int n_warps, int P, int nsteps) {
+  SwSchedule q{};
+  q.sliced = 4LL * P >= 5LL * n_warps && nsteps >= 64;
+  if (!q.sliced) {
+    q.n_parts = warp < P ? (P - warp + n_warps - 1) / n_warps : 0;
+    return q;
+  }
+  const long long T = (long long)P * nsteps, D = (T + n_warps - 1) / n_warps;
+  const long long rb = min(T, (long long)warp * D), re = min(T, rb + D);
+  if (rb >= re) return q;
+  q.p_tail = (int)(rb / nsteps);
+  q.it_tail = (int)(rb % nsteps);
+  q.has_tail = q.it_tail > 0;
+  q.p_head = (int)(re / nsteps);
+  q.it_head = (int)(re % nsteps);
+  q.has_head = q.it_head > 0;
+  q.p_first = q.has_tail ? q.p_tail + 1 : q.p_tail;
+  q.n_parts = (int)q.has_head + (q.p_head - q.p_first) + (int)q.has_tail;
+  return q;
+}
+
+// Upper bound on the polls of a hand-off flag (with a 1 us sleep between
+// polls, about 8 s of waiting at the least), after which the part is
+// skipped and the call returns GRIDFF_ETIMEOUT.
+constexpr int kHandoffPolls = 1 << 23;
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 template <int W, int R, int WPB, int MINB, int KIND>
 __global__ void __launch_bounds__(32 * WPB, MINB)
 relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, int n_rep,
                       float* pose, float* vel, float* fdt, float* falpha, int* fnp, int* status,
-                      int* steps, double* energy, int nsteps, FireP fp, Control ctl, int S) {
+                      int* steps, double* energy, int* handoff, int nsteps, FireP fp, Control ctl, int S) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   constexpr int RPW = 32 / W;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -1109,8 +1167,43 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
   const int warp = blockIdx.x * WPB + wib;
   const int n_warps = gridDim.x * WPB;
   const unsigned long long t0 = gtimer();
-  for (int r0 = warp * RPW; r0 < n_rep; r0 += n_warps * RPW) {      // uniform over the warp
-    const int r = r0 + sw;
+  const int n_tasks = (n_rep + RPW - 1) / RPW;
+  const SwSchedule sch = sw_schedule(warp, n_warps, n_tasks, nsteps);
+  for (int j = 0; j < sch.n_parts; ++j) {      // uniform over the warp
+    int p, it_b = 0, it_e = nsteps;
+    bool head = false, tail = false;
+    if (!sch.sliced) {
+      p = warp + j * n_warps;
+    } else if (sch.has_head && j == 0) {
+      p = sch.p_head;
+      it_e = sch.it_head;
+      head = true;
+    } else if (sch.has_tail && j == sch.n_parts - 1) {
+      p = sch.p_tail;
+      it_b = sch.it_tail;
+      tail = true;
+    } else {
+      p = sch.p_first + j - (int)sch.has_head;
+    }
+    if (tail) {
+      // wait until the previous warp has written the head of this task
+      int ok = 1;
+      if (lane == 0) {
+        ok = 0;
+        for (int k = 0; k < kHandoffPolls; ++k) {
+          if (ld_acquire(handoff + p)) {
+            ok = 1;
+            break;
+          }
+          __nanosleep(1000);
+        }
+        if (!ok) atomicAdd(&ctl.res->handoff_timeouts, 1);
+      }
+      ok = __shfl_sync(kFull, ok, 0);
+      __syncwarp();
+      if (!ok) continue;
+    }
+    const int r = p * RPW + sw;
     const bool valid = r < n_rep;
     int n = 0, ab = 0;
     float4 rig = make_float4(1.f, 1.f, 1.f, 1.f);
@@ -1124,16 +1217,17 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
       ab = tv.atom_off[t];
       rig = tv.rigid[t];
       rmax = tv.rmax[t];
+      // L2 loads: a tail part reads what another SM wrote in this launch
       for (int a = 0; a < 3; ++a) {
-        c[a] = pose[7 * (size_t)r + a];
-        v[a] = vel[6 * (size_t)r + a];
-        w[a] = vel[6 * (size_t)r + 3 + a];
+        c[a] = __ldcg(&pose[7 * (size_t)r + a]);
+        v[a] = __ldcg(&vel[6 * (size_t)r + a]);
+        w[a] = __ldcg(&vel[6 * (size_t)r + 3 + a]);
       }
-      for (int a = 0; a < 4; ++a) q[a] = pose[7 * (size_t)r + 3 + a];
-      dt = fdt[r];
-      al = falpha[r];
-      np = fnp[r];
-      st = status[r];
+      for (int a = 0; a < 4; ++a) q[a] = __ldcg(&pose[7 * (size_t)r + 3 + a]);
+      dt = __ldcg(&fdt[r]);
+      al = __ldcg(&falpha[r]);
+      np = __ldcg(&fnp[r]);
+      st = __ldcg(&status[r]);
     }
     // this lane's atoms i = k W + l, k < R (R W >= atoms): body coordinates
     // and grid factors stay in registers for the whole relaxation
@@ -1154,7 +1248,7 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
     const float ang_cap = fp.d_max / rmax;
     float elane = 0.f;
     bool done = !valid;
-    for (int it = 0; it < nsteps; ++it) {
+    for (int it = it_b; it < it_e; ++it) {
       if ((it & 31) == 0) {
         int sb = 0;
         if (l == 0 && !done) {
@@ -1241,7 +1335,7 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
 #pragma unroll
     for (int o = W / 2; o > 0; o >>= 1) et += __shfl_xor_sync(kFull, et, o);
     if (valid && l == 0) {
-      const double Etot = evals > 0 ? et : energy[r];
+      const double Etot = evals > 0 ? et : __ldcg(&energy[r]);
       if (evals > 0 && !isfinite(Etot)) st |= GRIDFF_REP_NONFINITE;
       for (int a = 0; a < 3; ++a) {
         pose[7 * (size_t)r + a] = c[a];
@@ -1253,10 +1347,18 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
       falpha[r] = al;
       fnp[r] = np;
       status[r] = st;
-      const int total = steps[r] + evals;
+      const int total = __ldcg(&steps[r]) + evals;
       steps[r] = total;
       energy[r] = Etot;
-      report(ctl, n, evals, st, total);
+      // a head part counts its evaluations; convergence is counted once,
+      // by the part that ends the task
+      report(ctl, n, evals, head ? (st & ~GRIDFF_REP_CONVERGED) : st, total);
+    }
+    if (head) {
+      // publish the head's state to the warp that runs the tail
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) st_release(handoff + p, 1);
     }
     __syncwarp();
   }
@@ -2076,7 +2178,7 @@ __global__ void fire_reset_kernel(int n, float dt0, float a0, float* dt, float* 
 }
 
 using SwFn = void (*)(GridView, TemplateView, const int*, int, float*, float*, float*, float*, int*, int*, int*,
-                     double*, int, FireP, Control, int);
+                     double*, int*, int, FireP, Control, int);
 
 // Sub-warp rigid kernel for W lanes per replica and R atoms per lane; FP32
 // four-slot grids get a build without the other record kinds' code.
@@ -2156,6 +2258,9 @@ gridff_status finish_launch(gridff_ctx* ctx, DevResult* hres) {
   if (hres->stop_bits & GRIDFF_REP_ABORTED) return set_err(ctx, GRIDFF_EABORTED, "aborted by the host flag");
   if (hres->stop_bits & GRIDFF_REP_STEPLIMIT)
     return set_err(ctx, GRIDFF_ESTEPLIMIT, "clock budget exhausted");
+  if (hres->handoff_timeouts)
+    return set_err(ctx, GRIDFF_ETIMEOUT, "%d split relaxations did not receive their first part in time",
+                   hres->handoff_timeouts);
   return GRIDFF_OK;
 }
 
@@ -2211,8 +2316,10 @@ gridff_status prepare_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_rep
   GRIDFF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, k.threads, k.dyn));
   if (per_sm < 1) return set_err(ctx, GRIDFF_EINVAL, "launch configuration does not fit on an SM");
   if (GRIDFF_BLOCK_CAP > 0 && per_sm > GRIDFF_BLOCK_CAP) per_sm = GRIDFF_BLOCK_CAP;
+  if (c.blocks < 0) return set_err(ctx, GRIDFF_EINVAL, "block cap %d", c.blocks);
   const int need = (R->n_rep + k.units_per_block - 1) / k.units_per_block;
   *blocks_out = need < per_sm * ctx->n_sm ? need : per_sm * ctx->n_sm;
+  if (c.blocks > 0 && *blocks_out > c.blocks) *blocks_out = c.blocks;
   if (c.l2win) {
     if (!grid || (flags & GRIDFF_NO_GRID)) return set_err(ctx, GRIDFF_EINVAL, "L2 window without a grid");
     int max_persist = 0, max_win = 0;
@@ -2290,9 +2397,11 @@ gridff_status enqueue_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_rep
   cudaError_t e = cudaSuccess;
   switch (c.kernel) {
     case GRIDFF_KERNEL_RIGID_SUBWARP:
+      // hand-off flags of the time-sliced schedule, cleared for this launch
+      GRIDFF_CUDA(ctx, cudaMemsetAsync(R->handoff, 0, R->n_rep * sizeof(int), s));
       e = launch_ex(rigid_sw_fn(c.W, sw_rounds(R, c.W), kind), blocks, k.threads, k.dyn, s, wp, gv, R->tv,
                     (const int*)R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha, R->fire_nplus,
-                    R->status, R->steps, R->energy, nsteps, fp, ctl, c.S);
+                    R->status, R->steps, R->energy, R->handoff, nsteps, fp, ctl, c.S);
       break;
     case GRIDFF_KERNEL_RIGID_QUAD:
       e = launch_ex(relax_rigid_kernel, blocks, k.threads, k.dyn, s, wp, gv, R->tv, (const int*)R->rep_tmpl,

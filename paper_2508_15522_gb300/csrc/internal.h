@@ -149,7 +149,8 @@ struct DevResult {
   int n_converged;
   int max_steps;
   int next;           // work-queue position (replicas handed out so far)
-  int pad[2];
+  int handoff_timeouts;   // split relaxations whose first part did not arrive in time
+  int pad;
 };
 
 // Launch configuration of a relaxation (mirrors gridff_launch_config).
@@ -160,6 +161,7 @@ struct LaunchCfg {
   int S = 0;         // stencil-cache slots per replica (0 = no staging)
   int queue = 0;     // work queue in decreasing cost order
   int l2win = 0;     // grid in an L2 persisting access-policy window
+  int blocks = 0;    // block cap (0 = every block resident at once)
 };
 
 struct gridff_replicas {
@@ -185,6 +187,7 @@ struct gridff_replicas {
   int* status = nullptr;
   int* steps = nullptr;
   double* energy = nullptr;
+  int* handoff = nullptr;      // [n_rep] sub-warp schedule: first part of a split warp task written
   // host copy of offsets
   int* h_rep_off = nullptr;
   LaunchCfg cfg;               // set by gridff_tune / gridff_set_launch_config

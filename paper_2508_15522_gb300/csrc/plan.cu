@@ -19,6 +19,7 @@ LaunchCfg from_public(const gridff_launch_config& p) {
   c.S = p.cache_slots;
   c.queue = p.queue;
   c.l2win = p.l2_window;
+  c.blocks = p.blocks;
   return c;
 }
 
@@ -30,12 +31,13 @@ gridff_launch_config to_public(const LaunchCfg& c) {
   p.cache_slots = c.S;
   p.queue = c.queue;
   p.l2_window = c.l2win;
+  p.blocks = c.blocks;
   return p;
 }
 
 bool same(const LaunchCfg& a, const LaunchCfg& b) {
   return a.kernel == b.kernel && a.W == b.W && a.wpb == b.wpb && a.S == b.S && a.queue == b.queue &&
-         a.l2win == b.l2win;
+         a.l2win == b.l2win && a.blocks == b.blocks;
 }
 
 // One copy of a replica set's mutable state (tuning trials restore it).

@@ -19,13 +19,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgridff.so")
 
 # status codes and flags (mirror gridff.h)
-OK, EINVAL, ENOMEM, ECUDA, EABORTED, ESTEPLIMIT, ENOTSUP = range(7)
+OK, EINVAL, ENOMEM, ECUDA, EABORTED, ESTEPLIMIT, ENOTSUP, ETIMEOUT = range(8)
 REP_CONVERGED, REP_BELOW, REP_NONFINITE, REP_ABORTED, REP_STEPLIMIT = 1, 2, 4, 8, 16
 DEVICE_PTRS, ASYNC, CONTINUE, NO_GRID, NO_INTRA = 1, 2, 4, 8, 16
 CH_C, CH_P, CH_L = 1, 2, 4
 STORE_F32, STORE_F16, STORE_BF16 = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EABORTED", 5: "ESTEPLIMIT",
-                6: "ENOTSUP"}
+                6: "ENOTSUP", 7: "ETIMEOUT"}
 
 
 class GridffError(RuntimeError):
@@ -79,7 +79,8 @@ class LangevinParams(C.Structure):
 
 class LaunchConfig(C.Structure):
     _fields_ = [("kernel", C.c_int32), ("lanes_per_replica", C.c_int32), ("warps_per_block", C.c_int32),
-                ("cache_slots", C.c_int32), ("queue", C.c_int32), ("l2_window", C.c_int32)]
+                ("cache_slots", C.c_int32), ("queue", C.c_int32), ("l2_window", C.c_int32),
+                ("blocks", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
