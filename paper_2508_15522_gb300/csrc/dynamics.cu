@@ -1109,34 +1109,44 @@ __device__ __forceinline__ void sw_forces(const GridView& g, const StencilCache&
 // 5/4 condition below guarantees with a margin of a quarter of a task.  The
 // head's final state goes through global memory (the same arrays a call
 // reads and writes) and a per-task flag; the tail's wait is bounded.
-struct SwSchedule {
-  bool sliced;
-  bool has_head, has_tail;
-  int p_head, it_head;   // head part: task p_head, iterations [0, it_head)
-  int p_tail, it_tail;   // tail part: task p_tail, iterations [it_tail, nsteps)
-  int p_first;           // first whole task
-  int n_parts;
+//
+// Part j of warp `warp`'s work: task p (p < 0: no part j), iterations
+// [it_b, it_e), and whether it is a head (hands its state on) or a tail
+// (waits for the head).  Not inlined: the schedule is recomputed per part
+// instead of holding registers through the relaxation loop.
+struct SwPart {
+  int p, it_b, it_e;
+  int role;   // 0 whole task, 1 head, 2 tail
 };
 
-__device__ __forceinline__ SwSchedule sw_schedule(int warp, int n_warps, int P, int nsteps) {
-  SwSchedule q{};
-  q.sliced = 4LL * P >= 5LL * n_warps && nsteps >= 64;
-  if (!q.sliced) {
-    q.n_parts = warp < P ? (P - warp + n_warps - 1) / n_warps : 0;
-    return q;
+__device__ __noinline__ SwPart sw_part(int warp, int n_warps, int P, int nsteps, int j) {
+  SwPart s{-1, 0, nsteps, 0};
+  if (4LL * P < 5LL * n_warps || nsteps < 64) {
+    const long long p = warp + (long long)j * n_warps;
+    if (p < P) s.p = (int)p;
+    return s;
   }
   const long long T = (long long)P * nsteps, D = (T + n_warps - 1) / n_warps;
   const long long rb = min(T, (long long)warp * D), re = min(T, rb + D);
-  if (rb >= re) return q;
-  q.p_tail = (int)(rb / nsteps);
-  q.it_tail = (int)(rb % nsteps);
-  q.has_tail = q.it_tail > 0;
-  q.p_head = (int)(re / nsteps);
-  q.it_head = (int)(re % nsteps);
-  q.has_head = q.it_head > 0;
-  q.p_first = q.has_tail ? q.p_tail + 1 : q.p_tail;
-  q.n_parts = (int)q.has_head + (q.p_head - q.p_first) + (int)q.has_tail;
-  return q;
+  if (rb >= re) return s;
+  const int p_tail = (int)(rb / nsteps), it_tail = (int)(rb % nsteps);
+  const int p_head = (int)(re / nsteps), it_head = (int)(re % nsteps);
+  const int has_head = it_head > 0, has_tail = it_tail > 0;
+  const int p_first = has_tail ? p_tail + 1 : p_tail;
+  const int n_parts = has_head + (p_head - p_first) + has_tail;
+  if (j >= n_parts) return s;
+  if (has_head && j == 0) {
+    s.p = p_head;
+    s.it_e = it_head;
+    s.role = 1;
+  } else if (has_tail && j == n_parts - 1) {
+    s.p = p_tail;
+    s.it_b = it_tail;
+    s.role = 2;
+  } else {
+    s.p = p_first + j - has_head;
+  }
+  return s;
 }
 
 // Upper bound on the polls of a hand-off flag (with a 1 us sleep between
@@ -1167,24 +1177,11 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
   const int warp = blockIdx.x * WPB + wib;
   const int n_warps = gridDim.x * WPB;
   const unsigned long long t0 = gtimer();
-  const int n_tasks = (n_rep + RPW - 1) / RPW;
-  const SwSchedule sch = sw_schedule(warp, n_warps, n_tasks, nsteps);
-  for (int j = 0; j < sch.n_parts; ++j) {      // uniform over the warp
-    int p, it_b = 0, it_e = nsteps;
-    bool head = false, tail = false;
-    if (!sch.sliced) {
-      p = warp + j * n_warps;
-    } else if (sch.has_head && j == 0) {
-      p = sch.p_head;
-      it_e = sch.it_head;
-      head = true;
-    } else if (sch.has_tail && j == sch.n_parts - 1) {
-      p = sch.p_tail;
-      it_b = sch.it_tail;
-      tail = true;
-    } else {
-      p = sch.p_first + j - (int)sch.has_head;
-    }
+  for (int j = 0;; ++j) {      // uniform over the warp
+    const SwPart part = sw_part(warp, n_warps, (n_rep + RPW - 1) / RPW, nsteps, j);
+    if (part.p < 0) break;
+    const int p = part.p, it_b = part.it_b, it_e = part.it_e;
+    const bool head = part.role == 1, tail = part.role == 2;
     if (tail) {
       // wait until the previous warp has written the head of this task
       int ok = 1;
