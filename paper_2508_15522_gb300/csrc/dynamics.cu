@@ -1182,23 +1182,22 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
     if (part.p < 0) break;
     const int p = part.p, it_b = part.it_b, it_e = part.it_e;
     const bool head = part.role == 1, tail = part.role == 2;
+    // flag value of a finished head: bit 0 set, bit 1 + s set when the
+    // abort flag or the clock budget stopped replica s of the task
+    int hv = 1;
     if (tail) {
       // wait until the previous warp has written the head of this task
-      int ok = 1;
       if (lane == 0) {
-        ok = 0;
-        for (int k = 0; k < kHandoffPolls; ++k) {
-          if (ld_acquire(handoff + p)) {
-            ok = 1;
-            break;
-          }
-          __nanosleep(1000);
+        hv = 0;
+        for (int k = 0; k < kHandoffPolls && hv == 0; ++k) {
+          hv = ld_acquire(handoff + p);
+          if (hv == 0) __nanosleep(1000);
         }
-        if (!ok) atomicAdd(&ctl.res->handoff_timeouts, 1);
+        if (hv == 0) atomicAdd(&ctl.res->handoff_timeouts, 1);
       }
-      ok = __shfl_sync(kFull, ok, 0);
+      hv = __shfl_sync(kFull, hv, 0);
       __syncwarp();
-      if (!ok) continue;
+      if (hv == 0) continue;
     }
     const int r = p * RPW + sw;
     const bool valid = r < n_rep;
@@ -1244,7 +1243,9 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
     const float3 inv_I = make_float3(1.f / rig.y, 1.f / rig.z, 1.f / rig.w);
     const float ang_cap = fp.d_max / rmax;
     float elane = 0.f;
-    bool done = !valid;
+    // a tail whose head was stopped stops too (the head's state is final)
+    bool done = !valid || ((hv >> (1 + sw)) & 1);
+    bool stopped = false;
     for (int it = it_b; it < it_e; ++it) {
       if ((it & 31) == 0) {
         int sb = 0;
@@ -1256,6 +1257,7 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
         if (sb) {
           st |= sb;
           done = true;
+          stopped = true;
         }
       }
       if (st & (GRIDFF_REP_CONVERGED | GRIDFF_REP_NONFINITE)) done = true;
@@ -1353,9 +1355,15 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
     }
     if (head) {
       // publish the head's state to the warp that runs the tail
+      const unsigned sm = __ballot_sync(kFull, stopped && l == 0);
       __threadfence();
       __syncwarp();
-      if (lane == 0) st_release(handoff + p, 1);
+      if (lane == 0) {
+        int v = 1;
+        for (int s2 = 0; s2 < RPW; ++s2)
+          if ((sm >> (s2 * W)) & 1u) v |= 2 << s2;
+        st_release(handoff + p, v);
+      }
     }
     __syncwarp();
   }
