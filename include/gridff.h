@@ -349,7 +349,8 @@ typedef struct {
   int32_t l2_window;          /* 1 = the grid is put in an L2 persisting access-policy window
                                  (reserves persisting L2 for the context until gridff_destroy) */
   int32_t blocks;             /* 0 = as many blocks as are resident on the GPU at once; > 0 = at
-                                 most this many (the kernels are persistent and loop over work) */
+                                 most this many (the kernels are persistent and loop over work);
+                                 also caps gridff_run's sub-warp kernel for rigid replicas */
 } gridff_launch_config;
 
 /* Fix the launch configuration of relaxations of `reps` (NULL: back to the

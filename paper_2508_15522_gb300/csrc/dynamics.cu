@@ -1946,8 +1946,8 @@ run_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, 
 template <int W, int R, int WPB, int MINB, int KIND>
 __global__ void __launch_bounds__(32 * WPB, MINB)
 run_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, int n_rep, float* pose, float* vel,
-                    int* status, double* energy, int nsteps, float dt, int rec_every, double* trace, Control ctl,
-                    int S) {
+                    int* status, double* energy, int* handoff, float4* handoff_p, int nsteps, float dt,
+                    int rec_every, double* trace, Control ctl, int S) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   constexpr int RPW = 32 / W;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -1957,9 +1957,30 @@ run_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmp
   const int warp = blockIdx.x * WPB + wib;
   const int n_warps = gridDim.x * WPB;
   const unsigned long long t0 = gtimer();
-  for (int r0 = warp * RPW; r0 < n_rep; r0 += n_warps * RPW) {      // uniform over the warp
-    const int r = r0 + sw;
-    const bool valid = r < n_rep;
+  // the time-sliced schedule of the relaxation kernel; a head hands on the
+  // quaternion momentum exactly (handoff_p) besides the state arrays
+  for (int j = 0;; ++j) {      // uniform over the warp
+    const SwPart part = sw_part(warp, n_warps, (n_rep + RPW - 1) / RPW, nsteps, j);
+    if (part.p < 0) break;
+    const int it_b = part.it_b, it_e = part.it_e;
+    const bool head = part.role == 1, tail = part.role == 2;
+    int hv = 1;
+    if (tail) {
+      if (lane == 0) {
+        hv = 0;
+        for (int k = 0; k < kHandoffPolls && hv == 0; ++k) {
+          hv = ld_acquire(handoff + part.p);
+          if (hv == 0) __nanosleep(1000);
+        }
+        if (hv == 0) atomicAdd(&ctl.res->handoff_timeouts, 1);
+      }
+      hv = __shfl_sync(kFull, hv, 0);
+      __syncwarp();
+      if (hv == 0) continue;
+    }
+    const int r = part.p * RPW + sw;
+    // a replica whose head was stopped keeps the head's final state
+    const bool valid = r < n_rep && !((hv >> (1 + sw)) & 1);
     int n = 0, ab = 0;
     float4 rig = make_float4(1.f, 1.f, 1.f, 1.f);
     float c[3] = {0.f, 0.f, 0.f}, q[4] = {1.f, 0.f, 0.f, 0.f}, v[3] = {0.f, 0.f, 0.f}, p[4] = {0.f, 0.f, 0.f, 0.f};
@@ -1970,17 +1991,26 @@ run_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmp
       ab = tv.atom_off[t];
       rig = tv.rigid[t];
       for (int a = 0; a < 3; ++a) {
-        c[a] = pose[7 * (size_t)r + a];
-        v[a] = vel[6 * (size_t)r + a];
+        c[a] = __ldcg(&pose[7 * (size_t)r + a]);
+        v[a] = __ldcg(&vel[6 * (size_t)r + a]);
       }
-      for (int a = 0; a < 4; ++a) q[a] = pose[7 * (size_t)r + 3 + a];
-      const float L[3] = {rig.y * vel[6 * (size_t)r + 3], rig.z * vel[6 * (size_t)r + 4],
-                          rig.w * vel[6 * (size_t)r + 5]};
-      p[0] = 2.f * (-q[1] * L[0] - q[2] * L[1] - q[3] * L[2]);
-      p[1] = 2.f * (q[0] * L[0] - q[3] * L[1] + q[2] * L[2]);
-      p[2] = 2.f * (q[3] * L[0] + q[0] * L[1] - q[1] * L[2]);
-      p[3] = 2.f * (-q[2] * L[0] + q[1] * L[1] + q[0] * L[2]);
-      st = status[r] & ~(GRIDFF_REP_ABORTED | GRIDFF_REP_STEPLIMIT);
+      for (int a = 0; a < 4; ++a) q[a] = __ldcg(&pose[7 * (size_t)r + 3 + a]);
+      if (tail) {
+        const float4 pp = __ldcg(&handoff_p[r]);
+        p[0] = pp.x;
+        p[1] = pp.y;
+        p[2] = pp.z;
+        p[3] = pp.w;
+        st = __ldcg(&status[r]);
+      } else {
+        const float L[3] = {rig.y * vel[6 * (size_t)r + 3], rig.z * vel[6 * (size_t)r + 4],
+                            rig.w * vel[6 * (size_t)r + 5]};
+        p[0] = 2.f * (-q[1] * L[0] - q[2] * L[1] - q[3] * L[2]);
+        p[1] = 2.f * (q[0] * L[0] - q[3] * L[1] + q[2] * L[2]);
+        p[2] = 2.f * (q[3] * L[0] + q[0] * L[1] - q[1] * L[2]);
+        p[3] = 2.f * (-q[2] * L[0] + q[1] * L[1] + q[0] * L[2]);
+        st = status[r] & ~(GRIDFF_REP_ABORTED | GRIDFF_REP_STEPLIMIT);
+      }
     }
     const float I[3] = {rig.y, rig.z, rig.w};
     float4 bk[R], pk[R];
@@ -2013,14 +2043,15 @@ run_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmp
     float Ft[3], tq[3];
     double e = 0.0;
     int flags = 0, evals = 0;
-    bool run = valid;
+    bool run = valid, stopped = false;
+    // forces at the start of the part (a tail recomputes those its head
+    // ended with: the same values)
     sw_forces<W, R, KIND, double>(g, sc, cval, S, sw, l, n, run, c, Rm, bk, pk, Ft, tq, e, flags);
-    {
+    if (it_b == 0) {
       const double e0 = sub_sum(e);
       if (trace && valid && l == 0) trace[r] = total(e0);
     }
-    int rec = 1;
-    for (int it = 0; it < nsteps; ++it) {
+    for (int it = it_b; it < it_e; ++it) {
       if ((it & 31) == 0) {
         int sb = 0;
         if (l == 0 && run) {
@@ -2031,6 +2062,7 @@ run_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmp
         if (sb) {
           st |= sb;
           run = false;
+          stopped = true;
         }
       }
       if (!__any_sync(kFull, run)) break;
@@ -2058,8 +2090,7 @@ run_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmp
       }
       if (rec_every > 0 && (it + 1) % rec_every == 0) {
         const double et = sub_sum(e);
-        if (trace && valid && run && l == 0) trace[(size_t)rec * n_rep + r] = total(et);
-        ++rec;
+        if (trace && valid && run && l == 0) trace[(size_t)((it + 1) / rec_every) * n_rep + r] = total(et);
       }
     }
     const double et = sub_sum(e);
@@ -2074,9 +2105,21 @@ run_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmp
         vel[6 * (size_t)r + 3 + a] = L[a] / I[a];
       }
       for (int a = 0; a < 4; ++a) pose[7 * (size_t)r + 3 + a] = q[a];
+      if (head) handoff_p[r] = make_float4(p[0], p[1], p[2], p[3]);
       status[r] = st;
       energy[r] = et;
-      report(ctl, n, evals, st & ~GRIDFF_REP_CONVERGED, evals);
+      report(ctl, n, evals, st & ~GRIDFF_REP_CONVERGED, it_b + evals);
+    }
+    if (head) {
+      const unsigned sm = __ballot_sync(kFull, stopped && l == 0);
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) {
+        int hvv = 1;
+        for (int s2 = 0; s2 < RPW; ++s2)
+          if ((sm >> (s2 * W)) & 1u) hvv |= 2 << s2;
+        st_release(handoff + part.p, hvv);
+      }
     }
     __syncwarp();
   }
@@ -2200,8 +2243,8 @@ SwFn rigid_sw_fn(int W, int R, int kind) {
 }
 int sw_rounds(const gridff_replicas* R, int W) { return (R->max_natoms + W - 1) / W; }
 
-using RunSwFn = void (*)(GridView, TemplateView, const int*, int, float*, float*, int*, double*, int, float, int,
-                         double*, Control, int);
+using RunSwFn = void (*)(GridView, TemplateView, const int*, int, float*, float*, int*, double*, int*, float4*, int,
+                         float, int, double*, Control, int);
 // NVE sub-warp kernel for W lanes per replica and R atoms per lane.
 RunSwFn run_sw_fn(int W, int R, int kind) {
 #define GRIDFF_RSW(w, r)                                                                  \
@@ -2599,9 +2642,11 @@ gridff_status gridff_run(gridff_ctx* ctx, const gridff_grid* grid, gridff_replic
       GRIDFF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)fn, 32 * kSwWarps, dyn));
       if (per_sm < 1) per_sm = 1;
       const int need = (R->n_rep + per_block - 1) / per_block;
-      const int blocks = need < per_sm * ctx->n_sm ? need : per_sm * ctx->n_sm;
+      int blocks = need < per_sm * ctx->n_sm ? need : per_sm * ctx->n_sm;
+      if (R->cfg.blocks > 0 && blocks > R->cfg.blocks) blocks = R->cfg.blocks;
+      GRIDFF_CUDA(ctx, cudaMemsetAsync(R->handoff, 0, R->n_rep * sizeof(int), s));
       fn<<<blocks, 32 * kSwWarps, dyn, s>>>(gv, R->tv, R->rep_tmpl, R->n_rep, R->x, R->v, R->status, R->energy,
-                                            nsteps, prm->dt, rec_every, dtrace, ctl, S);
+                                            R->handoff, R->handoff_p, nsteps, prm->dt, rec_every, dtrace, ctl, S);
       DevResult h{};
       gridff_status rs = finish_launch(ctx, &h);
       if (energy_trace && !dev) {

@@ -188,6 +188,7 @@ struct gridff_replicas {
   int* steps = nullptr;
   double* energy = nullptr;
   int* handoff = nullptr;      // [n_rep] sub-warp schedule: first part of a split warp task written
+  float4* handoff_p = nullptr; // [n_rep] rigid NVE: quaternion momentum at the end of a head part
   // host copy of offsets
   int* h_rep_off = nullptr;
   LaunchCfg cfg;               // set by gridff_tune / gridff_set_launch_config

@@ -278,7 +278,7 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
       cudaMalloc(&R->fire_dt, n_rep * sizeof(float)) || cudaMalloc(&R->fire_alpha, n_rep * sizeof(float)) ||
       cudaMalloc(&R->fire_nplus, n_rep * sizeof(int)) || cudaMalloc(&R->status, n_rep * sizeof(int)) ||
       cudaMalloc(&R->steps, n_rep * sizeof(int)) || cudaMalloc(&R->energy, n_rep * sizeof(double)) ||
-      cudaMalloc(&R->handoff, n_rep * sizeof(int)))
+      cudaMalloc(&R->handoff, n_rep * sizeof(int)) || cudaMalloc(&R->handoff_p, n_rep * sizeof(float4)))
     return bail(GRIDFF_ENOMEM, "replica state");
   R->h_rep_off = new int[n_rep + 1];
   memcpy(R->h_rep_off, rep_off.data(), (n_rep + 1) * sizeof(int));
@@ -311,7 +311,7 @@ void gridff_replicas_destroy(gridff_replicas* R) {
   cudaGetDevice(&prev);
   cudaSetDevice(R->device);
   void* ptrs[] = {R->tmpl_blob, R->rep_tmpl, R->rep_off, R->x, R->v, R->fire_dt, R->fire_alpha,
-                  R->fire_nplus, R->status, R->steps, R->energy, R->handoff};
+                  R->fire_nplus, R->status, R->steps, R->energy, R->handoff, R->handoff_p};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   cudaSetDevice(prev);

@@ -234,6 +234,34 @@ def test_rigid_time_sliced_schedule_bitwise(G, ctx, field, blocks):
     assert 0 < out[0.05, 0][2] < n_rep
 
 
+def test_rigid_nve_time_sliced_schedule_bitwise(G, ctx, field):
+    """Rigid NVE on the split schedule (block cap 3): positions, velocities,
+    energies and the recorded energy trace equal the unsplit run bit for
+    bit (the head hands its quaternion momentum on exactly)."""
+    sub, box, h, c32, grid = field
+    mol = synth.c24h8o6_core()
+    n_rep, nsteps = 301, 150
+    com, quat = synth.rigid_poses(mol, sub, n_rep, seed=151)
+    pose = np.concatenate([com, quat], 1).astype(np.float32).ravel()
+    g = np.random.default_rng(152)
+    vel = (g.standard_normal((n_rep, 6)) * np.array([2e-3] * 3 + [5e-3] * 3)).astype(np.float32).ravel()
+    out = []
+    for cap in (0, 3):
+        reps = G.Replicas(ctx, [mol], [0] * n_rep, rigid=True)
+        if cap:
+            reps.set_launch_config(G.LaunchConfig(kernel=G.KERNEL_RIGID_SUBWARP, lanes_per_replica=16,
+                                                  warps_per_block=4, cache_slots=mol.n, blocks=cap))
+        reps.set_state(pose, vel)
+        st, trace = G.run(ctx, grid, reps, nsteps, dt=1.0, record_every=10)
+        x, v = reps.get_state()
+        fs = reps.fire_state()
+        out.append((x, v, fs["status"], fs["energy"], trace))
+        reps.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+    assert np.isfinite(out[0][4]).all()
+
+
 def test_flex_graph_replay_matches_direct(G, ctx, field, uneven):
     sub, box, h, c32, grid = field
     mols, tof = uneven
