@@ -706,8 +706,10 @@ def profile_case(args):
     """A small, self-contained launch of one kernel family for ncu captures
     (no JSON line): `uneven` relaxes 4096 of the uneven flexible replicas
     for 20 FIRE iterations; `langevin` runs 20 Langevin steps on them;
-    `mlp` runs 20 training steps of the proposal network.  Each runs its
-    launch twice (the second is the one to capture with -s)."""
+    `mlp` runs 20 training steps of the proposal network; `interp` evaluates
+    the grid alone at 65536 x 38 uniform random points (the interpolation-
+    only workload of the bench line).  Each runs its launch twice (the
+    second is the one to capture with -s)."""
     import __graft_entry__ as ge
     ge.build()
     from paper_2508_15522_gb300 import gridff as G
@@ -739,6 +741,23 @@ def profile_case(args):
         for _ in range(2):
             S.train_on_device(net, np.zeros(S.N_DESC, np.float32), T, surf, 20, batch=256, K=8)
         print("mlp trained")
+    elif args.profile_case == "interp":
+        import torch
+        sub, box, _, _ = workload()
+        grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing)
+        n_rep, n_at = 65536, 38
+        mol = synth.rigid_molecule(n_at, 3003)
+        reps = G.Replicas(ctx, [mol], [0] * n_rep)
+        pts = synth.uniform_points(n_rep * n_at, box, 3004, zband=(2.0, 8.0)).astype(np.float32)
+        reps.set_state(pts.ravel())
+        dev = torch.device("cuda", 0)
+        E = torch.empty(n_rep, dtype=torch.float64, device=dev)
+        F = torch.empty(3 * n_rep * n_at, dtype=torch.float32, device=dev)
+        Ea = torch.empty(n_rep * n_at, dtype=torch.float32, device=dev)
+        St = torch.empty(n_rep, dtype=torch.int32, device=dev)
+        for _ in range(2):
+            G.eval(ctx, grid, reps, flags=G.NO_INTRA, out=(E, F, Ea, St))
+        print("interp evaluated")
 
 
 def main():
@@ -751,7 +770,7 @@ def main():
                     help="FIRE iterations per step (profiling runs use a short step)")
     ap.add_argument("--quick", action="store_true",
                     help="skip the e2e leg, the bandwidth probes and the CPU baseline (profiling runs)")
-    ap.add_argument("--profile-case", choices=["uneven", "langevin", "mlp"], default=None,
+    ap.add_argument("--profile-case", choices=["uneven", "langevin", "mlp", "interp"], default=None,
                     help="run one small kernel case for an ncu capture and exit (no JSON line)")
     args = ap.parse_args()
     if args.profile_case:
