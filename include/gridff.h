@@ -345,7 +345,11 @@ typedef struct {
                                  (the first cache_slots atoms keep their 4x4x4 stencil between
                                  steps); 0 = no staging, every gather from L2/HBM */
   int32_t queue;              /* FLEX_TERMS: 1 = replicas handed out by an atomic work queue in
-                                 decreasing cost order (uneven sizes), 0 = static round robin */
+                                 decreasing cost order (uneven sizes), 0 = static round robin.
+                                 RIGID_SUBWARP: 1 = warp tasks handed out by an atomic queue,
+                                 2 = the (task, iteration) grid cut into equal ranges per warp (a
+                                 task may be split between two warps), 0 = per call: the queue
+                                 when f_conv > 0 (replicas may stop early), else the ranges */
   int32_t l2_window;          /* 1 = the grid is put in an L2 persisting access-policy window
                                  (reserves persisting L2 for the context until gridff_destroy) */
   int32_t blocks;             /* 0 = as many blocks as are resident on the GPU at once; > 0 = at

@@ -1167,7 +1167,8 @@ template <int W, int R, int WPB, int MINB, int KIND>
 __global__ void __launch_bounds__(32 * WPB, MINB)
 relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, int n_rep,
                       float* pose, float* vel, float* fdt, float* falpha, int* fnp, int* status,
-                      int* steps, double* energy, int* handoff, int nsteps, FireP fp, Control ctl, int S) {
+                      int* steps, double* energy, int* handoff, int queued, int nsteps, FireP fp, Control ctl,
+                      int S) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   constexpr int RPW = 32 / W;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -1177,8 +1178,20 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
   const int warp = blockIdx.x * WPB + wib;
   const int n_warps = gridDim.x * WPB;
   const unsigned long long t0 = gtimer();
+  // Relaxations that may stop early (f_conv > 0) have unknown lengths:
+  // there the warps take whole tasks from an atomic queue (greedy list
+  // scheduling) instead of the time-sliced ranges.
+  const int n_tasks = (n_rep + RPW - 1) / RPW;
   for (int j = 0;; ++j) {      // uniform over the warp
-    const SwPart part = sw_part(warp, n_warps, (n_rep + RPW - 1) / RPW, nsteps, j);
+    SwPart part;
+    if (queued) {
+      int next = 0;
+      if (lane == 0) next = atomicAdd(&ctl.res->next, 1);
+      next = __shfl_sync(kFull, next, 0);
+      part = SwPart{next < n_tasks ? next : -1, 0, nsteps, 0};
+    } else {
+      part = sw_part(warp, n_warps, n_tasks, nsteps, j);
+    }
     if (part.p < 0) break;
     const int p = part.p, it_b = part.it_b, it_e = part.it_e;
     const bool head = part.role == 1, tail = part.role == 2;
@@ -2226,7 +2239,7 @@ __global__ void fire_reset_kernel(int n, float dt0, float a0, float* dt, float* 
 }
 
 using SwFn = void (*)(GridView, TemplateView, const int*, int, float*, float*, float*, float*, int*, int*, int*,
-                     double*, int*, int, FireP, Control, int);
+                     double*, int*, int, int, FireP, Control, int);
 
 // Sub-warp rigid kernel for W lanes per replica and R atoms per lane; FP32
 // four-slot grids get a build without the other record kinds' code.
@@ -2365,6 +2378,8 @@ gridff_status prepare_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_rep
   if (per_sm < 1) return set_err(ctx, GRIDFF_EINVAL, "launch configuration does not fit on an SM");
   if (GRIDFF_BLOCK_CAP > 0 && per_sm > GRIDFF_BLOCK_CAP) per_sm = GRIDFF_BLOCK_CAP;
   if (c.blocks < 0) return set_err(ctx, GRIDFF_EINVAL, "block cap %d", c.blocks);
+  if (c.queue < 0 || c.queue > (c.kernel == GRIDFF_KERNEL_RIGID_SUBWARP ? 2 : 1))
+    return set_err(ctx, GRIDFF_EINVAL, "queue mode %d", c.queue);
   const int need = (R->n_rep + k.units_per_block - 1) / k.units_per_block;
   *blocks_out = need < per_sm * ctx->n_sm ? need : per_sm * ctx->n_sm;
   if (c.blocks > 0 && *blocks_out > c.blocks) *blocks_out = c.blocks;
@@ -2449,7 +2464,8 @@ gridff_status enqueue_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_rep
       GRIDFF_CUDA(ctx, cudaMemsetAsync(R->handoff, 0, R->n_rep * sizeof(int), s));
       e = launch_ex(rigid_sw_fn(c.W, sw_rounds(R, c.W), kind), blocks, k.threads, k.dyn, s, wp, gv, R->tv,
                     (const int*)R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha, R->fire_nplus,
-                    R->status, R->steps, R->energy, R->handoff, nsteps, fp, ctl, c.S);
+                    R->status, R->steps, R->energy, R->handoff,
+                    (int)(c.queue == 1 || (c.queue == 0 && P.f_conv > 0)), nsteps, fp, ctl, c.S);
       break;
     case GRIDFF_KERNEL_RIGID_QUAD:
       e = launch_ex(relax_rigid_kernel, blocks, k.threads, k.dyn, s, wp, gv, R->tv, (const int*)R->rep_tmpl,

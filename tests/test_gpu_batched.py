@@ -195,43 +195,52 @@ def _rigid_state(reps):
 @pytest.mark.parametrize("blocks", [3, 7])
 def test_rigid_time_sliced_schedule_bitwise(G, ctx, field, blocks):
     """With fewer resident warps than warp tasks, the sub-warp relaxation
-    splits tasks between two warps (head and tail, handed over through
-    global memory).  The per-replica arithmetic is unchanged, so the final
-    state equals the unsplit run bit for bit; convergence is counted once;
-    a CUDA-graph replay of the split launch matches as well."""
+    either splits tasks between two warps (head and tail, handed over
+    through global memory; queue mode 2) or hands whole tasks out from an
+    atomic queue (mode 1; mode 0 picks the queue when f_conv > 0).  The
+    per-replica arithmetic is the same in every schedule, so the final
+    state equals the uncapped run bit for bit, also for a continued call;
+    convergence is counted once; a CUDA-graph replay of the split launch
+    matches as well."""
     sub, box, h, c32, grid = field
     mol = synth.c24h8o6_core()
     n_rep, nsteps = 301, 150          # odd: the last warp task has one replica
     com, quat = synth.rigid_poses(mol, sub, n_rep, seed=141)
     pose = np.concatenate([com, quat], 1).astype(np.float32).ravel()
     base = dict(kernel=G.KERNEL_RIGID_SUBWARP, lanes_per_replica=16, warps_per_block=4, cache_slots=mol.n,
-                queue=0, l2_window=0)
-    out = {}
+                l2_window=0)
     for f_conv in (0.0, 0.05):
-        for cap in (0, blocks):
+        out = {}
+        for cap, mode in ((0, 0), (blocks, 0), (blocks, 1), (blocks, 2)):
             reps = G.Replicas(ctx, [mol], [0] * n_rep, rigid=True)
-            reps.set_launch_config(G.LaunchConfig(blocks=cap, **base))
+            reps.set_launch_config(G.LaunchConfig(blocks=cap, queue=mode, **base))
             reps.set_state(pose)
-            st, res = G.relax(ctx, grid, reps, nsteps, G.fire_params(f_conv=f_conv), check=False)
-            out[f_conv, cap] = (_rigid_state(reps), res.atom_evals, res.n_converged, res.max_steps)
-            if cap and f_conv == 0.0:
-                graph = G.RelaxGraph(ctx, grid, reps, nsteps, G.fire_params(f_conv=0.0))
+            fp = G.fire_params(f_conv=f_conv)
+            st, res = G.relax(ctx, grid, reps, nsteps, fp, check=False)
+            first = (_rigid_state(reps), res.atom_evals, res.n_converged, res.max_steps)
+            st, res = G.relax(ctx, grid, reps, 100, fp, flags=G.CONTINUE, check=False)
+            out[cap, mode] = (first, (_rigid_state(reps), res.atom_evals, res.n_converged, res.max_steps))
+            if cap and mode == 2 and f_conv == 0.0:
+                graph = G.RelaxGraph(ctx, grid, reps, nsteps, fp)
                 reps.set_state(pose)
                 graph.launch()
                 xg, _ = reps.get_state()
-                assert np.array_equal(xg, out[f_conv, cap][0][0])
+                assert np.array_equal(xg, out[cap, mode][0][0][0])
                 graph.close()
             reps.close()
-        (xa, va, fa), ea, ca, ma = out[f_conv, 0]
-        (xb, vb, fb), eb, cb, mb = out[f_conv, blocks]
-        assert np.array_equal(xa, xb) and np.array_equal(va, vb)
-        for k in ("dt", "alpha", "nplus", "status", "steps", "energy"):
-            assert np.array_equal(fa[k], fb[k]), k
-        assert (ea, ca, mb) == (eb, cb, ma)
+        ref = out[0, 0]
+        for key, got in out.items():
+            for (sa, ea, ca, ma), (sb, eb, cb, mb) in zip(ref, got):
+                (xa, va, fa), (xb, vb, fb) = sa, sb
+                assert np.array_equal(xa, xb) and np.array_equal(va, vb), key
+                for k in ("dt", "alpha", "nplus", "status", "steps", "energy"):
+                    assert np.array_equal(fa[k], fb[k]), (key, k)
+                assert (ea, ca, ma) == (eb, cb, mb), key
         if f_conv == 0.0:
-            assert ea == n_rep * mol.n * nsteps and ca == 0
-    # the threshold lets part of the batch converge inside the window
-    assert 0 < out[0.05, 0][2] < n_rep
+            assert ref[0][1] == n_rep * mol.n * nsteps and ref[0][2] == 0
+        else:
+            # the threshold lets part of the batch converge inside the window
+            assert 0 < ref[0][2] < n_rep
 
 
 def test_rigid_nve_time_sliced_schedule_bitwise(G, ctx, field):
