@@ -207,7 +207,7 @@ __device__ __forceinline__ void gather_runs(const GridView& g, long long base, f
 // `slot` >= 0: the atom may use stencil-cache slot `slot`.
 // kPartial: return this lane's share (the 4 shares of a quad sum to the
 // atom's value) instead of the quad sum.
-template <bool kPartial = false>
+template <bool kPartial = false, int KIND = -1>
 __device__ __forceinline__ void grid_quad(const GridView& g, int q, bool act, float x, float y, float z,
                                           float4 par, float& e, float& fx, float& fy, float& fz, int& flags,
                                           const StencilCache& sc, int slot) {
@@ -232,7 +232,7 @@ __device__ __forceinline__ void grid_quad(const GridView& g, int q, bool act, fl
         cv[4 * j + 3] = v.w;
       }
     } else {
-      gather_runs(g, ((long long)cl.ix * g.nyp + cl.iy) * g.nzp + cl.iz + q, par, cv);
+      gather_runs<KIND>(g, ((long long)cl.ix * g.nyp + cl.iy) * g.nzp + cl.iz + q, par, cv);
       if (cached) {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
@@ -655,7 +655,7 @@ __device__ float intra_terms(const TemplateView& tv, int t, int lane, const floa
 // quads (stored per atom) followed by the unique-term intramolecular pass
 // (added with shared-memory atomics).  Writes s.f, s.eg; returns this
 // lane's share of the energy.
-template <class Acc = double>
+template <class Acc = double, int KIND = -1>
 __device__ __forceinline__ Acc flex_forces_terms(const GridView& g, bool use_grid, bool use_intra,
                                                  const TemplateView& tv, int t, int ab, int n, int lane,
                                                  WarpState& s, int& flags, const StencilCache& sc,
@@ -676,7 +676,7 @@ __device__ __forceinline__ Acc flex_forces_terms(const GridView& g, bool use_gri
       if (!finite3(x, y, z)) flags |= GRIDFF_REP_NONFINITE;
     }
     float eg = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
-    if (use_grid) grid_quad(g, q, act, x, y, z, par, eg, fx, fy, fz, flags, sc, i);
+    if (use_grid) grid_quad<false, KIND>(g, q, act, x, y, z, par, eg, fx, fy, fz, flags, sc, i);
     if (act && q == 0) {
       s.f[3 * i] = fx;
       s.f[3 * i + 1] = fy;
@@ -1502,7 +1502,7 @@ relax_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
 #ifndef GRIDFF_FLEX_WARPS_PER_SM
 #define GRIDFF_FLEX_WARPS_PER_SM 32    // register budget: 65536 / (32 * 32) = 64 per thread
 #endif
-template <int WPB>
+template <int WPB, int KIND>
 __global__ void __launch_bounds__(32 * WPB, GRIDFF_FLEX_WARPS_PER_SM / WPB)
 relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
                         const int* __restrict__ rep_off, const int* __restrict__ order, int n_rep, float* xs,
@@ -1557,7 +1557,8 @@ relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep
         }
       }
       int flags = 0;
-      const float e = flex_forces_terms<float>(g, use_grid, use_intra, tv, t, ab, n, lane, s, flags, sc, s_nb);
+      const float e = flex_forces_terms<float, KIND>(g, use_grid, use_intra, tv, t, ab, n, lane, s, flags, sc,
+                                                     s_nb);
       float f2 = 0.f, P = 0.f, v2 = 0.f;
       for (int m = lane; m < 3 * n; m += 32) {
         float f = s.f[m], v = s.v[m];
@@ -1640,7 +1641,7 @@ relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep
 //   normal_of(splitmix64(splitmix64(seed ^ splitmix64(r)) ^ (512 s + m))).
 // Layout as relax_flex_terms_kernel (warp per replica, work queue).
 // ---------------------------------------------------------------------------
-template <int WPB>
+template <int WPB, int KIND>
 __global__ void __launch_bounds__(32 * WPB, GRIDFF_FLEX_WARPS_PER_SM / WPB)
 langevin_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
                      const int* __restrict__ rep_off, const int* __restrict__ order, int n_rep, float* xs,
@@ -1686,7 +1687,7 @@ langevin_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tm
     }
     int st = status[r] & ~(GRIDFF_REP_CONVERGED | GRIDFF_REP_ABORTED | GRIDFF_REP_STEPLIMIT);
     int flags = 0, steps_done = 0;
-    float elane = flex_forces_terms<float>(g, use_grid, use_intra, tv, t, ab, n, lane, s, flags, sc, s_nb);
+    float elane = flex_forces_terms<float, KIND>(g, use_grid, use_intra, tv, t, ab, n, lane, s, flags, sc, s_nb);
     for (int it = 0; it < nsteps && !(st & GRIDFF_REP_NONFINITE); ++it) {
       if ((it & 31) == 0) {
         const int sb = stop_bits(ctl, t0, lane);
@@ -1705,7 +1706,7 @@ langevin_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tm
         s.x[m] = x + hdt * v;
         s.v[m] = v;
       }
-      elane = flex_forces_terms<float>(g, use_grid, use_intra, tv, t, ab, n, lane, s, flags, sc, s_nb);
+      elane = flex_forces_terms<float, KIND>(g, use_grid, use_intra, tv, t, ab, n, lane, s, flags, sc, s_nb);
       float f2 = 0.f;
       for (int m = lane; m < 3 * n; m += 32) {
         const float rsm = s_nb[m / 3].w;
@@ -2270,9 +2271,19 @@ RunSwFn run_sw_fn(int W, int R, int kind) {
 #undef GRIDFF_RSW
   return nullptr;
 }
-const void* flex_terms_ptr(int wpb) {
-  return wpb == 2 ? (const void*)relax_flex_terms_kernel<2>
-       : wpb == 8 ? (const void*)relax_flex_terms_kernel<8> : (const void*)relax_flex_terms_kernel<4>;
+// FP32 four-slot grids get their own instances (the record kind known at
+// compile time); other kinds dispatch at run time.
+using FlexTermsFn = void (*)(GridView, TemplateView, const int*, const int*, const int*, int, float*, float*, float*,
+                             float*, int*, int*, int*, double*, int, FireP, Control, int, int, int);
+template <int K>
+FlexTermsFn flex_terms_fn_k(int wpb) {
+  return wpb == 2 ? relax_flex_terms_kernel<2, K> : wpb == 8 ? relax_flex_terms_kernel<8, K>
+                                                             : relax_flex_terms_kernel<4, K>;
+}
+FlexTermsFn flex_terms_fn(int wpb, int kind) {
+  return kind == REC_F32x4 ? flex_terms_fn_k<REC_F32x4>(wpb) : flex_terms_fn_k<-1>(wpb);
+}
+const void* flex_terms_ptr(int wpb, int kind) { return (const void*)flex_terms_fn(wpb, kind);
 }
 
 struct KernelShape {
@@ -2301,7 +2312,7 @@ KernelShape shape_of(const gridff_replicas* R, const LaunchCfg& c, int kind) {
       return {(const void*)relax_flex_kernel, kThreads, kWarpsPerBlock, cache_bytes(c.S) * kWarpsPerBlock};
     case GRIDFF_KERNEL_FLEX_TERMS:
       if (R->rigid || (c.wpb != 2 && c.wpb != 4 && c.wpb != 8)) return k;
-      return {flex_terms_ptr(c.wpb), 32 * c.wpb, c.wpb, flex_terms_warp_bytes(c.S) * c.wpb};
+      return {flex_terms_ptr(c.wpb, kind), 32 * c.wpb, c.wpb, flex_terms_warp_bytes(c.S) * c.wpb};
     default:
       return k;
   }
@@ -2479,21 +2490,9 @@ gridff_status enqueue_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_rep
       break;
     case GRIDFF_KERNEL_FLEX_TERMS: {
       const int* ord = c.queue ? (const int*)R->order : nullptr;
-      if (c.wpb == 2)
-        e = launch_ex(relax_flex_terms_kernel<2>, blocks, k.threads, k.dyn, s, wp, gv, R->tv,
-                      (const int*)R->rep_tmpl, (const int*)R->rep_off, ord, R->n_rep, R->x, R->v, R->fire_dt,
-                      R->fire_alpha, R->fire_nplus, R->status, R->steps, R->energy, nsteps, fp, ctl, use_grid,
-                      use_intra, c.S);
-      else if (c.wpb == 8)
-        e = launch_ex(relax_flex_terms_kernel<8>, blocks, k.threads, k.dyn, s, wp, gv, R->tv,
-                      (const int*)R->rep_tmpl, (const int*)R->rep_off, ord, R->n_rep, R->x, R->v, R->fire_dt,
-                      R->fire_alpha, R->fire_nplus, R->status, R->steps, R->energy, nsteps, fp, ctl, use_grid,
-                      use_intra, c.S);
-      else
-        e = launch_ex(relax_flex_terms_kernel<4>, blocks, k.threads, k.dyn, s, wp, gv, R->tv,
-                      (const int*)R->rep_tmpl, (const int*)R->rep_off, ord, R->n_rep, R->x, R->v, R->fire_dt,
-                      R->fire_alpha, R->fire_nplus, R->status, R->steps, R->energy, nsteps, fp, ctl, use_grid,
-                      use_intra, c.S);
+      e = launch_ex(flex_terms_fn(c.wpb, kind), blocks, k.threads, k.dyn, s, wp, gv, R->tv, (const int*)R->rep_tmpl,
+                    (const int*)R->rep_off, ord, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha, R->fire_nplus,
+                    R->status, R->steps, R->energy, nsteps, fp, ctl, use_grid, use_intra, c.S);
       break;
     }
     default:
@@ -2592,8 +2591,16 @@ gridff_status gridff_langevin(gridff_ctx* ctx, const gridff_grid* grid, gridff_r
   const LaunchCfg c = R->cfg.kernel == GRIDFF_KERNEL_FLEX_TERMS ? R->cfg : default_launch_cfg(R, true);
   const int wpb = c.kernel == GRIDFF_KERNEL_FLEX_TERMS ? c.wpb : 8;
   const int S = c.kernel == GRIDFF_KERNEL_FLEX_TERMS ? c.S : 0;
-  const void* fn = wpb == 2 ? (const void*)langevin_flex_kernel<2>
-                 : wpb == 4 ? (const void*)langevin_flex_kernel<4> : (const void*)langevin_flex_kernel<8>;
+  using LangevinFn = void (*)(GridView, TemplateView, const int*, const int*, const int*, int, float*, float*, int*,
+                              double*, int, float, float, float, float, unsigned long long, long long, Control, int,
+                              int, int);
+  const bool f32 = !grid || grid->kind == REC_F32x4;
+  const LangevinFn lf =
+      f32 ? (wpb == 2 ? langevin_flex_kernel<2, REC_F32x4> : wpb == 4 ? langevin_flex_kernel<4, REC_F32x4>
+                                                                      : langevin_flex_kernel<8, REC_F32x4>)
+          : (wpb == 2 ? langevin_flex_kernel<2, -1> : wpb == 4 ? langevin_flex_kernel<4, -1>
+                                                               : langevin_flex_kernel<8, -1>);
+  const void* fn = (const void*)lf;
   const size_t dyn = flex_terms_warp_bytes(S) * wpb;
   GRIDFF_CUDA(ctx, set_dyn_smem(fn, dyn));
   int per_sm = 0;
@@ -2602,16 +2609,9 @@ gridff_status gridff_langevin(gridff_ctx* ctx, const gridff_grid* grid, gridff_r
   const int need = (R->n_rep + wpb - 1) / wpb;
   const int blocks = need < per_sm * ctx->n_sm ? need : per_sm * ctx->n_sm;
   GRIDFF_CUDA(ctx, cudaEventRecord(ctx->ev0, s));
-#define GRIDFF_LANGEVIN(W)                                                                                 \
-  langevin_flex_kernel<W><<<blocks, 32 * W, dyn, s>>>(gv, R->tv, R->rep_tmpl, R->rep_off, R->order, R->n_rep, \
-                                                      R->x, R->v, R->status, R->energy, nsteps, prm->dt,     \
-                                                      (float)c1, (float)c2, kT_acc,                         \
-                                                      (unsigned long long)prm->seed, (long long)prm->step0,  \
-                                                      ctl, use_grid, use_intra, S)
-  if (wpb == 2) GRIDFF_LANGEVIN(2);
-  else if (wpb == 4) GRIDFF_LANGEVIN(4);
-  else GRIDFF_LANGEVIN(8);
-#undef GRIDFF_LANGEVIN
+  lf<<<blocks, 32 * wpb, dyn, s>>>(gv, R->tv, R->rep_tmpl, R->rep_off, R->order, R->n_rep, R->x, R->v, R->status,
+                                   R->energy, nsteps, prm->dt, (float)c1, (float)c2, kT_acc,
+                                   (unsigned long long)prm->seed, (long long)prm->step0, ctl, use_grid, use_intra, S);
   DevResult h{};
   return finish_launch(ctx, &h);
 }

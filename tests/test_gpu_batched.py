@@ -243,6 +243,39 @@ def test_rigid_time_sliced_schedule_bitwise(G, ctx, field, blocks):
             assert 0 < ref[0][2] < n_rep
 
 
+def test_rigid_split_schedule_stops_on_abort_and_budget(G, ctx, field):
+    """On the split schedule a tail never runs on after its head was
+    stopped: with the abort flag set nothing moves; with a clock budget
+    every replica ends with STEPLIMIT and the context stays usable."""
+    sub, box, h, c32, grid = field
+    mol = synth.c24h8o6_core()
+    n_rep = 301
+    com, quat = synth.rigid_poses(mol, sub, n_rep, seed=161)
+    pose = np.concatenate([com, quat], 1).astype(np.float32).ravel()
+    reps = G.Replicas(ctx, [mol], [0] * n_rep, rigid=True)
+    reps.set_launch_config(G.LaunchConfig(kernel=G.KERNEL_RIGID_SUBWARP, lanes_per_replica=16, warps_per_block=4,
+                                          cache_slots=mol.n, queue=2, blocks=3))
+    reps.set_state(pose)
+    ctx.set_abort(True)
+    try:
+        st, res = G.relax(ctx, grid, reps, 200, G.fire_params(f_conv=0.0), check=False)
+    finally:
+        ctx.set_abort(False)
+    assert st == G.EABORTED
+    fs = reps.fire_state()
+    assert ((fs["status"] & G.REP_ABORTED) != 0).all() and (fs["steps"] == 0).all()
+    x, _ = reps.get_state()
+    assert np.array_equal(x, pose)
+    st, res = G.relax(ctx, grid, reps, 10_000_000, G.fire_params(f_conv=0.0, clock_budget_s=0.05), check=False)
+    assert st == G.ESTEPLIMIT
+    fs = reps.fire_state()
+    assert ((fs["status"] & G.REP_STEPLIMIT) != 0).all()
+    assert (fs["steps"] < 10_000_000).all() and (fs["steps"] > 0).any()
+    st, res = G.relax(ctx, grid, reps, 3, G.fire_params(f_conv=0.0))
+    assert st == G.OK and res.atom_evals == n_rep * mol.n * 3
+    reps.close()
+
+
 def test_rigid_nve_time_sliced_schedule_bitwise(G, ctx, field):
     """Rigid NVE on the split schedule (block cap 3): positions, velocities,
     energies and the recorded energy trace equal the unsplit run bit for
