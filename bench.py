@@ -209,10 +209,23 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 def kernel_source_hash():
+    """Hash of the source the rigid sub-warp relaxation kernel is built
+    from: the shared header, the device helpers at the top of dynamics.cu
+    (cell location, B-spline weights, record gathers) and the sub-warp
+    section (force routine, schedule, kernel).  Edits elsewhere in the file
+    (flexible kernels, host code) leave the committed counters valid."""
     h = hashlib.sha256()
-    for f in ("dynamics.cu", "internal.h"):
-        with open(os.path.join(ROOT, "paper_2508_15522_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    csrc = os.path.join(ROOT, "paper_2508_15522_gb300", "csrc")
+    with open(os.path.join(csrc, "internal.h"), "rb") as fh:
+        h.update(fh.read())
+    src = open(os.path.join(csrc, "dynamics.cu"), encoding="utf-8").read()
+    try:
+        top = src[:src.index("// Energy and force of one atom in the substrate field")]
+        a = src.index("// FIRE, rigid replicas, sub-warp form")
+        b = src.index("// FIRE, flexible replicas", a)
+        h.update((top + src[a:b]).encode())
+    except ValueError:
+        h.update(src.encode())
     return h.hexdigest()[:16]
 
 
