@@ -310,14 +310,20 @@ typedef struct {
 } gridff_relax_result;
 
 /* FIRE relaxation of every replica for up to nsteps iterations in one
- * persistent launch (one warp per replica; state kept in registers).
+ * persistent launch (layout per gridff_launch_config; state kept in
+ * registers or shared memory).
  * Iteration: forces; convergence test |F|_2 < f_conv (rigid: |F_tot|^2 +
  * |tau|^2); P = F.v; P > 0: mix v towards F, grow dt after n_min steps;
  * else v = 0, dt *= f_dec; semi-implicit Euler with per-atom cap d_max.
  * Rigid replicas apply the rule to (COM velocity, total force) and (body
  * angular velocity, body torque).  Without GRIDFF_CONTINUE the FIRE
- * scalars and status are reset first.  result may be NULL.
- * Errors: EINVAL, ECUDA, EABORTED, ESTEPLIMIT (state is consistent). */
+ * scalars and status are reset first.  result may be NULL.  The result
+ * does not depend on the layout or schedule beyond FP32 summation order
+ * (rigid layouts: bit for bit).
+ * Errors: EINVAL, ECUDA, EABORTED, ESTEPLIMIT (state is consistent),
+ * ETIMEOUT (rigid sub-warp layout: a split relaxation's second part gave up
+ * waiting for its first; the replicas concerned keep the first part's
+ * state). */
 gridff_status gridff_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* reps,
                            int32_t nsteps, const gridff_fire_params* params, int flags,
                            gridff_relax_result* result);
@@ -409,10 +415,12 @@ typedef struct {
 } gridff_md_params;
 
 /* NVE dynamics for nsteps: velocity Verlet (flexible) or the NO_SQUISH
- * symplectic rigid-body splitting (rigid).  energy_trace (may be NULL)
+ * symplectic rigid-body splitting (rigid; the sub-warp kernel with the
+ * time-sliced schedule of gridff_relax, the block cap of the replica set's
+ * launch configuration honoured).  energy_trace (may be NULL)
  * receives [(nsteps/record_every + 1) * n_rep] total energies (FP64, eV),
  * record k of replica r at [k*n_rep + r]; record 0 is the start.
- * Errors: EINVAL, ECUDA, EABORTED, ESTEPLIMIT. */
+ * Errors: EINVAL, ECUDA, EABORTED, ESTEPLIMIT, ETIMEOUT (as gridff_relax). */
 gridff_status gridff_run(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* reps,
                          int32_t nsteps, const gridff_md_params* params, int flags,
                          double* energy_trace);
