@@ -425,6 +425,54 @@ gridff_status gridff_run(gridff_ctx* ctx, const gridff_grid* grid, gridff_replic
                          int32_t nsteps, const gridff_md_params* params, int flags,
                          double* energy_trace);
 
+/* ------------------------------------------------------------------ poses */
+
+/* Poses of flexible molecules.  A pose is GRIDFF_MLP_OUT = 19 floats:
+ * centre of mass (3, A), orientation quaternion (w, x, y, z; normalised on
+ * use, zero = no rotation), torsion angles (GRIDFF_MAX_ROTORS = 12, rad).
+ * The torsions act on the template's rotatable bonds, defined from its
+ * bonds and torsion terms: root = the lowest-index atom with one bond
+ * (atom 0 if none); a breadth-first search from it (neighbours in
+ * increasing index order) gives parents and depths; the candidates are the
+ * distinct central bonds of the torsion terms in the order of their first
+ * term; a candidate is rotatable when it is a search-tree edge (b = parent
+ * end, c = child end) not in a ring, b has a parent and c another
+ * neighbour; the first 12 are kept and ordered by the depth of b (stable).
+ * Rotor k's coordinate is the dihedral of (parent(b), b, c, d), d the
+ * lowest-index neighbour of c other than b (IUPAC sign: positive for a
+ * right-handed turn about b -> c); its moving side is the set of atoms
+ * reached from c without crossing (b, c).  Rigid templates have none. */
+#define GRIDFF_MAX_ROTORS 12
+
+/* Rotatable bonds of template t: *n_rot, and quads[4k..4k+3] = (a, b, c, d)
+ * of rotor k in build order (quads may be NULL).  Errors: EINVAL. */
+gridff_status gridff_template_rotors(const gridff_replicas* reps, int32_t t, int32_t* n_rot, int32_t* quads);
+
+/* Set the state of every replica from poses[19 r .. 19 r + 18]: flexible
+ * replicas get the positions of the pose builder (from the template's
+ * reference geometry, set each rotor's dihedral to its torsion by rotating
+ * the moving side about the bond, in build order; then rotate about the
+ * centre of mass by the normalised quaternion and put the centre at the
+ * pose's), rigid replicas the pose (centre, normalised quaternion;
+ * torsions ignored); velocities are zeroed.  origin_xy, tile_xy (both or
+ * neither may be NULL): the centre is first folded into [origin, origin +
+ * tile) in x and y.  flags: GRIDFF_DEVICE_PTRS (poses on the device),
+ * GRIDFF_ASYNC.  Computed in FP32 on the device.  Errors: EINVAL, ECUDA. */
+gridff_status gridff_build_poses(gridff_replicas* reps, const float* poses, const double origin_xy[2],
+                                 const double tile_xy[2], int flags);
+
+/* Poses of the replicas' current state (the inverse of the builder, for
+ * training targets): torsions = the rotors' dihedrals, centre = the centre
+ * of mass (folded into the tile when origin_xy, tile_xy are given),
+ * orientation = the unit quaternion (w >= 0) of the rotation that best maps
+ * the built geometry with those torsions onto the state, mass-weighted
+ * (Horn's quaternion method, FP64 on the device).  Rigid replicas: their
+ * pose with w >= 0.  targets[19 n_rep]; tors_mask[12 n_rep] (may be NULL):
+ * 1 for the template's rotors, 0 past them.  flags: GRIDFF_DEVICE_PTRS.
+ * Errors: EINVAL, ECUDA. */
+gridff_status gridff_pose_targets(const gridff_replicas* reps, const double origin_xy[2], const double tile_xy[2],
+                                  float* targets, float* tors_mask, int flags);
+
 /* --------------------------------------------------------------- sampling */
 
 /* Random starting poses of a rigid replica set (Sec. 7: molecules start
@@ -537,7 +585,8 @@ gridff_status gridff_mlp_train(gridff_mlp* mlp, int32_t steps, int32_t n_targets
                                const float* descriptor, int32_t n_desc, uint64_t seed,
                                const gridff_train_params* params, float* losses);
 
-/* Propose one pose per replica of a rigid replica set: inputs are the
+/* Propose one pose per replica (rigid or flexible; flexible replicas are
+ * placed by the pose builder of gridff_build_poses): inputs are the
  * descriptor (n_desc <= sizes[0] floats, host) followed by
  * sizes[0] - n_desc <= 64 standard normal draws from a counter-based
  * generator: for row r (= replica) and noise index j,
@@ -547,8 +596,8 @@ gridff_status gridff_mlp_train(gridff_mlp* mlp, int32_t steps, int32_t n_targets
  *   z = sqrt(-2 ln u1) cos(2 pi u2)   (Box-Muller, FP32).  The output's
  * centre of mass is folded into the tile [origin, origin + tile) in x and
  * y; the quaternion is normalised (identity if zero).  Writes the replica
- * poses and zero velocities.  Errors: EINVAL, ENOTSUP (flexible replicas),
- * ENOMEM, ECUDA. */
+ * state (rigid: poses; flexible: built positions) and zero velocities.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
 gridff_status gridff_mlp_propose(gridff_mlp* mlp, gridff_replicas* reps, const float* descriptor,
                                  int32_t n_desc, uint64_t seed, const double origin_xy[2],
                                  const double tile_xy[2]);

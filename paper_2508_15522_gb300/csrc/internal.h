@@ -117,6 +117,14 @@ struct TorsionRec { int a, b, c, d; int role; int n; float V, cn0; };
 // Unique bond (each bond once).
 struct BondTerm { int i, j; float k, r0; };
 
+// Rotatable bond of a flexible template: reference quadruple (a, b, c, d)
+// whose dihedral is the torsion coordinate, and the atoms on c's side of
+// the bond (b, c) (bit i & 31 of move[i >> 5]).  Kept in build order.
+struct Rotor {
+  int a, b, c, d;
+  uint32_t move[4];
+};
+
 // Molecule templates as the kernels see them (all device pointers).
 struct TemplateView {
   const int* natoms;        // [T]
@@ -137,6 +145,8 @@ struct TemplateView {
   const AngleRec* ua;
   const int* ut_off;        // [T+1] unique torsions (TorsionRec, role unused)
   const TorsionRec* ut;
+  const int* rot_off;       // [T+1] rotatable bonds
+  const Rotor* rot;
   const float4* rigid;      // [T] {M, I1, I2, I3}
   const float* rmax;        // [T]
   float alpha;
@@ -191,6 +201,8 @@ struct gridff_replicas {
   float4* handoff_p = nullptr; // [n_rep] rigid NVE: quaternion momentum at the end of a head part
   // host copy of offsets
   int* h_rep_off = nullptr;
+  int* h_rot_off = nullptr;    // [n_tmpl+1] rotatable bonds (host copy)
+  Rotor* h_rot = nullptr;
   LaunchCfg cfg;               // set by gridff_tune / gridff_set_launch_config
 };
 
@@ -205,6 +217,11 @@ gridff_status set_err(gridff_ctx* ctx, gridff_status st, const char* fmt, ...);
 LaunchCfg default_launch_cfg(const gridff_replicas* R, bool use_grid);
 gridff_status prepare_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* R, const LaunchCfg& c,
                             int flags, int* blocks_out);
+// Pose builder on the context stream (poses.cu): d_poses on the device,
+// row r at d_poses + r * stride (GRIDFF_MLP_OUT floats used); centres
+// folded into the tile when origin_xy and tile_xy are given.
+gridff_status enqueue_build_poses(gridff_replicas* R, const float* d_poses, int stride, const double origin_xy[2],
+                                  const double tile_xy[2]);
 gridff_status enqueue_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* R, const LaunchCfg& c,
                             int blocks, int nsteps, const gridff_fire_params& P, int flags);
 gridff_status check_fire_params(gridff_ctx* ctx, const gridff_fire_params& P);

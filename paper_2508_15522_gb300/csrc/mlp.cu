@@ -733,9 +733,9 @@ gridff_status gridff_mlp_propose(gridff_mlp* m, gridff_replicas* R, const float*
                                  uint64_t seed, const double origin_xy[2], const double tile_xy[2]) {
   if (!m || !R || !descriptor || !origin_xy || !tile_xy) return set_err(m ? m->ctx : nullptr, GRIDFF_EINVAL, "null argument");
   gridff_ctx* ctx = m->ctx;
-  if (!R->rigid) return set_err(ctx, GRIDFF_ENOTSUP, "proposals are written for rigid replicas");
   if (n_desc < 0 || n_desc > m->sizes[0]) return set_err(ctx, GRIDFF_EINVAL, "descriptor longer than the input");
   if (m->sizes[0] - n_desc > 64) return set_err(ctx, GRIDFF_EINVAL, "at most 64 noise inputs per row");
+  if (!(tile_xy[0] > 0 && tile_xy[1] > 0)) return set_err(ctx, GRIDFF_EINVAL, "tile lengths must be positive");
   GRIDFF_CUDA(ctx, cudaSetDevice(ctx->device));
   const int rows = R->n_rep;
   gridff_status st = ensure_batch(m, rows);
@@ -747,9 +747,13 @@ gridff_status gridff_mlp_propose(gridff_mlp* m, gridff_replicas* R, const float*
                                                                          (unsigned long long)seed, Mp, m->pads[0],
                                                                          m->H[0], m->HT[0]);
   forward_rows(m, rows);
-  pose_kernel<<<grid1(rows, 128), 128, 0, s>>>(m->Y, rows, (float)origin_xy[0], (float)origin_xy[1],
-                                               (float)tile_xy[0], (float)tile_xy[1], R->x);
-  GRIDFF_CUDA(ctx, cudaMemsetAsync(R->v, 0, 6 * (size_t)rows * sizeof(float), s));
+  if (R->rigid) {
+    pose_kernel<<<grid1(rows, 128), 128, 0, s>>>(m->Y, rows, (float)origin_xy[0], (float)origin_xy[1],
+                                                 (float)tile_xy[0], (float)tile_xy[1], R->x);
+    GRIDFF_CUDA(ctx, cudaMemsetAsync(R->v, 0, 6 * (size_t)rows * sizeof(float), s));
+  } else if ((st = enqueue_build_poses(R, m->Y, kOut, origin_xy, tile_xy)) != GRIDFF_OK) {
+    return st;
+  }
   GRIDFF_CUDA(ctx, cudaGetLastError());
   GRIDFF_CUDA(ctx, cudaStreamSynchronize(s));
   return GRIDFF_OK;

@@ -35,6 +35,96 @@ gridff_status finish(gridff_ctx* ctx, int flags) {
   return GRIDFF_OK;
 }
 
+// Rotatable bonds of a flexible template (the torsion coordinates of a
+// pose).  Root: the lowest-index atom with one bond (atom 0 if none);
+// breadth-first search from it, neighbours in increasing index order,
+// gives parents and depths.  Candidates: the distinct central bonds of the
+// torsion terms in the order of their first term; a candidate is kept when
+// it is a search-tree edge (b the parent end, c the child end) that is not
+// in a ring, b has a parent and c another neighbour.  Quadruple (parent(b),
+// b, c, d), d the lowest-index neighbour of c other than b; moving side:
+// atoms reached from c without crossing (b, c).  At most GRIDFF_MAX_ROTORS
+// kept, then ordered by the depth of b (stable), so that a rotation only
+// moves atoms below every earlier rotor's quadruple.
+std::vector<Rotor> template_rotors(int n, const std::vector<std::vector<int>>& adj_in, const int32_t* tors,
+                                   int n_tors) {
+  std::vector<std::vector<int>> adj = adj_in;
+  for (auto& a : adj) std::sort(a.begin(), a.end());
+  int root = 0;
+  for (int i = 0; i < n; ++i)
+    if (adj[i].size() == 1) {
+      root = i;
+      break;
+    }
+  std::vector<int> parent(n, -1), depth(n, -1), queue{root};
+  depth[root] = 0;
+  for (size_t h = 0; h < queue.size(); ++h)
+    for (int v : adj[queue[h]])
+      if (depth[v] < 0) {
+        depth[v] = depth[queue[h]] + 1;
+        parent[v] = queue[h];
+        queue.push_back(v);
+      }
+  std::vector<Rotor> kept;
+  std::vector<int> kept_depth;
+  std::vector<std::pair<int, int>> seen;
+  for (int k = 0; k < n_tors && (int)kept.size() < GRIDFF_MAX_ROTORS; ++k) {
+    const int j = tors[4 * k + 1], l = tors[4 * k + 2];
+    const std::pair<int, int> key(std::min(j, l), std::max(j, l));
+    if (std::find(seen.begin(), seen.end(), key) != seen.end()) continue;
+    seen.push_back(key);
+    int b, c;
+    if (parent[l] == j) {
+      b = j;
+      c = l;
+    } else if (parent[j] == l) {
+      b = l;
+      c = j;
+    } else {
+      continue;
+    }
+    if (parent[b] < 0) continue;
+    int d = -1;
+    for (int v : adj[c])
+      if (v != b) {
+        d = v;
+        break;
+      }
+    if (d < 0) continue;
+    std::vector<char> in(n, 0);
+    std::vector<int> stack{c};
+    in[c] = 1;
+    bool ring = false;
+    while (!stack.empty()) {
+      const int u = stack.back();
+      stack.pop_back();
+      for (int v : adj[u]) {
+        if (u == c && v == b) continue;
+        if (v == b) {
+          ring = true;
+          continue;
+        }
+        if (!in[v]) {
+          in[v] = 1;
+          stack.push_back(v);
+        }
+      }
+    }
+    if (ring) continue;
+    Rotor R{parent[b], b, c, d, {0u, 0u, 0u, 0u}};
+    for (int i = 0; i < n; ++i)
+      if (in[i]) R.move[i >> 5] |= 1u << (i & 31);
+    kept.push_back(R);
+    kept_depth.push_back(depth[b]);
+  }
+  std::vector<int> order(kept.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return kept_depth[x] < kept_depth[y]; });
+  std::vector<Rotor> out;
+  for (int i : order) out.push_back(kept[i]);
+  return out;
+}
+
 // Lab-frame atom positions of rigid replicas: r_i = R(q) b_i + com.
 __global__ void rigid_positions_kernel(TemplateView tv, const int* rep_tmpl, const int* rep_off,
                                        const float* pose, int n_rep, float* out) {
@@ -81,6 +171,8 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
   std::vector<AngleRec> ua;
   std::vector<TorsionRec> ut;
   std::vector<double> tmpl_cost(n_templates);
+  std::vector<int> rot_off(1, 0);
+  std::vector<Rotor> rot;
   int max_n = 0;
   for (int t = 0; t < n_templates; ++t) {
     const gridff_molecule& m = T[t];
@@ -136,6 +228,15 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
                                 m.torsion_cos_nphi0[a]});
       }
     }
+    if (!rigid) {
+      for (int a = 0; a < m.n_torsions; ++a)
+        for (int k = 0; k < 4; ++k)
+          if (m.torsions[4 * a + k] < 0 || m.torsions[4 * a + k] >= n)
+            return set_err(ctx, GRIDFF_EINVAL, "template %d: torsion %d", t, a);
+      const std::vector<Rotor> tr = template_rotors(n, adj, m.torsions, m.n_torsions);
+      rot.insert(rot.end(), tr.begin(), tr.end());
+    }
+    rot_off.push_back((int)rot.size());
     ub.insert(ub.end(), tub.begin(), tub.end());
     ua.insert(ua.end(), tua.begin(), tua.end());
     ut.insert(ut.end(), tut.begin(), tut.end());
@@ -231,7 +332,8 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
          o_boff = push(blob, bond_off), o_b = push(blob, bonds), o_aof = push(blob, angle_off),
          o_a = push(blob, angles), o_tof = push(blob, tors_off), o_t = push(blob, tors),
          o_rig = push(blob, rig), o_rmax = push(blob, rmax), o_ubo = push(blob, ub_off), o_ub = push(blob, ub), o_uao = push(blob, ua_off),
-         o_ua = push(blob, ua), o_uto = push(blob, ut_off), o_ut = push(blob, ut), o_ord = push(blob, order);
+         o_ua = push(blob, ua), o_uto = push(blob, ut_off), o_ut = push(blob, ut), o_ord = push(blob, order),
+         o_roff = push(blob, rot_off), o_rot = push(blob, rot);
   gridff_replicas* R = new gridff_replicas();
   R->ctx = ctx;
   R->device = ctx->device;
@@ -270,6 +372,12 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
   R->tv.ut_off = (const int*)(B + o_uto);
   R->tv.ut = (const TorsionRec*)(B + o_ut);
   R->order = (int*)(B + o_ord);
+  R->tv.rot_off = (const int*)(B + o_roff);
+  R->tv.rot = (const Rotor*)(B + o_rot);
+  R->h_rot_off = new int[n_templates + 1];
+  memcpy(R->h_rot_off, rot_off.data(), (n_templates + 1) * sizeof(int));
+  R->h_rot = new Rotor[rot.size() + 1];
+  if (!rot.empty()) memcpy(R->h_rot, rot.data(), rot.size() * sizeof(Rotor));
   R->tv.alpha = (float)alpha;
   size_t nx = rigid ? 7 * (size_t)n_rep : 3 * (size_t)R->n_atoms;
   size_t nv = rigid ? 6 * (size_t)n_rep : 3 * (size_t)R->n_atoms;
@@ -317,6 +425,8 @@ void gridff_replicas_destroy(gridff_replicas* R) {
   cudaSetDevice(prev);
   cudaGetLastError();   // leave no error of this teardown behind
   delete[] R->h_rep_off;
+  delete[] R->h_rot_off;
+  delete[] R->h_rot;
   delete R;
 }
 

@@ -156,6 +156,9 @@ def _load():
         "gridff_relax_graph_create": (I32, [P, P, P, I32, C.POINTER(FireParams), C.c_int, C.POINTER(P)]),
         "gridff_graph_launch": (I32, [P, C.POINTER(RelaxResult)]),
         "gridff_graph_destroy": (None, [P]),
+        "gridff_template_rotors": (I32, [P, I32, C.POINTER(C.c_int32), P]),
+        "gridff_build_poses": (I32, [P, P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int]),
+        "gridff_pose_targets": (I32, [P, C.POINTER(C.c_double), C.POINTER(C.c_double), P, P, C.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -179,8 +182,10 @@ EXPORTED = (
     "gridff_set_launch_config", "gridff_get_launch_config", "gridff_tune", "gridff_relax_graph_create",
     "gridff_grid_storage", "gridff_langevin", "gridff_rmsd_unique_xyz", "gridff_mlp_set_targets",
     "gridff_mlp_train",
-    "gridff_graph_launch", "gridff_graph_destroy",
+    "gridff_graph_launch", "gridff_graph_destroy", "gridff_template_rotors", "gridff_build_poses",
+    "gridff_pose_targets",
 )
+MAX_ROTORS = 12
 
 KERNEL_RIGID_SUBWARP, KERNEL_RIGID_QUAD, KERNEL_FLEX_QUAD, KERNEL_FLEX_TERMS = 0, 1, 2, 3
 
@@ -416,6 +421,38 @@ class Replicas:
         o = (C.c_double * 2)(*origin_xy); t = (C.c_double * 2)(*tile_xy)
         self.ctx.check(lib.gridff_random_poses(self.h, C.c_uint64(seed), o, t, float(z_lo), float(z_hi),
                                                float(z_floor)))
+
+    def template_rotors(self, t=0) -> np.ndarray:
+        """(n_rot, 4) reference quadruples (a, b, c, d) of template t's
+        rotatable bonds in build order (gridff_template_rotors)."""
+        n = C.c_int32(0)
+        q = np.zeros(4 * MAX_ROTORS, np.int32)
+        st = lib.gridff_template_rotors(self.h, int(t), C.byref(n), q.ctypes.data_as(C.c_void_p))
+        if st != OK:
+            raise GridffError(st, "gridff_template_rotors")
+        return q[:4 * n.value].reshape(-1, 4)
+
+    def build_poses(self, poses, origin_xy=None, tile_xy=None):
+        """Set the state from (n_rep, 19) poses: centre, quaternion, torsions
+        (gridff_build_poses; flexible replicas through the pose builder)."""
+        o = (C.c_double * 2)(*origin_xy) if origin_xy is not None else None
+        t = (C.c_double * 2)(*tile_xy) if tile_xy is not None else None
+        if hasattr(poses, "data_ptr"):
+            self.ctx.check(lib.gridff_build_poses(self.h, C.c_void_p(poses.data_ptr()), o, t, DEVICE_PTRS))
+            return
+        p = np.ascontiguousarray(poses, np.float32).reshape(self.n_rep, MLP_OUT)
+        self.ctx.check(lib.gridff_build_poses(self.h, p.ctypes.data_as(C.c_void_p), o, t, 0))
+
+    def pose_targets(self, origin_xy=None, tile_xy=None):
+        """(targets (n_rep, 19), torsion masks (n_rep, 12)) of the current
+        state (gridff_pose_targets)."""
+        o = (C.c_double * 2)(*origin_xy) if origin_xy is not None else None
+        t = (C.c_double * 2)(*tile_xy) if tile_xy is not None else None
+        T = np.empty((self.n_rep, MLP_OUT), np.float32)
+        M = np.empty((self.n_rep, MAX_ROTORS), np.float32)
+        self.ctx.check(lib.gridff_pose_targets(self.h, o, t, T.ctypes.data_as(C.c_void_p),
+                                               M.ctypes.data_as(C.c_void_p), 0))
+        return T, M
 
     def rmsd_unique(self, poses, tile_xy, threshold=0.1, tmpl=0):
         """dup_of[i]: first earlier pose within `threshold` RMSD, else -1."""

@@ -197,10 +197,9 @@ def test_bad_arguments_are_rejected(gf, ctx):
     reps = gf.Replicas(ctx, [mol], np.zeros(4, np.int32), rigid=True)
     with pytest.raises(gf.GridffError):
         net.propose(reps, np.zeros(64, np.float32), 1, (0, 0), TILE)   # 136 noise inputs
-    flex = gf.Replicas(ctx, [mol], np.zeros(4, np.int32), rigid=False)
     with pytest.raises(gf.GridffError):
-        net.propose(flex, np.zeros(136, np.float32), 1, (0, 0), TILE)
-    net.close(); reps.close(); flex.close()
+        net.propose(reps, np.zeros(136, np.float32), 1, (0, 0), (0.0, TILE[1]))   # empty tile
+    net.close(); reps.close()
 
 
 def test_device_training_step_matches_oracle(gf, ctx):
