@@ -343,6 +343,61 @@ def minima_comparison(G, ctx, grid, mol, sub):
     return out
 
 
+def flexible_minima_comparison(G, ctx, grid, sub):
+    """The same comparison for a flexible molecule (24 atoms, 6 rotatable
+    bonds): poses carry torsions and become positions through the pose
+    builder.  Training data: 16 batches of 8192 random-start relaxations
+    (centre over the 5.64 A tile, uniform orientation and torsions); the
+    network is trained (K = 8, 3000 steps) on the poses of the converged
+    minima within 0.05 eV of the best-known energy; hits are converged
+    relaxations within 0.01 eV of it.  Both arms relax 4 batches of 8192."""
+    from paper_2508_15522_gb300 import sampling as S
+    from paper_2508_15522_gb300 import synth
+    a, n_rep = 5.64, 8192
+    mol = synth.random_flexible_molecule(24, 6, 4242)
+    surf = S.Surface((0.0, 0.0), (a, a), sub.z_top + 4.0, sub.z_top + 6.0, sub.z_top + 2.0)
+    sp = S.FlexSampler(ctx, grid, mol, surf, n_rep=n_rep, nsteps=FIRE_ITERS)
+    E, X, T, M = [], [], [], []
+    t0 = time.perf_counter()
+    for k in range(16):
+        b = sp.random_batch(10_000 + k)
+        Tk, Mk = sp.targets()
+        keep = b.converged
+        E.append(b.energy[keep]); X.append(b.poses[keep]); T.append(Tk[keep]); M.append(Mk[keep])
+    gen_s = time.perf_counter() - t0
+    E, X, T, M = (np.concatenate(v) for v in (E, X, T, M))
+    e_best = float(E.min())
+    low = E <= e_best + 0.05
+    h = E <= e_best + 0.01
+    best_set = len(sp.unique(X[h], E[h]))
+    net = S.new_network(ctx, T[low], seed=1)
+    net.set_targets(T[low], M[low])
+    t0 = time.perf_counter()
+    losses = net.train(3000, 256, 8, sp.desc, 7, G.train_params(lr=1e-3, tile=surf.tile_xy))
+    train_s = time.perf_counter() - t0
+    out = {"atoms": mol.n, "rotatable_bonds": sp.n_rot, "relaxations_for_training": 16 * n_rep,
+           "converged_minima": int(len(E)), "training_targets": int(low.sum()), "generation_s": gen_s,
+           "best_known_eV": e_best, "best_known_hits": int(h.sum()), "best_known_unique": best_set,
+           "tolerance_eV": 0.01, "batches": 4, "replicas_per_batch": n_rep,
+           "train": {"steps": 3000, "K": 8, "batch": 256, "seconds": train_s,
+                     "loss_first": float(losses[:20].mean()), "loss_last": float(losses[-100:].mean())}}
+    for name, fn in (("random", lambda k: sp.random_batch(20_000 + k)),
+                     ("mlp", lambda k: sp.proposal_batch(net, 30_000 + k))):
+        bs = [fn(k) for k in range(4)]
+        wall = sum(b.wall_s for b in bs)
+        hm = [S.hits(b, e_best) for b in bs]
+        Xh = np.concatenate([b.poses[m] for b, m in zip(bs, hm)])
+        Eh = np.concatenate([b.energy[m] for b, m in zip(bs, hm)])
+        n_hits = int(sum(m.sum() for m in hm))
+        out[name] = {"minima_per_s": n_hits / wall, "hit_fraction": n_hits / (4 * n_rep),
+                     "converged_fraction": float(np.mean([b.converged.mean() for b in bs])),
+                     "unique_hits": len(sp.unique(Xh[:20000], Eh[:20000])) if n_hits else 0, "wall_s": wall}
+    out["gain"] = out["mlp"]["minima_per_s"] / max(out["random"]["minima_per_s"], 1e-30)
+    net.close()
+    sp.close()
+    return out
+
+
 def uneven_positions(G, reps, mols, tof, sub, seed):
     from paper_2508_15522_gb300 import synth
     x0 = np.zeros((reps.n_atoms, 3), np.float32)
@@ -698,6 +753,7 @@ def run_gpu(args):
         G.relax(ctx, grid, reps, FIRE_ITERS, G.fire_params())
         line["nve_drift"] = nve_drift(G, ctx, grid, reps, mol, pose)
         line["minima"] = minima_comparison(G, ctx, grid, mol, sub)
+        line["minima_flexible"] = flexible_minima_comparison(G, ctx, grid, sub)
         line["uneven_batch"] = uneven_batch_comparison(G, ctx, grid, sub)
         line["precision_tiers"] = precision_comparison(G, ctx)
         line["minima_hopping"] = minima_hopping_curve(G, ctx)

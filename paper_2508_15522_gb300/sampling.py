@@ -3,11 +3,12 @@
 Minima hopping of flexible molecules (Sec. 7): Langevin thermalisation,
 FIRE relaxation and the RMSD uniqueness filter, repeated (`MinimaHopping`).
 
-For rigid molecules, two ways to choose where FIRE relaxations start, both
-on the device:
+Two ways to choose where FIRE relaxations start (rigid molecules:
+`Sampler`; flexible molecules, whose poses carry torsions: `FlexSampler`):
 
 * random starts (Sec. 7: random placements over the surface), drawn by
-  ``gridff_random_poses``;
+  ``gridff_random_poses`` (rigid) or drawn as poses with uniform torsions
+  and placed by ``gridff_build_poses`` (flexible);
 * learned proposals: a pose-proposal MLP (descriptor + noise in, pose out;
   bfloat16 tensor-core GEMMs) trained with a winner-takes-all pose loss on
   the low-energy minima that earlier relaxations found
@@ -92,6 +93,70 @@ class Sampler:
         """Indices of the structurally unique poses, lowest energy first."""
         order = np.argsort(energy, kind="stable")
         dup = self.reps.rmsd_unique(poses[order], self.surface.tile_xy, threshold)
+        return order[dup < 0]
+
+    def close(self):
+        self.reps.close()
+
+
+@dataclass
+class FlexSampler:
+    """Random starts and learned proposals for a flexible molecule.  A pose
+    is (centre, orientation, up to 12 torsions) and becomes atom positions
+    through the library's pose builder (`gridff_build_poses`); random starts
+    draw the centre over the tile and the height band, the orientation
+    uniformly and every torsion uniformly in (-pi, pi].  After each batch the
+    relaxed structures are also turned into poses (`gridff_pose_targets`),
+    the training targets of the proposal network."""
+    ctx: G.Context
+    grid: G.Grid
+    mol: object
+    surface: Surface
+    n_rep: int = 4096
+    nsteps: int = 2000
+    fire: G.FireParams = field(default_factory=lambda: G.fire_params(f_conv=1e-3))
+
+    def __post_init__(self):
+        self.reps = G.Replicas(self.ctx, [self.mol], [0] * self.n_rep)
+        self.desc = G.molecule_descriptor(self.mol)
+        self.n_rot = len(self.reps.template_rotors(0))
+
+    def _relax(self, t0) -> Batch:
+        G.relax(self.ctx, self.grid, self.reps, self.nsteps, self.fire, check=False)
+        fs = self.reps.fire_state()
+        x = self.reps.positions().reshape(self.n_rep, self.mol.n, 3)
+        wall = time.perf_counter() - t0
+        conv = (fs["status"] & G.REP_CONVERGED) != 0
+        return Batch(x, fs["energy"], conv, wall, self.ctx.last_kernel_ms())
+
+    def random_batch(self, seed: int) -> Batch:
+        s = self.surface
+        t0 = time.perf_counter()
+        g = np.random.default_rng(seed)
+        P = np.zeros((self.n_rep, G.MLP_OUT), np.float32)
+        P[:, 0] = s.origin_xy[0] + g.uniform(0, s.tile_xy[0], self.n_rep)
+        P[:, 1] = s.origin_xy[1] + g.uniform(0, s.tile_xy[1], self.n_rep)
+        P[:, 2] = g.uniform(s.z_lo, s.z_hi, self.n_rep)
+        P[:, 3:7] = g.standard_normal((self.n_rep, 4))
+        P[:, 7:7 + self.n_rot] = g.uniform(-np.pi, np.pi, (self.n_rep, self.n_rot))
+        self.reps.build_poses(P)
+        return self._relax(t0)
+
+    def proposal_batch(self, net: G.MLP, seed: int) -> Batch:
+        s = self.surface
+        t0 = time.perf_counter()
+        net.propose(self.reps, self.desc, seed, s.origin_xy, s.tile_xy)
+        return self._relax(t0)
+
+    def targets(self):
+        """Poses (n_rep, 19) and torsion masks of the current (relaxed) state."""
+        return self.reps.pose_targets(self.surface.origin_xy, self.surface.tile_xy)
+
+    def unique(self, x: np.ndarray, energy: np.ndarray, threshold: float = 0.1) -> np.ndarray:
+        """Indices of the structurally unique structures (n, atoms, 3),
+        lowest energy first (`gridff_rmsd_unique_xyz`)."""
+        order = np.argsort(energy, kind="stable")
+        dup = G.rmsd_unique_xyz(self.ctx, x[order], self.surface.tile_xy, threshold)
         return order[dup < 0]
 
     def close(self):
