@@ -271,6 +271,10 @@ __device__ __forceinline__ void grid_quad(const GridView& g, int q, bool act, fl
 // Bytes of one warp's cache with S slots (a multiple of 16).
 __host__ __device__ constexpr size_t cache_bytes(int S) { return (size_t)S * 256 + (((size_t)S * 4 + 15) & ~size_t(15)); }
 
+// Bytes of one replica's share in the sub-warp kernels: its stencil cache
+// and the cells its lanes publish for the refill queue (int2 per slot).
+__host__ __device__ constexpr size_t sw_cache_bytes(int S) { return cache_bytes(S) + (((size_t)S * 8 + 15) & ~size_t(15)); }
+
 // Bytes of one warp's dynamic shared memory in the unique-term flexible
 // kernel: its stencil cache and the staged nonbonded parameters.
 __host__ __device__ constexpr size_t flex_terms_warp_bytes(int S) { return cache_bytes(S) + (size_t)kMaxA * 16; }
@@ -948,10 +952,10 @@ __device__ __forceinline__ int pick_cell(const Cell (&c)[R], int k, int axis) {
 // body-frame torque summed over the sub-warp, this lane's share of the
 // energy (Acc: float for relaxations, double for NVE) and the BELOW flag.
 template <int W, int R, int KIND, class Acc>
-__device__ __forceinline__ void sw_forces(const GridView& g, const StencilCache& sc, float* cval, int S, int sw, int l,
-                                          int n, bool run, const float c[3], const float Rm[9],
-                                          const float4 (&bk)[R], const float4 (&pk)[R], float Ft[3], float tq[3],
-                                          Acc& e, int& flags) {
+__device__ __forceinline__ void sw_forces(const GridView& g, const StencilCache& sc, float* cval, int2* pub,
+                                          const float4* __restrict__ par, int S, int sw, int l, int n, bool run,
+                                          const float c[3], const float Rm[9], const float4 (&bk)[R],
+                                          const float4 (&pk)[R], float Ft[3], float tq[3], Acc& e, int& flags) {
   for (int a = 0; a < 3; ++a) Ft[a] = tq[a] = 0.f;
   e = Acc(0);
   // locate every atom of the lane
@@ -974,40 +978,42 @@ __device__ __forceinline__ void sw_forces(const GridView& g, const StencilCache&
     if constexpr (W < 32) msub = (msub >> (sw * W)) & ((1u << (W & 31)) - 1u);
     miss_mask[k] = msub;
   }
-  // refill the stencils that changed cell, W/4 atoms at a time (one per
-  // quad); one copy of the gather code for all rounds
+  // refill the stencils that changed cell.  Each lane publishes the cells
+  // of its atoms that missed; the misses of all rounds k form one queue
+  // (bit k W + l = atom index), served W/4 atoms at a time (one per quad)
+  // with one copy of the gather code
+#pragma unroll
+  for (int k = 0; k < R; ++k)
+    if ((miss_mask[k] >> l) & 1u) pub[k * W + l] = make_int2(cl[k].ix | (cl[k].iy << 16), cl[k].iz);
+  __syncwarp();
+  constexpr int kPerWord = 64 / W;   // rounds k whose miss bits share one 64-bit word
+#pragma unroll
+  for (int k0 = 0; k0 < R; k0 += kPerWord) {
+    unsigned long long mm = 0;
+#pragma unroll
+    for (int k = k0; k < R && k < k0 + kPerWord; ++k) mm |= (unsigned long long)miss_mask[k] << ((k - k0) * W);
 #pragma unroll 1
-  for (int k = 0; k < R; ++k) {
-    unsigned msub = pick_r<R>(miss_mask, k);
-    while (__any_sync(kFull, msub != 0)) {
+    while (__any_sync(kFull, mm != 0)) {
       const int qd = l >> 2, qq = l & 3;
-      unsigned m = msub;
+      unsigned long long m = mm;
       for (int j = 0; j < qd && m; ++j) m &= m - 1;
-      const int owner = m ? __ffs(m) - 1 : -1;
-      const int src = sw * W + (owner < 0 ? 0 : owner);
-      const int oix = __shfl_sync(kFull, pick_cell<R>(cl, k, 0), src);
-      const int oiy = __shfl_sync(kFull, pick_cell<R>(cl, k, 1), src);
-      const int oiz = __shfl_sync(kFull, pick_cell<R>(cl, k, 2), src);
-      const int okey = __shfl_sync(kFull, pick_r<R>(key, k), src);
-      const float4 pkk = pick_r<R>(pk, k);
-      const float oQ = __shfl_sync(kFull, pkk.x, src), oP = __shfl_sync(kFull, pkk.y, src);
-      const float oL = __shfl_sync(kFull, pkk.z, src);
-      if (owner >= 0) {
-        const int slot = k * W + owner;
+      if (m) {
+        const int slot = k0 * W + __ffsll((long long)m) - 1;
+        const int2 pc = pub[slot];
+        const int oix = (int)((unsigned)pc.x & 0xffffu), oiy = (int)((unsigned)pc.x >> 16), oiz = pc.y;
         float cv[16];
-        gather_runs<KIND>(g, ((long long)oix * g.nyp + oiy) * g.nzp + oiz + qq, make_float4(oQ, oP, oL, 0.f),
-                          cv);
+        gather_runs<KIND>(g, ((long long)oix * g.nyp + oiy) * g.nzp + oiz + qq, __ldg(&par[slot]), cv);
         // run mm = 4a + b, z-node qq goes to float4 2p + (qq >> 1) of
         // run pair p = 2a + (b >> 1), component 2 (qq & 1) + (b & 1)
 #pragma unroll
-        for (int mm = 0; mm < 16; ++mm) {
-          const int a = mm >> 2, bq = mm & 3;
+        for (int r2 = 0; r2 < 16; ++r2) {
+          const int a = r2 >> 2, bq = r2 & 3;
           const int f4 = 2 * (2 * a + (bq >> 1)) + (qq >> 1);
-          cval[((size_t)f4 * S + slot) * 4 + 2 * (qq & 1) + (bq & 1)] = cv[mm];
+          cval[((size_t)f4 * S + slot) * 4 + 2 * (qq & 1) + (bq & 1)] = cv[r2];
         }
-        if (qq == 0) sc.key[slot] = okey;
+        if (qq == 0) sc.key[slot] = (oix * g.ny + oiy) * g.nz + oiz;
       }
-      for (int j = 0; j < W / 4 && msub; ++j) msub &= msub - 1;
+      for (int j = 0; j < W / 4 && mm; ++j) mm &= mm - 1;
     }
   }
   __syncwarp();
@@ -1173,7 +1179,12 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
   constexpr int RPW = 32 / W;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int sw = lane / W, l = lane % W;
-  const StencilCache sc = warp_cache(dyn_smem, S, wib * RPW + sw);
+  unsigned char* const wbase = dyn_smem + (size_t)(wib * RPW + sw) * sw_cache_bytes(S);
+  StencilCache sc;
+  sc.val = (float4*)wbase;
+  sc.key = (int*)(wbase + (size_t)S * 256);
+  sc.S = S;
+  int2* const pub = (int2*)(wbase + cache_bytes(S));
   float* const cval = (float*)sc.val;
   const int warp = blockIdx.x * WPB + wib;
   const int n_warps = gridDim.x * WPB;
@@ -1281,7 +1292,8 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
       float Ft[3], tq[3];
       float e = 0.f;
       int flags = 0;
-      sw_forces<W, R, KIND, float>(g, sc, cval, S, sw, l, n, run, c, Rm, bk, pk, Ft, tq, e, flags);
+      sw_forces<W, R, KIND, float>(g, sc, cval, pub, tv.par + ab, S, sw, l, n, run, c, Rm, bk, pk, Ft, tq, e,
+                                    flags);
       if (!run) continue;
       st |= flags;
       ++evals;
@@ -1966,7 +1978,12 @@ run_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmp
   constexpr int RPW = 32 / W;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int sw = lane / W, l = lane % W;
-  const StencilCache sc = warp_cache(dyn_smem, S, wib * RPW + sw);
+  unsigned char* const wbase = dyn_smem + (size_t)(wib * RPW + sw) * sw_cache_bytes(S);
+  StencilCache sc;
+  sc.val = (float4*)wbase;
+  sc.key = (int*)(wbase + (size_t)S * 256);
+  sc.S = S;
+  int2* const pub = (int2*)(wbase + cache_bytes(S));
   float* const cval = (float*)sc.val;
   const int warp = blockIdx.x * WPB + wib;
   const int n_warps = gridDim.x * WPB;
@@ -2060,7 +2077,8 @@ run_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmp
     bool run = valid, stopped = false;
     // forces at the start of the part (a tail recomputes those its head
     // ended with: the same values)
-    sw_forces<W, R, KIND, double>(g, sc, cval, S, sw, l, n, run, c, Rm, bk, pk, Ft, tq, e, flags);
+    sw_forces<W, R, KIND, double>(g, sc, cval, pub, tv.par + ab, S, sw, l, n, run, c, Rm, bk, pk, Ft, tq, e,
+                                  flags);
     if (it_b == 0) {
       const double e0 = sub_sum(e);
       if (trace && valid && l == 0) trace[r] = total(e0);
@@ -2094,7 +2112,8 @@ run_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmp
       }
       quat_rot(q[0], q[1], q[2], q[3], Rm);
       int f2 = 0;
-      sw_forces<W, R, KIND, double>(g, sc, cval, S, sw, l, n, run, c, Rm, bk, pk, Ft, tq, e, f2);
+      sw_forces<W, R, KIND, double>(g, sc, cval, pub, tv.par + ab, S, sw, l, n, run, c, Rm, bk, pk, Ft, tq, e,
+                                    f2);
       if (run) {
         flags |= f2;
         ++evals;
@@ -2197,7 +2216,7 @@ int rigid_subwarp_width(const gridff_replicas* R) {
     }
   }
   if (best == 0) return 0;
-  return cache_bytes(n) * kSwWarps * (32 / best) <= 200 * 1024 ? best : 0;
+  return sw_cache_bytes(n) * kSwWarps * (32 / best) <= 200 * 1024 ? best : 0;
 }
 
 // Allow `bytes` of dynamic shared memory (needed whenever static plus
@@ -2302,7 +2321,7 @@ KernelShape shape_of(const gridff_replicas* R, const LaunchCfg& c, int kind) {
       if (!R->rigid || (c.W != 8 && c.W != 16 && c.W != 32) || c.S < R->max_natoms) return k;
       const SwFn fn = rigid_sw_fn(c.W, sw_rounds(R, c.W), kind);
       if (!fn) return k;
-      return {(const void*)fn, 32 * kSwWarps, kSwWarps * (32 / c.W), cache_bytes(c.S) * kSwWarps * (32 / c.W)};
+      return {(const void*)fn, 32 * kSwWarps, kSwWarps * (32 / c.W), sw_cache_bytes(c.S) * kSwWarps * (32 / c.W)};
     }
     case GRIDFF_KERNEL_RIGID_QUAD:
       if (!R->rigid || c.wpb != kWarpsPerBlock) return k;
@@ -2651,7 +2670,7 @@ gridff_status gridff_run(gridff_ctx* ctx, const gridff_grid* grid, gridff_replic
     if (fn) {
       // the sub-warp layout of the relaxation, every atom cached
       const int S = R->max_natoms;
-      const size_t dyn = cache_bytes(S) * kSwWarps * (32 / W);
+      const size_t dyn = sw_cache_bytes(S) * kSwWarps * (32 / W);
       GRIDFF_CUDA(ctx, set_dyn_smem((const void*)fn, dyn));
       const int per_block = kSwWarps * (32 / W);
       int per_sm = 0;
