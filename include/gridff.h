@@ -62,7 +62,7 @@ typedef enum {
   GRIDFF_ECUDA = 3,       /* CUDA runtime error (message has cudaGetErrorString) */
   GRIDFF_EABORTED = 4,    /* the host abort flag stopped a relax/run call */
   GRIDFF_ESTEPLIMIT = 5,  /* the clock budget of a relax/run call ran out */
-  GRIDFF_ENOTSUP = 6,     /* combination not supported by this build */
+  GRIDFF_ENOTSUP = 6,     /* combination the library does not support */
   GRIDFF_ETIMEOUT = 7     /* a bounded wait inside a kernel ran out (a relaxation split across
                              two warps did not receive its first part in time); the replicas
                              concerned keep the state of that first part */
