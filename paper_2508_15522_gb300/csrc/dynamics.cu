@@ -918,8 +918,10 @@ relax_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl
 // (W = 8, 16 or 32; 32/W replicas per warp), one lane per atom.  Per step
 // and per round of W atoms: the lane places its atom and finds its cell;
 // atoms whose cell is not in the stencil cache are refilled cooperatively
-// (the quads of the sub-warp gather the 16 z-runs, lane q taking record q
-// of each run, and store the channel-combined node values); then every lane
+// (their cells are published in shared memory and the quads of the
+// sub-warp serve all misses of the step from one queue, gathering the 16
+// z-runs, lane q taking record q of each run, and storing the channel-
+// combined node values); then every lane
 // contracts its own atom's 64 cached values (16 z passes, 4 y, 1 x) with
 // no work repeated across lanes.  Cache layout of a replica (S >= atoms
 // slots): the 16 (x, y) runs (a, b) form 8 pairs p = 2a + (b >> 1); float4
@@ -927,25 +929,6 @@ relax_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl
 // the pair's two runs interleaved, (A_2h, B_2h, A_2h+1, B_2h+1), so the
 // contraction runs on paired FP32 FMAs.
 // ---------------------------------------------------------------------------
-// Element k (runtime, k < R) of a register array, by selects (no local
-// memory).
-template <int R, class T>
-__device__ __forceinline__ T pick_r(const T (&a)[R], int k) {
-  T v = a[0];
-#pragma unroll
-  for (int j = 1; j < R; ++j)
-    if (k == j) v = a[j];
-  return v;
-}
-template <int R>
-__device__ __forceinline__ int pick_cell(const Cell (&c)[R], int k, int axis) {
-  int v = axis == 0 ? c[0].ix : axis == 1 ? c[0].iy : c[0].iz;
-#pragma unroll
-  for (int j = 1; j < R; ++j)
-    if (k == j) v = axis == 0 ? c[j].ix : axis == 1 ? c[j].iy : c[j].iz;
-  return v;
-}
-
 // Grid forces of the replica served by this sub-warp at pose (c, Rm): every
 // lane locates its R atoms, the stencils that changed cell are refilled by
 // the quads, every lane contracts its atoms; returns the total force and the
