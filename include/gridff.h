@@ -81,6 +81,10 @@ typedef enum {
 #define GRIDFF_CONTINUE 4        /* relax: keep FIRE scalars and status from the last call */
 #define GRIDFF_NO_GRID 8         /* eval/relax/run: skip the grid term */
 #define GRIDFF_NO_INTRA 16       /* eval/relax/run: skip the intramolecular terms */
+#define GRIDFF_TEST_NO_HANDOFF 256  /* relax (rigid sub-warp layout), test hook of the bounded wait:
+                                       the first parts of split relaxations publish no hand-off,
+                                       so their second parts give up after about a second and the
+                                       call returns GRIDFF_ETIMEOUT; the context stays usable */
 
 /* grid channels */
 #define GRIDFF_CH_C 1            /* Coulomb V^C (volts) */

@@ -1139,9 +1139,10 @@ __device__ __noinline__ SwPart sw_part(int warp, int n_warps, int P, int nsteps,
 }
 
 // Upper bound on the polls of a hand-off flag (with a 1 us sleep between
-// polls, about 8 s of waiting at the least), after which the part is
-// skipped and the call returns GRIDFF_ETIMEOUT.
-constexpr int kHandoffPolls = 1 << 23;
+// polls, about a second of waiting at the least), after which the part is
+// skipped and the call returns GRIDFF_ETIMEOUT.  A head finishes a quarter
+// of a task before its tail starts, so a working launch never waits long.
+constexpr int kHandoffPolls = 1 << 20;
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
@@ -1156,8 +1157,8 @@ template <int W, int R, int WPB, int MINB, int KIND>
 __global__ void __launch_bounds__(32 * WPB, MINB)
 relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, int n_rep,
                       float* pose, float* vel, float* fdt, float* falpha, int* fnp, int* status,
-                      int* steps, double* energy, int* handoff, int queued, int nsteps, FireP fp, Control ctl,
-                      int S) {
+                      int* steps, double* energy, int* handoff, int queued, int publish, int nsteps, FireP fp,
+                      Control ctl, int S) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   constexpr int RPW = 32 / W;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -1361,7 +1362,7 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
       // by the part that ends the task
       report(ctl, n, evals, head ? (st & ~GRIDFF_REP_CONVERGED) : st, total);
     }
-    if (head) {
+    if (head && publish) {
       // publish the head's state to the warp that runs the tail
       const unsigned sm = __ballot_sync(kFull, stopped && l == 0);
       __threadfence();
@@ -2242,7 +2243,7 @@ __global__ void fire_reset_kernel(int n, float dt0, float a0, float* dt, float* 
 }
 
 using SwFn = void (*)(GridView, TemplateView, const int*, int, float*, float*, float*, float*, int*, int*, int*,
-                     double*, int*, int, int, FireP, Control, int);
+                     double*, int*, int, int, int, FireP, Control, int);
 
 // Sub-warp rigid kernel for W lanes per replica and R atoms per lane; FP32
 // four-slot grids get a build without the other record kinds' code.
@@ -2478,7 +2479,8 @@ gridff_status enqueue_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_rep
       e = launch_ex(rigid_sw_fn(c.W, sw_rounds(R, c.W), kind), blocks, k.threads, k.dyn, s, wp, gv, R->tv,
                     (const int*)R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha, R->fire_nplus,
                     R->status, R->steps, R->energy, R->handoff,
-                    (int)(c.queue == 1 || (c.queue == 0 && P.f_conv > 0)), nsteps, fp, ctl, c.S);
+                    (int)(c.queue == 1 || (c.queue == 0 && P.f_conv > 0)), (int)!(flags & GRIDFF_TEST_NO_HANDOFF),
+                    nsteps, fp, ctl, c.S);
       break;
     case GRIDFF_KERNEL_RIGID_QUAD:
       e = launch_ex(relax_rigid_kernel, blocks, k.threads, k.dyn, s, wp, gv, R->tv, (const int*)R->rep_tmpl,

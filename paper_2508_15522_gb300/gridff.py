@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libgridff.so")
 OK, EINVAL, ENOMEM, ECUDA, EABORTED, ESTEPLIMIT, ENOTSUP, ETIMEOUT = range(8)
 REP_CONVERGED, REP_BELOW, REP_NONFINITE, REP_ABORTED, REP_STEPLIMIT = 1, 2, 4, 8, 16
 DEVICE_PTRS, ASYNC, CONTINUE, NO_GRID, NO_INTRA = 1, 2, 4, 8, 16
+TEST_NO_HANDOFF = 256
 CH_C, CH_P, CH_L = 1, 2, 4
 STORE_F32, STORE_F16, STORE_BF16 = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EABORTED", 5: "ESTEPLIMIT",

@@ -276,6 +276,29 @@ def test_rigid_split_schedule_stops_on_abort_and_budget(G, ctx, field):
     reps.close()
 
 
+def test_rigid_split_schedule_wait_is_bounded(G, ctx, field):
+    """Test hook GRIDFF_TEST_NO_HANDOFF: the first parts of split tasks
+    publish nothing, so every second part gives up after its bounded wait;
+    the call returns ETIMEOUT, the replicas of split tasks keep the state of
+    their first part, whole tasks finish, and the context stays usable."""
+    sub, box, h, c32, grid = field
+    mol = synth.c24h8o6_core()
+    n_rep, nsteps = 301, 150
+    com, quat = synth.rigid_poses(mol, sub, n_rep, seed=171)
+    pose = np.concatenate([com, quat], 1).astype(np.float32).ravel()
+    reps = G.Replicas(ctx, [mol], [0] * n_rep, rigid=True)
+    reps.set_launch_config(G.LaunchConfig(kernel=G.KERNEL_RIGID_SUBWARP, lanes_per_replica=16, warps_per_block=4,
+                                          cache_slots=mol.n, queue=2, blocks=3))
+    reps.set_state(pose)
+    st, res = G.relax(ctx, grid, reps, nsteps, G.fire_params(f_conv=0.0), flags=G.TEST_NO_HANDOFF, check=False)
+    assert st == G.ETIMEOUT
+    steps = reps.fire_state()["steps"]
+    assert (steps <= nsteps).all() and (steps < nsteps).any() and (steps == nsteps).any()
+    st, res = G.relax(ctx, grid, reps, 5, G.fire_params(f_conv=0.0))
+    assert st == G.OK and res.atom_evals == n_rep * mol.n * 5
+    reps.close()
+
+
 def test_rigid_nve_time_sliced_schedule_bitwise(G, ctx, field):
     """Rigid NVE on the split schedule (block cap 3): positions, velocities,
     energies and the recorded energy trace equal the unsplit run bit for
