@@ -576,39 +576,40 @@ def c2_accuracy(G, ctx, grid, sub, mol, pose, n_sample=8):
 
 
 def interpolation_roofline(G, ctx, grid, box, torch, dev, stream, l2_peak):
-    """Grid interpolation alone (gridff_eval, no intramolecular terms, no
-    stencil reuse) at uniform random points over the tile and the z band
-    [z0 + 2, z0 + 8] A: 65536 x 38 = 2.49 M points per launch, 20 launches
-    back to back on the stream (the grid stays L2-resident)."""
+    """Grid interpolation alone (gridff_eval_points: a quad of lanes per
+    point, no stencil reuse) at uniform random points over the tile and the
+    z band [z0 + 2, z0 + 8] A: 65536 x 38 = 2.49 M points per launch with
+    the grid factors of a 38-atom C/H/O set, 20 launches back to back on the
+    stream (the grid stays L2-resident)."""
     from paper_2508_15522_gb300 import synth
     n_rep, n_at = 65536, 38
     g = synth.rng(3003)
     els = list(g.choice(["C", "H", "O"], n_at))
     R = np.array([synth.ELEMENTS[e][0] for e in els]); eps = np.array([synth.ELEMENTS[e][1] for e in els])
     pm = synth.Molecule(els, np.zeros((n_at, 3)), g.uniform(-0.3, 0.3, n_at), R, eps, np.full(n_at, 12.0))
-    reps = G.Replicas(ctx, [pm], [0] * n_rep)
-    pts = synth.uniform_points(n_rep * n_at, box, 3004, zband=(2.0, 8.0)).astype(np.float32)
-    reps.set_state(torch.from_numpy(pts.ravel()).to(dev))
-    E = torch.empty(n_rep, dtype=torch.float64, device=dev)
-    F = torch.empty(3 * n_rep * n_at, dtype=torch.float32, device=dev)
-    Ea = torch.empty(n_rep * n_at, dtype=torch.float32, device=dev)
-    St = torch.empty(n_rep, dtype=torch.int32, device=dev)
+    reps = G.Replicas(ctx, [pm], [0])
+    qpl = np.tile(reps.template_factors(0), (n_rep, 1))
+    reps.close()
+    n = n_rep * n_at
+    pts = synth.uniform_points(n, box, 3004, zband=(2.0, 8.0)).astype(np.float32)
+    X = torch.from_numpy(pts.ravel()).to(dev)
+    Q = torch.from_numpy(qpl.ravel()).to(dev)
+    E = torch.empty(n, dtype=torch.float32, device=dev)
+    F = torch.empty(3 * n, dtype=torch.float32, device=dev)
     for _ in range(3):
-        G.eval(ctx, grid, reps, flags=G.NO_INTRA | G.ASYNC, out=(E, F, Ea, St))
+        G.eval_points(ctx, grid, X, Q, out=(E, F, None), flags=G.ASYNC)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
     e0.record(stream)
     iters = 20
     for _ in range(iters):
-        G.eval(ctx, grid, reps, flags=G.NO_INTRA | G.ASYNC, out=(E, F, Ea, St))
+        G.eval_points(ctx, grid, X, Q, out=(E, F, None), flags=G.ASYNC)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / iters
-    evals = n_rep * n_at
-    achieved = BYTES_PER_EVAL * evals / (ms * 1e-3) / 1e9
-    reps.close()
-    return {"kernel": "eval_kernel (quad gather, no stencil cache)", "atom_evals_per_s": evals / (ms * 1e-3),
-            "ms_per_launch": ms, "points_per_launch": evals, "points": "uniform over the tile, z0 + [2, 8] A",
+    achieved = BYTES_PER_EVAL * n / (ms * 1e-3) / 1e9
+    return {"kernel": "eval_points_kernel (quad gather, no stencil reuse)", "atom_evals_per_s": n / (ms * 1e-3),
+            "ms_per_launch": ms, "points_per_launch": n, "points": "uniform over the tile, z0 + [2, 8] A",
             "roofline": {"bound": "l2", "achieved": achieved, "peak": l2_peak, "unit": "GB/s",
                          "frac": achieved / l2_peak if l2_peak else None}}
 
@@ -776,8 +777,8 @@ def profile_case(args):
     (no JSON line): `uneven` relaxes 4096 of the uneven flexible replicas
     for 20 FIRE iterations; `langevin` runs 20 Langevin steps on them;
     `mlp` runs 20 training steps of the proposal network; `interp` evaluates
-    the grid alone at 65536 x 38 uniform random points (the interpolation-
-    only workload of the bench line).  Each runs its launch twice (the
+    the grid alone at 65536 x 38 uniform random points (gridff_eval_points,
+    the interpolation-only workload of the bench line).  Each runs its launch twice (the
     second is the one to capture with -s)."""
     import __graft_entry__ as ge
     ge.build()
@@ -814,18 +815,18 @@ def profile_case(args):
         import torch
         sub, box, _, _ = workload()
         grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing)
-        n_rep, n_at = 65536, 38
-        mol = synth.rigid_molecule(n_at, 3003)
-        reps = G.Replicas(ctx, [mol], [0] * n_rep)
-        pts = synth.uniform_points(n_rep * n_at, box, 3004, zband=(2.0, 8.0)).astype(np.float32)
-        reps.set_state(pts.ravel())
+        n = 65536 * 38
+        mol = synth.rigid_molecule(38, 3003)
+        reps = G.Replicas(ctx, [mol], [0])
+        qpl = np.tile(reps.template_factors(0), (65536, 1))
+        pts = synth.uniform_points(n, box, 3004, zband=(2.0, 8.0)).astype(np.float32)
         dev = torch.device("cuda", 0)
-        E = torch.empty(n_rep, dtype=torch.float64, device=dev)
-        F = torch.empty(3 * n_rep * n_at, dtype=torch.float32, device=dev)
-        Ea = torch.empty(n_rep * n_at, dtype=torch.float32, device=dev)
-        St = torch.empty(n_rep, dtype=torch.int32, device=dev)
+        X = torch.from_numpy(pts.ravel()).to(dev)
+        Q = torch.from_numpy(qpl.ravel()).to(dev)
+        E = torch.empty(n, dtype=torch.float32, device=dev)
+        F = torch.empty(3 * n, dtype=torch.float32, device=dev)
         for _ in range(2):
-            G.eval(ctx, grid, reps, flags=G.NO_INTRA, out=(E, F, Ea, St))
+            G.eval_points(ctx, grid, X, Q, out=(E, F, None))
         print("interp evaluated")
 
 

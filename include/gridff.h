@@ -313,6 +313,26 @@ typedef struct {
   int32_t max_steps;       /* most evaluations done by one replica */
 } gridff_relax_result;
 
+/* The substrate field alone at n independent points (the grid-interpolation
+ * steps of the path: fold into the tile, cell and fractional coordinates,
+ * cubic B-spline weights, gather of the 4x4x4 coefficient stencil,
+ * contraction, channel combination; Sec. 5 and Eqs. E, E_Coulomb, V_Morse).
+ * Point i at xyz[3i..3i+2] (A) with grid factors qpl[3i..3i+2] = (Q, P, L)
+ * (charge and the Morse factors of gridff_template_factors) gets
+ * E[i] = Q V^C + P V^P + L V^L (eV) and F[3i..3i+2] = -grad E (eV/A);
+ * status[i] (may be NULL): GRIDFF_REP_BELOW below the grid (clamped to its
+ * bottom cell), GRIDFF_REP_NONFINITE; above the grid E = F = 0.  One
+ * evaluation per point, no reuse between points (a quad of lanes per point).
+ * flags: GRIDFF_DEVICE_PTRS, GRIDFF_ASYNC.  The kernel time is kept for
+ * gridff_last_kernel_ms (synchronous calls).  Errors: EINVAL, ECUDA. */
+gridff_status gridff_eval_points(gridff_ctx* ctx, const gridff_grid* grid, int64_t n, const float* xyz,
+                                 const float* qpl, float* E, float* F, int32_t* status, int flags);
+
+/* Grid factors (Q, P, L) of the atoms of template t (Eqs. E_Coulomb,
+ * V_Morse: Q = q, P = eps e^{2 alpha R}, L = -2 eps e^{alpha R}), as the
+ * kernels use them: qpl[3 n_atoms(t)].  Errors: EINVAL, ECUDA. */
+gridff_status gridff_template_factors(const gridff_replicas* reps, int32_t t, float* qpl);
+
 /* FIRE relaxation of every replica for up to nsteps iterations in one
  * persistent launch (layout per gridff_launch_config; state kept in
  * registers or shared memory).

@@ -792,6 +792,44 @@ eval_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
   }
 }
 
+// Grid interpolation alone at independent points (steps a2-a6 of the path:
+// fold, cell, weights, gather, contraction, channel combination): a quad
+// per point, 8 points per warp per round, grid-stride over the points.
+#ifndef GRIDFF_POINTS_MINB
+#define GRIDFF_POINTS_MINB 1
+#endif
+template <int KIND>
+__global__ void __launch_bounds__(256, GRIDFF_POINTS_MINB)
+eval_points_kernel(GridView g, long long n, const float* __restrict__ xyz, const float* __restrict__ qpl,
+                   float* __restrict__ E, float* __restrict__ F, int* __restrict__ st) {
+  const int lane = threadIdx.x & 31, quad = lane >> 2, q = lane & 3;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const StencilCache nocache{nullptr, nullptr, 0};
+  for (long long b = warp * kQuads; b < n; b += n_warps * kQuads) {   // uniform over the warp
+    const long long i = b + quad;
+    const bool act = i < n;
+    float x = 0.f, y = 0.f, z = 0.f;
+    float4 par = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (act) {
+      x = __ldg(&xyz[3 * i]);
+      y = __ldg(&xyz[3 * i + 1]);
+      z = __ldg(&xyz[3 * i + 2]);
+      par = make_float4(__ldg(&qpl[3 * i]), __ldg(&qpl[3 * i + 1]), __ldg(&qpl[3 * i + 2]), 0.f);
+    }
+    int flags = 0;
+    float e, fx, fy, fz;
+    grid_quad<false, KIND>(g, q, act, x, y, z, par, e, fx, fy, fz, flags, nocache, -1);
+    if (act && q == 0) {
+      E[i] = e;
+      F[3 * i] = fx;
+      F[3 * i + 1] = fy;
+      F[3 * i + 2] = fz;
+      if (st) st[i] = flags | (finite3(fx, fy, fz) && isfinite(e) ? 0 : GRIDFF_REP_NONFINITE);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // FIRE, rigid replicas
 // ---------------------------------------------------------------------------
@@ -2544,6 +2582,61 @@ gridff_status gridff_eval(gridff_ctx* ctx, const gridff_grid* grid, gridff_repli
     if (st_out) GRIDFF_CUDA(ctx, cudaMemcpyAsync(st_out, dS, nS, cudaMemcpyDeviceToHost, s));
   }
   if (!(dev && (flags & GRIDFF_ASYNC))) GRIDFF_CUDA(ctx, cudaStreamSynchronize(s));
+  return GRIDFF_OK;
+}
+
+gridff_status gridff_eval_points(gridff_ctx* ctx, const gridff_grid* grid, int64_t n, const float* xyz,
+                                 const float* qpl, float* E, float* F, int32_t* status, int flags) {
+  if (!ctx) return GRIDFF_EINVAL;
+  if (!grid || n < 0 || (n > 0 && (!xyz || !qpl || !E || !F)))
+    return set_err(ctx, GRIDFF_EINVAL, "null argument or negative count");
+  if (n == 0) return GRIDFF_OK;
+  GRIDFF_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  const bool dev = flags & GRIDFF_DEVICE_PTRS;
+  const size_t n3 = 3 * (size_t)n * sizeof(float), n1 = (size_t)n * sizeof(float);
+  Staging stg(ctx);
+  const float *dx = xyz, *dq = qpl;
+  float *dE = E, *dF = F;
+  int* dS = status;
+  if (!dev) {
+    GRIDFF_CUDA(ctx, cudaMallocAsync(&stg.ptr, 3 * n3 + 2 * n1 + 64, s));
+    char* p = (char*)stg.ptr;
+    float* hx = (float*)p;
+    float* hq = (float*)(p + n3);
+    dF = (float*)(p + 2 * n3);
+    dE = (float*)(p + 3 * n3);
+    dS = status ? (int*)(p + 3 * n3 + n1) : nullptr;
+    GRIDFF_CUDA(ctx, cudaMemcpyAsync(hx, xyz, n3, cudaMemcpyHostToDevice, s));
+    GRIDFF_CUDA(ctx, cudaMemcpyAsync(hq, qpl, n3, cudaMemcpyHostToDevice, s));
+    dx = hx;
+    dq = hq;
+  }
+  const GridView gv = grid->view();
+  const void* fn = grid->kind == REC_F32x4 ? (const void*)eval_points_kernel<REC_F32x4>
+                                           : (const void*)eval_points_kernel<-1>;
+  int per_sm = 0;
+  GRIDFF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0));
+  const long long need = (n + 63) / 64;   // 8 warps x 8 points per block round
+  const long long cap = (long long)(per_sm > 0 ? per_sm : 1) * ctx->n_sm;
+  const int blocks = (int)(need < cap ? need : cap);
+  GRIDFF_CUDA(ctx, cudaEventRecord(ctx->ev0, s));
+  if (grid->kind == REC_F32x4)
+    eval_points_kernel<REC_F32x4><<<blocks, 256, 0, s>>>(gv, (long long)n, dx, dq, dE, dF, dS);
+  else
+    eval_points_kernel<-1><<<blocks, 256, 0, s>>>(gv, (long long)n, dx, dq, dE, dF, dS);
+  GRIDFF_CUDA(ctx, cudaGetLastError());
+  GRIDFF_CUDA(ctx, cudaEventRecord(ctx->ev1, s));
+  if (!dev) {
+    GRIDFF_CUDA(ctx, cudaMemcpyAsync(E, dE, n1, cudaMemcpyDeviceToHost, s));
+    GRIDFF_CUDA(ctx, cudaMemcpyAsync(F, dF, n3, cudaMemcpyDeviceToHost, s));
+    if (status) GRIDFF_CUDA(ctx, cudaMemcpyAsync(status, dS, n1, cudaMemcpyDeviceToHost, s));
+  }
+  if (!(dev && (flags & GRIDFF_ASYNC))) {
+    GRIDFF_CUDA(ctx, cudaStreamSynchronize(s));
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) == cudaSuccess) ctx->last_ms = ms;
+  }
   return GRIDFF_OK;
 }
 

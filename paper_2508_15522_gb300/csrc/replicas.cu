@@ -413,6 +413,23 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
   return GRIDFF_OK;
 }
 
+gridff_status gridff_template_factors(const gridff_replicas* R, int32_t t, float* qpl) {
+  if (!R || !qpl || t < 0 || t >= R->n_tmpl) return GRIDFF_EINVAL;
+  gridff_ctx* ctx = R->ctx;
+  GRIDFF_CUDA(ctx, cudaSetDevice(ctx->device));
+  int off[2];
+  GRIDFF_CUDA(ctx, cudaMemcpy(off, R->tv.atom_off + t, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+  std::vector<float4> par(off[1] - off[0]);
+  if (!par.empty())
+    GRIDFF_CUDA(ctx, cudaMemcpy(par.data(), R->tv.par + off[0], par.size() * sizeof(float4), cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < par.size(); ++i) {
+    qpl[3 * i] = par[i].x;
+    qpl[3 * i + 1] = par[i].y;
+    qpl[3 * i + 2] = par[i].z;
+  }
+  return GRIDFF_OK;
+}
+
 void gridff_replicas_destroy(gridff_replicas* R) {
   if (!R) return;
   int prev = 0;

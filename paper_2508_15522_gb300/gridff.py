@@ -160,6 +160,8 @@ def _load():
         "gridff_template_rotors": (I32, [P, I32, C.POINTER(C.c_int32), P]),
         "gridff_build_poses": (I32, [P, P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int]),
         "gridff_pose_targets": (I32, [P, C.POINTER(C.c_double), C.POINTER(C.c_double), P, P, C.c_int]),
+        "gridff_eval_points": (I32, [P, P, C.c_int64, P, P, P, P, P, C.c_int]),
+        "gridff_template_factors": (I32, [P, I32, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -184,7 +186,7 @@ EXPORTED = (
     "gridff_grid_storage", "gridff_langevin", "gridff_rmsd_unique_xyz", "gridff_mlp_set_targets",
     "gridff_mlp_train",
     "gridff_graph_launch", "gridff_graph_destroy", "gridff_template_rotors", "gridff_build_poses",
-    "gridff_pose_targets",
+    "gridff_pose_targets", "gridff_eval_points", "gridff_template_factors",
 )
 MAX_ROTORS = 12
 
@@ -358,6 +360,7 @@ class Replicas:
                                              tof.ctypes.data_as(C.POINTER(C.c_int32)), int(bool(rigid)),
                                              float(alpha), C.byref(h)))
         self.ctx, self.h, self.rigid = ctx, h, bool(rigid)
+        self.template_atoms = np.array([m.n for m in templates], np.int32)
         n_rep = C.c_int32(); n_at = C.c_int32()
         ctx.check(lib.gridff_replicas_info(h, C.byref(n_rep), C.byref(n_at), None))
         self.n_rep, self.n_atoms = n_rep.value, n_at.value
@@ -422,6 +425,16 @@ class Replicas:
         o = (C.c_double * 2)(*origin_xy); t = (C.c_double * 2)(*tile_xy)
         self.ctx.check(lib.gridff_random_poses(self.h, C.c_uint64(seed), o, t, float(z_lo), float(z_hi),
                                                float(z_floor)))
+
+    def template_factors(self, t=0) -> np.ndarray:
+        """(n_atoms, 3) grid factors (Q, P, L) of template t as the kernels
+        use them (gridff_template_factors)."""
+        n = int(self.template_atoms[t])
+        out = np.empty(3 * n, np.float32)
+        st = lib.gridff_template_factors(self.h, int(t), out.ctypes.data_as(C.c_void_p))
+        if st != OK:
+            raise GridffError(st, "gridff_template_factors")
+        return out.reshape(n, 3)
 
     def template_rotors(self, t=0) -> np.ndarray:
         """(n_rot, 4) reference quadruples (a, b, c, d) of template t's
@@ -493,6 +506,29 @@ def eval(ctx: Context, grid, reps: Replicas, flags=0, out=None):
                               E.ctypes.data_as(C.c_void_p), F.ctypes.data_as(C.c_void_p),
                               Ea.ctypes.data_as(C.c_void_p), S.ctypes.data_as(C.c_void_p)))
     return E, F.reshape(-1, 3), Ea, S
+
+
+def eval_points(ctx: Context, grid, xyz, qpl, out=None, flags=0):
+    """gridff_eval_points -> (E (n,), F (n, 3), status (n,)).  With `out`
+    = (E, F, status) device tensors and device-tensor inputs, nothing is
+    copied (status may be None)."""
+    if out is not None:
+        E, F, S = out
+        ctx.check(lib.gridff_eval_points(ctx.h, grid.h, int(E.numel()), C.c_void_p(xyz.data_ptr()),
+                                         C.c_void_p(qpl.data_ptr()), C.c_void_p(E.data_ptr()),
+                                         C.c_void_p(F.data_ptr()), C.c_void_p(S.data_ptr()) if S is not None else None,
+                                         flags | DEVICE_PTRS))
+        return out
+    x = np.ascontiguousarray(xyz, np.float32).reshape(-1, 3)
+    q = np.ascontiguousarray(qpl, np.float32).reshape(-1, 3)
+    n = len(x)
+    E = np.empty(n, np.float32)
+    F = np.empty((n, 3), np.float32)
+    S = np.empty(n, np.int32)
+    ctx.check(lib.gridff_eval_points(ctx.h, grid.h, n, x.ctypes.data_as(C.c_void_p), q.ctypes.data_as(C.c_void_p),
+                                     E.ctypes.data_as(C.c_void_p), F.ctypes.data_as(C.c_void_p),
+                                     S.ctypes.data_as(C.c_void_p), flags))
+    return E, F, S
 
 
 def fire_params(**kw) -> FireParams:

@@ -94,6 +94,42 @@ def test_eval_random_field_matches_fp32_oracle(G, ctx, shape, storage):
 
 
 @pytest.mark.parametrize("storage", [0, 1, 2])
+@pytest.mark.parametrize("shape", [(17, 13, 21), (9, 7, 5)])
+def test_eval_points_matches_oracle_and_replica_eval(G, ctx, shape, storage):
+    """gridff_eval_points: the grid alone at independent points (periodic
+    wraps, clamped z ends, below and above the grid, a ragged last round of
+    quads) against the FP32 oracle, and bit for bit equal to the per-atom
+    grid energies and forces of gridff_eval on the same points."""
+    h = (0.21, 0.17, 0.19)
+    origin = (0.3, -1.1, 2.0)
+    coefs = synth.random_coefficients(shape, 3, seed=23, scale=(0.8, 2.0, 1.0))
+    grid = G.grid_from_coefs(ctx, coefs, origin, h, G.CH_C | G.CH_P | G.CH_L, storage=storage)
+    n_at, n_rep = 70, 9
+    mol = _point_molecule(n_at)
+    g = synth.rng(24)
+    L = np.array(shape) * np.array(h)
+    pts = np.stack([g.uniform(-2 * L[0], 3 * L[0], n_at * n_rep), g.uniform(-L[1], 2 * L[1], n_at * n_rep),
+                    origin[2] + g.uniform(-0.3, L[2] + 0.2, n_at * n_rep)], 1).astype(np.float32)
+    reps = G.Replicas(ctx, [mol], [0] * n_rep)
+    reps.set_state(pts.ravel())
+    _, Fr, Ea, _ = G.eval(ctx, grid, reps, flags=G.NO_INTRA)
+    qpl = np.tile(reps.template_factors(0), (n_rep, 1))
+    n = len(pts) - 3                                    # not a multiple of the 8 points per warp round
+    E, F, S = G.eval_points(ctx, grid, pts[:n], qpl[:n])
+    assert np.array_equal(E, Ea[:n]) and np.array_equal(F, Fr.reshape(-1, 3)[:n])
+    cq = _check_storage(grid, coefs, storage, 4)
+    E32, F32, below = _oracle_grid(cq, ("C", "P", "L"), origin, h, pts[:n], np.tile(mol.q, n_rep)[:n],
+                                   np.tile(mol.R, n_rep)[:n], np.tile(mol.eps, n_rep)[:n], np.float32)
+    assert np.abs(F - F32).max() <= TOL_F * max(1.0, np.abs(F32).max())
+    assert np.abs(E - E32).max() <= TOL_E * max(1.0, np.abs(E32).max())
+    assert np.array_equal((S & G.REP_BELOW) != 0, below)
+    # empty input
+    E0, F0, S0 = G.eval_points(ctx, grid, np.zeros((0, 3), np.float32), np.zeros((0, 3), np.float32))
+    assert len(E0) == 0
+    reps.close()
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2])
 def test_eval_two_channel_grid(G, ctx, storage):
     shape, h, origin = (12, 10, 16), (0.25, 0.3, 0.2), (0.0, 0.0, 1.0)
     coefs = synth.random_coefficients(shape, 2, seed=15, scale=(1.0, 0.5))
