@@ -77,6 +77,29 @@ def test_ewald_madelung_constant():
     assert -phi[0] * (a / 2) == pytest.approx(M, abs=2e-6)
 
 
+def test_ewald_equals_direct_image_sums_of_a_neutral_dipole_free_cell():
+    """Bulk Ewald vs the direct Coulomb sum over expanding cubes of images:
+    for a neutral cell with no dipole and no second moment (rock salt on the
+    quarter positions) the cube sums converge to the Ewald potential itself,
+    faster than 1/N^3."""
+    a = 5.64
+    plus = np.array([[.25, .25, .25], [.75, .75, .25], [.75, .25, .75], [.25, .75, .75]])
+    minus = np.array([[.75, .75, .75], [.25, .25, .75], [.25, .75, .25], [.75, .25, .25]])
+    X = np.concatenate([plus, minus]) * a
+    q = np.array([1.0] * 4 + [-1.0] * 4)
+    pts = np.array([[0.03, 0.11, 0.07], [0.61, 0.12, 0.44], [0.37, 0.71, 0.93], [0.5, 0.5, 0.5]]) * a
+    beta, rc, kmax = substrate.ewald_params(1e-12, 8.0)
+    phi, _ = substrate.ewald_potential(pts, X, q, np.eye(3) * a, beta, rc, kmax, slab=False)
+    errs = []
+    for N in (6, 12):
+        r = np.arange(-N, N + 1)
+        n = np.stack(np.meshgrid(r, r, r, indexing="ij"), -1).reshape(-1, 3) * a
+        direct = np.array([(q[None, :] / np.linalg.norm(p[None, None, :] - X[None] - n[:, None, :], axis=2)).sum()
+                           for p in pts])
+        errs.append(np.abs(direct - phi).max())
+    assert errs[1] < 5e-7 and errs[1] < errs[0] / 8
+
+
 def test_ewald_matches_exact_slab_fourier_sum():
     """Above a neutral slab the EW3DC potential equals the exact 2D-periodic
     open-boundary potential (Sec. 4: vacuum padding + dipole correction)."""
