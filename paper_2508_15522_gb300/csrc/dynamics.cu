@@ -1874,13 +1874,22 @@ __device__ __forceinline__ void kick_rot(float p[4], const float q[4], const flo
   p[3] += s * (-q[2] * tb[0] + q[1] * tb[1] + q[0] * tb[2]);
 }
 
-__device__ __forceinline__ void free_rot(int k, float h, float Ik, float q[4], float p[4]) {
+// inv4I = 1 / (4 I_k).  Rotation angles of one step are small: below 0.05
+// rad the sine and cosine come from their Taylor series (truncation below
+// 2e-13, far under FP32 rounding), above from sincosf.
+__device__ __forceinline__ void free_rot(int k, float h, float inv4I, float q[4], float p[4]) {
   float Pq[4], Pp[4];
   perm(k, q, Pq);
   perm(k, p, Pp);
-  float zeta = h * (p[0] * Pq[0] + p[1] * Pq[1] + p[2] * Pq[2] + p[3] * Pq[3]) / (4.f * Ik);
+  const float zeta = h * (p[0] * Pq[0] + p[1] * Pq[1] + p[2] * Pq[2] + p[3] * Pq[3]) * inv4I;
   float sz, cz;
-  sincosf(zeta, &sz, &cz);
+  if (fabsf(zeta) < 0.05f) {
+    const float z2 = zeta * zeta;
+    sz = zeta * (1.f - z2 * (1.f / 6.f) * (1.f - z2 * (1.f / 20.f)));
+    cz = 1.f - z2 * 0.5f * (1.f - z2 * (1.f / 12.f) * (1.f - z2 * (1.f / 30.f)));
+  } else {
+    sincosf(zeta, &sz, &cz);
+  }
   for (int a = 0; a < 4; ++a) {
     q[a] = cz * q[a] + sz * Pq[a];
     p[a] = cz * p[a] + sz * Pp[a];
@@ -1909,6 +1918,7 @@ run_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, 
     const int t = rep_tmpl[r], n = tv.natoms[t], ab = tv.atom_off[t];
     const float4 rig = tv.rigid[t];
     const float I[3] = {rig.y, rig.z, rig.w};
+    const float i4I[3] = {0.25f / rig.y, 0.25f / rig.z, 0.25f / rig.w};
     float c[3], q[4], v[3], p[4];
     for (int a = 0; a < 3; ++a) {
       c[a] = pose[7 * (size_t)r + a];
@@ -1953,11 +1963,11 @@ run_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, 
       float tb[3] = {GRIDFF_ACC * tq[0], GRIDFF_ACC * tq[1], GRIDFF_ACC * tq[2]};
       kick_rot(p, q, tb, h);
       for (int a = 0; a < 3; ++a) c[a] += dt * v[a];
-      free_rot(3, h, I[2], q, p);
-      free_rot(2, h, I[1], q, p);
-      free_rot(1, dt, I[0], q, p);
-      free_rot(2, h, I[1], q, p);
-      free_rot(3, h, I[2], q, p);
+      free_rot(3, h, i4I[2], q, p);
+      free_rot(2, h, i4I[1], q, p);
+      free_rot(1, dt, i4I[0], q, p);
+      free_rot(2, h, i4I[1], q, p);
+      free_rot(3, h, i4I[2], q, p);
       quat_rot(q[0], q[1], q[2], q[3], Rm);
       rigid_forces(g, tv, ab, n, lane, c, Rm, Ft, tq, e, flags, sc);
       e = wsum(e);
@@ -2066,6 +2076,7 @@ run_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmp
       }
     }
     const float I[3] = {rig.y, rig.z, rig.w};
+    const float i4I[3] = {0.25f / I[0], 0.25f / I[1], 0.25f / I[2]};
     float4 bk[R], pk[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) {
@@ -2126,11 +2137,11 @@ run_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmp
         const float tb[3] = {GRIDFF_ACC * tq[0], GRIDFF_ACC * tq[1], GRIDFF_ACC * tq[2]};
         kick_rot(p, q, tb, h);
         for (int a = 0; a < 3; ++a) c[a] += dt * v[a];
-        free_rot(3, h, I[2], q, p);
-        free_rot(2, h, I[1], q, p);
-        free_rot(1, dt, I[0], q, p);
-        free_rot(2, h, I[1], q, p);
-        free_rot(3, h, I[2], q, p);
+        free_rot(3, h, i4I[2], q, p);
+        free_rot(2, h, i4I[1], q, p);
+        free_rot(1, dt, i4I[0], q, p);
+        free_rot(2, h, i4I[1], q, p);
+        free_rot(3, h, i4I[2], q, p);
       }
       quat_rot(q[0], q[1], q[2], q[3], Rm);
       int f2 = 0;
