@@ -303,6 +303,18 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
   return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
 
+// cos(n phi) and sin(n phi) from cos phi and sin phi by n rotations in the
+// complex plane (exact trigonometry, no angle): (c, s) <- (c, s) e^{i phi}.
+__device__ __forceinline__ void multiple_angle(float cphi, float sphi, int n, float& cn, float& sn) {
+  cn = 1.f;
+  sn = 0.f;
+  for (int k = 0; k < n; ++k) {
+    const float c2 = fmaf(cn, cphi, -sn * sphi);
+    sn = fmaf(sn, cphi, cn * sphi);
+    cn = c2;
+  }
+}
+
 // This lane's share (terms q, q+4, ... of each list; partners q, q+4, ...)
 // of the intramolecular force on template atom i, and of the energy counted
 // at i: bonded terms once (at their first atom), nonbonded pairs half at
@@ -350,9 +362,8 @@ __device__ void intra_quad(const TemplateView& tv, int ab, int n, int i, int q, 
     float iAB = rsqrtf(A2 * B2);
     float cphi = dot3(A, B) * iAB;
     float sphi = dot3(cross3(B, A), G) * iAB / Gn;
-    float phi = atan2f(sphi, cphi);
     float sn, cn;
-    sincosf(T.n * phi, &sn, &cn);
+    multiple_angle(cphi, sphi, T.n, cn, sn);
     float dEdphi = 0.5f * T.V * T.cn0 * T.n * sn;
     float FG = dot3(F, G) / (A2 * Gn), HG = dot3(H, G) / (B2 * Gn);
     float ca = -Gn / A2, cd = Gn / B2;
@@ -626,9 +637,8 @@ __device__ float intra_terms(const TemplateView& tv, int t, int lane, const floa
     const float iAB = rsqrtf(A2 * B2);
     const float cphi = dot3(A, B) * iAB;
     const float sphi = dot3(cross3(B, A), G) * iAB / Gn;
-    const float phi = atan2f(sphi, cphi);
     float sn, cn;
-    sincosf(T.n * phi, &sn, &cn);
+    multiple_angle(cphi, sphi, T.n, cn, sn);
     const float dEdphi = 0.5f * T.V * T.cn0 * T.n * sn;
     const float FG = dot3(F, G) / (A2 * Gn), HG = dot3(H, G) / (B2 * Gn);
     const float ca = -Gn / A2, cd = Gn / B2;
