@@ -669,10 +669,10 @@ gridff_status gridff_build_grid(gridff_ctx* ctx, const gridff_substrate* sub,
   cudaStream_t s = ctx->stream;
   size_t n_nodes = (size_t)g->dims[0] * g->dims[1] * g->dims[2];
   double* vals = nullptr;
-  if (df.alloc(&vals, n_nodes * g->n_ch * sizeof(double)) != cudaSuccess) {
+  const size_t vals_bytes = n_nodes * g->n_ch * sizeof(double);
+  if (df.alloc(&vals, vals_bytes) != cudaSuccess) {
     delete g;
-    return set_err(ctx, GRIDFF_ENOMEM, "cannot allocate %zu bytes of node values",
-                   n_nodes * g->n_ch * sizeof(double));
+    return set_err(ctx, GRIDFF_ENOMEM, "cannot allocate %zu bytes of node values", vals_bytes);
   }
   auto bail = [&](gridff_status st) {
     gridff_grid_destroy(g);
