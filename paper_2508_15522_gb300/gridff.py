@@ -451,9 +451,12 @@ class Replicas:
         (gridff_build_poses; flexible replicas through the pose builder)."""
         o = (C.c_double * 2)(*origin_xy) if origin_xy is not None else None
         t = (C.c_double * 2)(*tile_xy) if tile_xy is not None else None
-        if hasattr(poses, "data_ptr"):
-            self.ctx.check(lib.gridff_build_poses(self.h, C.c_void_p(poses.data_ptr()), o, t, DEVICE_PTRS))
+        if getattr(poses, "is_cuda", False):
+            self.ctx.check(lib.gridff_build_poses(self.h, C.c_void_p(poses.contiguous().data_ptr()), o, t,
+                                                  DEVICE_PTRS))
             return
+        if hasattr(poses, "numpy"):
+            poses = poses.numpy()
         p = np.ascontiguousarray(poses, np.float32).reshape(self.n_rep, MLP_OUT)
         self.ctx.check(lib.gridff_build_poses(self.h, p.ctypes.data_as(C.c_void_p), o, t, 0))
 
