@@ -264,18 +264,24 @@ def reduce_over_ranks(seconds, evals, dist=None, device=None):
     return float(t.item()), float(e.item())
 
 
-def nve_drift(G, ctx, grid, reps, mol, pose, n_steps=10_000, dt=1.0, seed=SEED):
-    """10k-step NVE (NO_SQUISH, 1 fs) of the relaxed replicas with 300 K
-    Maxwell-Boltzmann velocities; returns the energy drift statistics and
-    the NVE throughput (outside the timed region)."""
+def mb_velocities(mol, n, seed):
+    """(n, 6) rigid-body velocities (centre of mass, body angular) drawn
+    from the 300 K Maxwell-Boltzmann distribution (synthetic NVE input)."""
     kT, acc = 0.025852, 9.648533e-3
     M = float(mol.mass.sum())
     b = mol.xyz
     I = np.array([np.sum(mol.mass * (np.sum(b * b, 1) - b[:, k] ** 2)) for k in range(3)])
     g = np.random.Generator(np.random.PCG64(seed + 7))
+    return np.concatenate([g.standard_normal((n, 3)) * np.sqrt(kT * acc / M),
+                           g.standard_normal((n, 3)) * np.sqrt(kT * acc / I)], 1).astype(np.float32)
+
+
+def nve_drift(G, ctx, grid, reps, mol, pose, n_steps=10_000, dt=1.0, seed=SEED):
+    """10k-step NVE (NO_SQUISH, 1 fs) of the relaxed replicas with 300 K
+    Maxwell-Boltzmann velocities; returns the energy drift statistics and
+    the NVE throughput (outside the timed region)."""
     n = len(pose)
-    vel = np.concatenate([g.standard_normal((n, 3)) * np.sqrt(kT * acc / M),
-                          g.standard_normal((n, 3)) * np.sqrt(kT * acc / I)], 1).astype(np.float32)
+    vel = mb_velocities(mol, n, seed)
     x, _ = reps.get_state()
     reps.set_state(x, vel.ravel())
     t0 = time.perf_counter()
@@ -778,7 +784,9 @@ def profile_case(args):
     for 20 FIRE iterations; `langevin` runs 20 Langevin steps on them;
     `mlp` runs 20 training steps of the proposal network; `interp` evaluates
     the grid alone at 65536 x 38 uniform random points (gridff_eval_points,
-    the interpolation-only workload of the bench line).  Each runs its launch twice (the
+    the interpolation-only workload of the bench line); `nve` runs 200 rigid
+    NVE steps of the bench's 4096 replicas, relaxed and given 300 K
+    velocities as in the bench's NVE run.  Each runs its launch twice (the
     second is the one to capture with -s)."""
     import __graft_entry__ as ge
     ge.build()
@@ -811,6 +819,18 @@ def profile_case(args):
         for _ in range(2):
             S.train_on_device(net, np.zeros(S.N_DESC, np.float32), T, surf, 20, batch=256, K=8)
         print("mlp trained")
+    elif args.profile_case == "nve":
+        sub, box, mol, pose = workload()
+        grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing)
+        reps = G.Replicas(ctx, [mol], [0] * N_REP, rigid=True)
+        reps.set_state(pose.ravel())
+        G.relax(ctx, grid, reps, FIRE_ITERS, G.fire_params(f_conv=0.0))      # as the bench's NVE run
+        x, _ = reps.get_state()
+        vel = mb_velocities(mol, N_REP, SEED)
+        for _ in range(2):
+            reps.set_state(x, vel.ravel())
+            G.run(ctx, grid, reps, 200, dt=1.0)
+        print("nve kernel ms", ctx.last_kernel_ms())
     elif args.profile_case == "interp":
         import torch
         sub, box, _, _ = workload()
@@ -840,7 +860,7 @@ def main():
                     help="FIRE iterations per step (profiling runs use a short step)")
     ap.add_argument("--quick", action="store_true",
                     help="skip the e2e leg, the bandwidth probes and the CPU baseline (profiling runs)")
-    ap.add_argument("--profile-case", choices=["uneven", "langevin", "mlp", "interp"], default=None,
+    ap.add_argument("--profile-case", choices=["uneven", "langevin", "mlp", "interp", "nve"], default=None,
                     help="run one small kernel case for an ncu capture and exit (no JSON line)")
     args = ap.parse_args()
     if args.profile_case:
