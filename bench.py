@@ -346,6 +346,13 @@ def minima_comparison(G, ctx, grid, mol, sub):
     out["gain"] = out["mlp"]["minima_per_s"] / max(out["random"]["minima_per_s"], 1e-30)
     net.close()
     sp.close()
+    low = np.argsort(E, kind="stable")[:8]
+    pr = G.Replicas(ctx, [mol], [0] * len(low), rigid=True)
+    pr.set_state(np.ascontiguousarray(P[low], np.float32).ravel())
+    xl = pr.positions().reshape(len(low), mol.n, 3)
+    pr.close()
+    out["error_vs_fp64_pairwise"] = grid_error_vs_pairwise(
+        G, ctx, grid, sub, [(mol, v) for v in xl], "the 8 lowest converged minima of the training relaxations")
     return out
 
 
@@ -401,6 +408,10 @@ def flexible_minima_comparison(G, ctx, grid, sub):
     out["gain"] = out["mlp"]["minima_per_s"] / max(out["random"]["minima_per_s"], 1e-30)
     net.close()
     sp.close()
+    low = np.argsort(E, kind="stable")[:8]
+    out["error_vs_fp64_pairwise"] = grid_error_vs_pairwise(
+        G, ctx, grid, sub, [(mol, v) for v in X[low]],
+        "the 8 lowest converged minima of the training relaxations (grid term)")
     return out
 
 
@@ -467,6 +478,11 @@ def uneven_batch_comparison(G, ctx, grid, sub):
     measure("batched", batched)
     for g in graphs.values():
         g.close()
+    xr = reps.positions()
+    off = reps.atom_offset
+    out["error_vs_fp64_pairwise"] = grid_error_vs_pairwise(
+        G, ctx, grid, sub, [(mols[tof[r]], xr[off[r]:off[r + 1]]) for r in np.linspace(0, len(tof) - 1, 8).astype(int)],
+        "8 replicas spread over the batch after the batched minima run (grid term)")
     reps.set_launch_config(G.LaunchConfig(kernel=G.KERNEL_FLEX_QUAD, lanes_per_replica=32, warps_per_block=4,
                                           cache_slots=48, queue=0, l2_window=0))
     measure("static", lambda fconv: G.relax(ctx, grid, reps, 1000, G.fire_params(f_conv=fconv)))
@@ -581,6 +597,40 @@ def c2_accuracy(G, ctx, grid, sub, mol, pose, n_sample=8):
             "reference": "FP64 pairwise (Morse direct sums within 17 A + EW3DC Ewald)"}
 
 
+def grid_error_vs_pairwise(G, ctx, grid, sub, items, what):
+    """Error of the grid term at given molecule structures against the FP64
+    pairwise reference of the substrate: `items` is a list of (molecule,
+    positions (n, 3)); the GPU side is gridff_eval_points at those positions
+    with the molecule's (Q, P, L) factors, the reference the oracle's direct
+    Morse sums within 17 A plus the EW3DC Ewald potential.  Intramolecular
+    terms are not part of either side."""
+    from oracle import substrate as osub
+    factors = {}
+    x, qpl, q, R, eps, n_at = [], [], [], [], [], []
+    for mol, xyz in items:
+        if id(mol) not in factors:
+            one = G.Replicas(ctx, [mol], [0])
+            factors[id(mol)] = one.template_factors(0)
+            one.close()
+        x.append(np.asarray(xyz, np.float32).reshape(-1, 3))
+        qpl.append(factors[id(mol)])
+        q.append(mol.q); R.append(mol.R); eps.append(mol.eps); n_at.append(mol.n)
+    x = np.concatenate(x)
+    E, F, S = G.eval_points(ctx, grid, x, np.concatenate(qpl))
+    t0 = time.perf_counter()
+    Er, Fr = osub.pairwise_reference(x.astype(np.float64), np.concatenate(q), np.concatenate(R),
+                                     np.concatenate(eps), sub)
+    pair_s = time.perf_counter() - t0
+    cut = np.cumsum([0] + n_at)
+    dmol = [abs(float(E[a:b].astype(np.float64).sum() - Er[a:b].sum())) for a, b in zip(cut[:-1], cut[1:])]
+    return {"structures": what, "molecules": len(items), "atoms": int(len(x)),
+            "max_abs_dE_per_molecule_eV": max(dmol),
+            "max_abs_dE_per_atom_eV": float(np.abs(E - Er).max()),
+            "max_abs_dF_eV_per_A": float(np.abs(F - Fr).max()),
+            "points_flagged": int(np.count_nonzero(S)), "pairwise_s": pair_s,
+            "reference": "FP64 pairwise (Morse direct sums within 17 A + EW3DC Ewald)"}
+
+
 def interpolation_roofline(G, ctx, grid, box, torch, dev, stream, l2_peak):
     """Grid interpolation alone (gridff_eval_points: a quad of lanes per
     point, no stencil reuse) at uniform random points over the tile and the
@@ -639,8 +689,13 @@ def minima_hopping_curve(G, ctx):
     mh = S.MinimaHopping(ctx, grid, mol, x0, sub.tile)
     curve = [mh.hop() for _ in range(12)]
     out = {"replicas": 5000, "atoms": mol.n, "grid": list(grid.dims), "grid_build_s": build_s, "hops": len(curve),
-           "curve": [{"t_s": t, "unique_minima": u, "converged": c} for t, u, c in curve],
+           "curve": [{"t_s": t, "unique_minima": u, "accepted": c, "restarted": b}
+                     for (t, u, c), b in zip(curve, mh.below)],
            "lowest_eV": float(mh.db_E.min()) if len(mh.db_E) else None}
+    if len(mh.db_E):
+        low = np.argsort(mh.db_E, kind="stable")[:8]
+        out["error_vs_fp64_pairwise"] = grid_error_vs_pairwise(
+            G, ctx, grid, sub, [(mol, v) for v in mh.db_x[low]], "the 8 lowest unique minima found (grid term)")
     mh.close()
     grid.close()
     return out

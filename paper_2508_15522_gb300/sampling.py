@@ -15,8 +15,13 @@ Two ways to choose where FIRE relaxations start (rigid molecules:
   (``gridff_mlp_train_step``), sampled by ``gridff_mlp_propose``.
 
 Every batch then relaxes all replicas in one ``gridff_relax`` launch and
-reads back the final poses, energies and status words.  A relaxation is a
-*hit* when it converged and its energy is within ``tol`` (0.01 eV) of the
+reads back the final poses, energies and status words.  A relaxation counts
+as a minimum only when it converged with finite values and no atom of the
+final structure below the grid floor (`accepted`; for rigid batches, whose
+positions are not read back, no atom below the floor at any step): the grid
+defines no energy below its floor, where the kernels clamp to the bottom
+plane.  It is a
+*hit* when it is a minimum and its energy is within ``tol`` (0.01 eV) of the
 best-known minimum energy; hits are deduplicated with the RMSD filter of
 Sec. 7 (``gridff_rmsd_unique``, 0.1 A).  This module only orders the calls
 and moves their inputs and outputs; the arithmetic runs in the library.
@@ -37,11 +42,24 @@ HIDDEN = (256, 256, 256)
 
 @dataclass
 class Batch:
-    poses: np.ndarray        # (n, 7) final poses
+    poses: np.ndarray        # (n, 7) final poses (rigid) or (n, atoms, 3) positions (flexible)
     energy: np.ndarray       # (n,) eV
-    converged: np.ndarray    # (n,) bool
+    converged: np.ndarray    # (n,) bool: accepted minima (see `accepted`)
     wall_s: float            # proposal + relaxation + read-back, host clock
     kernel_ms: float         # the relaxation launch alone (CUDA events)
+
+
+def accepted(status: np.ndarray, x: np.ndarray | None = None, z_floor: float | None = None) -> np.ndarray:
+    """Relaxations that count as minima: converged with finite values and,
+    given the final structures x (n, atoms, 3) and the grid floor z_floor,
+    no atom of the final structure below the floor; without them, no atom
+    below the grid at any step of the relaxation (the status bit, which also
+    rejects an excursion that the relaxation came back from)."""
+    status = np.asarray(status)
+    ok = ((status & G.REP_CONVERGED) != 0) & ((status & G.REP_NONFINITE) == 0)
+    if x is None:
+        return ok & ((status & G.REP_BELOW) == 0)
+    return ok & (np.asarray(x)[..., 2] >= z_floor).all(axis=-1)
 
 
 @dataclass
@@ -74,7 +92,7 @@ class Sampler:
         fs = self.reps.fire_state()
         x, _ = self.reps.get_state()
         wall = time.perf_counter() - t0
-        conv = (fs["status"] & G.REP_CONVERGED) != 0
+        conv = accepted(fs["status"])
         return Batch(x.reshape(-1, 7), fs["energy"], conv, wall, self.ctx.last_kernel_ms())
 
     def random_batch(self, seed: int) -> Batch:
@@ -126,7 +144,7 @@ class FlexSampler:
         fs = self.reps.fire_state()
         x = self.reps.positions().reshape(self.n_rep, self.mol.n, 3)
         wall = time.perf_counter() - t0
-        conv = (fs["status"] & G.REP_CONVERGED) != 0
+        conv = accepted(fs["status"], x, self.grid.origin[2])
         return Batch(x, fs["energy"], conv, wall, self.ctx.last_kernel_ms())
 
     def random_batch(self, seed: int) -> Batch:
@@ -164,7 +182,7 @@ class FlexSampler:
 
 
 def hits(b: Batch, e_best: float, tol: float = 0.01) -> np.ndarray:
-    """Converged relaxations within tol of the best-known energy."""
+    """Accepted minima within tol of the best-known energy."""
     return b.converged & (b.energy <= e_best + tol)
 
 
@@ -232,18 +250,24 @@ class MinimaHopping:
     """Minima hopping of flexible replicas adsorbed on the substrate (Sec. 7):
     every hop thermalises all replicas by Langevin dynamics at T for
     `md_steps` steps (BAOAB, `gridff_langevin`), relaxes them by FIRE until
-    |F| < f_conv (0.1 meV/A in the paper), and compares every converged
+    |F| < f_conv (0.1 meV/A in the paper), and compares every accepted
     structure with all minima found so far by the RMSD criterion
     (`gridff_rmsd_unique_xyz`, 0.1 A), lowest energy first.  The next hop
-    starts from the relaxed structures.  `curve` records (seconds of
-    sampling, unique minima, converged relaxations) after each hop."""
+    starts from the relaxed structures; a replica whose relaxed structure
+    has an atom below the grid floor, or that went non-finite, starts it
+    from its initial structure instead (`restart`).  `curve` records
+    (seconds of sampling, unique minima, accepted relaxations) after each
+    hop, `below` the replicas restarted."""
 
     def __init__(self, ctx: G.Context, grid: G.Grid, mol, x0: np.ndarray, tile_xy, temperature=300.0,
-                 md_steps=1000, dt=1.0, gamma=0.01, f_conv=1e-4, relax_steps=5000, rmsd=0.1, seed=1):
+                 md_steps=1000, dt=1.0, gamma=0.01, f_conv=1e-4, relax_steps=5000, rmsd=0.1, seed=1,
+                 restart=True):
         self.ctx, self.grid, self.mol, self.tile = ctx, grid, mol, tuple(tile_xy)
         n_rep = len(x0)
+        self.x0 = np.array(x0, np.float32).reshape(n_rep, mol.n, 3)
+        self.restart = restart
         self.reps = G.Replicas(ctx, [mol], [0] * n_rep)
-        self.reps.set_state(np.ascontiguousarray(x0, np.float32).ravel())
+        self.reps.set_state(self.x0.ravel())
         self.T, self.md_steps, self.dt, self.gamma = temperature, md_steps, dt, gamma
         self.fire = G.fire_params(f_conv=f_conv)
         self.relax_steps, self.rmsd, self.seed = relax_steps, rmsd, seed
@@ -252,6 +276,7 @@ class MinimaHopping:
         self.db_E = np.zeros(0)
         self.elapsed = 0.0
         self.curve = []
+        self.below = []                  # replicas restarted, per hop
 
     def hop(self):
         t0 = time.perf_counter()
@@ -260,8 +285,10 @@ class MinimaHopping:
         self.step += self.md_steps
         G.relax(self.ctx, self.grid, self.reps, self.relax_steps, self.fire, check=False)
         fs = self.reps.fire_state()
-        conv = (fs["status"] & G.REP_CONVERGED) != 0
-        x = self.reps.positions().reshape(len(conv), self.mol.n, 3)
+        x = self.reps.positions().reshape(self.x0.shape)
+        conv = accepted(fs["status"], x, self.grid.origin[2])
+        lost = ((fs["status"] & G.REP_NONFINITE) != 0) | (x[..., 2] < self.grid.origin[2]).any(axis=-1)
+        self.below.append(int(np.count_nonzero(lost)))
         cand_x, cand_E = x[conv], fs["energy"][conv]
         order = np.argsort(cand_E, kind="stable")
         cand_x, cand_E = cand_x[order], cand_E[order]
@@ -270,6 +297,13 @@ class MinimaHopping:
         new = dup[len(self.db_x):] < 0
         self.db_x = np.concatenate([self.db_x, cand_x[new]])
         self.db_E = np.concatenate([self.db_E, cand_E[new]])
+        if self.restart and lost.any():
+            xs, vs = self.reps.get_state()
+            xs = xs.reshape(self.x0.shape)
+            vs = vs.reshape(self.x0.shape)
+            xs[lost] = self.x0[lost]
+            vs[lost] = 0.0
+            self.reps.set_state(xs.ravel(), vs.ravel())
         self.elapsed += time.perf_counter() - t0
         self.curve.append((self.elapsed, len(self.db_x), int(conv.sum())))
         return self.curve[-1]
