@@ -41,4 +41,3 @@ def test_oracle_is_not_imported_by_the_product():
             if f.endswith((".py", ".cu", ".h", ".cpp")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in re.findall(r"^\s*(?:from|import)\s+(\w+)", txt, flags=re.M), f
-
