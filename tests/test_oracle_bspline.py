@@ -113,6 +113,43 @@ def test_interpolation_error_within_classical_bound_for_exponential():
     assert (err <= bound).all()
 
 
+def test_clamped_z_end_closed_form_and_order():
+    """Reading of the z ends: coefficients beyond the first and last node
+    repeat the end coefficient.  Closed form at the floor node (t = 0, B
+    weights 1/6, 4/6, 1/6 and slope weights -1/2, 0, 1/2 per h): value
+    (5 b_0 + b_1) / 6 and z-slope (b_1 - b_0) / (2 h).  Consequence for a
+    smooth field: fourth order in the interior, but in the first cell above
+    the floor the value is first order and the slope error does not shrink
+    with h (about 40 % of the slope of exp(-3 z) at the floor)."""
+    g = np.random.default_rng(2)
+    h = 0.1
+    b = g.standard_normal((1, 4, 4, 12))
+    f, grad, below = bspline.eval_grid(b, (0, 0, 0), (1.0, 1.0, h), np.array([[1.0, 2.0, 0.0]]))
+    # at x, y nodes the x and y weights are (1/6, 4/6, 1/6) too
+    col = lambda k: (b[0, 0:3, 1:4, k] * np.outer([1, 4, 1], [1, 4, 1]) / 36).sum()
+    assert not below[0]
+    assert f[0, 0] == pytest.approx((5 * col(0) + col(1)) / 6, abs=1e-13)
+    assert grad[0, 0, 2] == pytest.approx((col(1) - col(0)) / (2 * h), abs=1e-12)
+
+    def errors(h):
+        nz = int(round(4.0 / h)) + 1
+        v = np.broadcast_to(np.exp(-3.0 * np.arange(nz) * h), (1, 4, 4, nz)).copy()
+        c = bspline.fit_exact(v)
+        out = []
+        for lo, hi in ((0.0, h), (1.5, 2.5)):
+            zq = np.linspace(lo, hi, 201)
+            pts = np.stack([np.full_like(zq, 0.3), np.full_like(zq, 0.7), zq], 1)
+            fv, gv, _ = bspline.eval_grid(c, (0, 0, 0), (1.0, 1.0, h), pts)
+            out.append((np.abs(fv[:, 0] - np.exp(-3 * zq)).max(), np.abs(gv[:, 0, 2] + 3 * np.exp(-3 * zq)).max()))
+        return out
+
+    (fe1, fs1), (ie1, _) = errors(0.1)
+    (fe2, fs2), (ie2, _) = errors(0.05)
+    assert 1.7 < fe1 / fe2 < 2.5               # first cell: O(h) in the value
+    assert min(fs1, fs2) > 0.3 * 3.0           # ... and no convergence of the slope
+    assert 12.0 < ie1 / ie2 < 20.0             # interior: O(h^4)
+
+
 def test_gradient_matches_finite_difference():
     g = synth.rng(21)
     b = g.standard_normal((3, 6, 5, 9))
