@@ -337,7 +337,11 @@ gridff_status gridff_build_poses(gridff_replicas* R, const float* poses, const d
   void* tmp = nullptr;
   if (!(flags & GRIDFF_DEVICE_PTRS)) {
     GRIDFF_CUDA(ctx, cudaMallocAsync(&tmp, bytes, s));
-    GRIDFF_CUDA(ctx, cudaMemcpyAsync(tmp, poses, bytes, cudaMemcpyHostToDevice, s));
+    const cudaError_t e = cudaMemcpyAsync(tmp, poses, bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+      cudaFreeAsync(tmp, s);
+      return set_err(ctx, GRIDFF_ECUDA, "pose upload: %s", cudaGetErrorString(e));
+    }
     d = (const float*)tmp;
   }
   gridff_status st = enqueue_build_poses(R, d, kPoseLen, origin_xy, tile_xy);

@@ -500,11 +500,13 @@ gridff_status gridff_get_positions(gridff_replicas* R, float* x, int flags) {
   }
   rigid_positions_kernel<<<R->n_rep, 64, 0, ctx->stream>>>(R->tv, R->rep_tmpl, R->rep_off, R->x,
                                                            R->n_rep, dst);
-  GRIDFF_CUDA(ctx, cudaGetLastError());
+  cudaError_t e = cudaGetLastError();
   if (tmp) {
-    GRIDFF_CUDA(ctx, cudaMemcpyAsync(x, tmp, bytes, cudaMemcpyDeviceToHost, ctx->stream));
-    GRIDFF_CUDA(ctx, cudaFreeAsync(tmp, ctx->stream));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(x, tmp, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    const cudaError_t ef = cudaFreeAsync(tmp, ctx->stream);
+    if (e == cudaSuccess) e = ef;
   }
+  if (e != cudaSuccess) return set_err(ctx, GRIDFF_ECUDA, "positions: %s", cudaGetErrorString(e));
   return finish(ctx, flags);
 }
 
