@@ -1,0 +1,52 @@
+"""Host bookkeeping of bench.py's error report against the FP64 pairwise
+reference (`grid_error_vs_pairwise`), with the library calls faked: the fake
+returns the oracle's own values, shifted on one molecule, so the report's
+per-molecule, per-atom and force maxima are known in closed form."""
+import types
+
+import numpy as np
+
+import bench
+from oracle import substrate as osub
+from paper_2508_15522_gb300 import synth
+
+
+def test_grid_error_report_bookkeeping():
+    sub = synth.rocksalt_slab(a=5.64, ncell=2, layers=2, charge=0.7)
+    m1, m2 = synth.chain_molecule(), synth.random_flexible_molecule(12, 2, 3)
+    items = [(m1, m1.xyz + [0.0, 0.0, sub.z_top + 3.0]), (m2, m2.xyz + [1.0, 1.0, sub.z_top + 4.0]),
+             (m1, m1.xyz + [2.0, 0.0, sub.z_top + 3.5])]
+    x = np.concatenate([v for _, v in items]).astype(np.float32)
+    mols = [m for m, _ in items]
+    Er, Fr = osub.pairwise_reference(x.astype(np.float64), np.concatenate([m.q for m in mols]),
+                                     np.concatenate([m.R for m in mols]), np.concatenate([m.eps for m in mols]), sub)
+    lo, hi = m1.n, m1.n + m2.n                 # atoms of the second molecule
+    dE, dF = 1e-3, 2e-3
+
+    class FakeReps:
+        def __init__(self, ctx, mols, tof):
+            self.n = mols[0].n
+
+        def template_factors(self, t):
+            return np.zeros((self.n, 3), np.float32)
+
+        def close(self):
+            pass
+
+    def eval_points(ctx, grid, pts, qpl):
+        assert pts.shape == qpl.shape == (len(x), 3)
+        assert np.array_equal(pts, x)
+        E = Er.copy()
+        F = Fr.copy()
+        E[lo:hi] += dE
+        F[lo, 1] -= dF
+        S = np.zeros(len(x), np.int32)
+        S[-1] = 2
+        return E, F, S
+
+    G = types.SimpleNamespace(Replicas=FakeReps, eval_points=eval_points)
+    r = bench.grid_error_vs_pairwise(G, None, None, sub, items, "three molecules")
+    assert r["molecules"] == 3 and r["atoms"] == len(x) and r["points_flagged"] == 1
+    assert abs(r["max_abs_dE_per_molecule_eV"] - m2.n * dE) < 1e-12
+    assert abs(r["max_abs_dE_per_atom_eV"] - dE) < 1e-15
+    assert abs(r["max_abs_dF_eV_per_A"] - dF) < 1e-15
