@@ -676,7 +676,9 @@ def minima_hopping_curve(G, ctx):
     over the 22.56 x 22.56 A defect period, 0.1 A): 5000 replicas, 12 hops
     of 1000 Langevin steps at 300 K (dt 1 fs, gamma 0.01/fs), FIRE to
     1e-4 eV/A (at most 5000 iterations) and the RMSD-0.1 A filter against
-    every minimum found so far.  Returns the unique-minima-vs-time curve."""
+    every minimum found so far; relaxed structures with an atom below the
+    grid floor are no minima and restart from their initial structures.
+    Returns the unique-minima-vs-time curve."""
     from paper_2508_15522_gb300 import sampling as S
     from paper_2508_15522_gb300 import synth
     sub = synth.with_top_vacancy(synth.rocksalt_slab(a=5.64, ncell=4, layers=3, charge=0.7))
