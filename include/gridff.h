@@ -68,9 +68,13 @@ typedef enum {
                              concerned keep the state of that first part */
 } gridff_status;
 
-/* per-replica status bits (status_out arrays, gridff_get_fire_state) */
+/* per-replica status bits (status_out arrays, gridff_get_fire_state).  A
+ * call ORs in what it meets over all its steps; gridff_relax starts from
+ * zero unless GRIDFF_CONTINUE, the MD calls may carry BELOW and NONFINITE
+ * over from earlier calls */
 #define GRIDFF_REP_CONVERGED 1   /* FIRE force norm fell below f_conv */
-#define GRIDFF_REP_BELOW 2       /* an atom was below the grid (clamped to its bottom) */
+#define GRIDFF_REP_BELOW 2       /* an atom was below the grid at some evaluation
+                                    (evaluated on the grid's bottom plane) */
 #define GRIDFF_REP_NONFINITE 4   /* a force or position was NaN/Inf: replica frozen */
 #define GRIDFF_REP_ABORTED 8     /* stopped by the abort flag before finishing */
 #define GRIDFF_REP_STEPLIMIT 16  /* stopped by the clock budget before finishing */
