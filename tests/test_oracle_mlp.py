@@ -76,6 +76,18 @@ def test_adam_first_step_is_signed_learning_rate():
     assert np.allclose(p[0], [1.0 - 0.01, -2.0 + 0.01, 0.5 - 0.01], atol=1e-6)
 
 
+def test_adam_constant_gradient_moves_by_the_learning_rate_every_step():
+    # with a constant gradient the bias-corrected moments are exactly g and
+    # g^2 at every step t, so each step moves lr * g / (|g| + eps)
+    p = [np.array([1.0, -2.0, 0.5, 3.0])]
+    g = np.array([0.3, -4.0, 1e-3, -1e-6])
+    state = {}
+    for t in range(1, 8):
+        mlp.adam(p, [g], state, lr=0.01, t=t)
+    want = np.array([1.0, -2.0, 0.5, 3.0]) - 7 * 0.01 * g / (np.abs(g) + 1e-8)
+    assert np.abs(p[0] - want).max() < 1e-12
+
+
 def test_wta_gradient_only_on_the_winner():
     T = np.zeros((2, 19)); T[:, 3] = 1.0
     out = np.zeros((6, 19)); out[:, 3] = 1.0
