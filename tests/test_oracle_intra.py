@@ -41,6 +41,22 @@ def test_torsion_energy_special_angles():
         assert E[0] == pytest.approx(want, abs=1e-12)
 
 
+def test_bond_and_angle_energy_closed_forms():
+    """k_b (r - r0)^2 per bond and k_theta (cos theta - cos theta0)^2 per
+    angle, on a three-atom molecule with chosen lengths and angle."""
+    th, th0 = math.radians(100.0), math.radians(120.0)
+    x = np.array([[1.2, 0.0, 0.0], [0.0, 0.0, 0.0], [0.9 * math.cos(th), 0.9 * math.sin(th), 0.0]])
+    m = synth.Molecule(["C", "C", "O"], x.copy(), np.zeros(3), np.full(3, 1.9), np.full(3, 0.07), np.full(3, 12.0))
+    m.bonds = np.array([[0, 1], [1, 2]], np.int32)
+    m.bond_k = np.array([3.0, 5.0]); m.bond_r0 = np.array([1.0, 1.0])
+    m.angles = np.array([[0, 1, 2]], np.int32)
+    m.angle_k = np.array([0.7]); m.angle_cos0 = np.array([math.cos(th0)])
+    Eb, _ = intra.energy_forces(x[None], m, terms=("bond",))
+    assert Eb[0] == pytest.approx(3.0 * 0.2 ** 2 + 5.0 * 0.1 ** 2, abs=1e-12)
+    Ea, _ = intra.energy_forces(x[None], m, terms=("angle",))
+    assert Ea[0] == pytest.approx(0.7 * (math.cos(th) - math.cos(th0)) ** 2, abs=1e-12)
+
+
 def test_reference_geometry_is_bonded_minimum():
     mol = synth.chain_molecule()
     E, F = intra.energy_forces(mol.xyz[None], mol, terms=("bond", "angle"))
