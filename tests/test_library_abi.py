@@ -1,5 +1,6 @@
 """CPU-only checks of the C-ABI library: it builds, loads, exports every
-symbol that include/gridff.h declares, and rejects use without a GPU."""
+symbol that include/gridff.h declares with the signature the binding gives
+it, and rejects use without a GPU."""
 import os
 import re
 
@@ -41,3 +42,50 @@ def test_oracle_is_not_imported_by_the_product():
             if f.endswith((".py", ".cu", ".h", ".cpp")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in re.findall(r"^\s*(?:from|import)\s+(\w+)", txt, flags=re.M), f
+
+
+def _prototypes():
+    txt = open(os.path.join(ROOT, "include", "gridff.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    txt = re.sub(r"//[^\n]*", "", txt)
+    out = {}
+    for ret, name, params in re.findall(r"([A-Za-z_][\w \t\*]*?)\s*\b(gridff_\w+)\s*\(([^;{]*?)\)\s*;", txt,
+                                        flags=re.S):
+        ps = [p.strip() for p in params.split(",")] if params.strip() not in ("", "void") else []
+        out[name] = (" ".join(ret.split()), ps)
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    """Every ctypes signature of the binding has the header's argument count,
+    a pointer where the header has one, the header's scalar width elsewhere,
+    and the header's return type (a mismatch would corrupt a call at run
+    time, which only a GPU run would otherwise show)."""
+    import ctypes as C
+    import __graft_entry__ as g
+    g.build()
+    from paper_2508_15522_gb300 import gridff
+    protos = _prototypes()
+    assert set(protos) == set(_declared())
+    scalar = {"int": C.c_int, "int32_t": C.c_int32, "int64_t": C.c_int64, "uint64_t": C.c_uint64,
+              "size_t": C.c_size_t, "double": C.c_double, "float": C.c_float}
+    ret_of = {"gridff_status": C.c_int32, "void": None, "double": C.c_double, "int64_t": C.c_int64,
+              "const char*": C.c_char_p, "void*": C.c_void_p}
+    bad = []
+    for name, (ret, params) in protos.items():
+        f = getattr(gridff.lib, name)
+        if ret.replace(" *", "*") not in ret_of or f.restype is not ret_of[ret.replace(" *", "*")]:
+            bad.append((name, "return", ret, f.restype))
+        if len(params) != len(f.argtypes):
+            bad.append((name, "count", len(params), len(f.argtypes)))
+            continue
+        for p, a in zip(params, f.argtypes):
+            if "*" in p or "[" in p:
+                ok = a in (C.c_void_p, C.c_char_p) or issubclass(a, C._Pointer)
+            else:
+                t = re.sub(r"\bconst\b", "", p).split()[0]
+                ok = t in scalar and C.sizeof(a) == C.sizeof(scalar[t]) and \
+                    issubclass(a, C._SimpleCData) and a._type_ == scalar[t]._type_
+            if not ok:
+                bad.append((name, p, a))
+    assert not bad, bad
