@@ -89,3 +89,40 @@ def test_binding_signatures_match_the_header():
             if not ok:
                 bad.append((name, p, a))
     assert not bad, bad
+
+
+STRUCTS = {"Substrate": "gridff_substrate", "GridOpts": "gridff_grid_opts", "Molecule": "gridff_molecule",
+           "FireParams": "gridff_fire_params", "RelaxResult": "gridff_relax_result", "MDParams": "gridff_md_params",
+           "LangevinParams": "gridff_langevin_params", "LaunchConfig": "gridff_launch_config",
+           "TuneTrial": "gridff_tune_trial", "TrainParams": "gridff_train_params"}
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """The ctypes mirrors of the header's parameter structs have the C
+    compiler's size and field offsets (a C program built from the header
+    prints them)."""
+    import ctypes as C
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2508_15522_gb300 import gridff
+    lines = ['#include <stdio.h>', '#include "gridff.h"', "int main(void) {"]
+    want = {}
+    for py, cname in STRUCTS.items():
+        cls = getattr(gridff, py)
+        want[cname] = C.sizeof(cls)
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for f in cls._fields_:
+            want[f"{cname}.{f[0]}"] = getattr(cls, f[0]).offset
+            lines.append(f'  printf("{cname}.{f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.splitlines())
+    assert {k: int(v) for k, v in got.items()} == want
