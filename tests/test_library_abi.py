@@ -126,3 +126,26 @@ def test_binding_structs_match_the_header_layout(tmp_path):
     got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
                                                        text=True).stdout.splitlines())
     assert {k: int(v) for k, v in got.items()} == want
+
+
+def test_parameter_defaults_match_the_oracle_and_the_header():
+    """FIRE defaults of the library (Bitzek et al. 2006 constants, the
+    displacement cap and the convergence threshold) equal the oracle's,
+    stated independently; grid defaults are those the header documents
+    (alpha 1.5 1/A and the 17 A Morse cutoff of Sec. 6)."""
+    import ctypes as C
+    import dataclasses
+    import __graft_entry__ as g
+    g.build()
+    from oracle import dynamics as odyn
+    from paper_2508_15522_gb300 import gridff
+    p = gridff.FireParams()
+    gridff.lib.gridff_fire_params_default(C.byref(p))
+    for f in dataclasses.fields(odyn.FireParams):
+        assert getattr(p, f.name) == pytest.approx(getattr(odyn.FireParams(), f.name), rel=1e-7), f.name
+    assert p.clock_budget_s == 0.0
+    o = gridff.GridOpts()
+    gridff.lib.gridff_grid_opts_default(C.byref(o))
+    assert (o.alpha, o.rcut, o.ewald_tol, o.ewald_rcut) == (1.5, 17.0, 1e-10, 12.0)
+    assert o.channels == gridff.CH_C | gridff.CH_P | gridff.CH_L and o.storage == gridff.STORE_F32
+    assert o.keep_f64 == 0 and o.spacing == 0.0 and list(o.origin) == [0.0] * 3 and list(o.length) == [0.0] * 3
