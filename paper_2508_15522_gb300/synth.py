@@ -378,27 +378,28 @@ def random_flexible_molecule(n_atoms: int, n_torsions: int, seed: int) -> Molecu
     elements = list(g.choice(["C", "C", "C", "O"], size=n_heavy))
     parent = [-1] + [int(g.integers(max(0, k - 2), k)) for k in range(1, n_heavy)]
     pos = np.zeros((n_atoms, 3))
-    for k in range(1, n_heavy):
-        p = pos[parent[k]]
-        others = np.delete(pos[:k], parent[k], axis=0)
+
+    def place(anchor, others, length, clearance):
+        # up to 200 random directions: the first that keeps `clearance` from
+        # every other atom, else the one farthest from its nearest atom
+        best, best_d = None, -1.0
         for _ in range(200):
             d = g.normal(size=3)
             d /= np.linalg.norm(d)
-            cand = p + 1.50 * d
-            if np.all(np.linalg.norm(others - cand, axis=1) > 2.2):
-                break
-        pos[k] = cand
+            cand = anchor + length * d
+            near = np.linalg.norm(others - cand, axis=1).min() if len(others) else np.inf
+            if near > clearance:
+                return cand
+            if near > best_d:
+                best, best_d = cand, near
+        return best
+
+    for k in range(1, n_heavy):
+        pos[k] = place(pos[parent[k]], np.delete(pos[:k], parent[k], axis=0), 1.50, 2.2)
     bonds = [(parent[k], k) for k in range(1, n_heavy)]
     for h in range(n_h):
         host = int(g.integers(0, n_heavy))
-        others = np.delete(pos[:n_heavy + h], host, axis=0)
-        for _ in range(200):
-            d = g.normal(size=3)
-            d /= np.linalg.norm(d)
-            cand = pos[host] + 1.09 * d
-            if np.all(np.linalg.norm(others - cand, axis=1) > 1.6):
-                break
-        pos[n_heavy + h] = cand
+        pos[n_heavy + h] = place(pos[host], np.delete(pos[:n_heavy + h], host, axis=0), 1.09, 1.6)
         elements.append("H")
         bonds.append((host, n_heavy + h))
     xyz = pos.copy()
