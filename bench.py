@@ -308,19 +308,20 @@ def minima_comparison(G, ctx, grid, mol, sub):
     a, n_rep = 5.64, 16384
     surf = S.Surface((0.0, 0.0), (a, a), sub.z_top + 3.0, sub.z_top + 5.0, sub.z_top + 2.0)
     sp = S.Sampler(ctx, grid, mol, surf, n_rep=n_rep, nsteps=FIRE_ITERS)
-    E, P, C = [], [], []
+    E, P, T, C = [], [], [], []
     t0 = time.perf_counter()
     for k in range(64):
         b = sp.random_batch(10_000 + k)
         keep = b.converged
-        E.append(b.energy[keep]); P.append(b.poses[keep]); C.append(int(keep.sum()))
+        E.append(b.energy[keep]); P.append(b.poses[keep]); T.append(sp.targets()[keep]); C.append(int(keep.sum()))
     gen_s = time.perf_counter() - t0
     E = np.concatenate(E)
     P = np.concatenate(P)
+    T = np.concatenate(T)
     e_best = float(E.min())
     h = E <= e_best + 0.01
     best_set = len(sp.unique(P[h][:20000], E[h][:20000]))
-    T = S.pose_targets(P[h], surf)
+    T = T[h]
     net = S.new_network(ctx, T, seed=1)
     t0 = time.perf_counter()
     losses = S.train_on_device(net, sp.desc, T, surf, 3000, batch=256, K=8, lr=1e-3, seed=7)
@@ -632,11 +633,14 @@ def grid_error_vs_pairwise(G, ctx, grid, sub, items, what):
 
 
 def interpolation_roofline(G, ctx, grid, box, torch, dev, stream, l2_peak):
-    """Grid interpolation alone (gridff_eval_points: a quad of lanes per
-    point, no stencil reuse) at uniform random points over the tile and the
-    z band [z0 + 2, z0 + 8] A: 65536 x 38 = 2.49 M points per launch with
-    the grid factors of a 38-atom C/H/O set, 20 launches back to back on the
-    stream (the grid stays L2-resident)."""
+    """Grid interpolation alone (gridff_eval_points, no stencil reuse) at
+    uniform random points over the tile and the z band [z0 + 2, z0 + 8] A:
+    65536 x 38 = 2.49 M points per call with the grid factors of a 38-atom
+    C/H/O set, 20 calls back to back on the stream (the grid stays
+    L2-resident).  Two layouts: binned (the points put in cell order on the
+    device by a counting sort, then one lane per point; the sort is inside
+    the timed region) and direct (a quad of lanes per point in input
+    order)."""
     from paper_2508_15522_gb300 import synth
     n_rep, n_at = 65536, 38
     g = synth.rng(3003)
@@ -652,22 +656,30 @@ def interpolation_roofline(G, ctx, grid, box, torch, dev, stream, l2_peak):
     Q = torch.from_numpy(qpl.ravel()).to(dev)
     E = torch.empty(n, dtype=torch.float32, device=dev)
     F = torch.empty(3 * n, dtype=torch.float32, device=dev)
-    for _ in range(3):
-        G.eval_points(ctx, grid, X, Q, out=(E, F, None), flags=G.ASYNC)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize(dev)
-    e0.record(stream)
-    iters = 20
-    for _ in range(iters):
-        G.eval_points(ctx, grid, X, Q, out=(E, F, None), flags=G.ASYNC)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1) / iters
-    achieved = BYTES_PER_EVAL * n / (ms * 1e-3) / 1e9
-    return {"kernel": "eval_points_kernel (quad gather, no stencil reuse)", "atom_evals_per_s": n / (ms * 1e-3),
-            "ms_per_launch": ms, "points_per_launch": n, "points": "uniform over the tile, z0 + [2, 8] A",
-            "roofline": {"bound": "l2", "achieved": achieved, "peak": l2_peak, "unit": "GB/s",
-                         "frac": achieved / l2_peak if l2_peak else None}}
+    out = {}
+    for name, flags in (("binned", G.POINTS_BINNED), ("direct", 0)):
+        for _ in range(3):
+            G.eval_points(ctx, grid, X, Q, out=(E, F, None), flags=G.ASYNC | flags)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        iters = 20
+        for _ in range(iters):
+            G.eval_points(ctx, grid, X, Q, out=(E, F, None), flags=G.ASYNC | flags)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / iters
+        achieved = BYTES_PER_EVAL * n / (ms * 1e-3) / 1e9
+        out[name] = {"atom_evals_per_s": n / (ms * 1e-3), "ms_per_call": ms,
+                     "roofline": {"bound": "l2", "achieved": achieved, "peak": l2_peak, "unit": "GB/s",
+                                  "frac": achieved / l2_peak if l2_peak else None}}
+    out["binned"]["kernels"] = ("bin_count_kernel, scan_tiles/scan_top/scan_apply_kernel, bin_scatter_kernel, "
+                                "eval_sorted_kernel (lane per point); the sort is inside the timed region")
+    out["direct"]["kernels"] = "eval_points_kernel (quad of lanes per point, input order)"
+    return {"kernel": "gridff_eval_points, binned layout (counting sort by cell + lane per point)",
+            "atom_evals_per_s": out["binned"]["atom_evals_per_s"], "ms_per_call": out["binned"]["ms_per_call"],
+            "points_per_call": n, "points": "uniform over the tile, z0 + [2, 8] A",
+            "roofline": out["binned"]["roofline"], "layouts": out}
 
 
 def minima_hopping_curve(G, ctx):
@@ -841,7 +853,8 @@ def profile_case(args):
     for 20 FIRE iterations; `langevin` runs 20 Langevin steps on them;
     `mlp` runs 20 training steps of the proposal network; `interp` evaluates
     the grid alone at 65536 x 38 uniform random points (gridff_eval_points,
-    the interpolation-only workload of the bench line); `nve` runs 200 rigid
+    the interpolation-only workload of the bench line), twice in the direct
+    layout, then twice binned; `nve` runs 200 rigid
     NVE steps of the bench's 4096 replicas, relaxed and given 300 K
     velocities as in the bench's NVE run.  Each runs its launch twice (the
     second is the one to capture with -s)."""
@@ -902,9 +915,9 @@ def profile_case(args):
         Q = torch.from_numpy(qpl.ravel()).to(dev)
         E = torch.empty(n, dtype=torch.float32, device=dev)
         F = torch.empty(3 * n, dtype=torch.float32, device=dev)
-        for _ in range(2):
-            G.eval_points(ctx, grid, X, Q, out=(E, F, None))
-        print("interp evaluated")
+        for flags in (0, 0, G.POINTS_BINNED, G.POINTS_BINNED):
+            G.eval_points(ctx, grid, X, Q, out=(E, F, None), flags=flags)
+        print("interp evaluated (direct and binned)")
 
 
 def main():

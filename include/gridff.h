@@ -85,6 +85,7 @@ typedef enum {
 #define GRIDFF_CONTINUE 4        /* relax: keep FIRE scalars and status from the last call */
 #define GRIDFF_NO_GRID 8         /* eval/relax/run: skip the grid term */
 #define GRIDFF_NO_INTRA 16       /* eval/relax/run: skip the intramolecular terms */
+#define GRIDFF_POINTS_BINNED 32  /* eval_points: put the points in cell order on the device first */
 #define GRIDFF_TEST_NO_HANDOFF 256  /* relax (rigid sub-warp layout), test hook of the bounded wait:
                                        the first parts of split relaxations publish no hand-off,
                                        so their second parts give up after about a second and the
@@ -197,8 +198,9 @@ gridff_status gridff_grid_from_coefs(gridff_ctx* ctx, const double origin[3],
  * stream capture.  All calls share the array and it keeps the last call's
  * tables (each call rewrites them before use): calls that overlap on the
  * GPU (different streams or contexts on one device) race.
- * Errors: EINVAL (null pointer, n_channels < 1, or a dimension outside
- * 4..4096, with a message naming it), ECUDA. */
+ * Errors: EINVAL (null pointer, n_channels < 1, a dimension outside
+ * 4..4096, a pointer that is not memory of the context's device, or values
+ * and coefs that overlap without being equal; the message names it), ECUDA. */
 gridff_status gridff_fit_coefs_noalloc(gridff_ctx* ctx, const double* values, double* coefs,
                                        const int32_t dims[3], int32_t n_channels, int flags);
 
@@ -282,6 +284,21 @@ gridff_status gridff_get_fire_state(gridff_replicas* reps, float* dt, float* alp
                                     int32_t* nplus, int32_t* status, int32_t* steps,
                                     double* energy, int flags);
 
+/* Final evaluation of each replica in the last gridff_relax call: the state
+ * at which the relaxation last evaluated the forces without moving on
+ * afterwards (its last iteration, convergence, or a non-finite value), and
+ * the forces there, i.e. the forces that produced gridff_get_fire_state's
+ * energy (Sec. 6: FIRE reads these forces; Sec. 7: force threshold).
+ * Rigid: x [n_rep*7] pose (centre, quaternion), f [n_rep*6] total force
+ * (lab frame, eV/A) and torque about the centre of mass (body frame,
+ * eV).  Flexible: x [n_atoms_total*3] positions, f [n_atoms_total*3] forces
+ * (grid + intramolecular).  Entries of replicas that the last call stopped
+ * by the abort flag or the clock budget, or that it did not evaluate, keep
+ * their earlier record; never-recorded entries are NaN.  Written once per
+ * replica and call (not per step).  Either pointer may be NULL; host arrays
+ * unless GRIDFF_DEVICE_PTRS.  Errors: EINVAL, ECUDA. */
+gridff_status gridff_get_last_eval(gridff_replicas* reps, float* x, float* f, int flags);
+
 /* ------------------------------------------------------------- evaluation */
 
 /* Energies and forces at the current state (Sec. 3, Sec. 5):
@@ -325,10 +342,20 @@ typedef struct {
  * (charge and the Morse factors of gridff_template_factors) gets
  * E[i] = Q V^C + P V^P + L V^L (eV) and F[3i..3i+2] = -grad E (eV/A);
  * status[i] (may be NULL): GRIDFF_REP_BELOW below the grid (clamped to its
- * bottom cell), GRIDFF_REP_NONFINITE; above the grid E = F = 0.  One
- * evaluation per point, no reuse between points (a quad of lanes per point).
- * flags: GRIDFF_DEVICE_PTRS, GRIDFF_ASYNC.  The kernel time is kept for
- * gridff_last_kernel_ms (synchronous calls).  Errors: EINVAL, ECUDA. */
+ * bottom cell), GRIDFF_REP_NONFINITE for a non-finite position (E = F = 0
+ * then) or result; above the grid E = F = 0.  One
+ * evaluation per point, no reuse between points.  Default layout: a quad of
+ * lanes per point, points in input order.  GRIDFF_POINTS_BINNED: the points
+ * are first put in the order of their grid cell by a counting sort on the
+ * device (bins of 1 x 1 x 4 cells, z fastest, as the coefficient records lie
+ * in memory), then evaluated one lane per point in that order, so that
+ * neighbouring lanes gather from the same cache lines; the results go to
+ * the points' own indices and agree with the default layout up to FP32
+ * summation order.  It takes stream-ordered scratch of about 12 B per point
+ * and 8 B per bin (n < 2^31; ENOTSUP beyond 2^30 bins).
+ * flags: GRIDFF_DEVICE_PTRS, GRIDFF_ASYNC, GRIDFF_POINTS_BINNED.  The kernel
+ * time (every launch of the call) is kept for gridff_last_kernel_ms
+ * (synchronous calls).  Errors: EINVAL, ENOTSUP, ECUDA. */
 gridff_status gridff_eval_points(gridff_ctx* ctx, const gridff_grid* grid, int64_t n, const float* xyz,
                                  const float* qpl, float* E, float* F, int32_t* status, int flags);
 
@@ -339,7 +366,9 @@ gridff_status gridff_template_factors(const gridff_replicas* reps, int32_t t, fl
 
 /* FIRE relaxation of every replica for up to nsteps iterations in one
  * persistent launch (layout per gridff_launch_config; state kept in
- * registers or shared memory).
+ * registers or shared memory).  FIRE as the paper's relaxations use it
+ * (Sec. 6: relaxed scans and the timing runs; Sec. 7: relaxation of every
+ * replica on the GPU with a force-norm threshold).
  * Iteration: forces; convergence test |F|_2 < f_conv (rigid: |F_tot|^2 +
  * |tau|^2); P = F.v; P > 0: mix v towards F, grow dt after n_min steps;
  * else v = 0, dt *= f_dec; semi-implicit Euler with per-atom cap d_max.
@@ -442,7 +471,8 @@ typedef struct {
   double clock_budget_s;  /* as in gridff_fire_params */
 } gridff_md_params;
 
-/* NVE dynamics for nsteps: velocity Verlet (flexible) or the NO_SQUISH
+/* NVE dynamics for nsteps (Sec. 7: the molecular-dynamics loop of all
+ * replicas runs on the GPU): velocity Verlet (flexible) or the NO_SQUISH
  * symplectic rigid-body splitting (rigid; the sub-warp kernel with the
  * time-sliced schedule of gridff_relax, the block cap of the replica set's
  * launch configuration honoured).  energy_trace (may be NULL)

@@ -17,6 +17,7 @@
 #include <cuda_fp16.h>
 
 #include "internal.h"
+#include "interp.cuh"
 
 namespace {
 
@@ -71,21 +72,6 @@ __device__ __forceinline__ float qsum(float v) {
   return v;
 }
 
-// Cubic B-spline weights w_j = B(t - j), j = -1..2, and dB/dt for t in [0,1),
-// the polynomial pieces of Eq. Bspline on the four intervals.
-__device__ __forceinline__ void bspline_weights(float t, float w[4], float dw[4]) {
-  const float s = 1.f - t, t2 = t * t, t3 = t2 * t;
-  const float sixth = 1.f / 6.f;
-  w[0] = s * s * s * sixth;
-  w[1] = fmaf(3.f, t3, fmaf(-6.f, t2, 4.f)) * sixth;
-  w[2] = fmaf(-3.f, t3, fmaf(3.f, t2, fmaf(3.f, t, 1.f))) * sixth;
-  w[3] = t3 * sixth;
-  dw[0] = -0.5f * s * s;
-  dw[1] = fmaf(1.5f, t2, -2.f * t);
-  dw[2] = fmaf(-1.5f, t2, t + 0.5f);
-  dw[3] = 0.5f * t2;
-}
-
 // Per-warp stencil cache in shared memory.  Slot i (i < S) holds, for the
 // atom evaluated by a quad, the 64 node values c = Q b^C + P b^P + L b^L
 // of its 4x4x4 stencil (combined with that atom's fixed factors) and the
@@ -100,37 +86,6 @@ struct StencilCache {
   int* key;      // [S] packed cell index, -1 = empty
   int S;
 };
-
-// Fold into the periodic tile (Sec. 4), cell index and fractional
-// coordinates of one atom.
-struct Cell {
-  int ix, iy, iz;
-  float tx, ty, tz;
-  bool inside;   // inside the grid's z range (else the field is ~0)
-};
-
-__device__ __forceinline__ Cell locate(const GridView& g, bool act, float x, float y, float z, int& flags) {
-  Cell c;
-  float xr = x - g.x0, yr = y - g.y0;
-  xr = fmaf(-g.Lx, floorf(xr * g.inv_Lx), xr);
-  yr = fmaf(-g.Ly, floorf(yr * g.inv_Ly), yr);
-  float ux = xr * g.inv_dx, uy = yr * g.inv_dy, uz = (z - g.z0) * g.inv_dz;
-  float flx = floorf(ux), fly = floorf(uy);
-  c.tx = fminf(fmaxf(ux - flx, 0.f), 1.f);
-  c.ty = fminf(fmaxf(uy - fly, 0.f), 1.f);
-  int ix = (int)flx, iy = (int)fly;
-  if (ix >= g.nx) ix -= g.nx;
-  if (iy >= g.ny) iy -= g.ny;
-  c.ix = min(max(ix, 0), g.nx - 1);     // any input, even non-finite, stays in bounds
-  c.iy = min(max(iy, 0), g.ny - 1);
-  if (act && uz < 0.f) flags |= GRIDFF_REP_BELOW;
-  uz = fmaxf(uz, 0.f);
-  c.inside = act && (uz < (float)(g.nz - 1));   // above the grid (or NaN): field ~ 0
-  float flz = floorf(c.inside ? uz : 0.f);
-  c.tz = (c.inside ? uz : 0.f) - flz;
-  c.iz = min(max((int)flz, 0), g.nz - 2);
-  return c;
-}
 
 // Channel-combined values c = Q C + P P + L L of the 16 (x, y) runs at one
 // z-node: records base + a sx + b nzp, run m = 4a + b, for the grid's record
@@ -459,6 +414,31 @@ __device__ __forceinline__ void report(const Control& ctl, int n, int evals, int
   atomicMax(&ctl.res->max_steps, steps);
   int sb = st & (GRIDFF_REP_ABORTED | GRIDFF_REP_STEPLIMIT);
   if (sb) atomicOr(&ctl.res->stop_bits, sb);
+}
+
+// Record of a replica's final evaluation (the one after which a relaxation
+// makes no further move: its last iteration, convergence, or a non-finite
+// value): rigid: pose (7) into last_x[7 r..], total force (lab frame) and
+// body-frame torque into last_f[6 r..]; flexible: positions and forces of
+// its atoms (rows off..off+n-1 of last_x, last_f).  One lane (rigid) or the
+// warp (flexible) writes it, once per replica and call.
+__device__ __forceinline__ void record_rigid(float* last_x, float* last_f, int r, const float c[3], const float q[4],
+                                             const float Ft[3], const float tq[3]) {
+  float* px = last_x + 7 * (size_t)r;
+  float* pf = last_f + 6 * (size_t)r;
+  for (int a = 0; a < 3; ++a) {
+    px[a] = c[a];
+    pf[a] = Ft[a];
+    pf[3 + a] = tq[a];
+  }
+  for (int a = 0; a < 4; ++a) px[3 + a] = q[a];
+}
+__device__ __forceinline__ void record_flex(float* last_x, float* last_f, int off, int n, int lane, const float* sx,
+                                            const float* sf) {
+  for (int m = lane; m < 3 * n; m += 32) {
+    last_x[3 * (size_t)off + m] = sx[m];
+    last_f[3 * (size_t)off + m] = sf[m];
+  }
 }
 
 // Forces of one flexible replica whose positions are in s.x: grid term
@@ -827,9 +807,11 @@ eval_points_kernel(GridView g, long long n, const float* __restrict__ xyz, const
       z = __ldg(&xyz[3 * i + 2]);
       par = make_float4(__ldg(&qpl[3 * i]), __ldg(&qpl[3 * i + 1]), __ldg(&qpl[3 * i + 2]), 0.f);
     }
-    int flags = 0;
+    // a non-finite position is reported and evaluates to zero
+    const bool fin = finite3(x, y, z);
+    int flags = fin ? 0 : GRIDFF_REP_NONFINITE;
     float e, fx, fy, fz;
-    grid_quad<false, KIND>(g, q, act, x, y, z, par, e, fx, fy, fz, flags, nocache, -1);
+    grid_quad<false, KIND>(g, q, act && fin, x, y, z, par, e, fx, fy, fz, flags, nocache, -1);
     if (act && q == 0) {
       E[i] = e;
       F[3 * i] = fx;
@@ -846,7 +828,8 @@ eval_points_kernel(GridView g, long long n, const float* __restrict__ xyz, const
 __global__ void __launch_bounds__(kThreads, kMinBlocksPerSM)
 relax_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, int n_rep,
                    float* pose, float* vel, float* fdt, float* falpha, int* fnp, int* status,
-                   int* steps, double* energy, int nsteps, FireP fp, Control ctl, int use_grid, int S) {
+                   int* steps, double* energy, float* last_x, float* last_f, int nsteps, FireP fp, Control ctl,
+                   int use_grid, int S) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   const int lane = threadIdx.x & 31;
   const StencilCache sc = warp_cache(dyn_smem, S, threadIdx.x >> 5);
@@ -890,12 +873,14 @@ relax_rigid_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl
       st |= __reduce_or_sync(kFull, flags);
       ++evals;
       elane = e;
-      if (!(finite3(Ft[0], Ft[1], Ft[2]) && finite3(tq[0], tq[1], tq[2]) && finite3(c[0], c[1], c[2]))) {
+      const bool fin = finite3(Ft[0], Ft[1], Ft[2]) && finite3(tq[0], tq[1], tq[2]) && finite3(c[0], c[1], c[2]);
+      float f2 = Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2] + tq[0] * tq[0] + tq[1] * tq[1] +
+                 tq[2] * tq[2];
+      if (lane == 0 && (s == nsteps - 1 || !fin || f2 < fp.f_conv2)) record_rigid(last_x, last_f, r, c, q, Ft, tq);
+      if (!fin) {
         st |= GRIDFF_REP_NONFINITE;
         break;
       }
-      float f2 = Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2] + tq[0] * tq[0] + tq[1] * tq[1] +
-                 tq[2] * tq[2];
       if (f2 < fp.f_conv2) {
         st |= GRIDFF_REP_CONVERGED;
         break;
@@ -1186,11 +1171,14 @@ __device__ __noinline__ SwPart sw_part(int warp, int n_warps, int P, int nsteps,
   return s;
 }
 
-// Upper bound on the polls of a hand-off flag (with a 1 us sleep between
-// polls, about a second of waiting at the least), after which the part is
-// skipped and the call returns GRIDFF_ETIMEOUT.  A head finishes a quarter
-// of a task before its tail starts, so a working launch never waits long.
-constexpr int kHandoffPolls = 1 << 20;
+// Bound of the wait for a hand-off flag: one second of %globaltimer time,
+// after which the part is skipped and the call returns GRIDFF_ETIMEOUT.
+// The poll count is only a backstop that ends the loop should the timer
+// not advance (polls are about a microsecond apart: an acquire load from
+// L2 and a requested 1 us sleep).  A head finishes a quarter of a task
+// before its tail starts, so a working launch never waits long.
+constexpr unsigned long long kHandoffWaitNs = 1000000000ull;
+constexpr int kHandoffPolls = 1 << 23;
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
@@ -1201,12 +1189,25 @@ __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// The hand-off flag's value once it is set, or 0 when the bounded wait ran
+// out (one lane calls it).
+__device__ __noinline__ int wait_handoff(const int* flag) {
+  const unsigned long long deadline = gtimer() + kHandoffWaitNs;
+  int hv = 0;
+  for (int k = 0; k < kHandoffPolls; ++k) {
+    hv = ld_acquire(flag);
+    if (hv != 0 || gtimer() > deadline) break;
+    __nanosleep(1000);
+  }
+  return hv;
+}
+
 template <int W, int R, int WPB, int MINB, int KIND>
 __global__ void __launch_bounds__(32 * WPB, MINB)
 relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl, int n_rep,
                       float* pose, float* vel, float* fdt, float* falpha, int* fnp, int* status,
-                      int* steps, double* energy, int* handoff, int queued, int publish, int nsteps, FireP fp,
-                      Control ctl, int S) {
+                      int* steps, double* energy, float* last_x, float* last_f, int* handoff, int queued,
+                      int publish, int nsteps, FireP fp, Control ctl, int S) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   constexpr int RPW = 32 / W;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -1244,11 +1245,7 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
     if (tail) {
       // wait until the previous warp has written the head of this task
       if (lane == 0) {
-        hv = 0;
-        for (int k = 0; k < kHandoffPolls && hv == 0; ++k) {
-          hv = ld_acquire(handoff + p);
-          if (hv == 0) __nanosleep(1000);
-        }
+        hv = wait_handoff(handoff + p);
         if (hv == 0) atomicAdd(&ctl.res->handoff_timeouts, 1);
       }
       hv = __shfl_sync(kFull, hv, 0);
@@ -1333,7 +1330,9 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
       const float f2 = Ft[0] * Ft[0] + Ft[1] * Ft[1] + Ft[2] * Ft[2] + tq[0] * tq[0] + tq[1] * tq[1] +
                        tq[2] * tq[2];
       // a NaN or infinity in any force or torque component reaches f2
-      if (!isfinite(f2) || !isfinite(c[0] + c[1] + c[2])) {
+      const bool fin = isfinite(f2) && isfinite(c[0] + c[1] + c[2]);
+      if (l == 0 && (it == nsteps - 1 || !fin || f2 < fp.f_conv2)) record_rigid(last_x, last_f, r, c, q, Ft, tq);
+      if (!fin) {
         st |= GRIDFF_REP_NONFINITE;
         continue;
       }
@@ -1432,8 +1431,8 @@ relax_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_t
 __global__ void __launch_bounds__(kThreads, kMinBlocksPerSM)
 relax_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
                   const int* __restrict__ rep_off, int n_rep, float* xs, float* vs, float* fdt,
-                  float* falpha, int* fnp, int* status, int* steps, double* energy, int nsteps,
-                  FireP fp, Control ctl, int use_grid, int use_intra, int S) {
+                  float* falpha, int* fnp, int* status, int* steps, double* energy, float* last_x,
+                  float* last_f, int nsteps, FireP fp, Control ctl, int use_grid, int use_intra, int S) {
   __shared__ WarpState s_all[kWarpsPerBlock];
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -1477,6 +1476,8 @@ relax_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
       st |= __reduce_or_sync(kFull, flags);
       ++evals;
       elane = e;
+      if (it == nsteps - 1 || (st & GRIDFF_REP_NONFINITE) || !(f2 >= fp.f_conv2))
+        record_flex(last_x, last_f, off, n, lane, s.x, s.f);
       if ((st & GRIDFF_REP_NONFINITE) || !isfinite(f2)) {
         st |= GRIDFF_REP_NONFINITE;
         break;
@@ -1551,7 +1552,8 @@ __global__ void __launch_bounds__(32 * WPB, GRIDFF_FLEX_WARPS_PER_SM / WPB)
 relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
                         const int* __restrict__ rep_off, const int* __restrict__ order, int n_rep, float* xs,
                         float* vs, float* fdt, float* falpha, int* fnp, int* status, int* steps, double* energy,
-                        int nsteps, FireP fp, Control ctl, int use_grid, int use_intra, int S) {
+                        float* last_x, float* last_f, int nsteps, FireP fp, Control ctl, int use_grid,
+                        int use_intra, int S) {
   __shared__ WarpState s_all[WPB];
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -1616,6 +1618,8 @@ relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep
       st |= __reduce_or_sync(kFull, flags);
       ++evals;
       elane = e;
+      if (it == nsteps - 1 || (st & GRIDFF_REP_NONFINITE) || !(f2 >= fp.f_conv2))
+        record_flex(last_x, last_f, off, n, lane, s.x, s.f);
       if ((st & GRIDFF_REP_NONFINITE) || !isfinite(f2)) {
         st |= GRIDFF_REP_NONFINITE;
         break;
@@ -2040,11 +2044,7 @@ run_rigid_sw_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmp
     int hv = 1;
     if (tail) {
       if (lane == 0) {
-        hv = 0;
-        for (int k = 0; k < kHandoffPolls && hv == 0; ++k) {
-          hv = ld_acquire(handoff + part.p);
-          if (hv == 0) __nanosleep(1000);
-        }
+        hv = wait_handoff(handoff + part.p);
         if (hv == 0) atomicAdd(&ctl.res->handoff_timeouts, 1);
       }
       hv = __shfl_sync(kFull, hv, 0);
@@ -2302,7 +2302,7 @@ __global__ void fire_reset_kernel(int n, float dt0, float a0, float* dt, float* 
 }
 
 using SwFn = void (*)(GridView, TemplateView, const int*, int, float*, float*, float*, float*, int*, int*, int*,
-                     double*, int*, int, int, int, FireP, Control, int);
+                     double*, float*, float*, int*, int, int, int, FireP, Control, int);
 
 // Sub-warp rigid kernel for W lanes per replica and R atoms per lane; FP32
 // four-slot grids get a build without the other record kinds' code.
@@ -2336,7 +2336,7 @@ RunSwFn run_sw_fn(int W, int R, int kind) {
 // FP32 four-slot grids get their own instances (the record kind known at
 // compile time); other kinds dispatch at run time.
 using FlexTermsFn = void (*)(GridView, TemplateView, const int*, const int*, const int*, int, float*, float*, float*,
-                             float*, int*, int*, int*, double*, int, FireP, Control, int, int, int);
+                             float*, int*, int*, int*, double*, float*, float*, int, FireP, Control, int, int, int);
 template <int K>
 FlexTermsFn flex_terms_fn_k(int wpb) {
   return wpb == 2 ? relax_flex_terms_kernel<2, K> : wpb == 8 ? relax_flex_terms_kernel<8, K>
@@ -2537,25 +2537,25 @@ gridff_status enqueue_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_rep
       GRIDFF_CUDA(ctx, cudaMemsetAsync(R->handoff, 0, R->n_rep * sizeof(int), s));
       e = launch_ex(rigid_sw_fn(c.W, sw_rounds(R, c.W), kind), blocks, k.threads, k.dyn, s, wp, gv, R->tv,
                     (const int*)R->rep_tmpl, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha, R->fire_nplus,
-                    R->status, R->steps, R->energy, R->handoff,
+                    R->status, R->steps, R->energy, R->last_x, R->last_f, R->handoff,
                     (int)(c.queue == 1 || (c.queue == 0 && P.f_conv > 0)), (int)!(flags & GRIDFF_TEST_NO_HANDOFF),
                     nsteps, fp, ctl, c.S);
       break;
     case GRIDFF_KERNEL_RIGID_QUAD:
       e = launch_ex(relax_rigid_kernel, blocks, k.threads, k.dyn, s, wp, gv, R->tv, (const int*)R->rep_tmpl,
                     R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha, R->fire_nplus, R->status, R->steps, R->energy,
-                    nsteps, fp, ctl, use_grid, c.S);
+                    R->last_x, R->last_f, nsteps, fp, ctl, use_grid, c.S);
       break;
     case GRIDFF_KERNEL_FLEX_QUAD:
       e = launch_ex(relax_flex_kernel, blocks, k.threads, k.dyn, s, wp, gv, R->tv, (const int*)R->rep_tmpl,
                     (const int*)R->rep_off, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha, R->fire_nplus,
-                    R->status, R->steps, R->energy, nsteps, fp, ctl, use_grid, use_intra, c.S);
+                    R->status, R->steps, R->energy, R->last_x, R->last_f, nsteps, fp, ctl, use_grid, use_intra, c.S);
       break;
     case GRIDFF_KERNEL_FLEX_TERMS: {
       const int* ord = c.queue ? (const int*)R->order : nullptr;
       e = launch_ex(flex_terms_fn(c.wpb, kind), blocks, k.threads, k.dyn, s, wp, gv, R->tv, (const int*)R->rep_tmpl,
                     (const int*)R->rep_off, ord, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha, R->fire_nplus,
-                    R->status, R->steps, R->energy, nsteps, fp, ctl, use_grid, use_intra, c.S);
+                    R->status, R->steps, R->energy, R->last_x, R->last_f, nsteps, fp, ctl, use_grid, use_intra, c.S);
       break;
     }
     default:
@@ -2633,20 +2633,25 @@ gridff_status gridff_eval_points(gridff_ctx* ctx, const gridff_grid* grid, int64
     dx = hx;
     dq = hq;
   }
-  const GridView gv = grid->view();
-  const void* fn = grid->kind == REC_F32x4 ? (const void*)eval_points_kernel<REC_F32x4>
-                                           : (const void*)eval_points_kernel<-1>;
-  int per_sm = 0;
-  GRIDFF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0));
-  const long long need = (n + 63) / 64;   // 8 warps x 8 points per block round
-  const long long cap = (long long)(per_sm > 0 ? per_sm : 1) * ctx->n_sm;
-  const int blocks = (int)(need < cap ? need : cap);
   GRIDFF_CUDA(ctx, cudaEventRecord(ctx->ev0, s));
-  if (grid->kind == REC_F32x4)
-    eval_points_kernel<REC_F32x4><<<blocks, 256, 0, s>>>(gv, (long long)n, dx, dq, dE, dF, dS);
-  else
-    eval_points_kernel<-1><<<blocks, 256, 0, s>>>(gv, (long long)n, dx, dq, dE, dF, dS);
-  GRIDFF_CUDA(ctx, cudaGetLastError());
+  if (flags & GRIDFF_POINTS_BINNED) {
+    const gridff_status bst = enqueue_eval_points_binned(ctx, grid, n, dx, dq, dE, dF, dS);
+    if (bst != GRIDFF_OK) return bst;
+  } else {
+    const GridView gv = grid->view();
+    const void* fn = grid->kind == REC_F32x4 ? (const void*)eval_points_kernel<REC_F32x4>
+                                             : (const void*)eval_points_kernel<-1>;
+    int per_sm = 0;
+    GRIDFF_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0));
+    const long long need = (n + 63) / 64;   // 8 warps x 8 points per block round
+    const long long cap = (long long)(per_sm > 0 ? per_sm : 1) * ctx->n_sm;
+    const int blocks = (int)(need < cap ? need : cap);
+    if (grid->kind == REC_F32x4)
+      eval_points_kernel<REC_F32x4><<<blocks, 256, 0, s>>>(gv, (long long)n, dx, dq, dE, dF, dS);
+    else
+      eval_points_kernel<-1><<<blocks, 256, 0, s>>>(gv, (long long)n, dx, dq, dE, dF, dS);
+    GRIDFF_CUDA(ctx, cudaGetLastError());
+  }
   GRIDFF_CUDA(ctx, cudaEventRecord(ctx->ev1, s));
   if (!dev) {
     GRIDFF_CUDA(ctx, cudaMemcpyAsync(E, dE, n1, cudaMemcpyDeviceToHost, s));

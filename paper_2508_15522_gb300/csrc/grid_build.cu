@@ -870,6 +870,24 @@ gridff_status gridff_fit_coefs_noalloc(gridff_ctx* ctx, const double* values, do
                      "gridff_fit_coefs_noalloc: dims[%d] = %d outside 4..%d (the size of its fixed "
                      "device table)", a, dims[a], kNoAllocMaxN);
   GRIDFF_CUDA(ctx, cudaSetDevice(ctx->device));
+  const size_t bytes = (size_t)dims[0] * dims[1] * dims[2] * n_channels * sizeof(double);
+  // both arrays must be memory of this context's device (a host pointer
+  // handed to the line-solve kernels would be an out-of-bounds access)
+  for (const void* p : {(const void*)values, (const void*)coefs}) {
+    cudaPointerAttributes pa{};
+    const cudaError_t pe = cudaPointerGetAttributes(&pa, p);
+    if (pe != cudaSuccess) cudaGetLastError();
+    if (pe != cudaSuccess || (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) ||
+        (pa.type == cudaMemoryTypeDevice && pa.device != ctx->device))
+      return set_err(ctx, GRIDFF_EINVAL, "gridff_fit_coefs_noalloc: %s is not memory of device %d",
+                     p == (const void*)values ? "values" : "coefs", ctx->device);
+  }
+  {
+    // in place (equal pointers) is allowed; partly overlapping ranges are not
+    const char *v0 = (const char*)values, *c0 = (const char*)coefs;
+    if (v0 != c0 && v0 < c0 + bytes && c0 < v0 + bytes)
+      return set_err(ctx, GRIDFF_EINVAL, "gridff_fit_coefs_noalloc: values and coefs overlap without being equal");
+  }
   cudaError_t e;
   double* tab = noalloc_tables_address(ctx->device, &e);
   if (!tab) return set_err(ctx, GRIDFF_ECUDA, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));

@@ -199,6 +199,8 @@ struct gridff_replicas {
   double* energy = nullptr;
   int* handoff = nullptr;      // [n_rep] sub-warp schedule: first part of a split warp task written
   float4* handoff_p = nullptr; // [n_rep] rigid NVE: quaternion momentum at the end of a head part
+  float* last_x = nullptr;     // final evaluation of the last relaxation: rigid [7 n_rep] poses,
+  float* last_f = nullptr;     //   [6 n_rep] total force + body torque; flexible [3N] positions, [3N] forces
   // host copy of offsets
   int* h_rep_off = nullptr;
   int* h_rot_off = nullptr;    // [n_tmpl+1] rotatable bonds (host copy)
@@ -225,6 +227,10 @@ gridff_status enqueue_build_poses(gridff_replicas* R, const float* d_poses, int 
 gridff_status enqueue_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* R, const LaunchCfg& c,
                             int blocks, int nsteps, const gridff_fire_params& P, int flags);
 gridff_status check_fire_params(gridff_ctx* ctx, const gridff_fire_params& P);
+// Binned point evaluation (points.cu): device arrays, enqueued on the
+// context stream (gridff_eval_points with GRIDFF_POINTS_BINNED).
+gridff_status enqueue_eval_points_binned(gridff_ctx* ctx, const gridff_grid* grid, int64_t n, const float* xyz,
+                                         const float* qpl, float* E, float* F, int32_t* status);
 #define GRIDFF_CUDA(ctx, call)                                                     \
   do {                                                                             \
     cudaError_t e_ = (call);                                                       \

@@ -25,11 +25,6 @@ inline int pad16(int n) { return (n + 15) & ~15; }
 // C[M][N] (FP32) = A[M][K] * B, A row-major bf16 (lda), B given as Bt[N][K]
 // row-major bf16 (ldb), i.e. B is K x N column-major.  M % 16 == 0,
 // N % 8 == 0, K % 16 == 0.  One warp per 16 x 8 output tile, K in steps of
-// 16 with one tensor-core mma per step.
-// ---------------------------------------------------------------------------
-// C[M][N] (FP32) = A[M][K] * B, A row-major bf16 (lda), B given as Bt[N][K]
-// row-major bf16 (ldb), i.e. B is K x N column-major.  M % 16 == 0,
-// N % 8 == 0, K % 16 == 0.  One warp per 16 x 8 output tile, K in steps of
 // 16 with one tensor-core mma per step.  Split K: block row y handles
 // K range [y K, (y + 1) K) and writes its partial product to C + y * cstride.
 __global__ void gemm_bf16_kernel(const __nv_bfloat16* __restrict__ A, int lda,

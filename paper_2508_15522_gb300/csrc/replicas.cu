@@ -386,7 +386,8 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
       cudaMalloc(&R->fire_dt, n_rep * sizeof(float)) || cudaMalloc(&R->fire_alpha, n_rep * sizeof(float)) ||
       cudaMalloc(&R->fire_nplus, n_rep * sizeof(int)) || cudaMalloc(&R->status, n_rep * sizeof(int)) ||
       cudaMalloc(&R->steps, n_rep * sizeof(int)) || cudaMalloc(&R->energy, n_rep * sizeof(double)) ||
-      cudaMalloc(&R->handoff, n_rep * sizeof(int)) || cudaMalloc(&R->handoff_p, n_rep * sizeof(float4)))
+      cudaMalloc(&R->handoff, n_rep * sizeof(int)) || cudaMalloc(&R->handoff_p, n_rep * sizeof(float4)) ||
+      cudaMalloc(&R->last_x, nx * sizeof(float)) || cudaMalloc(&R->last_f, nv * sizeof(float)))
     return bail(GRIDFF_ENOMEM, "replica state");
   R->h_rep_off = new int[n_rep + 1];
   memcpy(R->h_rep_off, rep_off.data(), (n_rep + 1) * sizeof(int));
@@ -399,7 +400,9 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
       cudaMemsetAsync(R->fire_nplus, 0, n_rep * sizeof(int), s) ||
       cudaMemsetAsync(R->status, 0, n_rep * sizeof(int), s) ||
       cudaMemsetAsync(R->steps, 0, n_rep * sizeof(int), s) ||
-      cudaMemsetAsync(R->energy, 0, n_rep * sizeof(double), s))
+      cudaMemsetAsync(R->energy, 0, n_rep * sizeof(double), s) ||
+      cudaMemsetAsync(R->last_x, 0xff, nx * sizeof(float), s) ||   // all bits set: NaN (nothing recorded)
+      cudaMemsetAsync(R->last_f, 0xff, nv * sizeof(float), s))
     return bail(GRIDFF_ECUDA, "replica init");
   if (rigid) {
     // identity orientation
@@ -436,7 +439,8 @@ void gridff_replicas_destroy(gridff_replicas* R) {
   cudaGetDevice(&prev);
   cudaSetDevice(R->device);
   void* ptrs[] = {R->tmpl_blob, R->rep_tmpl, R->rep_off, R->x, R->v, R->fire_dt, R->fire_alpha,
-                  R->fire_nplus, R->status, R->steps, R->energy, R->handoff, R->handoff_p};
+                  R->fire_nplus, R->status, R->steps, R->energy, R->handoff, R->handoff_p,
+                  R->last_x, R->last_f};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   cudaSetDevice(prev);
@@ -507,6 +511,19 @@ gridff_status gridff_get_positions(gridff_replicas* R, float* x, int flags) {
     if (e == cudaSuccess) e = ef;
   }
   if (e != cudaSuccess) return set_err(ctx, GRIDFF_ECUDA, "positions: %s", cudaGetErrorString(e));
+  return finish(ctx, flags);
+}
+
+gridff_status gridff_get_last_eval(gridff_replicas* R, float* x, float* f, int flags) {
+  if (!R) return GRIDFF_EINVAL;
+  gridff_ctx* ctx = R->ctx;
+  GRIDFF_CUDA(ctx, cudaSetDevice(ctx->device));
+  size_t nx = R->rigid ? 7 * (size_t)R->n_rep : 3 * (size_t)R->n_atoms;
+  size_t nf = R->rigid ? 6 * (size_t)R->n_rep : 3 * (size_t)R->n_atoms;
+  bool ok = true;
+  if (x) ok &= copy_out(ctx, x, R->last_x, nx * sizeof(float), flags);
+  if (f) ok &= copy_out(ctx, f, R->last_f, nf * sizeof(float), flags);
+  if (!ok) return set_err(ctx, GRIDFF_ECUDA, "copy");
   return finish(ctx, flags);
 }
 

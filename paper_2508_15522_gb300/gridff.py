@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libgridff.so")
 OK, EINVAL, ENOMEM, ECUDA, EABORTED, ESTEPLIMIT, ENOTSUP, ETIMEOUT = range(8)
 REP_CONVERGED, REP_BELOW, REP_NONFINITE, REP_ABORTED, REP_STEPLIMIT = 1, 2, 4, 8, 16
 DEVICE_PTRS, ASYNC, CONTINUE, NO_GRID, NO_INTRA = 1, 2, 4, 8, 16
+POINTS_BINNED = 32
 TEST_NO_HANDOFF = 256
 CH_C, CH_P, CH_L = 1, 2, 4
 STORE_F32, STORE_F16, STORE_BF16 = 0, 1, 2
@@ -131,6 +132,7 @@ def _load():
         "gridff_get_state": (I32, [P, P, P, C.c_int]),
         "gridff_get_positions": (I32, [P, P, C.c_int]),
         "gridff_get_fire_state": (I32, [P, P, P, P, P, P, P, C.c_int]),
+        "gridff_get_last_eval": (I32, [P, P, P, C.c_int]),
         "gridff_eval": (I32, [P, P, P, C.c_int, P, P, P, P]),
         "gridff_fire_params_default": (None, [C.POINTER(FireParams)]),
         "gridff_relax": (I32, [P, P, P, I32, C.POINTER(FireParams), C.c_int, C.POINTER(RelaxResult)]),
@@ -177,7 +179,7 @@ EXPORTED = (
     "gridff_fit_coefs_noalloc",
     "gridff_grid_download_f64", "gridff_grid_destroy", "gridff_replicas_create",
     "gridff_replicas_destroy", "gridff_replicas_info", "gridff_set_state", "gridff_get_state",
-    "gridff_get_positions", "gridff_get_fire_state", "gridff_eval", "gridff_fire_params_default",
+    "gridff_get_positions", "gridff_get_fire_state", "gridff_get_last_eval", "gridff_eval", "gridff_fire_params_default",
     "gridff_relax", "gridff_run", "gridff_probe_read_bandwidth", "gridff_last_kernel_ms",
     "gridff_mlp_create", "gridff_mlp_destroy", "gridff_mlp_num_params", "gridff_mlp_set_params",
     "gridff_mlp_get_params", "gridff_mlp_forward", "gridff_mlp_train_step", "gridff_mlp_propose",
@@ -324,10 +326,17 @@ def grid_from_coefs(ctx: Context, coefs, origin, spacing, channels, storage=STOR
 
 
 def fit_coefs_noalloc(ctx: Context, values, coefs, flags: int = 0):
-    """gridff_fit_coefs_noalloc on device tensors (float64, shape (C, nx, ny, nz))."""
+    """gridff_fit_coefs_noalloc on CUDA tensors: contiguous float64 of one
+    shape (C, nx, ny, nz); returns the library's status."""
+    for name, t in (("values", values), ("coefs", coefs)):
+        if not _is_torch(t) or not t.is_cuda or t.ndim != 4:
+            raise TypeError(f"{name} must be a 4-d CUDA tensor (C, nx, ny, nz)")
+    if tuple(coefs.shape) != tuple(values.shape):
+        raise TypeError("coefs must have the shape of values")
+    pv, _, _ = _ptr(values, np.float64)
+    pc, _, _ = _ptr(coefs, np.float64)
     dims = (C.c_int32 * 3)(*values.shape[1:])
-    return lib.gridff_fit_coefs_noalloc(ctx.h, C.c_void_p(values.data_ptr()), C.c_void_p(coefs.data_ptr()),
-                                        dims, int(values.shape[0]), flags)
+    return lib.gridff_fit_coefs_noalloc(ctx.h, pv, pc, dims, int(values.shape[0]), flags)
 
 
 def _mol_struct(m, keep):
@@ -404,6 +413,18 @@ class Replicas:
         self.ctx.check(lib.gridff_get_fire_state(self.h, p["dt"], p["alpha"], p["nplus"], p["status"],
                                                  p["steps"], p["energy"], 0))
         return out
+
+    def last_eval(self):
+        """(state, forces) of every replica's final evaluation in the last
+        relaxation (gridff_get_last_eval): rigid (n_rep, 7) poses and
+        (n_rep, 6) total force + body torque; flexible (n_atoms, 3) each."""
+        nx, nf = self.state_sizes
+        x = np.empty(nx, np.float32); f = np.empty(nf, np.float32)
+        self.ctx.check(lib.gridff_get_last_eval(self.h, x.ctypes.data_as(C.c_void_p),
+                                                f.ctypes.data_as(C.c_void_p), 0))
+        if self.rigid:
+            return x.reshape(-1, 7), f.reshape(-1, 6)
+        return x.reshape(-1, 3), f.reshape(-1, 3)
 
     def set_launch_config(self, cfg=None, **kw):
         """Fix the relaxation layout (None: the library's heuristic)."""

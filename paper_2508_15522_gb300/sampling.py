@@ -107,6 +107,12 @@ class Sampler:
         net.propose(self.reps, self.desc, seed, s.origin_xy, s.tile_xy)
         return self._relax(t0)
 
+    def targets(self) -> np.ndarray:
+        """Training targets (n_rep, 19) of the current (relaxed) poses: centre
+        folded into the tile, unit quaternion with w >= 0, no torsions
+        (`gridff_pose_targets`)."""
+        return self.reps.pose_targets(self.surface.origin_xy, self.surface.tile_xy)[0]
+
     def unique(self, poses: np.ndarray, energy: np.ndarray, threshold: float = 0.1) -> np.ndarray:
         """Indices of the structurally unique poses, lowest energy first."""
         order = np.argsort(energy, kind="stable")
@@ -184,19 +190,6 @@ class FlexSampler:
 def hits(b: Batch, e_best: float, tol: float = 0.01) -> np.ndarray:
     """Accepted minima within tol of the best-known energy."""
     return b.converged & (b.energy <= e_best + tol)
-
-
-def pose_targets(poses: np.ndarray, surface: Surface) -> np.ndarray:
-    """(n, 19) training targets: centre folded into the tile, unit
-    quaternion, no torsions (rigid)."""
-    T = np.zeros((len(poses), G.MLP_OUT), np.float32)
-    c = poses[:, :3].astype(np.float64)
-    for a in range(2):
-        c[:, a] = surface.origin_xy[a] + np.mod(c[:, a] - surface.origin_xy[a], surface.tile_xy[a])
-    q = poses[:, 3:7].astype(np.float64)
-    T[:, :3] = c
-    T[:, 3:7] = q / np.linalg.norm(q, axis=1, keepdims=True)
-    return T
 
 
 def init_params(sizes, seed: int, out_bias=None):

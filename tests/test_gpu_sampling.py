@@ -81,14 +81,18 @@ def test_mlp_proposals_beat_random_starts(gf, ctx):
     mol = synth.c24h8o6_core()
     surf = S.Surface((0.0, 0.0), (5.64, 5.64), sub.z_top + 3.0, sub.z_top + 5.0, sub.z_top + 2.0)
     sp = S.Sampler(ctx, grid, mol, surf, n_rep=2048, nsteps=2000)
-    runs = [sp.random_batch(100 + k) for k in range(8)]
+    runs, targets = [], []
+    for k in range(8):
+        runs.append(sp.random_batch(100 + k))
+        targets.append(sp.targets())
     E = np.concatenate([b.energy for b in runs]); P = np.concatenate([b.poses for b in runs])
     C = np.concatenate([b.converged for b in runs])
+    T = np.concatenate(targets)
     e_best = E[C].min()
     h = C & (E <= e_best + 0.01)
     n_unique = len(sp.unique(P[h], E[h]))
-    net = S.new_network(ctx, S.pose_targets(P[h], surf), seed=3)
-    S.train_on_device(net, sp.desc, S.pose_targets(P[h], surf), surf, 3000, batch=256, K=8, lr=1e-3, seed=4)
+    net = S.new_network(ctx, T[h], seed=3)
+    S.train_on_device(net, sp.desc, T[h], surf, 3000, batch=256, K=8, lr=1e-3, seed=4)
     rnd = [sp.random_batch(200 + k) for k in range(2)]
     mlp = [sp.proposal_batch(net, 300 + k) for k in range(2)]
     frac_r = np.mean([S.hits(b, e_best).mean() for b in rnd])
