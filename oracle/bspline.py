@@ -135,12 +135,16 @@ def fit_gradient_descent(values: np.ndarray, iterations: int, step: float = 1.0,
 
 
 def eval_grid(coefs: np.ndarray, origin, spacing, points: np.ndarray,
-              dtype=np.float64):
+              dtype=np.float64, below_u: float = 0.0):
     """Tricubic B-spline value and gradient of every channel at the points.
 
     coefs: (C, nx, ny, nz); origin, spacing: 3-vectors; points: (N, 3).
     All arithmetic is done in ``dtype`` (float64, or float32 for the
     single-precision mirror, which also rounds the coefficients first).
+    ``below_u``: the floor of the grid in units of the z spacing above the
+    first node (the number of ghost node planes below the floor, see
+    grid.py); a point is flagged below when its z coordinate in those units
+    is smaller.  Below the first node the point is still clamped to it.
     Returns (f (N, C), grad (N, C, 3), below (N,) bool).
     """
     dt = np.dtype(dtype).type
@@ -162,8 +166,8 @@ def eval_grid(coefs: np.ndarray, origin, spacing, points: np.ndarray,
     ux = (P[:, 0] - o[0]) / h[0]
     uy = (P[:, 1] - o[1]) / h[1]
     uz = (P[:, 2] - o[2]) / h[2]
-    below = uz < 0
-    uz = np.where(below, dt(0), uz)
+    below = uz < dt(below_u)
+    uz = np.where(uz < 0, dt(0), uz)
     above = uz >= nz - 1
     uz = np.where(above, dt(0), uz)
     ix, wx, dwx = axis_setup(ux, nx, True)

@@ -114,7 +114,7 @@ def _rotate_body(quat, w, angle):
 # force functions
 # ---------------------------------------------------------------------------
 def make_force_fn(coefs, channels, origin, spacing, mol, alpha=1.5, intra=True,
-                  dtype=np.float64):
+                  dtype=np.float64, ghost=0):
     """Force function x (R, n, 3) -> (E (R,), F (R, n, 3), flags (R,)): grid
     interaction (Sec. 3, Sec. 5) plus, for flexible molecules, the
     intramolecular terms."""
@@ -126,7 +126,7 @@ def make_force_fn(coefs, channels, origin, spacing, mol, alpha=1.5, intra=True,
         pts = x.reshape(-1, 3)
         Q = np.tile(mol.q, Rn); Rr = np.tile(mol.R, Rn); ep = np.tile(mol.eps, Rn)
         E, F, below = ogrid.grid_energy_forces(coefs, channels, origin, spacing, pts,
-                                               Q, Rr, ep, alpha, dtype)
+                                               Q, Rr, ep, alpha, dtype, ghost)
         E = E.astype(np.float64).reshape(Rn, n).sum(1)
         F = F.astype(np.float64).reshape(Rn, n, 3)
         flags = np.where(below.reshape(Rn, n).any(1), BELOW_GRID, 0)

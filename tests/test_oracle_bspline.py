@@ -150,6 +150,50 @@ def test_clamped_z_end_closed_form_and_order():
     assert 12.0 < ie1 / ie2 < 20.0             # interior: O(h^4)
 
 
+def test_ghost_nodes_make_the_floor_cell_interior_accurate():
+    """Ghost nodes (reading of the z boundary): node values of exp(-3 z)
+    also taken on G planes below the floor z = 0 and fitted with the rest.
+    With G = 8 the floor cell [0, h] meets the interior bounds of cubic
+    spline interpolation (Hall and Meyer 1976): |f - s| <= (5/384) h^4 M4
+    and |f' - s'| <= (1/24) h^3 M4, M4 = max |4th derivative| = 81 on the
+    cell; without them (G = 0) the value and the slope miss those bounds by
+    two orders of magnitude and more."""
+    def floor_cell_errors(h, G):
+        nz = int(round(4.0 / h)) + 1 + G
+        z = (np.arange(nz) - G) * h
+        v = np.broadcast_to(np.exp(-3.0 * z), (1, 4, 4, nz)).copy()
+        c = bspline.fit_exact(v)
+        zq = np.linspace(0.0, h, 201)
+        pts = np.stack([np.full_like(zq, 0.3), np.full_like(zq, 0.7), zq + G * h], 1)
+        f, gr, below = bspline.eval_grid(c, (0, 0, 0), (1.0, 1.0, h), pts, below_u=G)
+        assert not below.any()
+        return np.abs(f[:, 0] - np.exp(-3 * zq)).max(), np.abs(gr[:, 0, 2] + 3 * np.exp(-3 * zq)).max()
+
+    for h in (0.1, 0.05):
+        hm_value, hm_slope = 5.0 / 384.0 * h ** 4 * 81.0, h ** 3 / 24.0 * 81.0
+        ev, es = floor_cell_errors(h, 8)
+        assert ev <= hm_value and es <= hm_slope, (h, ev, es)
+        ev0, es0 = floor_cell_errors(h, 0)
+        assert ev0 > 50 * hm_value and es0 > 200 * hm_slope
+
+
+def test_ghost_floor_flags_points_but_evaluates_them():
+    """With G ghost planes the floor is G spacings above the first node:
+    a point between the first node and the floor is flagged below but
+    evaluated on its own cell (not clamped); below the first node it is
+    clamped to the first node plane."""
+    g = np.random.default_rng(5)
+    h, G = 0.2, 3
+    b = g.standard_normal((1, 5, 5, 12))
+    pts = np.array([[0.5, 0.5, 0.5 * h], [0.5, 0.5, (G + 0.01) * h], [0.5, 0.5, (G - 0.01) * h],
+                    [0.5, 0.5, -0.7], [0.5, 0.5, 0.0]])
+    f, _, below = bspline.eval_grid(b, (0, 0, 0), (1.0, 1.0, h), pts, below_u=G)
+    assert below.tolist() == [True, False, True, True, True]
+    f0, _, _ = bspline.eval_grid(b, (0, 0, 0), (1.0, 1.0, h), pts[:1])
+    assert f[0, 0] == f0[0, 0]                       # evaluated where it is
+    assert f[3, 0] == f[4, 0]                         # clamped to the first node plane
+
+
 def test_gradient_matches_finite_difference():
     g = synth.rng(21)
     b = g.standard_normal((3, 6, 5, 9))

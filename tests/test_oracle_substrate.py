@@ -212,3 +212,36 @@ def test_grid_interpolation_vs_pairwise_morse_at_0p1():
     assert (np.abs(E - Eref) <= bound).all()
     assert np.abs(E - Eref).max() < 5e-5          # eV per atom at 0.1 A
     assert np.abs(F - Fref).max() < 2e-3
+
+
+@pytest.mark.slow
+def test_ghost_nodes_floor_cells_vs_pairwise_morse():
+    """Eight ghost planes below the floor: Morse energies of atoms in the
+    first three cells above the floor (1.0-1.3 A above the top ions) match
+    the direct pair sums within the interior cubic-spline bound of the test
+    above (Hall & Meyer), where the clamped fit without ghost planes is off
+    by far more; the node values of the planes above the floor are those of
+    the grid without ghosts."""
+    sub = synth.rocksalt_slab(ncell=2)
+    a, G = 5.64, 8
+    origin, length = (0.0, 0.0, sub.z_top + 1.0), (a, a, 2.0)
+    mol = synth.c24h8o6_core()
+    g = synth.rng(41)
+    pts = np.stack([g.uniform(0, a, 76), g.uniform(0, a, 76), g.uniform(0.0, 0.3, 76) + sub.z_top + 1.0], 1)
+    Q = np.zeros(76); R = np.resize(mol.R, 76); eps = np.resize(mol.eps, 76)
+    Eref, _ = substrate.pairwise_reference(pts, Q, R, eps, sub)
+    P, _ = substrate.factor_params(R, eps, 1.5)
+    VP, _, _, _ = substrate.morse_channels(pts, sub.xyz, sub.R, sub.eps, sub.cell)
+    bound = 3 * 5 / 384 * 0.1 ** 4 * 3.0 ** 4 * np.abs(P * VP) * math.exp(3.0 * 0.1) + 1e-9
+    err = {}
+    for ghost in (0, G):
+        vals, coefs, n, h = grid.build_grid(sub, origin, length, 0.1, channels=("P", "L"), ghost=ghost)
+        o = grid.node_origin(origin, length, 0.1, ghost)
+        E, F, below = grid.grid_energy_forces(coefs, ("P", "L"), o, h, pts, Q, R, eps, ghost=ghost)
+        assert not below.any()
+        err[ghost] = np.abs(E - Eref)
+        if ghost:
+            v0, _, _, _ = grid.build_grid(sub, origin, length, 0.1, channels=("P", "L"))
+            assert np.abs(vals[:, :, :, ghost:] - v0).max() <= 1e-12 * np.abs(v0).max()
+    assert (err[G] <= bound).all()
+    assert (err[0] > bound).mean() > 0.5 and err[0].max() > 10 * err[G].max()
