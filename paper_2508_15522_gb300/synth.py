@@ -79,7 +79,8 @@ def _params(elements):
 
 def rocksalt_slab(a: float = 5.64, ncell: int = 4, layers: int = 2,
                   charge: float = 0.7, grid_height: float = 20.0,
-                  z_gap: float = 1.0, vacuum_factor: float = 3.0) -> Substrate:
+                  z_gap: float = 1.0, vacuum_factor: float = 3.0,
+                  cation_morse: tuple | None = None) -> Substrate:
     """NaCl(001)-like slab: ``ncell`` x ``ncell`` primitive surface cells.
 
     Primitive in-plane vectors a1 = (a/2)(1, 1, 0), a2 = (a/2)(1, -1, 0), one
@@ -87,6 +88,8 @@ def rocksalt_slab(a: float = 5.64, ncell: int = 4, layers: int = 2,
     alternating between layers.  The orthogonal tile 2a x 2a is a period of
     the pristine slab.  The Ewald height Lz is ``vacuum_factor`` times the
     z-extent from the bottom layer to the top of the grid box.
+    ``cation_morse`` = (R, eps) replaces the cation's Morse parameters
+    (default: the Na entry of ELEMENTS).
     """
     a1 = np.array([a / 2, a / 2, 0.0])
     a2 = np.array([a / 2, -a / 2, 0.0])
@@ -105,7 +108,29 @@ def rocksalt_slab(a: float = 5.64, ncell: int = 4, layers: int = 2,
     Lz = vacuum_factor * (z_top + z_gap + grid_height)
     cell = np.array([ncell * a1, ncell * a2, [0.0, 0.0, Lz]])
     R, eps = _params(el)
+    if cation_morse is not None:
+        na = np.array(el) == "Na"
+        R[na], eps[na] = cation_morse
     return Substrate(xyz, np.array(q), R, eps, el, cell, z_top, (2 * a, 2 * a))
+
+
+# Cation Morse parameters (R [A], eps [sqrt(eV)]) of the minima-hopping
+# stand-in substrate, synthetic: a hard cation whose repulsive wall keeps
+# molecule atoms (charges up to +-0.3 e) at least 2 A above the top ion
+# plane over cations, anions and the anion vacancy alike, where the default
+# Na entry lets a negative atom sink into the vacancy below the grid floor.
+# With it the minima over the vacancy (O -0.3 e: 2.4 A, -1.44 eV) stay the
+# deepest, over cations 3.4-4.0 A and anions 3.2-3.5 A (pairwise Morse +
+# Ewald energies of single atoms, 4 x 4 x 3 slab with one Cl vacancy).
+HARD_CATION = (2.5, 0.3)
+
+
+def hopping_substrate() -> Substrate:
+    """Stand-in of the minima-hopping substrate (Sec. 7: NaCl(001) with a Cl
+    vacancy): the 4 x 4 primitive-cell, 3-layer rock-salt slab with hard
+    cations (HARD_CATION) and the top-layer anion nearest the supercell
+    centre removed."""
+    return with_top_vacancy(rocksalt_slab(a=5.64, ncell=4, layers=3, charge=0.7, cation_morse=HARD_CATION))
 
 
 def with_top_vacancy(sub: Substrate, element: str = "Cl") -> Substrate:
@@ -378,28 +403,38 @@ def random_flexible_molecule(n_atoms: int, n_torsions: int, seed: int) -> Molecu
     elements = list(g.choice(["C", "C", "C", "O"], size=n_heavy))
     parent = [-1] + [int(g.integers(max(0, k - 2), k)) for k in range(1, n_heavy)]
     pos = np.zeros((n_atoms, 3))
+    nbr = [[] for _ in range(n_atoms)]
+    cos_max = math.cos(math.radians(150.0))    # bond angles at most 150 degrees
 
-    def place(anchor, others, length, clearance):
-        # up to 200 random directions: the first that keeps `clearance` from
-        # every other atom, else the one farthest from its nearest atom
-        best, best_d = None, -1.0
+    def place(a, others, length, clearance):
+        # up to 200 random directions from atom a: the first that keeps
+        # `clearance` from every other atom and opens no angle wider than
+        # 150 degrees with a's bonds (near-linear angles leave the torsions
+        # about the bond ill-defined), else the best by (angle kept, distance
+        # to the nearest atom)
+        bonded = [(pos[j] - pos[a]) / np.linalg.norm(pos[j] - pos[a]) for j in nbr[a]]
+        best, best_key = None, None
         for _ in range(200):
             d = g.normal(size=3)
             d /= np.linalg.norm(d)
-            cand = anchor + length * d
+            cand = pos[a] + length * d
             near = np.linalg.norm(others - cand, axis=1).min() if len(others) else np.inf
-            if near > clearance:
+            angle_ok = all(float(d @ u) > cos_max for u in bonded)
+            if near > clearance and angle_ok:
                 return cand
-            if near > best_d:
-                best, best_d = cand, near
+            key = (angle_ok, near)
+            if best_key is None or key > best_key:
+                best, best_key = cand, key
         return best
 
     for k in range(1, n_heavy):
-        pos[k] = place(pos[parent[k]], np.delete(pos[:k], parent[k], axis=0), 1.50, 2.2)
+        pos[k] = place(parent[k], np.delete(pos[:k], parent[k], axis=0), 1.50, 2.2)
+        nbr[parent[k]].append(k); nbr[k].append(parent[k])
     bonds = [(parent[k], k) for k in range(1, n_heavy)]
     for h in range(n_h):
         host = int(g.integers(0, n_heavy))
-        pos[n_heavy + h] = place(pos[host], np.delete(pos[:n_heavy + h], host, axis=0), 1.09, 1.6)
+        pos[n_heavy + h] = place(host, np.delete(pos[:n_heavy + h], host, axis=0), 1.09, 1.6)
+        nbr[host].append(n_heavy + h); nbr[n_heavy + h].append(host)
         elements.append("H")
         bonds.append((host, n_heavy + h))
     xyz = pos.copy()
