@@ -41,6 +41,7 @@ BYTES_PER_EVAL = 768          # 64 stencil nodes x 3 channels x 4 B (algorithmic
 N_REP = 4096
 FIRE_ITERS = 2000
 SEED = 1002
+GHOST = 8                     # node planes below the grid floor (fit boundary far from the floor cells)
 
 
 def workload():
@@ -340,11 +341,13 @@ def minima_comparison(G, ctx, grid, mol, sub):
         Ph = np.concatenate([b.poses[m] for b, m in zip(bs, hm)])
         Eh = np.concatenate([b.energy[m] for b, m in zip(bs, hm)])
         n_hits = int(sum(m.sum() for m in hm))
-        out[name] = {"minima_per_s": n_hits / wall, "hit_fraction": n_hits / (4 * n_rep),
+        out[name] = {"minima_per_s": n_hits / wall, "hits_per_s": n_hits / wall, "hits": n_hits,
+                     "hit_fraction": n_hits / (4 * n_rep),
                      "converged_fraction": float(np.mean([b.converged.mean() for b in bs])),
                      "unique_of_best_set": len(sp.unique(Ph[:20000], Eh[:20000])) if n_hits else 0,
                      "wall_s": wall}
     out["gain"] = out["mlp"]["minima_per_s"] / max(out["random"]["minima_per_s"], 1e-30)
+    out["amortised"] = amortised_gain(out, int(h.sum()), gen_s, train_s)
     net.close()
     sp.close()
     low = np.argsort(E, kind="stable")[:8]
@@ -355,6 +358,27 @@ def minima_comparison(G, ctx, grid, mol, sub):
     out["error_vs_fp64_pairwise"] = grid_error_vs_pairwise(
         G, ctx, grid, sub, [(mol, v) for v in xl], "the 8 lowest converged minima of the training relaxations")
     return out
+
+
+def amortised_gain(out, train_hits, gen_s, train_s):
+    """The learned arm with the cost of its training: the random-start
+    relaxations that found the training targets (gen_s, which found
+    train_hits hits themselves) and the training (train_s) are charged to
+    it, and their hits credited.  After N proposal batches of b hits in t
+    seconds each: rate(N) = (train_hits + N b) / (gen_s + train_s + N t),
+    gain(N) = rate(N) / random rate; break-even N where gain = 1."""
+    r = out["random"]["hits_per_s"]
+    b = out["mlp"]["hits"] / out["batches"]
+    t = out["mlp"]["wall_s"] / out["batches"]
+    res = {"training_data_s": gen_s, "training_s": train_s, "training_hits": train_hits,
+           "proposal_batch_hits": b, "proposal_batch_s": t}
+    for n in (out["batches"], 16, 64, 256):
+        rate = (train_hits + n * b) / (gen_s + train_s + n * t)
+        res[f"hits_per_s_after_{n}_batches"] = rate
+        res[f"gain_after_{n}_batches"] = rate / max(r, 1e-30)
+    den = b - r * t
+    res["break_even_batches"] = (r * (gen_s + train_s) - train_hits) / den if den > 0 else None
+    return res
 
 
 def flexible_minima_comparison(G, ctx, grid, sub):
@@ -403,10 +427,12 @@ def flexible_minima_comparison(G, ctx, grid, sub):
         Xh = np.concatenate([b.poses[m] for b, m in zip(bs, hm)])
         Eh = np.concatenate([b.energy[m] for b, m in zip(bs, hm)])
         n_hits = int(sum(m.sum() for m in hm))
-        out[name] = {"minima_per_s": n_hits / wall, "hit_fraction": n_hits / (4 * n_rep),
+        out[name] = {"minima_per_s": n_hits / wall, "hits_per_s": n_hits / wall, "hits": n_hits,
+                     "hit_fraction": n_hits / (4 * n_rep),
                      "converged_fraction": float(np.mean([b.converged.mean() for b in bs])),
                      "unique_hits": len(sp.unique(Xh[:20000], Eh[:20000])) if n_hits else 0, "wall_s": wall}
     out["gain"] = out["mlp"]["minima_per_s"] / max(out["random"]["minima_per_s"], 1e-30)
+    out["amortised"] = amortised_gain(out, int(h.sum()), gen_s, train_s)
     net.close()
     sp.close()
     low = np.argsort(E, kind="stable")[:8]
@@ -439,17 +465,63 @@ def uneven_batch_comparison(G, ctx, grid, sub):
     * static: the same launch with the quad kernel and round-robin replica
       assignment (the layout before the tuner);
     * per-replica: one gridff_relax call per replica (a replica set of
-      one), timed on 64 replicas of the batch and scaled to 16384.
-    Throughput runs use f_conv = 0 (every replica does every iteration);
-    minima/s runs use f_conv = 1e-3 eV/A and count converged replicas."""
+      one), timed on 64 replicas of the batch (same starts) and scaled.
+    Throughput runs use f_conv = 0 (every replica does every iteration).
+    Minima runs use f_conv = 1e-3 eV/A; a relaxation is a minimum when it
+    converged with finite values and no atom below the grid floor.
+    Best-known energy per template: the lowest minimum of 8 further
+    random-start batches of all 16384 replicas (batched form).  A hit is a
+    minimum within 0.01 eV of its template's best-known energy; unique hits
+    are the hits left after the RMSD-0.1 A filter per template.  hits/s and
+    minima/s are per second of wall time of the arm's relaxation call."""
     from paper_2508_15522_gb300 import synth
     mols, tof = synth.uneven_batch(16384, 256, 77)
     reps = G.Replicas(ctx, mols, tof)
     x0 = uneven_positions(G, reps, mols, tof, sub, 5000)
-    out = {"replicas": len(tof), "atoms": int(reps.n_atoms), "templates": len(mols), "fire_iterations": 1000}
+    off = reps.atom_offset
+    n_rep = len(tof)
+    out = {"replicas": n_rep, "atoms": int(reps.n_atoms), "templates": len(mols), "fire_iterations": 1000,
+           "f_conv_eV_per_A": 1e-3, "tolerance_eV": 0.01, "rmsd_threshold_A": 0.1}
     best, log = G.tune(ctx, grid, reps, G.fire_params(f_conv=0.0), trial_steps=20)
     out["tuned_config"] = best.as_dict()
     out["tuner_trials"] = len(log)
+
+    def accepted_now():
+        fs = reps.fire_state()
+        x = reps.positions()
+        lowest = np.minimum.reduceat(x[:, 2], off[:-1])
+        ok = (((fs["status"] & G.REP_CONVERGED) != 0) & ((fs["status"] & G.REP_NONFINITE) == 0)
+              & (lowest >= grid.floor))
+        return ok, fs["energy"], x
+
+    graphs = {}
+
+    def batched(fconv):
+        if fconv not in graphs:
+            graphs[fconv] = G.RelaxGraph(ctx, grid, reps, 1000, G.fire_params(f_conv=fconv))
+        return graphs[fconv].launch()
+
+    # best-known energy of every template
+    e_best = np.full(len(mols), np.inf)
+    t0 = time.perf_counter()
+    for k in range(8):
+        reps.set_state(uneven_positions(G, reps, mols, tof, sub, 20_000 + 1000 * k))
+        batched(1e-3)
+        ok, E, _ = accepted_now()
+        np.minimum.at(e_best, tof[ok], E[ok])
+    out["best_known"] = {"batches": 8, "relaxations": 8 * n_rep, "seconds": time.perf_counter() - t0,
+                         "templates_with_a_minimum": int(np.isfinite(e_best).sum())}
+
+    def hits_of(ok, E, x, idx):
+        """hits and unique hits among replicas idx (minima within tolerance)."""
+        hit = ok & (E <= e_best[tof[idx]] + 0.01)
+        uniq = 0
+        for t in np.unique(tof[idx][hit]):
+            sel = np.where(hit & (tof[idx] == t))[0]
+            sel = sel[np.argsort(E[sel], kind="stable")]
+            X = np.stack([x[off[idx[r]]:off[idx[r] + 1]] for r in sel])
+            uniq += int((G.rmsd_unique_xyz(ctx, X, sub.tile, 0.1) < 0).sum())
+        return int(hit.sum()), uniq
 
     def measure(label, runner):
         res = {}
@@ -461,49 +533,62 @@ def uneven_batch_comparison(G, ctx, grid, sub):
             ms = ctx.last_kernel_ms()
             if key == "throughput":
                 res["atom_evals_per_s"] = r.atom_evals / (ms * 1e-3)
-                res["replica_steps_per_s"] = len(tof) * 1000 / (ms * 1e-3)
+                res["replica_steps_per_s"] = n_rep * 1000 / (ms * 1e-3)
                 res["kernel_ms"] = ms
             else:
-                res["minima_per_s"] = r.n_converged / wall
-                res["converged"] = int(r.n_converged)
-                res["wall_s"] = wall
+                ok, E, x = accepted_now()
+                n_hits, n_unique = hits_of(ok, E, x, np.arange(n_rep))
+                res.update({"minima": int(ok.sum()), "minima_per_s": int(ok.sum()) / wall, "hits": n_hits,
+                            "hits_per_s": n_hits / wall, "unique_hits": n_unique,
+                            "unique_hits_per_s": n_unique / wall, "wall_s": wall})
         out[label] = res
-
-    graphs = {}
-
-    def batched(fconv):
-        if fconv not in graphs:
-            graphs[fconv] = G.RelaxGraph(ctx, grid, reps, 1000, G.fire_params(f_conv=fconv))
-        return graphs[fconv].launch()
 
     measure("batched", batched)
     for g in graphs.values():
         g.close()
-    xr = reps.positions()
-    off = reps.atom_offset
+    ok, _, xr = accepted_now()
+    lowest = np.minimum.reduceat(xr[:, 2], off[:-1])
+    out["batched"]["below_floor_after_relaxation"] = int((lowest < grid.floor).sum())
+    pick = np.where(ok)[0]
+    pick = pick[np.linspace(0, len(pick) - 1, 8).astype(int)] if len(pick) else pick
     out["error_vs_fp64_pairwise"] = grid_error_vs_pairwise(
-        G, ctx, grid, sub, [(mols[tof[r]], xr[off[r]:off[r + 1]]) for r in np.linspace(0, len(tof) - 1, 8).astype(int)],
-        "8 replicas spread over the batch after the batched minima run (grid term)")
+        G, ctx, grid, sub, [(mols[tof[r]], xr[off[r]:off[r + 1]]) for r in pick],
+        "8 minima (accepted relaxations) spread over the batch after the batched minima run (grid term)")
     reps.set_launch_config(G.LaunchConfig(kernel=G.KERNEL_FLEX_QUAD, lanes_per_replica=32, warps_per_block=4,
                                           cache_slots=48, queue=0, l2_window=0))
     measure("static", lambda fconv: G.relax(ctx, grid, reps, 1000, G.fire_params(f_conv=fconv)))
     reps.close()
-    # plain per-replica relaxation on a sample
-    sample = np.linspace(0, len(tof) - 1, 64).astype(int)
-    conv, wall, evals = 0, 0.0, 0
+    # plain per-replica relaxation of 64 replicas of the batch from the same starts
+    sample = np.linspace(0, n_rep - 1, 64).astype(int)
+    x0r = x0.reshape(-1, 3)
+    wall, evals, ok_s, E_s, X_s = 0.0, 0, [], [], []
     for r in sample:
         m = mols[tof[r]]
         one = G.Replicas(ctx, [m], [0])
-        one.set_state(synth.flexible_positions(m, sub, 1, seed=7000 + int(r)).astype(np.float32).ravel())
+        one.set_state(np.ascontiguousarray(x0r[off[r]:off[r + 1]]).ravel())
         t0 = time.perf_counter()
         st, res = G.relax(ctx, grid, one, 1000, G.fire_params(f_conv=1e-3))
         wall += time.perf_counter() - t0
-        conv += res.n_converged
         evals += res.atom_evals
+        fs = one.fire_state()
+        xo = one.positions()
+        ok_s.append(bool((fs["status"][0] & G.REP_CONVERGED) and not (fs["status"][0] & G.REP_NONFINITE)
+                         and xo[:, 2].min() >= grid.floor))
+        E_s.append(fs["energy"][0])
+        X_s.append(xo)
         one.close()
-    scale = len(tof) / len(sample)
-    out["per_replica"] = {"minima_per_s": conv * scale / (wall * scale), "atom_evals_per_s": evals / wall,
-                          "sampled_replicas": len(sample), "projected_wall_s": wall * scale}
+    ok_s, E_s = np.array(ok_s), np.array(E_s)
+    hit_s = ok_s & (E_s <= e_best[tof[sample]] + 0.01)
+    per = wall / len(sample)
+    out["per_replica"] = {"sampled_replicas": len(sample), "wall_s": wall, "projected_wall_s": per * n_rep,
+                          "atom_evals_per_s": evals / wall, "minima": int(ok_s.sum()), "hits": int(hit_s.sum()),
+                          "minima_per_s": int(ok_s.sum()) / wall, "hits_per_s": int(hit_s.sum()) / wall,
+                          "hits_per_s_projected": out["batched"]["hits"] / (per * n_rep),
+                          "projection": "the batched run's hits over the per-replica time of all 16384 relaxations "
+                                        "(the same relaxations; the sampled hit count is small)"}
+    bh = out["batched"]["hits_per_s"]
+    out["hits_gain_vs_per_replica"] = bh / max(out["per_replica"]["hits_per_s_projected"], 1e-30)
+    out["hits_gain_vs_static"] = bh / max(out["static"]["hits_per_s"], 1e-30)
     out["minima_gain_vs_per_replica"] = out["batched"]["minima_per_s"] / max(out["per_replica"]["minima_per_s"],
                                                                             1e-30)
     out["minima_gain_vs_static"] = out["batched"]["minima_per_s"] / max(out["static"]["minima_per_s"], 1e-30)
@@ -531,7 +616,7 @@ def precision_comparison(G, ctx):
     out = {"grid": None, "replicas": n_rep, "atoms_per_replica": mol.n, "fire_iterations": 200}
     errs = {}
     t0 = time.perf_counter()
-    grid32 = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, channels=G.CH_P | G.CH_L,
+    grid32 = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, ghost_below=GHOST, channels=G.CH_P | G.CH_L,
                           keep_f64=True)
     out["build_s"] = time.perf_counter() - t0
     coefs = grid32.download_f64("coefs")
@@ -684,8 +769,9 @@ def interpolation_roofline(G, ctx, grid, box, torch, dev, stream, l2_peak):
 
 def minima_hopping_curve(G, ctx):
     """Minima hopping (Sec. 7) of a flexible 22-atom molecule on a NaCl(001)
-    slab with a Cl vacancy (4 x 4 primitive cells, 3 layers, 95 atoms; grid
-    over the 22.56 x 22.56 A defect period, 0.1 A): 5000 replicas, 12 hops
+    slab with a Cl vacancy (4 x 4 primitive cells, 3 layers, 95 atoms, hard
+    cations: synth.hopping_substrate; grid over the 22.56 x 22.56 A defect
+    period, 0.1 A, 8 ghost planes below the floor): 5000 replicas, 12 hops
     of 1000 Langevin steps at 300 K (dt 1 fs, gamma 0.01/fs), FIRE to
     1e-4 eV/A (at most 5000 iterations) and the RMSD-0.1 A filter against
     every minimum found so far; relaxed structures with an atom below the
@@ -693,13 +779,13 @@ def minima_hopping_curve(G, ctx):
     Returns the unique-minima-vs-time curve."""
     from paper_2508_15522_gb300 import sampling as S
     from paper_2508_15522_gb300 import synth
-    sub = synth.with_top_vacancy(synth.rocksalt_slab(a=5.64, ncell=4, layers=3, charge=0.7))
+    sub = synth.hopping_substrate()
     box = synth.grid_box_for(sub, 0.1, height=20.0)
     t0 = time.perf_counter()
-    grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing)
+    grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, ghost_below=GHOST)
     build_s = time.perf_counter() - t0
     mol = synth.random_flexible_molecule(22, 4, 2222)
-    x0 = synth.flexible_positions(mol, sub, 5000, seed=2223, h_lo=3.0, h_hi=4.0)
+    x0 = synth.flexible_positions(mol, sub, 5000, seed=2223, h_lo=3.5, h_hi=4.5, min_clear=3.0)
     mh = S.MinimaHopping(ctx, grid, mol, x0, sub.tile)
     curve = [mh.hop() for _ in range(12)]
     out = {"replicas": 5000, "atoms": mol.n, "grid": list(grid.dims), "grid_build_s": build_s, "hops": len(curve),
@@ -739,7 +825,7 @@ def run_gpu(args):
     assert ctx.stream == stream.cuda_stream
 
     sub, box, mol, pose = workload()
-    grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing)
+    grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, ghost_below=GHOST)
     reps = G.Replicas(ctx, [mol], [0] * N_REP, rigid=True)
     pose_dev = torch.from_numpy(pose.ravel()).to(dev)
     params = G.fire_params(f_conv=0.0)
@@ -856,7 +942,9 @@ def profile_case(args):
     the interpolation-only workload of the bench line), twice in the direct
     layout, then twice binned; `nve` runs 200 rigid
     NVE steps of the bench's 4096 replicas, relaxed and given 300 K
-    velocities as in the bench's NVE run.  Each runs its launch twice (the
+    velocities as in the bench's NVE run; `fcc-f32`, `fcc-f16`, `fcc-bf16`
+    relax the 65536 rigid replicas of the fcc(111) precision workload for 20
+    FIRE iterations on the tier's grid.  Each runs its launch twice (the
     second is the one to capture with -s)."""
     import __graft_entry__ as ge
     ge.build()
@@ -865,7 +953,7 @@ def profile_case(args):
     ctx = G.Context(0)
     if args.profile_case in ("uneven", "langevin"):
         sub, box, _, _ = workload()
-        grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing)
+        grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, ghost_below=GHOST)
         mols, tof = synth.uneven_batch(16384, 256, 77)
         tof = tof[:4096]
         reps = G.Replicas(ctx, mols, tof)
@@ -891,7 +979,7 @@ def profile_case(args):
         print("mlp trained")
     elif args.profile_case == "nve":
         sub, box, mol, pose = workload()
-        grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing)
+        grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, ghost_below=GHOST)
         reps = G.Replicas(ctx, [mol], [0] * N_REP, rigid=True)
         reps.set_state(pose.ravel())
         G.relax(ctx, grid, reps, FIRE_ITERS, G.fire_params(f_conv=0.0))      # as the bench's NVE run
@@ -901,10 +989,26 @@ def profile_case(args):
             reps.set_state(x, vel.ravel())
             G.run(ctx, grid, reps, 200, dt=1.0)
         print("nve kernel ms", ctx.last_kernel_ms())
+    elif args.profile_case in ("fcc-f32", "fcc-f16", "fcc-bf16"):
+        sub = synth.fcc111_slab(a=4.08, ncell=12, layers=4)
+        box = synth.grid_box_for(sub, 0.05, height=20.0)
+        mol = synth.rigid_molecule(24, 2024)
+        com, quat = synth.rigid_poses(mol, sub, 65536, seed=2025)
+        pose = np.concatenate([com, quat], 1).astype(np.float32).ravel()
+        grid32 = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, ghost_below=GHOST,
+                              channels=G.CH_P | G.CH_L, keep_f64=True)
+        st = {"fcc-f32": G.STORE_F32, "fcc-f16": G.STORE_F16, "fcc-bf16": G.STORE_BF16}[args.profile_case]
+        grid = grid32 if st == G.STORE_F32 else G.grid_from_coefs(ctx, grid32.download_f64("coefs"), grid32.origin,
+                                                                  grid32.spacing, G.CH_P | G.CH_L, storage=st)
+        reps = G.Replicas(ctx, [mol], [0] * 65536, rigid=True)
+        for _ in range(2):
+            reps.set_state(pose)
+            G.relax(ctx, grid, reps, 20, G.fire_params(f_conv=0.0))
+        print(args.profile_case, "kernel ms", ctx.last_kernel_ms(), "grid bytes", grid.device_bytes)
     elif args.profile_case == "interp":
         import torch
         sub, box, _, _ = workload()
-        grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing)
+        grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, ghost_below=GHOST)
         n = 65536 * 38
         mol = synth.rigid_molecule(38, 3003)
         reps = G.Replicas(ctx, [mol], [0])
@@ -930,7 +1034,8 @@ def main():
                     help="FIRE iterations per step (profiling runs use a short step)")
     ap.add_argument("--quick", action="store_true",
                     help="skip the e2e leg, the bandwidth probes and the CPU baseline (profiling runs)")
-    ap.add_argument("--profile-case", choices=["uneven", "langevin", "mlp", "interp", "nve"], default=None,
+    ap.add_argument("--profile-case", choices=["uneven", "langevin", "mlp", "interp", "nve", "fcc-f32", "fcc-f16",
+                                               "fcc-bf16"], default=None,
                     help="run one small kernel case for an ncu capture and exit (no JSON line)")
     args = ap.parse_args()
     if args.profile_case:

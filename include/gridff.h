@@ -73,8 +73,9 @@ typedef enum {
  * zero unless GRIDFF_CONTINUE, the MD calls may carry BELOW and NONFINITE
  * over from earlier calls */
 #define GRIDFF_REP_CONVERGED 1   /* FIRE force norm fell below f_conv */
-#define GRIDFF_REP_BELOW 2       /* an atom was below the grid at some evaluation
-                                    (evaluated on the grid's bottom plane) */
+#define GRIDFF_REP_BELOW 2       /* an atom was below the grid's floor at some evaluation
+                                    (evaluated on its ghost planes, or clamped to the
+                                    lowest node plane below them) */
 #define GRIDFF_REP_NONFINITE 4   /* a force or position was NaN/Inf: replica frozen */
 #define GRIDFF_REP_ABORTED 8     /* stopped by the abort flag before finishing */
 #define GRIDFF_REP_STEPLIMIT 16  /* stopped by the clock budget before finishing */
@@ -154,6 +155,15 @@ typedef struct {
   int32_t storage;     /* GRIDFF_STORE_*, default F32 */
   int32_t keep_f64;    /* keep the FP64 node values and coefficients for
                           gridff_grid_download_f64 */
+  int32_t ghost_below; /* node planes below the box (0..64, default 0): the
+                          node values are also computed at z0 - k dz,
+                          k = 1..ghost_below, and fitted with the rest, so
+                          that the clamped end of the fit lies that far below
+                          the floor z0; the floor stays z0 (points below it
+                          are flagged GRIDFF_REP_BELOW).  The grid's nodes
+                          (gridff_grid_info) then start at z0 - ghost_below dz,
+                          which must lie more than 0.1 A above every substrate
+                          atom (else EINVAL) */
 } gridff_grid_opts;
 
 /* Fill opts with the defaults above (origin/length/spacing zeroed). */
@@ -163,7 +173,8 @@ void gridff_grid_opts_default(gridff_grid_opts* opts);
  * node values V^C (3D Ewald sum with the slab dipole correction, FP64),
  * V^P, V^L (direct sums over atoms and in-plane images within rcut, FP64),
  * then the exact B-spline coefficients (separable line solves, FP64:
- * periodic in x, y; clamped end coefficients in z), stored as `storage`.
+ * periodic in x, y; clamped end coefficients in z, at the lowest ghost
+ * plane when opts->ghost_below > 0), stored as `storage`.
  * Substrate arrays are host pointers.  Errors: EINVAL (sizes, cell, box),
  * ENOMEM, ECUDA. */
 gridff_status gridff_build_grid(gridff_ctx* ctx, const gridff_substrate* sub,
@@ -204,7 +215,14 @@ gridff_status gridff_grid_from_coefs(gridff_ctx* ctx, const double origin[3],
 gridff_status gridff_fit_coefs_noalloc(gridff_ctx* ctx, const double* values, double* coefs,
                                        const int32_t dims[3], int32_t n_channels, int flags);
 
-/* Grid metadata; any output pointer may be NULL. */
+/* The floor of the grid (A): the lowest z of its domain; evaluations
+ * below it are flagged GRIDFF_REP_BELOW.  The box origin z0 of
+ * gridff_build_grid (its nodes start ghost_below planes lower), the first
+ * node plane of gridff_grid_from_coefs. */
+gridff_status gridff_grid_floor(const gridff_grid* grid, double* z_floor);
+
+/* Grid metadata; any output pointer may be NULL.  dims and origin describe
+ * the node lattice, ghost planes included. */
 gridff_status gridff_grid_info(const gridff_grid* grid, int32_t dims[3], double origin[3],
                                double spacing[3], int32_t* channels, size_t* device_bytes);
 

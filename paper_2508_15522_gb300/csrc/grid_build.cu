@@ -592,6 +592,7 @@ GridView gridff_grid::view() const {
   v.Ly = (float)(spacing[1] * dims[1]);
   v.inv_Lx = (float)(1.0 / (spacing[0] * dims[0]));
   v.inv_Ly = (float)(1.0 / (spacing[1] * dims[1]));
+  v.uzf = (float)ghost;
   return v;
 }
 
@@ -639,14 +640,29 @@ gridff_status gridff_build_grid(gridff_ctx* ctx, const gridff_substrate* sub,
   g->channels = chans;
   int sC, sP, sL;
   channel_slots(chans, sC, sP, sL, g->n_ch);
+  if (opts->ghost_below < 0 || opts->ghost_below > 64) {
+    delete g;
+    return set_err(ctx, GRIDFF_EINVAL, "ghost_below = %d outside 0..64", opts->ghost_below);
+  }
   for (int a = 0; a < 3; ++a) {
     g->dims[a] = (int)ceil(opts->length[a] / opts->spacing - 1e-9);
     g->spacing[a] = opts->length[a] / g->dims[a];
     g->origin[a] = opts->origin[a];
   }
+  // ghost planes: nodes also below the box; the floor stays at its face
+  g->ghost = opts->ghost_below;
+  g->floor_z = opts->origin[2];
+  g->dims[2] += g->ghost;
+  g->origin[2] = opts->origin[2] - g->ghost * g->spacing[2];
   if (!dims_ok(g->dims)) {
     delete g;
     return set_err(ctx, GRIDFF_EINVAL, "grid needs at least 4 nodes per axis");
+  }
+  if (g->ghost > 0 && !(g->origin[2] > zmax + 0.1)) {
+    const double low = g->origin[2];
+    delete g;
+    return set_err(ctx, GRIDFF_EINVAL,
+                   "ghost planes reach z = %g, not above the substrate's highest atom (z = %g) by 0.1 A", low, zmax);
   }
   double alpha = opts->alpha > 0 ? opts->alpha : 1.5;
   double rcut = opts->rcut > 0 ? opts->rcut : 17.0;
@@ -833,6 +849,7 @@ gridff_status gridff_grid_from_coefs(gridff_ctx* ctx, const double origin[3], co
     g->origin[a] = origin[a];
     g->spacing[a] = spacing[a];
   }
+  g->floor_z = origin[2];
   size_t n = (size_t)dims[0] * dims[1] * dims[2] * g->n_ch;
   DevFree df;
   double* d = nullptr;
@@ -910,6 +927,12 @@ gridff_status gridff_fit_coefs_noalloc(gridff_ctx* ctx, const double* values, do
       coefs, nx, (long long)ny * nz, lines, ny * nz, 1, N, tab, 1);
   GRIDFF_CUDA(ctx, cudaGetLastError());
   if (!(flags & GRIDFF_ASYNC)) GRIDFF_CUDA(ctx, cudaStreamSynchronize(s));
+  return GRIDFF_OK;
+}
+
+gridff_status gridff_grid_floor(const gridff_grid* g, double* z_floor) {
+  if (!g || !z_floor) return GRIDFF_EINVAL;
+  *z_floor = g->floor_z;
   return GRIDFF_OK;
 }
 

@@ -88,6 +88,7 @@ struct GridView {
   float x0, y0, z0;
   float inv_dx, inv_dy, inv_dz;
   float Lx, Ly, inv_Lx, inv_Ly;
+  float uzf;             // floor in z spacings above the first node (ghost planes)
 };
 
 struct gridff_grid {
@@ -106,6 +107,8 @@ struct gridff_grid {
   double* f64_values = nullptr;   // [C][nx][ny][nz] if kept
   double* f64_coefs = nullptr;
   int n_ch = 0;                   // channels present, in order C, P, L
+  int ghost = 0;                  // node planes below the floor
+  double floor_z = 0.0;           // floor = origin[2] + ghost * spacing[2]
   GridView view() const;
 };
 

@@ -45,7 +45,7 @@ __device__ __forceinline__ Cell locate(const GridView& g, bool act, float x, flo
   if (iy >= g.ny) iy -= g.ny;
   c.ix = min(max(ix, 0), g.nx - 1);     // any input, even non-finite, stays in bounds
   c.iy = min(max(iy, 0), g.ny - 1);
-  if (act && uz < 0.f) flags |= GRIDFF_REP_BELOW;
+  if (act && uz < g.uzf) flags |= GRIDFF_REP_BELOW;   // below the floor (ghost planes or lower)
   uz = fmaxf(uz, 0.f);
   c.inside = act && (uz < (float)(g.nz - 1));   // above the grid (or NaN): field ~ 0
   float flz = floorf(c.inside ? uz : 0.f);

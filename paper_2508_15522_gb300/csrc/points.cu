@@ -22,8 +22,9 @@
 //      before it);
 //   2. exclusive scan of the bin counts (three passes: tile sums, scan of
 //      the tile sums in one block, scan inside each tile);
-//   3. scatter: sorted position = start of the bin + rank;
-//   4. evaluate in sorted order, results written at the original index.
+//   3. scatter: the point's position, factors and index go to sorted
+//      position = start of the bin + rank (one 32-byte record);
+//   4. evaluate the records in order, results written at the original index.
 #include <math.h>
 
 #include <cuda_bf16.h>
@@ -143,12 +144,23 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(const int* __r
     }
 }
 
+// A point in sorted order: position and charge, then the two Morse factors
+// and the point's original index (32 bytes, one sector).
+struct SortedPoint {
+  float4 xyzq;
+  float4 pli;   // P, L, index (bit pattern), unused
+};
+
 __global__ void bin_scatter_kernel(int n, const int2* __restrict__ keyrank, const int* __restrict__ start,
-                                   int* __restrict__ perm) {
+                                   const float* __restrict__ xyz, const float* __restrict__ qpl,
+                                   SortedPoint* __restrict__ sorted) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int2 kr = keyrank[i];
-  perm[start[kr.x] + kr.y] = i;
+  SortedPoint p;
+  p.xyzq = make_float4(xyz[3 * (size_t)i], xyz[3 * (size_t)i + 1], xyz[3 * (size_t)i + 2], qpl[3 * (size_t)i]);
+  p.pli = make_float4(qpl[3 * (size_t)i + 1], qpl[3 * (size_t)i + 2], __int_as_float(i), 0.f);
+  sorted[start[kr.x] + kr.y] = p;
 }
 
 // Channel-combined values of one z-run (four consecutive records from
@@ -209,21 +221,20 @@ __device__ __forceinline__ void run_values(const GridView& g, long long base, fl
 }
 
 #ifndef GRIDFF_SORTED_MINB
-#define GRIDFF_SORTED_MINB 2
+#define GRIDFF_SORTED_MINB 4
 #endif
-// One lane per point, points taken in sorted order (perm), results written
-// at the point's own index.
+// One lane per point, points taken in sorted order (contiguous records),
+// results written at the point's own index.
 template <int KIND>
 __global__ void __launch_bounds__(kEvalThreads, GRIDFF_SORTED_MINB)
-eval_sorted_kernel(GridView g, int n, const int* __restrict__ perm, const float* __restrict__ xyz,
-                   const float* __restrict__ qpl, float* __restrict__ E, float* __restrict__ F,
-                   int* __restrict__ st) {
+eval_sorted_kernel(GridView g, int n, const SortedPoint* __restrict__ sorted, float* __restrict__ E,
+                   float* __restrict__ F, int* __restrict__ st) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  const int i = __ldg(&perm[j]);
-  const float x = __ldg(&xyz[3 * (size_t)i]), y = __ldg(&xyz[3 * (size_t)i + 1]), z = __ldg(&xyz[3 * (size_t)i + 2]);
-  const float fc = __ldg(&qpl[3 * (size_t)i]) * g.sC, fp = __ldg(&qpl[3 * (size_t)i + 1]) * g.sP,
-              fl = __ldg(&qpl[3 * (size_t)i + 2]) * g.sL;
+  const float4 a4 = __ldg(&sorted[j].xyzq), b4 = __ldg(&sorted[j].pli);
+  const int i = __float_as_int(b4.z);
+  const float x = a4.x, y = a4.y, z = a4.z;
+  const float fc = a4.w * g.sC, fp = b4.x * g.sP, fl = b4.y * g.sL;
   // a non-finite position is reported and evaluates to zero
   const bool fin = isfinite(x) && isfinite(y) && isfinite(z);
   int flags = fin ? 0 : GRIDFF_REP_NONFINITE;
@@ -285,14 +296,14 @@ gridff_status enqueue_eval_points_binned(gridff_ctx* ctx, const gridff_grid* gri
   const int n_tiles = (nb + kScanTile - 1) / kScanTile;
   cudaStream_t s = ctx->stream;
   const size_t b_counts = ((size_t)nb * 4 + 255) & ~size_t(255), b_tiles = ((size_t)n_tiles * 4 + 255) & ~size_t(255),
-               b_kr = ((size_t)ni * 8 + 255) & ~size_t(255), b_perm = (size_t)ni * 4;
+               b_kr = ((size_t)ni * 8 + 255) & ~size_t(255), b_sorted = (size_t)ni * sizeof(SortedPoint);
   char* scratch = nullptr;
-  GRIDFF_CUDA(ctx, cudaMallocAsync((void**)&scratch, 2 * b_counts + b_tiles + b_kr + b_perm, s));
+  GRIDFF_CUDA(ctx, cudaMallocAsync((void**)&scratch, 2 * b_counts + b_tiles + b_kr + b_sorted, s));
   int* counts = (int*)scratch;
   int* start = (int*)(scratch + b_counts);
   int* tiles = (int*)(scratch + 2 * b_counts);
   int2* keyrank = (int2*)(scratch + 2 * b_counts + b_tiles);
-  int* perm = (int*)(scratch + 2 * b_counts + b_tiles + b_kr);
+  SortedPoint* sorted = (SortedPoint*)(scratch + 2 * b_counts + b_tiles + b_kr);
   cudaError_t e = cudaMemsetAsync(counts, 0, (size_t)nb * 4, s);
   const int pb = (ni + 255) / 256;
   if (e == cudaSuccess) {
@@ -300,12 +311,12 @@ gridff_status enqueue_eval_points_binned(gridff_ctx* ctx, const gridff_grid* gri
     scan_tiles_kernel<<<n_tiles, kScanThreads, 0, s>>>(counts, nb, tiles);
     scan_top_kernel<<<1, kScanThreads, 0, s>>>(tiles, n_tiles);
     scan_apply_kernel<<<n_tiles, kScanThreads, 0, s>>>(counts, nb, tiles, start);
-    bin_scatter_kernel<<<pb, 256, 0, s>>>(ni, keyrank, start, perm);
+    bin_scatter_kernel<<<pb, 256, 0, s>>>(ni, keyrank, start, xyz, qpl, sorted);
     const int eb = (ni + kEvalThreads - 1) / kEvalThreads;
     if (grid->kind == REC_F32x4)
-      eval_sorted_kernel<REC_F32x4><<<eb, kEvalThreads, 0, s>>>(g, ni, perm, xyz, qpl, E, F, status);
+      eval_sorted_kernel<REC_F32x4><<<eb, kEvalThreads, 0, s>>>(g, ni, sorted, E, F, status);
     else
-      eval_sorted_kernel<-1><<<eb, kEvalThreads, 0, s>>>(g, ni, perm, xyz, qpl, E, F, status);
+      eval_sorted_kernel<-1><<<eb, kEvalThreads, 0, s>>>(g, ni, sorted, E, F, status);
     e = cudaGetLastError();
   }
   const cudaError_t ef = cudaFreeAsync(scratch, s);

@@ -45,7 +45,7 @@ class GridOpts(C.Structure):
     _fields_ = [("origin", C.c_double * 3), ("length", C.c_double * 3), ("spacing", C.c_double),
                 ("alpha", C.c_double), ("rcut", C.c_double), ("ewald_tol", C.c_double),
                 ("ewald_rcut", C.c_double), ("channels", C.c_int32), ("storage", C.c_int32),
-                ("keep_f64", C.c_int32)]
+                ("keep_f64", C.c_int32), ("ghost_below", C.c_int32)]
 
 
 class Molecule(C.Structure):
@@ -119,6 +119,7 @@ def _load():
                                    C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_size_t)]),
         "gridff_grid_download_f64": (I32, [P, C.c_int, C.POINTER(C.c_double)]),
         "gridff_grid_storage": (I32, [P, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
+        "gridff_grid_floor": (I32, [P, C.POINTER(C.c_double)]),
         "gridff_langevin": (I32, [P, P, P, I32, C.POINTER(LangevinParams), C.c_int]),
         "gridff_mlp_set_targets": (I32, [P, I32, P, P]),
         "gridff_mlp_train": (I32, [P, I32, I32, I32, P, I32, C.c_uint64, C.POINTER(TrainParams), P]),
@@ -185,7 +186,7 @@ EXPORTED = (
     "gridff_mlp_get_params", "gridff_mlp_forward", "gridff_mlp_train_step", "gridff_mlp_propose",
     "gridff_molecule_descriptor", "gridff_random_poses", "gridff_rmsd_unique",
     "gridff_set_launch_config", "gridff_get_launch_config", "gridff_tune", "gridff_relax_graph_create",
-    "gridff_grid_storage", "gridff_langevin", "gridff_rmsd_unique_xyz", "gridff_mlp_set_targets",
+    "gridff_grid_storage", "gridff_grid_floor", "gridff_langevin", "gridff_rmsd_unique_xyz", "gridff_mlp_set_targets",
     "gridff_mlp_train",
     "gridff_graph_launch", "gridff_graph_destroy", "gridff_template_rotors", "gridff_build_poses",
     "gridff_pose_targets", "gridff_eval_points", "gridff_template_factors",
@@ -268,6 +269,11 @@ class Grid:
         st = C.c_int32(); sc = (C.c_float * 3)()
         ctx.check(lib.gridff_grid_storage(handle, C.byref(st), sc))
         self.storage, self.scales = st.value, tuple(sc)
+        fl = C.c_double()
+        ctx.check(lib.gridff_grid_floor(handle, C.byref(fl)))
+        self.floor = fl.value
+        # node planes below the floor
+        self.ghost = int(round((self.floor - self.origin[2]) / self.spacing[2]))
 
     @property
     def n_channels(self):
@@ -293,8 +299,9 @@ class Grid:
 
 def build_grid(ctx: Context, sub, origin, length, spacing, channels=CH_C | CH_P | CH_L,
                alpha=1.5, rcut=17.0, ewald_tol=1e-10, ewald_rcut=12.0, keep_f64=False,
-               storage=STORE_F32) -> Grid:
-    """gridff_build_grid: substrate (object with xyz, q, R, eps, cell) -> Grid."""
+               storage=STORE_F32, ghost_below=0) -> Grid:
+    """gridff_build_grid: substrate (object with xyz, q, R, eps, cell) -> Grid.
+    `origin` is the floor; `ghost_below` node planes are added under it."""
     xyz = np.ascontiguousarray(sub.xyz, np.float64).ravel()
     q = np.ascontiguousarray(sub.q, np.float64)
     R = np.ascontiguousarray(sub.R, np.float64)
@@ -308,7 +315,7 @@ def build_grid(ctx: Context, sub, origin, length, spacing, channels=CH_C | CH_P 
     o.length = (C.c_double * 3)(*length)
     o.spacing, o.alpha, o.rcut = spacing, alpha, rcut
     o.ewald_tol, o.ewald_rcut, o.channels, o.keep_f64 = ewald_tol, ewald_rcut, channels, int(keep_f64)
-    o.storage = storage
+    o.storage, o.ghost_below = storage, int(ghost_below)
     h = C.c_void_p()
     ctx.check(lib.gridff_build_grid(ctx.h, C.byref(s), C.byref(o), C.byref(h)))
     return Grid(ctx, h)

@@ -150,7 +150,7 @@ class FlexSampler:
         fs = self.reps.fire_state()
         x = self.reps.positions().reshape(self.n_rep, self.mol.n, 3)
         wall = time.perf_counter() - t0
-        conv = accepted(fs["status"], x, self.grid.origin[2])
+        conv = accepted(fs["status"], x, self.grid.floor)
         return Batch(x, fs["energy"], conv, wall, self.ctx.last_kernel_ms())
 
     def random_batch(self, seed: int) -> Batch:
@@ -279,8 +279,8 @@ class MinimaHopping:
         G.relax(self.ctx, self.grid, self.reps, self.relax_steps, self.fire, check=False)
         fs = self.reps.fire_state()
         x = self.reps.positions().reshape(self.x0.shape)
-        conv = accepted(fs["status"], x, self.grid.origin[2])
-        lost = ((fs["status"] & G.REP_NONFINITE) != 0) | (x[..., 2] < self.grid.origin[2]).any(axis=-1)
+        conv = accepted(fs["status"], x, self.grid.floor)
+        lost = ((fs["status"] & G.REP_NONFINITE) != 0) | (x[..., 2] < self.grid.floor).any(axis=-1)
         self.below.append(int(np.count_nonzero(lost)))
         cand_x, cand_E = x[conv], fs["energy"][conv]
         order = np.argsort(cand_E, kind="stable")

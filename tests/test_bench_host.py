@@ -50,3 +50,20 @@ def test_grid_error_report_bookkeeping():
     assert abs(r["max_abs_dE_per_molecule_eV"] - m2.n * dE) < 1e-12
     assert abs(r["max_abs_dE_per_atom_eV"] - dE) < 1e-15
     assert abs(r["max_abs_dF_eV_per_A"] - dF) < 1e-15
+
+
+def test_amortised_gain_charges_training_and_credits_its_hits():
+    """The learned arm's amortised rate: training-data relaxations and
+    training time charged, their hits credited; break-even where the
+    amortised rate equals the random-start rate."""
+    import bench
+    out = {"batches": 4, "random": {"hits_per_s": 100.0},
+           "mlp": {"hits": 4000, "wall_s": 4.0}}
+    a = bench.amortised_gain(out, train_hits=250, gen_s=2.5, train_s=1.0)
+    assert a["proposal_batch_hits"] == 1000 and a["proposal_batch_s"] == 1.0
+    assert abs(a["hits_per_s_after_4_batches"] - (250 + 4000) / (3.5 + 4.0)) < 1e-12
+    assert abs(a["gain_after_4_batches"] - (4250 / 7.5) / 100.0) < 1e-12
+    n = a["break_even_batches"]
+    assert abs((250 + n * 1000) / (3.5 + n * 1.0) - 100.0) < 1e-9
+    out["mlp"]["hits"] = 400                      # proposals no better than random starts: no break-even
+    assert bench.amortised_gain(out, 250, 2.5, 1.0)["break_even_batches"] is None

@@ -304,3 +304,61 @@ def test_interpolation_error_against_pairwise_reference(G, ctx, storage):
           "max |dF| per atom:", np.abs(F - Fref).max(), "eV/A")
     assert dE_mol.max() < 2e-4
     assert np.abs(F - Fref).max() < 5e-3
+
+
+def test_build_grid_with_ghost_planes_matches_oracle(G, ctx):
+    """Ghost planes below the floor: node values and coefficients of every
+    plane (ghosts included) against the oracle's ghost build, FP64 on both
+    sides; the node lattice starts ghost spacings below the floor."""
+    sub = synth.rocksalt_slab(ncell=2)
+    origin, length, h, ghost = (0.0, 0.0, sub.z_top + 1.0), (11.28, 11.28, 2.4), 0.3, 2
+    grid = G.build_grid(ctx, sub, origin, length, h, keep_f64=True, ghost_below=ghost)
+    vals, coefs, n, hh = ogrid.build_grid(sub, origin, length, h, ewald=osub.ewald_params(1e-10, 12.0),
+                                          ghost=ghost)
+    assert grid.dims == n and grid.ghost == ghost
+    assert grid.floor == origin[2]
+    assert abs(grid.origin[2] - ogrid.node_origin(origin, length, h, ghost)[2]) < 1e-12
+    vg, cg = grid.download_f64("values"), grid.download_f64("coefs")
+    for c in range(3):
+        assert np.abs(vg[c] - vals[c]).max() <= 1e-8 * np.abs(vals[c]).max(), c
+        assert np.abs(cg[c] - coefs[c]).max() <= 1e-7 * np.abs(coefs[c]).max(), c
+    grid.close()
+
+
+def test_eval_across_the_floor_with_ghost_planes(G, ctx):
+    """Points from 0.4 A below to 0.6 A above the floor of a grid with 3
+    ghost planes (0.2 A spacing, down to 0.4 A above the top ions): both point layouts against the oracle's
+    FP32 mirror on the same coefficients; BELOW exactly where the oracle
+    puts it (below the floor, not below the first node).  The field here is
+    the Pauli wall of the top ions (|F| up to about 100 eV/A), so the gates
+    are relative to the magnitude, as in the full-size near-floor check."""
+    sub = synth.rocksalt_slab(ncell=2)
+    box = synth.grid_box_for(sub, 0.2, height=4.0)
+    grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, keep_f64=True, ghost_below=3)
+    c32 = grid.download_f64("coefs").astype(np.float32).astype(np.float64)
+    mol = _point_molecule(40)
+    g = synth.rng(33)
+    n = 40 * 50
+    pts = np.stack([g.uniform(0, box.length[0], n), g.uniform(0, box.length[1], n),
+                    grid.floor + g.uniform(-0.4, 0.6, n)], 1).astype(np.float32)
+    near = np.abs(pts[:, 2].astype(np.float64) - grid.floor) < 1e-4
+    pts[near, 2] += 1e-3                                  # no point on the floor itself
+    reps = G.Replicas(ctx, [mol], [0])
+    fac = reps.template_factors(0)
+    k = np.arange(n) % 40
+    Eo, Fo, below = _oracle_grid(c32, ("C", "P", "L"), grid.origin, grid.spacing, pts, mol.q[k], mol.R[k],
+                                 mol.eps[k], np.float32)
+    _, _, below_g = ogrid.grid_energy_forces(c32, ("C", "P", "L"), grid.origin, grid.spacing, pts, mol.q[k],
+                                             mol.R[k], mol.eps[k], dtype=np.float32, ghost=3)
+    assert 0.2 < below_g.mean() < 0.6 and not below[pts[:, 2] >= grid.origin[2]].any()
+    assert np.isfinite(Fo).all()
+    # ghost planes that would reach the substrate's atoms are refused
+    with pytest.raises(G.GridffError):
+        G.build_grid(ctx, sub, box.origin, box.length, box.spacing, ghost_below=6)
+    for flags in (0, G.POINTS_BINNED):
+        E, F, S = G.eval_points(ctx, grid, pts, fac[k], flags=flags)
+        assert (np.abs(F - Fo) <= TOL_F * np.maximum(1.0, np.abs(Fo))).all()
+        assert (np.abs(E - Eo) <= TOL_E * np.maximum(1.0, np.abs(Eo))).all()
+        assert np.array_equal((S & G.REP_BELOW) != 0, below_g)
+    reps.close()
+    grid.close()

@@ -48,12 +48,13 @@ def ctx(G):
 
 @pytest.fixture(scope="module")
 def nacl(G, ctx):
-    """The 113 x 113 x 200 FP32 grid of the 8 x 8 x 3 NaCl(001) slab and its
+    """The 113 x 113 x 200 FP32 grid of the 8 x 8 x 3 NaCl(001) slab with
+    8 ghost planes below its floor, as the benchmark builds it, and its
     coefficients rounded to FP32 (what the kernels read)."""
     sub = synth.rocksalt_slab(a=5.64, ncell=8, layers=3, charge=0.7)
     box = synth.grid_box_for(sub, 0.1, height=20.0)
-    grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, keep_f64=True)
-    assert grid.dims == (113, 113, 200)
+    grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, keep_f64=True, ghost_below=8)
+    assert grid.dims == (113, 113, 208) and grid.ghost == 8
     c32 = grid.download_f64("coefs").astype(np.float32).astype(np.float64)
     yield sub, box, grid, c32
     grid.close()
@@ -65,7 +66,7 @@ def oracle_grid_ef(c32, grid, pts, Q, R, eps):
     for a in range(0, len(pts), CHUNK):
         b = min(a + CHUNK, len(pts))
         e, f, bl = ogrid.grid_energy_forces(c32, ("C", "P", "L"), grid.origin, grid.spacing, pts[a:b], Q[a:b],
-                                            R[a:b], eps[a:b], dtype=np.float32)
+                                            R[a:b], eps[a:b], dtype=np.float32, ghost=grid.ghost)
         E[a:b], F[a:b], below[a:b] = e, f, bl
     return E, F, below
 
@@ -207,9 +208,20 @@ def test_uneven_batch_per_atom_forces(G, ctx, nacl, wpb):
             x = xl[off[r]:off[r + 1]].astype(np.float64)
             Eg, Fg, _ = oracle_grid_ef(c32, grid, x, m.q, m.R, m.eps)
             Ei, Fi = ointra.energy_forces(x[None], m)
-            dF = np.abs(fl[off[r]:off[r + 1]] - (Fg + Fi[0])).max()
+            dFa = np.abs(fl[off[r]:off[r + 1]] - (Fg + Fi[0])).max(1)
+            dF = dFa.max()
             dE = abs(E[r] - (Eg.sum() + Ei[0]))
             worst_f, worst_e = max(worst_f, dF), max(worst_e, dE / m.n)
+            if dF > TOL_F:
+                import torch
+                a = int(np.argmax(dFa))
+                xt = torch.tensor(x, dtype=torch.float32, requires_grad=True)
+                (g32,) = torch.autograd.grad(ointra.energy(xt[None], m).sum(), xt)
+                print(f"replica {r} atom {a}: |dF| {dF:.2e}, z - floor {x[a, 2] - grid.floor:.3f} A, "
+                      f"|F_grid| {np.linalg.norm(Fg[a]):.2f}, |F_intra| {np.linalg.norm(Fi[0, a]):.2f}, "
+                      f"FP32 autograd intra vs FP64 {np.abs(-g32.numpy()[a] - Fi[0, a]).max():.2e}")
+                for t in ("bond", "angle", "torsion", "nonbonded"):
+                    print("  ", t, np.linalg.norm(ointra.energy_forces(x[None], m, terms=(t,))[1][0, a]))
             assert dF <= TOL_F, (r, m.n, nsteps, dF)
             assert dE <= TOL_E * m.n, (r, m.n, nsteps, dE)
         print(f"uneven batch, {wpb} warps per block, {nsteps} iterations: max|dF| {worst_f:.2e} eV/A, "
@@ -221,7 +233,8 @@ def test_uneven_batch_per_atom_forces(G, ctx, nacl, wpb):
 def fcc(G, ctx):
     sub = synth.fcc111_slab(a=4.08, ncell=12, layers=4)
     box = synth.grid_box_for(sub, 0.05, height=20.0)
-    grid32 = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, channels=G.CH_P | G.CH_L, keep_f64=True)
+    grid32 = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, channels=G.CH_P | G.CH_L, keep_f64=True,
+                          ghost_below=8)
     yield sub, grid32, grid32.download_f64("coefs")
     grid32.close()
 
@@ -255,7 +268,7 @@ def test_fcc111_workload_energy_force_torque(G, ctx, fcc, tier):
         ns = len(sample)
         Eo, Fo, _ = ogrid.grid_energy_forces(cq, ("P", "L"), grid32.origin, grid32.spacing, x.reshape(-1, 3),
                                              np.tile(mol.q, ns), np.tile(mol.R, ns), np.tile(mol.eps, ns),
-                                             dtype=np.float32)
+                                             dtype=np.float32, ghost=grid32.ghost)
         Ft, tau = odyn.rigid_reduce(Fo.astype(np.float64).reshape(ns, mol.n, 3), p[:, 3:].astype(np.float64), body)
         Eo = Eo.astype(np.float64).reshape(ns, mol.n).sum(1)
         dE, dF, dT = np.abs(E[sample] - Eo).max(), np.abs(fl[sample, :3] - Ft).max(), np.abs(fl[sample, 3:] - tau).max()

@@ -35,14 +35,14 @@ def test_rigid_4096_replicas_full_grid_sampled(G, ctx):
     mol = synth.c24h8o6_core()
     com, quat = synth.rigid_poses(mol, sub, 4096, seed=1002)
     pose = np.concatenate([com, quat], 1).astype(np.float32)
-    grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, keep_f64=True)
-    assert grid.dims == (113, 113, 200)
+    grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, keep_f64=True, ghost_below=8)
+    assert grid.dims == (113, 113, 208)
     c32 = grid.download_f64("coefs").astype(np.float32).astype(np.float64)
     reps = G.Replicas(ctx, [mol], [0] * 4096, rigid=True)
     cfg = reps.launch_config()
     assert cfg.kernel == G.KERNEL_RIGID_SUBWARP and cfg.lanes_per_replica == 16
     body = mol.xyz.astype(np.float32).astype(np.float64)
-    fn = odyn.make_force_fn(c32, ("C", "P", "L"), grid.origin, grid.spacing, mol, intra=False)
+    fn = odyn.make_force_fn(c32, ("C", "P", "L"), grid.origin, grid.spacing, mol, intra=False, ghost=grid.ghost)
     sample = np.r_[0:8, 2040:2048, 4088:4096]          # first, middle and last waves
     for nsteps, tol in ((1, 2e-6), (10, 1e-4)):
         reps.set_state(pose.ravel())
@@ -77,7 +77,7 @@ def test_rigid_4096_replicas_full_grid_sampled(G, ctx):
 def test_uneven_batch_full_size_sampled(G, ctx):
     sub = synth.rocksalt_slab(a=5.64, ncell=8, layers=3, charge=0.7)
     box = synth.grid_box_for(sub, 0.1, height=20.0)
-    grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, keep_f64=True)
+    grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, keep_f64=True, ghost_below=8)
     c32 = grid.download_f64("coefs").astype(np.float32).astype(np.float64)
     mols, tof = synth.uneven_batch(16384, 256, 77)
     reps = G.Replicas(ctx, mols, tof)
@@ -99,7 +99,7 @@ def test_uneven_batch_full_size_sampled(G, ctx):
     x = x.reshape(-1, 3)
     for r in sample:
         m = mols[tof[r]]
-        fn = odyn.make_force_fn(c32, ("C", "P", "L"), grid.origin, grid.spacing, m)
+        fn = odyn.make_force_fn(c32, ("C", "P", "L"), grid.origin, grid.spacing, m, ghost=grid.ghost)
         ref = odyn.fire_flexible(x0[off[r]:off[r + 1]][None].astype(np.float64), np.zeros((1, m.n, 3)), m.mass,
                                  fn, 20, odyn.FireParams(f_conv=0.0))
         assert np.abs(x[off[r]:off[r + 1]] - ref["x"][0]).max() <= 2e-4, (r, m.n)
@@ -114,7 +114,8 @@ def test_fcc111_precision_workload_full_size_sampled(G, ctx, tier):
     n_rep = 65536
     com, quat = synth.rigid_poses(mol, sub, n_rep, seed=2025)
     pose = np.concatenate([com, quat], 1).astype(np.float32)
-    grid32 = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, channels=G.CH_P | G.CH_L, keep_f64=True)
+    grid32 = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, channels=G.CH_P | G.CH_L, keep_f64=True,
+                          ghost_below=8)
     coefs = grid32.download_f64("coefs")
     grid = grid32 if tier == "f32" else G.grid_from_coefs(ctx, coefs, grid32.origin, grid32.spacing,
                                                           G.CH_P | G.CH_L, storage=oprec.STORAGE[tier])
@@ -127,7 +128,7 @@ def test_fcc111_precision_workload_full_size_sampled(G, ctx, tier):
     sample = np.r_[0:4, 32766:32770, 65532:65536]
     x = x.reshape(n_rep, 7)[sample]
     body = mol.xyz.astype(np.float32).astype(np.float64)
-    fn = odyn.make_force_fn(cq, ("P", "L"), grid32.origin, grid32.spacing, mol, intra=False)
+    fn = odyn.make_force_fn(cq, ("P", "L"), grid32.origin, grid32.spacing, mol, intra=False, ghost=grid32.ghost)
     ref = odyn.fire_rigid(pose[sample, :3].astype(np.float64), pose[sample, 3:].astype(np.float64),
                           np.zeros((len(sample), 3)), np.zeros((len(sample), 3)), body, mol.mass, fn, 10,
                           odyn.FireParams(f_conv=0.0))
@@ -142,12 +143,12 @@ def test_fcc111_precision_workload_full_size_sampled(G, ctx, tier):
 def test_oracle_size_configuration(G, ctx):
     sub = synth.rocksalt_slab(a=5.64, ncell=4, layers=2, charge=0.7)
     box = synth.grid_box_for(sub, 0.2, height=20.0)
-    grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, keep_f64=True)
-    assert grid.dims == (57, 57, 100)
+    grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, keep_f64=True, ghost_below=4)
+    assert grid.dims == (57, 57, 104)
     c32 = grid.download_f64("coefs").astype(np.float32).astype(np.float64)
     mol = synth.chain_molecule()
     x0 = synth.flexible_positions(mol, sub, 64, seed=1001).astype(np.float32)
-    fn = odyn.make_force_fn(c32, ("C", "P", "L"), grid.origin, grid.spacing, mol)
+    fn = odyn.make_force_fn(c32, ("C", "P", "L"), grid.origin, grid.spacing, mol, ghost=grid.ghost)
     reps = G.Replicas(ctx, [mol], [0] * 64)
     reps.set_state(x0.ravel())
     G.relax(ctx, grid, reps, 20, G.fire_params(f_conv=0.0))

@@ -109,7 +109,7 @@ def test_minima_hopping_database(G, ctx, field):
     curve = [mh.hop() for _ in range(3)]
     counts = [c[1] for c in curve]
     assert counts[0] > 0 and counts == sorted(counts)
-    assert (mh.db_x[..., 2] >= grid.origin[2]).all()         # no accepted minimum below the grid
+    assert (mh.db_x[..., 2] >= grid.floor).all()         # no accepted minimum below the grid
     db = mh.db_x[:40].astype(np.float64)
     assert (osamp.dup_of_xyz(db, sub.tile, 0.1) == -1).all()
     fn = odyn.make_force_fn(c32, ("C", "P", "L"), box.origin, h, mol)

@@ -71,7 +71,7 @@ def test_minima_hopping_restarts_replicas_that_left_the_grid(monkeypatch):
                                  REP_NONFINITE=G.REP_NONFINITE)
     monkeypatch.setattr(S, "G", fake)
     x0 = np.ones((n_rep, n_at, 3), np.float32) * np.arange(1, n_rep + 1, dtype=np.float32)[:, None, None]
-    grid = types.SimpleNamespace(origin=(0.0, 0.0, z0))
+    grid = types.SimpleNamespace(origin=(0.0, 0.0, z0 - 0.8), floor=z0)
     mh = S.MinimaHopping(None, grid, types.SimpleNamespace(n=n_at), x0, (1.0, 1.0))
     t, unique, acc = mh.hop()
     assert (unique, acc) == (3, 3) and mh.below == [2]
