@@ -211,20 +211,24 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 def kernel_source_hash():
     """Hash of the source the rigid sub-warp relaxation kernel is built
-    from: the shared header, the device helpers at the top of dynamics.cu
-    (cell location, B-spline weights, record gathers) and the sub-warp
-    section (force routine, schedule, kernel).  Edits elsewhere in the file
-    (flexible kernels, host code) leave the committed counters valid."""
+    from: the shared headers (internal.h, interp.cuh: cell location and
+    B-spline weights), the device helpers at the top of dynamics.cu (record
+    gathers), the final-evaluation record and the sub-warp section (force
+    routine, schedule, kernel).  Edits elsewhere in the file (flexible
+    kernels, host code) leave the committed counters valid."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2508_15522_gb300", "csrc")
-    with open(os.path.join(csrc, "internal.h"), "rb") as fh:
-        h.update(fh.read())
+    for name in ("internal.h", "interp.cuh"):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
     src = open(os.path.join(csrc, "dynamics.cu"), encoding="utf-8").read()
     try:
         top = src[:src.index("// Energy and force of one atom in the substrate field")]
+        r0 = src.index("// Record of a replica's final evaluation")
+        r1 = src.index("// Forces of one flexible replica whose positions are in s.x", r0)
         a = src.index("// FIRE, rigid replicas, sub-warp form")
         b = src.index("// FIRE, flexible replicas", a)
-        h.update((top + src[a:b]).encode())
+        h.update((top + src[r0:r1] + src[a:b]).encode())
     except ValueError:
         h.update(src.encode())
     return h.hexdigest()[:16]
@@ -387,8 +391,9 @@ def flexible_minima_comparison(G, ctx, grid, sub):
     builder.  Training data: 16 batches of 8192 random-start relaxations
     (centre over the 5.64 A tile, uniform orientation and torsions); the
     network is trained (K = 8, 3000 steps) on the poses of the converged
-    minima within 0.05 eV of the best-known energy; hits are converged
-    relaxations within 0.01 eV of it.  Both arms relax 4 batches of 8192."""
+    minima within 0.05 eV of the best-known energy, or of the 256 lowest if
+    that set is larger; hits are converged relaxations within 0.01 eV of it.
+    Both arms relax 4 batches of 8192."""
     from paper_2508_15522_gb300 import sampling as S
     from paper_2508_15522_gb300 import synth
     a, n_rep = 5.64, 8192
@@ -405,7 +410,10 @@ def flexible_minima_comparison(G, ctx, grid, sub):
     gen_s = time.perf_counter() - t0
     E, X, T, M = (np.concatenate(v) for v in (E, X, T, M))
     e_best = float(E.min())
-    low = E <= e_best + 0.05
+    # training set: every minimum within 0.05 eV of the best, at least the
+    # 256 lowest (a handful of targets is learned poorly: measured, 95 targets
+    # gave 5 hits in 4 proposal batches, the 288 within 0.1 eV gave 128)
+    low = E <= max(e_best + 0.05, np.sort(E)[min(255, len(E) - 1)])
     h = E <= e_best + 0.01
     best_set = len(sp.unique(X[h], E[h]))
     net = S.new_network(ctx, T[low], seed=1)
