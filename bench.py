@@ -915,7 +915,7 @@ def run_gpu(args):
                      "hbm_peak_measured": peaks.get("hbm_gbs"), "hbm_read_this_run": hbm_read},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 7 * 4 * N_REP,
                 "d2h_bytes_per_step": (7 + 6) * 4 * N_REP + (5 * 4 + 8) * N_REP},
-        "gpu_launches": args.steps,
+        "gpu_launches": 2 * args.steps,     # per step: fire_reset_kernel + the relaxation kernel
         "clocks": clocks,
     }
     if not args.quick:

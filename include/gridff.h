@@ -236,6 +236,20 @@ gridff_status gridff_grid_storage(const gridff_grid* grid, int32_t* storage, flo
 gridff_status gridff_grid_download_f64(const gridff_grid* grid, int what, double* host_out);
 void gridff_grid_destroy(gridff_grid* grid);
 
+/* Grid files (a substrate's grid is built once and reused in many
+ * simulations, Sec. 5).  gridff_grid_save writes the grid to `path`: an 8-byte magic
+ * "GRIDFF\1\0", the header size (int32) and header (node counts, padded
+ * extents, channels, storage, record kind, ghost planes, origin, spacing,
+ * floor, channel scales, record bytes), the padded record array the
+ * kernels read, and, when the grid kept them, its FP64 node values and
+ * coefficients; little-endian as the host writes it.  gridff_grid_load
+ * reads such a file into a new grid on ctx's device (identical records:
+ * evaluations are bit for bit those of the saved grid).
+ * Errors: EINVAL (null argument, unreadable file, another format or an
+ * inconsistent header, a short file), ENOMEM, ECUDA. */
+gridff_status gridff_grid_save(const gridff_grid* grid, const char* path);
+gridff_status gridff_grid_load(gridff_ctx* ctx, const char* path, gridff_grid** out);
+
 /* --------------------------------------------------------------- replicas */
 
 /* One molecule template (host arrays).  Per-atom parameters of Sec. 3:
@@ -536,6 +550,16 @@ gridff_status gridff_template_rotors(const gridff_replicas* reps, int32_t t, int
  * GRIDFF_ASYNC.  Computed in FP32 on the device.  Errors: EINVAL, ECUDA. */
 gridff_status gridff_build_poses(gridff_replicas* reps, const float* poses, const double origin_xy[2],
                                  const double tile_xy[2], int flags);
+
+/* Lift every replica whose lowest atom lies below z_floor (A) by the
+ * difference, so that its lowest atom is at z_floor (rigid: the centre of
+ * mass moves; flexible: every atom moves by the same amount); replicas at or
+ * above it, or with non-finite positions, are left as they are.  The rule of
+ * gridff_random_poses' z_floor, applied to starting structures from other
+ * sources (learned proposals, built poses; Sec. 7 starts molecules from
+ * placements above the surface).  flags: GRIDFF_ASYNC.
+ * Errors: EINVAL, ECUDA. */
+gridff_status gridff_lift(gridff_replicas* reps, double z_floor, int flags);
 
 /* Poses of the replicas' current state (the inverse of the builder, for
  * training targets): torsions = the rotors' dihedrals, centre = the centre

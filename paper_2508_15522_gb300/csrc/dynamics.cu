@@ -2565,10 +2565,14 @@ gridff_status enqueue_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_rep
   return GRIDFF_OK;
 }
 
+// host entry points (traced with NVTX ranges)
+#include "trace.h"
+
 extern "C" {
 
 gridff_status gridff_eval(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* R, int flags,
                           double* E_out, float* F_out, float* Ea_out, int32_t* st_out) {
+  NvtxRange nvtx_range("gridff_eval");
   gridff_status st = check_common(ctx, grid, R, flags);
   if (st != GRIDFF_OK) return st;
   if (!E_out || !F_out) return set_err(ctx, GRIDFF_EINVAL, "E_out and F_out are required");
@@ -2608,6 +2612,7 @@ gridff_status gridff_eval(gridff_ctx* ctx, const gridff_grid* grid, gridff_repli
 
 gridff_status gridff_eval_points(gridff_ctx* ctx, const gridff_grid* grid, int64_t n, const float* xyz,
                                  const float* qpl, float* E, float* F, int32_t* status, int flags) {
+  NvtxRange nvtx_range("gridff_eval_points");
   if (!ctx) return GRIDFF_EINVAL;
   if (!grid || n < 0 || (n > 0 && (!xyz || !qpl || !E || !F)))
     return set_err(ctx, GRIDFF_EINVAL, "null argument or negative count");
@@ -2668,6 +2673,7 @@ gridff_status gridff_eval_points(gridff_ctx* ctx, const gridff_grid* grid, int64
 
 gridff_status gridff_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* R, int32_t nsteps,
                            const gridff_fire_params* prm, int flags, gridff_relax_result* result) {
+  NvtxRange nvtx_range("gridff_relax");
   gridff_status st = check_common(ctx, grid, R, flags);
   if (st != GRIDFF_OK) return st;
   if (nsteps < 0) return set_err(ctx, GRIDFF_EINVAL, "nsteps < 0");
@@ -2694,6 +2700,7 @@ gridff_status gridff_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_repl
 
 gridff_status gridff_langevin(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* R, int32_t nsteps,
                               const gridff_langevin_params* prm, int flags) {
+  NvtxRange nvtx_range("gridff_langevin");
   gridff_status st = check_common(ctx, grid, R, flags);
   if (st != GRIDFF_OK) return st;
   if (!prm || !(prm->dt > 0) || !(prm->temperature >= 0) || !(prm->gamma >= 0) || nsteps < 0 || prm->step0 < 0)
@@ -2741,6 +2748,7 @@ gridff_status gridff_langevin(gridff_ctx* ctx, const gridff_grid* grid, gridff_r
 
 gridff_status gridff_run(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* R, int32_t nsteps,
                          const gridff_md_params* prm, int flags, double* energy_trace) {
+  NvtxRange nvtx_range("gridff_run");
   gridff_status st = check_common(ctx, grid, R, flags);
   if (st != GRIDFF_OK) return st;
   if (!prm || !(prm->dt > 0) || nsteps < 0 || prm->record_every < 0)

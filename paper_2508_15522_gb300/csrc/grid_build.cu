@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "trace.h"
 
 namespace {
 
@@ -600,6 +601,7 @@ extern "C" {
 
 gridff_status gridff_build_grid(gridff_ctx* ctx, const gridff_substrate* sub,
                                 const gridff_grid_opts* opts, gridff_grid** out) {
+  NvtxRange nvtx_range("gridff_build_grid");
   if (!ctx || !sub || !opts || !out) return set_err(ctx, GRIDFF_EINVAL, "null argument");
   *out = nullptr;
   if (sub->n_atoms <= 0 || !sub->xyz || !sub->q || !sub->R || !sub->eps)
@@ -828,6 +830,7 @@ gridff_status gridff_build_grid(gridff_ctx* ctx, const gridff_substrate* sub,
 gridff_status gridff_grid_from_coefs(gridff_ctx* ctx, const double origin[3], const double spacing[3],
                                      const int32_t dims[3], int32_t channels, const double* coefs,
                                      int32_t storage, gridff_grid** out) {
+  NvtxRange nvtx_range("gridff_grid_from_coefs");
   if (!ctx || !origin || !spacing || !dims || !coefs || !out)
     return set_err(ctx, GRIDFF_EINVAL, "null argument");
   *out = nullptr;
@@ -879,6 +882,7 @@ gridff_status gridff_grid_from_coefs(gridff_ctx* ctx, const double origin[3], co
 
 gridff_status gridff_fit_coefs_noalloc(gridff_ctx* ctx, const double* values, double* coefs,
                                        const int32_t dims[3], int32_t n_channels, int flags) {
+  NvtxRange nvtx_range("gridff_fit_coefs_noalloc");
   if (!ctx || !values || !coefs || !dims) return set_err(ctx, GRIDFF_EINVAL, "null argument");
   if (n_channels < 1) return set_err(ctx, GRIDFF_EINVAL, "n_channels must be >= 1");
   for (int a = 0; a < 3; ++a)

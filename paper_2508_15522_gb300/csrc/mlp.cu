@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "trace.h"
 
 namespace {
 
@@ -24,42 +25,113 @@ inline int pad16(int n) { return (n + 15) & ~15; }
 // ---------------------------------------------------------------------------
 // C[M][N] (FP32) = A[M][K] * B, A row-major bf16 (lda), B given as Bt[N][K]
 // row-major bf16 (ldb), i.e. B is K x N column-major.  M % 16 == 0,
-// N % 8 == 0, K % 16 == 0.  One warp per 16 x 8 output tile, K in steps of
-// 16 with one tensor-core mma per step.  Split K: block row y handles
-// K range [y K, (y + 1) K) and writes its partial product to C + y * cstride.
-__global__ void gemm_bf16_kernel(const __nv_bfloat16* __restrict__ A, int lda,
-                                 const __nv_bfloat16* __restrict__ Bt, int ldb, float* __restrict__ C,
-                                 int ldc, int M, int N, int K, long long cstride) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  const int tiles_n = N / 8;
-  if (warp >= (M / 16) * tiles_n) return;
-  const int ks = blockIdx.y;
-  A += (size_t)ks * K;
-  Bt += (size_t)ks * K;
-  C += (size_t)ks * cstride;
-  const int tm = warp / tiles_n, tn = warp % tiles_n;
-  const int g = lane >> 2, t = lane & 3;
-  float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
-  const __nv_bfloat16* a0p = A + (size_t)(tm * 16 + g) * lda + 2 * t;
-  const __nv_bfloat16* a1p = a0p + (size_t)8 * lda;
-  const __nv_bfloat16* bp = Bt + (size_t)(tn * 8 + g) * ldb + 2 * t;
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    const unsigned a0 = *(const unsigned*)(a0p + k0);
-    const unsigned a1 = *(const unsigned*)(a1p + k0);
-    const unsigned a2 = *(const unsigned*)(a0p + k0 + 8);
-    const unsigned a3 = *(const unsigned*)(a1p + k0 + 8);
-    const unsigned b0 = *(const unsigned*)(bp + k0);
-    const unsigned b1 = *(const unsigned*)(bp + k0 + 8);
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c0), "+f"(c1), "+f"(c2), "+f"(c3)
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+// N % 8 == 0, K % 16 == 0, lda and ldb multiples of 8.  Block tile
+// 64 x 64, K in slices of 32 staged in shared memory by 16-byte cp.async
+// copies (two stages: the next slice loads while the tensor cores work on
+// this one; rows and K beyond the matrix are zero-filled); four warps, each
+// a 32 x 32 tile of 2 x 4 mma.sync m16n8k16 products per 16 of K, fragments
+// read with ldmatrix (rows padded to 40 elements: conflict-free).  Split K:
+// block z handles K range [z K, (z + 1) K) and writes its partial product
+// to C + z * cstride.
+constexpr int kBM = 64, kBN = 64, kBK = 32, kPad = 8, kLds = kBK + kPad;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gmem), "r"(valid ? 16 : 0)
+               : "memory");
+}
+
+__device__ __forceinline__ void ldmatrix_x4(const void* smem, unsigned& r0, unsigned& r1, unsigned& r2,
+                                            unsigned& r3) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(a));
+}
+
+__global__ void __launch_bounds__(128) gemm_bf16_kernel(const __nv_bfloat16* __restrict__ A, int lda,
+                                                        const __nv_bfloat16* __restrict__ Bt, int ldb,
+                                                        float* __restrict__ C, int ldc, int M, int N, int K,
+                                                        long long cstride) {
+  __shared__ __align__(16) __nv_bfloat16 sA[2][kBM][kLds];
+  __shared__ __align__(16) __nv_bfloat16 sB[2][kBN][kLds];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp >> 1, wn = warp & 1;            // warp tile (32 x 32) in the block tile
+  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+  A += (size_t)blockIdx.z * K;
+  Bt += (size_t)blockIdx.z * K;
+  C += (size_t)blockIdx.z * cstride;
+  // a slice is 64 rows x 32 K of A and of Bt: 256 chunks of 8 elements each
+  auto load = [&](int stage, int k0) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int chunk = tid + 128 * c, r = chunk >> 2, kc = (chunk & 3) * 8;
+      const bool ka = k0 + kc < K;
+      const bool va = ka && m0 + r < M, vb = ka && n0 + r < N;
+      cp_async16(&sA[stage][r][kc], va ? (const void*)(A + (size_t)(m0 + r) * lda + k0 + kc) : (const void*)A, va);
+      cp_async16(&sB[stage][r][kc], vb ? (const void*)(Bt + (size_t)(n0 + r) * ldb + k0 + kc) : (const void*)Bt,
+                 vb);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[i][j][v] = 0.f;
+  const int n_slices = (K + kBK - 1) / kBK;
+  load(0, 0);
+  for (int sl = 0; sl < n_slices; ++sl) {
+    const int stage = sl & 1;
+    if (sl + 1 < n_slices) {
+      load(stage ^ 1, (sl + 1) * kBK);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncthreads();
+    // ldmatrix addresses: lane i serves row (i & 7) of 8 x 8 matrix i >> 3
+    const int q = lane >> 3, r8 = lane & 7;
+#pragma unroll
+    for (int kk = 0; kk < kBK; kk += 16) {
+      unsigned a[2][4], b[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i)   // A 16 x 16: matrices (rows 0-7 | 8-15) x (k 0-7 | 8-15)
+        ldmatrix_x4(&sA[stage][wm * 32 + i * 16 + r8 + (q & 1) * 8][kk + (q >> 1) * 8], a[i][0], a[i][1], a[i][2],
+                    a[i][3]);
+#pragma unroll
+      for (int jp = 0; jp < 2; ++jp)   // two n8 blocks: matrices (n 0-7 | 8-15) x (k 0-7 | 8-15)
+        ldmatrix_x4(&sB[stage][wn * 32 + jp * 16 + r8 + (q >> 1) * 8][kk + (q & 1) * 8], b[2 * jp][0],
+                    b[2 * jp][1], b[2 * jp + 1][0], b[2 * jp + 1][1]);
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+              "{%0,%1,%2,%3};\n"
+              : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
+              : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(b[j][0]), "r"(b[j][1]));
+    }
+    __syncthreads();   // this stage is reloaded two slices later
   }
-  float* r0 = C + (size_t)(tm * 16 + g) * ldc + tn * 8 + 2 * t;
-  float* r1 = r0 + (size_t)8 * ldc;
-  r0[0] = c0; r0[1] = c1; r1[0] = c2; r1[1] = c3;
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int row = m0 + wm * 32 + i * 16 + g, col = n0 + wn * 32 + j * 8 + 2 * t;
+      if (row < M && col < N) {   // M % 16 == 0, N % 8 == 0: a fragment is all in or all out
+        float* r0 = C + (size_t)row * ldc + col;
+        float* r1 = r0 + (size_t)8 * ldc;
+        r0[0] = acc[i][j][0];
+        r0[1] = acc[i][j][1];
+        r1[0] = acc[i][j][2];
+        r1[1] = acc[i][j][3];
+      }
+    }
 }
 
 // C = sum over the S partial products (fixed order: deterministic).
@@ -429,12 +501,13 @@ void gemm(cudaStream_t s, const __nv_bfloat16* A, int lda, const __nv_bfloat16* 
         S = cand;
         break;
       }
+  const dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM, S);
   if (S == 1) {
-    gemm_bf16_kernel<<<grid1(warps * 32, 128), 128, 0, s>>>(A, lda, Bt, ldb, C, ldc, M, N, K, 0);
+    gemm_bf16_kernel<<<grid, 128, 0, s>>>(A, lda, Bt, ldb, C, ldc, M, N, K, 0);
     return;
   }
   const long long cstride = (long long)M * ldc;
-  gemm_bf16_kernel<<<dim3(grid1(warps * 32, 128), S), 128, 0, s>>>(A, lda, Bt, ldb, part, ldc, M, N, K / S, cstride);
+  gemm_bf16_kernel<<<grid, 128, 0, s>>>(A, lda, Bt, ldb, part, ldc, M, N, K / S, cstride);
   splitk_sum_kernel<<<grid1((long long)M * N), 256, 0, s>>>(part, cstride, S, M, N, ldc, C);
 }
 
@@ -605,6 +678,7 @@ gridff_status gridff_mlp_get_params(gridff_mlp* m, float* params, float* grads) 
 }
 
 gridff_status gridff_mlp_forward(gridff_mlp* m, int32_t rows, const float* x, float* y) {
+  NvtxRange nvtx_range("gridff_mlp_forward");
   if (!m || !x || !y || rows < 1) return set_err(m ? m->ctx : nullptr, GRIDFF_EINVAL, "bad argument");
   gridff_ctx* ctx = m->ctx;
   GRIDFF_CUDA(ctx, cudaSetDevice(ctx->device));
@@ -625,6 +699,7 @@ gridff_status gridff_mlp_forward(gridff_mlp* m, int32_t rows, const float* x, fl
 gridff_status gridff_mlp_train_step(gridff_mlp* m, int32_t n_targets, int32_t K, const float* x,
                                     const float* targets, const float* tors_mask,
                                     const gridff_train_params* tp, float* loss_out, int flags) {
+  NvtxRange nvtx_range("gridff_mlp_train_step");
   if (!m || !x || !targets || !tp || n_targets < 1 || K < 1)
     return set_err(m ? m->ctx : nullptr, GRIDFF_EINVAL, "bad argument");
   gridff_ctx* ctx = m->ctx;
@@ -682,6 +757,7 @@ gridff_status gridff_mlp_set_targets(gridff_mlp* m, int32_t n, const float* targ
 
 gridff_status gridff_mlp_train(gridff_mlp* m, int32_t steps, int32_t n_targets, int32_t K, const float* descriptor,
                                int32_t n_desc, uint64_t seed, const gridff_train_params* tp, float* losses) {
+  NvtxRange nvtx_range("gridff_mlp_train");
   if (!m || !tp || steps < 0 || n_targets < 1 || K < 1 || n_desc < 0 || (n_desc > 0 && !descriptor))
     return set_err(m ? m->ctx : nullptr, GRIDFF_EINVAL, "bad argument");
   gridff_ctx* ctx = m->ctx;
@@ -726,6 +802,7 @@ gridff_status gridff_mlp_train(gridff_mlp* m, int32_t steps, int32_t n_targets, 
 
 gridff_status gridff_mlp_propose(gridff_mlp* m, gridff_replicas* R, const float* descriptor, int32_t n_desc,
                                  uint64_t seed, const double origin_xy[2], const double tile_xy[2]) {
+  NvtxRange nvtx_range("gridff_mlp_propose");
   if (!m || !R || !descriptor || !origin_xy || !tile_xy) return set_err(m ? m->ctx : nullptr, GRIDFF_EINVAL, "null argument");
   gridff_ctx* ctx = m->ctx;
   if (n_desc < 0 || n_desc > m->sizes[0]) return set_err(ctx, GRIDFF_EINVAL, "descriptor longer than the input");

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "trace.h"
 
 namespace {
 
@@ -111,6 +112,7 @@ gridff_status gridff_tune(gridff_ctx* ctx, const gridff_grid* grid, gridff_repli
                           const gridff_fire_params* prm, int32_t trial_steps, int flags,
                           gridff_launch_config* best_out, gridff_tune_trial* trials, int32_t max_trials,
                           int32_t* n_trials) {
+  NvtxRange nvtx_range("gridff_tune");
   if (!ctx || !R || R->ctx != ctx) return set_err(ctx, GRIDFF_EINVAL, "bad context or replicas");
   if (!(flags & GRIDFF_NO_GRID) && !grid) return set_err(ctx, GRIDFF_EINVAL, "grid is NULL");
   if (trial_steps < 1) return set_err(ctx, GRIDFF_EINVAL, "trial_steps < 1");
@@ -261,6 +263,7 @@ gridff_status gridff_tune(gridff_ctx* ctx, const gridff_grid* grid, gridff_repli
 gridff_status gridff_relax_graph_create(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* R,
                                         int32_t nsteps, const gridff_fire_params* prm, int flags,
                                         gridff_graph** out) {
+  NvtxRange nvtx_range("gridff_relax_graph_create");
   if (!ctx || !R || !out || R->ctx != ctx) return set_err(ctx, GRIDFF_EINVAL, "null argument");
   *out = nullptr;
   if (!(flags & GRIDFF_NO_GRID) && !grid) return set_err(ctx, GRIDFF_EINVAL, "grid is NULL");
@@ -300,6 +303,7 @@ gridff_status gridff_relax_graph_create(gridff_ctx* ctx, const gridff_grid* grid
 }
 
 gridff_status gridff_graph_launch(gridff_graph* G, gridff_relax_result* result) {
+  NvtxRange nvtx_range("gridff_graph_launch");
   if (!G) return GRIDFF_EINVAL;
   gridff_ctx* ctx = G->ctx;
   GRIDFF_CUDA(ctx, cudaSetDevice(ctx->device));

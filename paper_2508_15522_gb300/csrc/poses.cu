@@ -7,6 +7,7 @@
 #include <math.h>
 
 #include "internal.h"
+#include "trace.h"
 
 namespace {
 
@@ -288,6 +289,41 @@ int pose_blocks(gridff_ctx* ctx, int n_rep) {
   return need < cap ? need : cap;
 }
 
+// Lift of a replica set: one warp per replica finds the lowest atom (rigid:
+// of R(q) b + c) and, when it lies below z_floor, moves the replica up by
+// the difference (rigid: the centre of mass; flexible: every atom).
+__global__ void lift_kernel(TemplateView tv, const int* __restrict__ rep_tmpl, const int* __restrict__ rep_off,
+                            int n_rep, int rigid, float z_floor, float* __restrict__ x) {
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= n_rep) return;
+  const int t = rep_tmpl[r];
+  const int n = tv.natoms[t], ab = tv.atom_off[t];
+  float lowest = INFINITY;
+  float* p = rigid ? x + 7 * (size_t)r : x + 3 * (size_t)rep_off[r];
+  float Rm[9];
+  if (rigid) {
+    const float qn = rsqrtf(p[3] * p[3] + p[4] * p[4] + p[5] * p[5] + p[6] * p[6]);
+    quat_rot(p[3] * qn, p[4] * qn, p[5] * qn, p[6] * qn, Rm);
+  }
+  for (int i = lane; i < n; i += 32) {
+    if (rigid) {
+      const float4 b = tv.body[ab + i];
+      lowest = fminf(lowest, p[2] + Rm[6] * b.x + Rm[7] * b.y + Rm[8] * b.z);
+    } else {
+      lowest = fminf(lowest, p[3 * i + 2]);
+    }
+  }
+  for (int o = 16; o; o >>= 1) lowest = fminf(lowest, __shfl_xor_sync(kAll, lowest, o));
+  if (!(lowest < z_floor)) return;   // also leaves replicas with non-finite positions alone
+  const float dz = z_floor - lowest;
+  if (rigid) {
+    if (lane == 0) p[2] += dz;
+  } else {
+    for (int i = lane; i < n; i += 32) p[3 * i + 2] += dz;
+  }
+}
+
 }  // namespace
 
 gridff_status enqueue_build_poses(gridff_replicas* R, const float* d_poses, int stride, const double origin_xy[2],
@@ -326,6 +362,7 @@ gridff_status gridff_template_rotors(const gridff_replicas* R, int32_t t, int32_
 
 gridff_status gridff_build_poses(gridff_replicas* R, const float* poses, const double origin_xy[2],
                                  const double tile_xy[2], int flags) {
+  NvtxRange nvtx_range("gridff_build_poses");
   if (!R || !poses) return set_err(R ? R->ctx : nullptr, GRIDFF_EINVAL, "null argument");
   if ((origin_xy == nullptr) != (tile_xy == nullptr))
     return set_err(R->ctx, GRIDFF_EINVAL, "origin_xy and tile_xy go together");
@@ -352,8 +389,25 @@ gridff_status gridff_build_poses(gridff_replicas* R, const float* poses, const d
   return GRIDFF_OK;
 }
 
+gridff_status gridff_lift(gridff_replicas* R, double z_floor, int flags) {
+  NvtxRange nvtx_range("gridff_lift");
+  if (!R) return GRIDFF_EINVAL;
+  gridff_ctx* ctx = R->ctx;
+  if (!isfinite(z_floor)) return set_err(ctx, GRIDFF_EINVAL, "z_floor must be finite");
+  GRIDFF_CUDA(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  const int threads = 128;
+  const long long blocks = ((long long)R->n_rep * 32 + threads - 1) / threads;
+  lift_kernel<<<(unsigned)blocks, threads, 0, s>>>(R->tv, R->rep_tmpl, R->rep_off, R->n_rep, R->rigid,
+                                                   (float)z_floor, R->x);
+  GRIDFF_CUDA(ctx, cudaGetLastError());
+  if (!(flags & GRIDFF_ASYNC)) GRIDFF_CUDA(ctx, cudaStreamSynchronize(s));
+  return GRIDFF_OK;
+}
+
 gridff_status gridff_pose_targets(const gridff_replicas* R, const double origin_xy[2], const double tile_xy[2],
                                   float* targets, float* tors_mask, int flags) {
+  NvtxRange nvtx_range("gridff_pose_targets");
   if (!R || !targets) return set_err(R ? R->ctx : nullptr, GRIDFF_EINVAL, "null argument");
   if ((origin_xy == nullptr) != (tile_xy == nullptr))
     return set_err(R->ctx, GRIDFF_EINVAL, "origin_xy and tile_xy go together");

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "trace.h"
 
 namespace {
 
@@ -152,6 +153,7 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
                                      const gridff_molecule* T, int32_t n_rep,
                                      const int32_t* template_of, int32_t rigid, double alpha,
                                      gridff_replicas** out) {
+  NvtxRange nvtx_range("gridff_replicas_create");
   if (!ctx || !T || !template_of || !out || n_templates <= 0 || n_rep <= 0)
     return set_err(ctx, GRIDFF_EINVAL, "null argument or empty set");
   *out = nullptr;

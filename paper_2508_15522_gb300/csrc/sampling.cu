@@ -6,6 +6,7 @@
 #include <math.h>
 
 #include "internal.h"
+#include "trace.h"
 
 namespace {
 
@@ -181,6 +182,7 @@ extern "C" {
 
 gridff_status gridff_random_poses(gridff_replicas* R, uint64_t seed, const double origin_xy[2],
                                   const double tile_xy[2], double z_lo, double z_hi, double z_floor) {
+  NvtxRange nvtx_range("gridff_random_poses");
   if (!R || !origin_xy || !tile_xy) return GRIDFF_EINVAL;
   gridff_ctx* ctx = R->ctx;
   if (!R->rigid) return set_err(ctx, GRIDFF_ENOTSUP, "random poses are drawn for rigid replicas");
@@ -199,6 +201,7 @@ gridff_status gridff_random_poses(gridff_replicas* R, uint64_t seed, const doubl
 
 gridff_status gridff_rmsd_unique(gridff_replicas* R, int32_t tmpl, int32_t n, const float* poses,
                                  const double tile_xy[2], double threshold, int32_t* dup_of, int flags) {
+  NvtxRange nvtx_range("gridff_rmsd_unique");
   if (!R || !tile_xy || n < 0 || (n > 0 && (!poses || !dup_of))) return GRIDFF_EINVAL;
   gridff_ctx* ctx = R->ctx;
   if (tmpl < 0 || tmpl >= R->n_tmpl) return set_err(ctx, GRIDFF_EINVAL, "template %d out of range", tmpl);
@@ -237,6 +240,7 @@ gridff_status gridff_rmsd_unique(gridff_replicas* R, int32_t tmpl, int32_t n, co
 extern "C" gridff_status gridff_rmsd_unique_xyz(gridff_ctx* ctx, int32_t na, int32_t n, const float* xyz,
                                                 const double tile_xy[2], double threshold, int32_t* dup_of,
                                                 int flags) {
+  NvtxRange nvtx_range("gridff_rmsd_unique_xyz");
   if (!ctx || !tile_xy || n < 0 || (n > 0 && (!xyz || !dup_of))) return set_err(ctx, GRIDFF_EINVAL, "null argument");
   if (na < 1 || na > GRIDFF_MAX_ATOMS) return set_err(ctx, GRIDFF_EINVAL, "n_atoms %d outside 1..%d", na, GRIDFF_MAX_ATOMS);
   if (!(threshold > 0) || !(tile_xy[0] > 0 && tile_xy[1] > 0))

@@ -120,6 +120,8 @@ def _load():
         "gridff_grid_download_f64": (I32, [P, C.c_int, C.POINTER(C.c_double)]),
         "gridff_grid_storage": (I32, [P, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
         "gridff_grid_floor": (I32, [P, C.POINTER(C.c_double)]),
+        "gridff_grid_save": (I32, [P, C.c_char_p]),
+        "gridff_grid_load": (I32, [P, C.c_char_p, C.POINTER(P)]),
         "gridff_langevin": (I32, [P, P, P, I32, C.POINTER(LangevinParams), C.c_int]),
         "gridff_mlp_set_targets": (I32, [P, I32, P, P]),
         "gridff_mlp_train": (I32, [P, I32, I32, I32, P, I32, C.c_uint64, C.POINTER(TrainParams), P]),
@@ -163,6 +165,7 @@ def _load():
         "gridff_template_rotors": (I32, [P, I32, C.POINTER(C.c_int32), P]),
         "gridff_build_poses": (I32, [P, P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int]),
         "gridff_pose_targets": (I32, [P, C.POINTER(C.c_double), C.POINTER(C.c_double), P, P, C.c_int]),
+        "gridff_lift": (I32, [P, C.c_double, C.c_int]),
         "gridff_eval_points": (I32, [P, P, C.c_int64, P, P, P, P, P, C.c_int]),
         "gridff_template_factors": (I32, [P, I32, P]),
     }
@@ -186,10 +189,10 @@ EXPORTED = (
     "gridff_mlp_get_params", "gridff_mlp_forward", "gridff_mlp_train_step", "gridff_mlp_propose",
     "gridff_molecule_descriptor", "gridff_random_poses", "gridff_rmsd_unique",
     "gridff_set_launch_config", "gridff_get_launch_config", "gridff_tune", "gridff_relax_graph_create",
-    "gridff_grid_storage", "gridff_grid_floor", "gridff_langevin", "gridff_rmsd_unique_xyz", "gridff_mlp_set_targets",
+    "gridff_grid_storage", "gridff_grid_floor", "gridff_grid_save", "gridff_grid_load", "gridff_langevin", "gridff_rmsd_unique_xyz", "gridff_mlp_set_targets",
     "gridff_mlp_train",
     "gridff_graph_launch", "gridff_graph_destroy", "gridff_template_rotors", "gridff_build_poses",
-    "gridff_pose_targets", "gridff_eval_points", "gridff_template_factors",
+    "gridff_pose_targets", "gridff_eval_points", "gridff_template_factors", "gridff_lift",
 )
 MAX_ROTORS = 12
 
@@ -285,6 +288,10 @@ class Grid:
                                                      out.ctypes.data_as(C.POINTER(C.c_double))))
         return out
 
+    def save(self, path):
+        """gridff_grid_save: write the grid to a file."""
+        self.ctx.check(lib.gridff_grid_save(self.h, os.fsencode(path)))
+
     def close(self):
         if getattr(self, "h", None):
             lib.gridff_grid_destroy(self.h)
@@ -318,6 +325,13 @@ def build_grid(ctx: Context, sub, origin, length, spacing, channels=CH_C | CH_P 
     o.storage, o.ghost_below = storage, int(ghost_below)
     h = C.c_void_p()
     ctx.check(lib.gridff_build_grid(ctx.h, C.byref(s), C.byref(o), C.byref(h)))
+    return Grid(ctx, h)
+
+
+def load_grid(ctx: Context, path) -> Grid:
+    """gridff_grid_load: a grid file written by Grid.save."""
+    h = C.c_void_p()
+    ctx.check(lib.gridff_grid_load(ctx.h, os.fsencode(path), C.byref(h)))
     return Grid(ctx, h)
 
 
@@ -487,6 +501,10 @@ class Replicas:
             poses = poses.numpy()
         p = np.ascontiguousarray(poses, np.float32).reshape(self.n_rep, MLP_OUT)
         self.ctx.check(lib.gridff_build_poses(self.h, p.ctypes.data_as(C.c_void_p), o, t, 0))
+
+    def lift(self, z_floor):
+        """gridff_lift: raise replicas whose lowest atom is below z_floor."""
+        self.ctx.check(lib.gridff_lift(self.h, float(z_floor), 0))
 
     def pose_targets(self, origin_xy=None, tile_xy=None):
         """(targets (n_rep, 19), torsion masks (n_rep, 12)) of the current

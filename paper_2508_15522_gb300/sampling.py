@@ -14,7 +14,11 @@ Two ways to choose where FIRE relaxations start (rigid molecules:
   the low-energy minima that earlier relaxations found
   (``gridff_mlp_train_step``), sampled by ``gridff_mlp_propose``.
 
-Every batch then relaxes all replicas in one ``gridff_relax`` launch and
+Every start is raised, if needed, until its lowest atom is at the surface's
+z_floor (``gridff_random_poses`` does it for rigid random starts,
+``gridff_lift`` for the others), so that no arm starts atoms inside the
+substrate's repulsive wall.  Every batch then relaxes all replicas in one
+``gridff_relax`` launch and
 reads back the final poses, energies and status words.  A relaxation counts
 as a minimum only when it converged with finite values and no atom of the
 final structure below the grid floor (`accepted`; for rigid batches, whose
@@ -105,6 +109,7 @@ class Sampler:
         s = self.surface
         t0 = time.perf_counter()
         net.propose(self.reps, self.desc, seed, s.origin_xy, s.tile_xy)
+        self.reps.lift(s.z_floor)           # no atom below the floor of the random starts
         return self._relax(t0)
 
     def targets(self) -> np.ndarray:
@@ -164,12 +169,14 @@ class FlexSampler:
         P[:, 3:7] = g.standard_normal((self.n_rep, 4))
         P[:, 7:7 + self.n_rot] = g.uniform(-np.pi, np.pi, (self.n_rep, self.n_rot))
         self.reps.build_poses(P)
+        self.reps.lift(s.z_floor)
         return self._relax(t0)
 
     def proposal_batch(self, net: G.MLP, seed: int) -> Batch:
         s = self.surface
         t0 = time.perf_counter()
         net.propose(self.reps, self.desc, seed, s.origin_xy, s.tile_xy)
+        self.reps.lift(s.z_floor)
         return self._relax(t0)
 
     def targets(self):

@@ -191,18 +191,23 @@ def test_clock_budget_stops_long_run(G, ctx, small_field):
 def test_nonfinite_and_invalid_inputs_are_reported(G, ctx, small_field):
     sub, box, h, c32, grid = small_field
     mol = synth.chain_molecule()
-    reps = G.Replicas(ctx, [mol], [0] * 3)
-    x = synth.flexible_positions(mol, sub, 3, seed=41).astype(np.float32)
+    reps = G.Replicas(ctx, [mol], [0] * 4)
+    x = synth.flexible_positions(mol, sub, 4, seed=41).astype(np.float32)
     x[1, 2, 0] = np.nan
     x[2, :, 2] = sub.z_top - 3.0                      # below the grid
+    b0, b1 = mol.bonds[0]
+    x[3, b1] = x[3, b0]                               # a zero-length bond: its angles are undefined
     reps.set_state(x.ravel())
     E, F, Ea, S = G.eval(ctx, grid, reps)
     assert S[0] == 0
     assert S[1] & G.REP_NONFINITE
     assert S[2] & G.REP_BELOW
+    assert S[3] & G.REP_NONFINITE
     st, res = G.relax(ctx, grid, reps, 10, G.fire_params(f_conv=0.0))
     fs = reps.fire_state()
     assert fs["status"][1] & G.REP_NONFINITE and fs["steps"][1] == 1
+    assert fs["status"][3] & G.REP_NONFINITE and fs["steps"][3] == 1
+    assert fs["steps"][0] == 10 and not fs["status"][0] & G.REP_NONFINITE   # the others go on
     bad = synth.chain_molecule()
     bad.bonds = bad.bonds.copy()
     bad.bonds[0] = (0, 0)                            # self bond

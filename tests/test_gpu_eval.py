@@ -362,3 +362,35 @@ def test_eval_across_the_floor_with_ghost_planes(G, ctx):
         assert np.array_equal((S & G.REP_BELOW) != 0, below_g)
     reps.close()
     grid.close()
+
+
+def test_grid_file_round_trip(G, ctx, tmp_path):
+    """gridff_grid_save / gridff_grid_load: the loaded grid has the saved
+    grid's metadata, FP64 arrays and records (evaluations bit for bit equal);
+    a truncated file, a file of another kind and a missing file are refused."""
+    sub = synth.rocksalt_slab(ncell=2)
+    box = synth.grid_box_for(sub, 0.3, height=3.0)
+    for storage in (G.STORE_F32, G.STORE_F16):
+        grid = G.build_grid(ctx, sub, box.origin, box.length, box.spacing, keep_f64=True, ghost_below=2,
+                            storage=storage)
+        path = tmp_path / f"nacl_{storage}.gridff"
+        grid.save(path)
+        back = G.load_grid(ctx, path)
+        for k in ("dims", "origin", "spacing", "channels", "device_bytes", "storage", "scales", "floor", "ghost"):
+            assert getattr(back, k) == getattr(grid, k), k
+        for what in ("values", "coefs"):
+            assert np.array_equal(back.download_f64(what), grid.download_f64(what))
+        pts = synth.uniform_points(500, box, 7, zband=(-0.5, 2.5)).astype(np.float32)
+        qpl = np.tile(np.array([[0.2, 5.0, -1.5]], np.float32), (500, 1))
+        a, b = G.eval_points(ctx, grid, pts, qpl), G.eval_points(ctx, back, pts, qpl)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+        back.close()
+        grid.close()
+    raw = path.read_bytes()
+    (tmp_path / "short.gridff").write_bytes(raw[: len(raw) // 2])
+    (tmp_path / "other.bin").write_bytes(b"not a grid file at all, just bytes")
+    for bad in ("short.gridff", "other.bin", "missing.gridff"):
+        with pytest.raises(G.GridffError) as e:
+            G.load_grid(ctx, tmp_path / bad)
+        assert e.value.status == G.EINVAL

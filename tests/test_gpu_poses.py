@@ -191,3 +191,40 @@ def test_flexible_learned_proposal_loop(G, ctx):
     st, res = G.relax(ctx, grid, reps, 100, G.fire_params(f_conv=1e-3), check=False)
     assert st in (G.OK,) and res.atom_evals > 0
     net.close(); reps.close(); grid.close()
+
+
+def test_lift_raises_only_replicas_below_the_floor(G, ctx):
+    """gridff_lift: flexible replicas lowered below z_floor come back with
+    their lowest atom at z_floor, shifted as a whole; rigid replicas move
+    their centre so that the oracle's lowest atom of R(q) b + c is at z_floor;
+    replicas above it are left bit for bit."""
+    from oracle import dynamics as odyn
+    mol = synth.random_flexible_molecule(20, 3, 31)
+    sub = synth.rocksalt_slab(ncell=2)
+    x = synth.flexible_positions(mol, sub, 6, seed=32).astype(np.float32)
+    zf = float(sub.z_top + 1.8)                  # the starts keep 2 A: the odd replicas lie above it
+    x[::2, :, 2] -= x[::2, :, 2].min(1, keepdims=True) - (zf - 1.3)    # replicas 0, 2, 4 start 1.3 A too low
+    reps = G.Replicas(ctx, [mol], [0] * 6)
+    reps.set_state(x.ravel())
+    reps.lift(zf)
+    y = reps.get_state()[0].reshape(x.shape)
+    for r in range(6):
+        if r % 2:
+            assert np.array_equal(y[r], x[r])
+        else:
+            assert abs(y[r, :, 2].min() - zf) < 1e-5
+            d = y[r] - x[r]
+            assert np.abs(d[:, :2]).max() == 0 and np.ptp(d[:, 2]) < 1e-5
+    core = synth.c24h8o6_core()
+    com, quat = synth.rigid_poses(core, sub, 5, seed=33)
+    com[:3, 2] = sub.z_top - 1.0                                      # three centres inside the slab
+    pose = np.concatenate([com, quat], 1).astype(np.float32)
+    rig = G.Replicas(ctx, [core], [0] * 5, rigid=True)
+    rig.set_state(pose.ravel())
+    rig.lift(zf)
+    p = rig.get_state()[0].reshape(5, 7)
+    low = odyn.rigid_positions(p[:, :3].astype(np.float64), p[:, 3:].astype(np.float64),
+                               core.xyz.astype(np.float32).astype(np.float64))[..., 2].min(1)
+    assert np.abs(low[:3] - zf).max() < 1e-4 and np.array_equal(p[3:], pose[3:])
+    assert np.array_equal(p[:3, [0, 1, 3, 4, 5, 6]], pose[:3, [0, 1, 3, 4, 5, 6]])
+    rig.close(); reps.close()
