@@ -58,7 +58,7 @@ def config(extra=None):
     c = {"workload": "rigid C24H8O6 core x 4096 replicas, NaCl(001) 8x8x3 slab, 0.1 A grid "
                      "113x113x200 FP32 (C,P,L), 2000 FIRE iterations per step",
          "n_replicas": N_REP, "atoms_per_replica": 38, "fire_iterations_per_step": FIRE_ITERS,
-         "grid": [113, 113, 200], "grid_bytes_fp32_padded": None,
+         "grid": [113, 113, 200], "ghost_planes_below_floor": GHOST, "grid_bytes_fp32_padded": None,
          "l2_policy": "L2 flushed (256 MB write) between timed steps; the 44 MB grid is L2-resident "
                       "within a step by design"}
     if extra:
@@ -381,7 +381,9 @@ def amortised_gain(out, train_hits, gen_s, train_s):
         res[f"hits_per_s_after_{n}_batches"] = rate
         res[f"gain_after_{n}_batches"] = rate / max(r, 1e-30)
     den = b - r * t
-    res["break_even_batches"] = (r * (gen_s + train_s) - train_hits) / den if den > 0 else None
+    # None: the proposals never catch up; 0: ahead from the first batch (the
+    # training relaxations found hits at least at the random-start rate)
+    res["break_even_batches"] = max(0.0, (r * (gen_s + train_s) - train_hits) / den) if den > 0 else None
     return res
 
 

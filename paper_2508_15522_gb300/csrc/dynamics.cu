@@ -50,6 +50,16 @@ struct WarpState {
   float eg[kMaxA];     // grid energy per atom
 };
 
+// per-warp shared state of the unique-term relaxation: positions and forces
+// only (velocities stay in global memory, read and written once per step,
+// which leaves more of the SM's shared storage to the L1 cache)
+struct WarpStateXF {
+  float x[3 * kMaxA];
+  float f[3 * kMaxA];
+};
+__device__ __forceinline__ void store_eg(WarpState& s, int i, float e) { s.eg[i] = e; }
+__device__ __forceinline__ void store_eg(WarpStateXF&, int, float) {}
+
 __device__ __forceinline__ unsigned long long gtimer() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -649,10 +659,10 @@ __device__ float intra_terms(const TemplateView& tv, int t, int lane, const floa
 // quads (stored per atom) followed by the unique-term intramolecular pass
 // (added with shared-memory atomics).  Writes s.f, s.eg; returns this
 // lane's share of the energy.
-template <class Acc = double, int KIND = -1>
+template <class Acc = double, int KIND = -1, class St = WarpState>
 __device__ __forceinline__ Acc flex_forces_terms(const GridView& g, bool use_grid, bool use_intra,
                                                  const TemplateView& tv, int t, int ab, int n, int lane,
-                                                 WarpState& s, int& flags, const StencilCache& sc,
+                                                 St& s, int& flags, const StencilCache& sc,
                                                  const float4* s_nb) {
   __syncwarp();
   const int quad = lane >> 2, q = lane & 3;
@@ -675,7 +685,7 @@ __device__ __forceinline__ Acc flex_forces_terms(const GridView& g, bool use_gri
       s.f[3 * i] = fx;
       s.f[3 * i + 1] = fy;
       s.f[3 * i + 2] = fz;
-      s.eg[i] = eg;
+      store_eg(s, i, eg);
       e += (Acc)eg;
     }
   }
@@ -1554,10 +1564,10 @@ relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep
                         float* vs, float* fdt, float* falpha, int* fnp, int* status, int* steps, double* energy,
                         float* last_x, float* last_f, int nsteps, FireP fp, Control ctl, int use_grid,
                         int use_intra, int S) {
-  __shared__ WarpState s_all[WPB];
+  __shared__ WarpStateXF s_all[WPB];
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  WarpState& s = s_all[wib];
+  WarpStateXF& s = s_all[wib];
   // per-warp dynamic shared memory: stencil cache, then the template's
   // nonbonded parameters {q, R, eps, 0}
   unsigned char* wbase = dyn_smem + (size_t)wib * flex_terms_warp_bytes(S);
@@ -1580,10 +1590,8 @@ relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep
     const int t = rep_tmpl[r], n = tv.natoms[t], ab = tv.atom_off[t], off = rep_off[r];
     __syncwarp();
     cache_reset(sc, lane);
-    for (int m = lane; m < 3 * n; m += 32) {
-      s.x[m] = xs[3 * (size_t)off + m];
-      s.v[m] = vs[3 * (size_t)off + m];
-    }
+    float* const v_r = vs + 3 * (size_t)off;   // this replica's velocities (global memory)
+    for (int m = lane; m < 3 * n; m += 32) s.x[m] = xs[3 * (size_t)off + m];
     // nonbonded parameters, and the inverse mass in the free fourth slot
     for (int i = lane; i < n; i += 32) {
       float4 p = __ldg(&tv.nb[ab + i]);
@@ -1607,7 +1615,7 @@ relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep
                                                      s_nb);
       float f2 = 0.f, P = 0.f, v2 = 0.f;
       for (int m = lane; m < 3 * n; m += 32) {
-        float f = s.f[m], v = s.v[m];
+        float f = s.f[m], v = v_r[m];
         f2 = fmaf(f, f, f2);
         P = fmaf(f, v, P);
         v2 = fmaf(v, v, v2);
@@ -1650,9 +1658,9 @@ relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep
         float d[3];
         for (int a = 0; a < 3; ++a) {
           float f = s.f[3 * i + a];
-          float vv = keep * s.v[3 * i + a] + mixf * f;
+          float vv = keep * v_r[3 * i + a] + mixf * f;
           vv += adt * im * f;
-          s.v[3 * i + a] = vv;
+          v_r[3 * i + a] = vv;
           d[a] = vv * dt;
         }
         const float dn2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -1661,10 +1669,7 @@ relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep
       }
     }
     __syncwarp();
-    for (int m = lane; m < 3 * n; m += 32) {
-      xs[3 * (size_t)off + m] = s.x[m];
-      vs[3 * (size_t)off + m] = s.v[m];
-    }
+    for (int m = lane; m < 3 * n; m += 32) xs[3 * (size_t)off + m] = s.x[m];
     const double Etot = evals > 0 ? wsum((double)elane) : energy[r];
     if (evals > 0 && !isfinite(Etot)) st |= GRIDFF_REP_NONFINITE;
     if (lane == 0) {

@@ -65,5 +65,6 @@ def test_amortised_gain_charges_training_and_credits_its_hits():
     assert abs(a["gain_after_4_batches"] - (4250 / 7.5) / 100.0) < 1e-12
     n = a["break_even_batches"]
     assert abs((250 + n * 1000) / (3.5 + n * 1.0) - 100.0) < 1e-9
+    assert bench.amortised_gain(out, 400, 2.5, 1.0)["break_even_batches"] == 0.0   # ahead from the start
     out["mlp"]["hits"] = 400                      # proposals no better than random starts: no break-even
     assert bench.amortised_gain(out, 250, 2.5, 1.0)["break_even_batches"] is None
