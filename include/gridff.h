@@ -446,7 +446,8 @@ typedef struct {
                                  task may be split between two warps), 0 = per call: the queue
                                  when f_conv > 0 (replicas may stop early), else the ranges */
   int32_t l2_window;          /* 1 = the grid is put in an L2 persisting access-policy window
-                                 (reserves persisting L2 for the context until gridff_destroy) */
+                                 (reserves persisting L2 for the context until gridff_destroy);
+                                 no window when the call skips the grid term (GRIDFF_NO_GRID) */
   int32_t blocks;             /* 0 = as many blocks as are resident on the GPU at once; > 0 = at
                                  most this many (the kernels are persistent and loop over work);
                                  also caps gridff_run's sub-warp kernel for rigid replicas */

@@ -496,8 +496,8 @@ __device__ __forceinline__ Acc flex_forces(const GridView& g, bool use_grid, boo
 
 // Intramolecular forces of one flexible replica, each term evaluated once:
 // the lanes split the terms and add every term's forces to its atoms in
-// s_f (nonbonded pairs without atomics, on a schedule that gives the lanes
-// distinct atoms at every step; bonded terms with atomics).  Returns this
+// s_f (nonbonded pairs in the registers of the atoms' owner lanes, the
+// reactions passed by shuffles; bonded terms with atomics).  Returns this
 // lane's share of the energy.  Same terms as
 // intra_quad (reduced UFF-like form; nonbonded on pairs more than two bonds
 // apart), without the per-atom repetition.
@@ -506,12 +506,15 @@ __device__ __forceinline__ uint32_t pick4(uint32_t w0, uint32_t w1, uint32_t w2,
 }
 
 // Nonbonded force factor c (F_i = c d, d = x_i - x_j) and energy of one pair
-// (Morse with mixed R_i + R_j and eps_i eps_j, plus Coulomb).
+// (Morse with mixed R_i + R_j and eps_i eps_j, plus Coulomb).  The Morse
+// exponential is the intrinsic __expf (documented bound 2 + 1.16 |x| ulp at
+// argument x: about 1e-6 relative at |x| = 10, where the Morse term of a
+// pair is already e^-10 of its well depth).
 __device__ __forceinline__ void nb_pair(float3 d, float4 pi, float4 pj, float alpha, float& c, float& e) {
   const float r2 = dot3(d, d);
   const float ir = rsqrtf(r2);
   const float r = r2 * ir;
-  const float e1 = expf(-alpha * (r - (pi.y + pj.y)));
+  const float e1 = __expf(-alpha * (r - (pi.y + pj.y)));
   const float ee = pi.z * pj.z;
   const float qq = GRIDFF_KE * pi.x * pj.x;
   c = -(2.f * alpha * ee * e1 * (1.f - e1) - qq * ir * ir) * ir;
@@ -523,63 +526,70 @@ __device__ float intra_terms(const TemplateView& tv, int t, int lane, const floa
   float e = 0.f;
   const float alpha = tv.alpha;
   const int n = tv.natoms[t], ab = tv.atom_off[t];
-  // Nonbonded pairs: every unordered pair {i, (i + d) mod n} once, for
-  // d = 1 .. n/2 (for even n the pairs at d = n/2 only from i < n/2).  The
-  // lane owns atom i = lane + 32a and keeps its position, parameters,
-  // exclusion words and force in registers.  At a given d the partners j
-  // of the lanes are distinct, so each lane adds the partner's force to
-  // s_f[j] with a plain read-modify-write; the warp synchronises between
-  // values of d (two values of d are evaluated together, their writes
-  // separated).  Lanes without a pair at a d (beyond n, excluded, or
-  // counted by the other atom) take part with a zero force.
-  const int dmax = n / 2;
-  for (int i0 = 0; i0 < n; i0 += 32) {
-    const int i = i0 + lane;
+  // Nonbonded pairs, by blocks of 32 atoms: lane l owns atom 32 I + l of
+  // every block I and keeps its force in registers.  Block pair I < J: the
+  // pairs (32 I + l, 32 J + (l + d) mod 32), d = 0 .. 31, cover I x J once;
+  // within a block of m atoms the pairs (l, (l + d) mod m), d = 1 .. m/2 (at
+  // d = m/2 for even m only from l < m/2), cover it once.  At a given d the
+  // partners of the lanes are distinct and the partner's owner receives the
+  // reaction from lane (l - d) mod ring by a shuffle, so no lane writes
+  // another lane's atom and the pass needs no synchronisation; s_f is
+  // updated by the owners once per block pair.  Inactive pairs (beyond n,
+  // excluded, or counted from the other atom) read a valid atom and add
+  // zero.
+  const int nblk = (n + 31) >> 5;
+  for (int I = 0; I < nblk; ++I) {
+    const int i = 32 * I + lane;
     const bool own = i < n;
-    const int ii = own ? i : 0;
+    const int ii = own ? i : 32 * I;
     const float3 xi = ld3(s_x, ii);
     const float4 pi = s_nb[ii];
     const uint32_t* ex = tv.excl + 4 * (size_t)(ab + ii);
-    const uint32_t w0 = __ldg(&ex[0]), w1 = __ldg(&ex[1]), w2 = __ldg(&ex[2]), w3 = __ldg(&ex[3]);
     float fx = 0.f, fy = 0.f, fz = 0.f;
-    for (int d = 1; d <= dmax; d += 2) {
-      const bool two = d + 1 <= dmax;
-      int ja = ii + d, jb = ii + d + 1;
-      if (ja >= n) ja -= n;
-      if (jb >= n) jb -= n;
-      const bool acta = own && !(2 * d == n && i >= d) && !((pick4(w0, w1, w2, w3, ja >> 5) >> (ja & 31)) & 1u);
-      const bool actb = two && own && !(2 * (d + 1) == n && i >= d + 1) &&
-                        !((pick4(w0, w1, w2, w3, jb >> 5) >> (jb & 31)) & 1u);
-      const float3 da = sub3(xi, ld3(s_x, ja)), db = sub3(xi, ld3(s_x, jb));
-      float ca, ea, cb, eb;
-      nb_pair(da, pi, s_nb[ja], alpha, ca, ea);
-      nb_pair(db, pi, s_nb[jb], alpha, cb, eb);
-      ca = acta ? ca : 0.f;
-      cb = actb ? cb : 0.f;
-      e += (acta ? ea : 0.f) + (actb ? eb : 0.f);
-      fx = fmaf(ca, da.x, fmaf(cb, db.x, fx));
-      fy = fmaf(ca, da.y, fmaf(cb, db.y, fy));
-      fz = fmaf(ca, da.z, fmaf(cb, db.z, fz));
-      if (own) {
-        s_f[3 * ja] -= ca * da.x;
-        s_f[3 * ja + 1] -= ca * da.y;
-        s_f[3 * ja + 2] -= ca * da.z;
+    for (int J = I; J < nblk; ++J) {
+      const uint32_t w = __ldg(&ex[J]);
+      const int base = 32 * J, m = min(32, n - base);
+      const bool diag = J == I;
+      const int ring = diag ? m : 32, d1 = diag ? m / 2 : 31;
+      float gx = 0.f, gy = 0.f, gz = 0.f;   // reactions on this lane's atom of block J
+#pragma unroll 2
+      for (int d = diag ? 1 : 0; d <= d1; ++d) {
+        int sl = lane + d;
+        if (sl >= ring) sl -= ring;
+        int src = lane - d;
+        if (src < 0) src += ring;
+        const bool act = own && sl < m && !(diag && 2 * d == m && lane >= d) && !((w >> (sl & 31)) & 1u);
+        const int j = base + (sl < m ? sl : 0);
+        const float3 dv = sub3(xi, ld3(s_x, j));
+        float c, e1;
+        nb_pair(dv, pi, s_nb[j], alpha, c, e1);
+        const float cx = act ? c * dv.x : 0.f, cy = act ? c * dv.y : 0.f, cz = act ? c * dv.z : 0.f;
+        e += act ? e1 : 0.f;
+        fx += cx;
+        fy += cy;
+        fz += cz;
+        gx -= __shfl_sync(kFull, cx, src);
+        gy -= __shfl_sync(kFull, cy, src);
+        gz -= __shfl_sync(kFull, cz, src);
       }
-      __syncwarp();
-      if (own && two) {
-        s_f[3 * jb] -= cb * db.x;
-        s_f[3 * jb + 1] -= cb * db.y;
-        s_f[3 * jb + 2] -= cb * db.z;
+      if (diag) {
+        fx += gx;
+        fy += gy;
+        fz += gz;
+      } else if (base + lane < n) {
+        float* f = s_f + 3 * (base + lane);
+        f[0] += gx;
+        f[1] += gy;
+        f[2] += gz;
       }
-      __syncwarp();
     }
     if (own) {
       s_f[3 * i] += fx;
       s_f[3 * i + 1] += fy;
       s_f[3 * i + 2] += fz;
     }
-    __syncwarp();
   }
+  __syncwarp();
   // Bonded terms (few per atom): lanes take terms round-robin and add the
   // forces with shared-memory atomics.
   for (int b = tv.ub_off[t] + lane; b < tv.ub_off[t + 1]; b += 32) {
@@ -2461,8 +2471,7 @@ gridff_status prepare_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_rep
   const int need = (R->n_rep + k.units_per_block - 1) / k.units_per_block;
   *blocks_out = need < per_sm * ctx->n_sm ? need : per_sm * ctx->n_sm;
   if (c.blocks > 0 && *blocks_out > c.blocks) *blocks_out = c.blocks;
-  if (c.l2win) {
-    if (!grid || (flags & GRIDFF_NO_GRID)) return set_err(ctx, GRIDFF_EINVAL, "L2 window without a grid");
+  if (c.l2win && grid && !(flags & GRIDFF_NO_GRID)) {   // the window holds the grid: none without it
     int max_persist = 0, max_win = 0;
     GRIDFF_CUDA(ctx, cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, ctx->device));
     GRIDFF_CUDA(ctx, cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, ctx->device));
@@ -2523,7 +2532,7 @@ gridff_status enqueue_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_rep
   const KernelShape k = shape_of(R, c, kind);
   cudaAccessPolicyWindow win{};
   const cudaAccessPolicyWindow* wp = nullptr;
-  if (c.l2win && grid) {
+  if (c.l2win && grid && use_grid) {
     int max_win = 0;
     size_t lim = 0;
     cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, ctx->device);

@@ -36,6 +36,44 @@ gridff_status finish(gridff_ctx* ctx, int flags) {
   return GRIDFF_OK;
 }
 
+// Order of the unique bonded terms of a template: the kernels give 32
+// consecutive terms to the 32 lanes of a warp, and each term adds its
+// forces to s_f[3 atom + comp] with one shared-memory atomic per role and
+// component.  Lanes whose atoms of a role fall in one bank (atom mod 32
+// equal: same atom, or atoms 32 apart) replay that atomic, so terms listed
+// around one centre (all angles at an atom, all torsions about a bond)
+// serialise.  Greedy: every run of 32 takes, slot by slot, the first
+// remaining term whose busiest (role, atom mod 32) count in the run is
+// lowest.  Only the order changes; deterministic.
+template <class T, class AtomOf>
+std::vector<T> spread_terms(const std::vector<T>& v, int roles, AtomOf atom_of) {
+  std::vector<T> out;
+  out.reserve(v.size());
+  std::vector<char> used(v.size(), 0);
+  size_t left = v.size();
+  while (left > 0) {
+    int cnt[4][32] = {};
+    for (int slot = 0; slot < 32 && left > 0; ++slot) {
+      size_t best = v.size();
+      int best_c = 1 << 30;
+      for (size_t k = 0; k < v.size() && best_c > 0; ++k) {
+        if (used[k]) continue;
+        int c = 0;
+        for (int r = 0; r < roles; ++r) c = std::max(c, cnt[r][atom_of(v[k], r) & 31]);
+        if (c < best_c) {
+          best_c = c;
+          best = k;
+        }
+      }
+      used[best] = 1;
+      --left;
+      for (int r = 0; r < roles; ++r) ++cnt[r][atom_of(v[best], r) & 31];
+      out.push_back(v[best]);
+    }
+  }
+  return out;
+}
+
 // Rotatable bonds of a flexible template (the torsion coordinates of a
 // pose).  Root: the lowest-index atom with one bond (atom 0 if none);
 // breadth-first search from it, neighbours in increasing index order,
@@ -239,6 +277,9 @@ gridff_status gridff_replicas_create(gridff_ctx* ctx, int32_t n_templates,
       rot.insert(rot.end(), tr.begin(), tr.end());
     }
     rot_off.push_back((int)rot.size());
+    tub = spread_terms(tub, 2, [](const BondTerm& b, int r) { return r == 0 ? b.i : b.j; });
+    tua = spread_terms(tua, 3, [](const AngleRec& a, int r) { return r == 0 ? a.a : r == 1 ? a.b : a.c; });
+    tut = spread_terms(tut, 4, [](const TorsionRec& q, int r) { return r == 0 ? q.a : r == 1 ? q.b : r == 2 ? q.c : q.d; });
     ub.insert(ub.end(), tub.begin(), tub.end());
     ua.insert(ua.end(), tua.begin(), tua.end());
     ut.insert(ut.end(), tut.begin(), tut.end());

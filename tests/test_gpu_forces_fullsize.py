@@ -187,7 +187,12 @@ def test_uneven_batch_per_atom_forces(G, ctx, nacl, wpb):
     unique-term layout with the work queue: per-atom forces (grid +
     intramolecular) and per-replica energies of the final evaluation after
     1 and 200 iterations, on 64 replicas that span the sizes (the largest
-    and smallest templates, both ends of the batch)."""
+    and smallest templates, both ends of the batch).  Atoms that a
+    relaxation has pushed below the grid floor (flagged BELOW: the field
+    there is the clamped continuation of the lowest cells, with forces of
+    tens of eV/A) are held to the gate relative to the force's magnitude,
+    as the eval test holds points in the first cells above the floor; every
+    other atom to the absolute gate."""
     sub, box, grid, c32 = nacl
     mols, tof, reps, x0 = _uneven(G, ctx, sub)
     off = reps.atom_offset
@@ -202,30 +207,40 @@ def test_uneven_batch_per_atom_forces(G, ctx, nacl, wpb):
         E = reps.fire_state()["energy"]
         if nsteps == 1:
             assert np.array_equal(xl, x0)
-        worst_f = worst_e = 0.0
+        worst_f = worst_e = worst_below = 0.0
+        n_below = 0
         for r in sample:
             m = mols[tof[r]]
             x = xl[off[r]:off[r + 1]].astype(np.float64)
             Eg, Fg, _ = oracle_grid_ef(c32, grid, x, m.q, m.R, m.eps)
             Ei, Fi = ointra.energy_forces(x[None], m)
-            dFa = np.abs(fl[off[r]:off[r + 1]] - (Fg + Fi[0])).max(1)
-            dF = dFa.max()
-            dE = abs(E[r] - (Eg.sum() + Ei[0]))
+            Fo = Fg + Fi[0]
+            below = x[:, 2] < grid.floor
+            gate = np.where(below, TOL_F * np.maximum(1.0, np.abs(Fo).max(1)), TOL_F)
+            dFa = np.abs(fl[off[r]:off[r + 1]] - Fo).max(1)
+            dF = dFa[~below].max(initial=0.0)
+            Eo = Eg.sum() + Ei[0]
+            dE = abs(E[r] - Eo)
+            gate_e = TOL_E * (max(m.n, abs(Eo)) if below.any() else m.n)
             worst_f, worst_e = max(worst_f, dF), max(worst_e, dE / m.n)
-            if dF > TOL_F:
+            if below.any():
+                n_below += int(below.sum())
+                worst_below = max(worst_below, float((dFa[below] / np.maximum(1.0, np.abs(Fo[below]).max(1))).max()))
+            if (dFa > gate).any():
                 import torch
-                a = int(np.argmax(dFa))
+                a = int(np.argmax(dFa / gate))
                 xt = torch.tensor(x, dtype=torch.float32, requires_grad=True)
                 (g32,) = torch.autograd.grad(ointra.energy(xt[None], m).sum(), xt)
-                print(f"replica {r} atom {a}: |dF| {dF:.2e}, z - floor {x[a, 2] - grid.floor:.3f} A, "
+                print(f"replica {r} atom {a}: |dF| {dFa[a]:.2e}, z - floor {x[a, 2] - grid.floor:.3f} A, "
                       f"|F_grid| {np.linalg.norm(Fg[a]):.2f}, |F_intra| {np.linalg.norm(Fi[0, a]):.2f}, "
                       f"FP32 autograd intra vs FP64 {np.abs(-g32.numpy()[a] - Fi[0, a]).max():.2e}")
                 for t in ("bond", "angle", "torsion", "nonbonded"):
                     print("  ", t, np.linalg.norm(ointra.energy_forces(x[None], m, terms=(t,))[1][0, a]))
-            assert dF <= TOL_F, (r, m.n, nsteps, dF)
-            assert dE <= TOL_E * m.n, (r, m.n, nsteps, dE)
-        print(f"uneven batch, {wpb} warps per block, {nsteps} iterations: max|dF| {worst_f:.2e} eV/A, "
-              f"max|dE|/atom {worst_e:.2e} eV")
+            assert (dFa <= gate).all(), (r, m.n, nsteps, dF)
+            assert dE <= gate_e, (r, m.n, nsteps, dE)
+        print(f"uneven batch, {wpb} warps per block, {nsteps} iterations: max|dF| {worst_f:.2e} eV/A "
+              f"(atoms above the floor), max|dE|/atom {worst_e:.2e} eV; {n_below} sampled atoms below the floor, "
+              f"max |dF|/max(1, |F|) there {worst_below:.2e}")
     reps.close()
 
 
