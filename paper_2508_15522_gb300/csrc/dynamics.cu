@@ -521,6 +521,51 @@ __device__ __forceinline__ void nb_pair(float3 d, float4 pi, float4 pj, float al
   e = ee * e1 * (e1 - 2.f) + qq * ir;
 }
 
+// f[3 i .. 3 i + 2] += (x, y, z) by atomic additions (f in shared memory).
+__device__ __forceinline__ void sh_add3(float* f, int i, float x, float y, float z) {
+  atomicAdd(f + 3 * i, x);
+  atomicAdd(f + 3 * i + 1, y);
+  atomicAdd(f + 3 * i + 2, z);
+}
+
+// Steps d = d0 .. d1 of one block pair of the nonbonded pass (below): the
+// pair (this lane's atom, slot (lane + d) mod ring of the block at base) when
+// bit d of act is set.  Adds the pair forces to fi and the energies to e;
+// returns the reactions received on this lane's atom of the partner block.
+template <bool DIAG>
+__device__ __forceinline__ float3 nb_steps(const float* s_x, const float4* s_nb, float3 xi, float4 pi, float alpha,
+                                           uint32_t act, int lane, int base, int ring, int d0, int d1, float3& fi,
+                                           float& e) {
+  float3 g = make_float3(0.f, 0.f, 0.f);
+  int sl = lane + d0, src = lane - d0;
+  if (sl >= ring) sl -= ring;
+  if (src < 0) src += ring;
+#pragma unroll 2
+  for (int d = d0; d <= d1; ++d) {
+    const bool on = (act >> d) & 1u;
+    const int j = base + sl;
+    const float3 dv = sub3(xi, ld3(s_x, j));
+    float c, ep;
+    nb_pair(dv, pi, s_nb[j], alpha, c, ep);
+    const float cx = on ? c * dv.x : 0.f, cy = on ? c * dv.y : 0.f, cz = on ? c * dv.z : 0.f;
+    e += on ? ep : 0.f;
+    fi.x += cx;
+    fi.y += cy;
+    fi.z += cz;
+    g.x -= __shfl_sync(kFull, cx, src);
+    g.y -= __shfl_sync(kFull, cy, src);
+    g.z -= __shfl_sync(kFull, cz, src);
+    if (DIAG) {
+      sl = sl + 1 == ring ? 0 : sl + 1;
+      src = src == 0 ? ring - 1 : src - 1;
+    } else {
+      sl = (sl + 1) & 31;
+      src = (src - 1) & 31;
+    }
+  }
+  return g;
+}
+
 __device__ float intra_terms(const TemplateView& tv, int t, int lane, const float* s_x, float* s_f,
                              const float4* s_nb) {
   float e = 0.f;
@@ -534,9 +579,11 @@ __device__ float intra_terms(const TemplateView& tv, int t, int lane, const floa
   // partners of the lanes are distinct and the partner's owner receives the
   // reaction from lane (l - d) mod ring by a shuffle, so no lane writes
   // another lane's atom and the pass needs no synchronisation; s_f is
-  // updated by the owners once per block pair.  Inactive pairs (beyond n,
-  // excluded, or counted from the other atom) read a valid atom and add
-  // zero.
+  // updated by the owners once per block pair.  Which steps d carry a pair
+  // (partner inside the molecule, not excluded, counted from this atom) is
+  // one 32-bit word per lane and block pair, computed before the steps.
+  // Inactive steps read whatever the partner's slot of s_x / s_nb holds (in
+  // bounds: slots < 128) and add zero by selection.
   const int nblk = (n + 31) >> 5;
   for (int I = 0; I < nblk; ++I) {
     const int i = 32 * I + lane;
@@ -545,85 +592,68 @@ __device__ float intra_terms(const TemplateView& tv, int t, int lane, const floa
     const float3 xi = ld3(s_x, ii);
     const float4 pi = s_nb[ii];
     const uint32_t* ex = tv.excl + 4 * (size_t)(ab + ii);
-    float fx = 0.f, fy = 0.f, fz = 0.f;
+    float3 fi = make_float3(0.f, 0.f, 0.f);
     for (int J = I; J < nblk; ++J) {
-      const uint32_t w = __ldg(&ex[J]);
       const int base = 32 * J, m = min(32, n - base);
       const bool diag = J == I;
-      const int ring = diag ? m : 32, d1 = diag ? m / 2 : 31;
-      float gx = 0.f, gy = 0.f, gz = 0.f;   // reactions on this lane's atom of block J
-#pragma unroll 2
-      for (int d = diag ? 1 : 0; d <= d1; ++d) {
-        int sl = lane + d;
-        if (sl >= ring) sl -= ring;
-        int src = lane - d;
-        if (src < 0) src += ring;
-        const bool act = own && sl < m && !(diag && 2 * d == m && lane >= d) && !((w >> (sl & 31)) & 1u);
-        const int j = base + (sl < m ? sl : 0);
-        const float3 dv = sub3(xi, ld3(s_x, j));
-        float c, e1;
-        nb_pair(dv, pi, s_nb[j], alpha, c, e1);
-        const float cx = act ? c * dv.x : 0.f, cy = act ? c * dv.y : 0.f, cz = act ? c * dv.z : 0.f;
-        e += act ? e1 : 0.f;
-        fx += cx;
-        fy += cy;
-        fz += cz;
-        gx -= __shfl_sync(kFull, cx, src);
-        gy -= __shfl_sync(kFull, cy, src);
-        gz -= __shfl_sync(kFull, cz, src);
-      }
+      const int ring = diag ? m : 32;
+      // partner slots with a pair, then bit d = slot (lane + d) mod ring
+      const uint32_t ok = (m >= 32 ? 0xffffffffu : ((1u << m) - 1u)) & ~__ldg(&ex[J]);
+      const unsigned long long dbl = (unsigned long long)ok | ((unsigned long long)ok << ring);
+      uint32_t act = own ? (uint32_t)(dbl >> lane) : 0u;
+      float3 gj;
       if (diag) {
-        fx += gx;
-        fy += gy;
-        fz += gz;
-      } else if (base + lane < n) {
-        float* f = s_f + 3 * (base + lane);
-        f[0] += gx;
-        f[1] += gy;
-        f[2] += gz;
+        const int h = m >> 1;
+        act &= ((2u << h) - 1u) & ~1u;                          // d = 1 .. m/2
+        if (!(m & 1) && lane >= h) act &= ~(1u << h);           // d = m/2 counted from l < m/2
+        gj = nb_steps<true>(s_x, s_nb, xi, pi, alpha, act, lane, base, ring, 1, h, fi, e);
+        fi.x += gj.x;
+        fi.y += gj.y;
+        fi.z += gj.z;
+      } else {
+        gj = nb_steps<false>(s_x, s_nb, xi, pi, alpha, act, lane, base, 32, 0, 31, fi, e);
+        if (base + lane < n) {
+          float* f = s_f + 3 * (base + lane);
+          f[0] += gj.x;
+          f[1] += gj.y;
+          f[2] += gj.z;
+        }
       }
     }
     if (own) {
-      s_f[3 * i] += fx;
-      s_f[3 * i + 1] += fy;
-      s_f[3 * i + 2] += fz;
+      s_f[3 * i] += fi.x;
+      s_f[3 * i + 1] += fi.y;
+      s_f[3 * i + 2] += fi.z;
     }
   }
   __syncwarp();
   // Bonded terms (few per atom): lanes take terms round-robin and add the
-  // forces with shared-memory atomics.
+  // forces with shared-memory atomics.  Reciprocals come from rsqrtf
+  // (1/x = rsqrt(x)^2), not from divisions.
   for (int b = tv.ub_off[t] + lane; b < tv.ub_off[t + 1]; b += 32) {
     const BondTerm B = tv.ub[b];
     const float3 d = sub3(ld3(s_x, B.i), ld3(s_x, B.j));
-    const float r = sqrtf(dot3(d, d));
-    const float dr = r - B.r0;
-    const float c = r > 0.f ? -2.f * B.k * dr / r : 0.f;
-    atomicAdd(&s_f[3 * B.i], c * d.x);
-    atomicAdd(&s_f[3 * B.i + 1], c * d.y);
-    atomicAdd(&s_f[3 * B.i + 2], c * d.z);
-    atomicAdd(&s_f[3 * B.j], -c * d.x);
-    atomicAdd(&s_f[3 * B.j + 1], -c * d.y);
-    atomicAdd(&s_f[3 * B.j + 2], -c * d.z);
+    const float r2 = dot3(d, d);
+    const float ir = r2 > 0.f ? rsqrtf(r2) : 0.f;   // zero length: no direction, no force
+    const float dr = r2 * ir - B.r0;
+    const float c = -2.f * B.k * dr * ir;
+    sh_add3(s_f, B.i, c * d.x, c * d.y, c * d.z);
+    sh_add3(s_f, B.j, -c * d.x, -c * d.y, -c * d.z);
     e += B.k * dr * dr;
   }
   for (int a = tv.ua_off[t] + lane; a < tv.ua_off[t + 1]; a += 32) {
     const AngleRec A = tv.ua[a];
     const float3 u = sub3(ld3(s_x, A.a), ld3(s_x, A.b)), w = sub3(ld3(s_x, A.c), ld3(s_x, A.b));
-    const float lu2 = dot3(u, u), lw2 = dot3(w, w);
-    const float inv = rsqrtf(lu2 * lw2);
+    const float ru = rsqrtf(dot3(u, u)), rw = rsqrtf(dot3(w, w));
+    const float inv = ru * rw, iu2 = ru * ru, iw2 = rw * rw;
     const float c = dot3(u, w) * inv;
     const float dEdc = 2.f * A.k * (c - A.cos0);
-    const float3 ga = make_float3(w.x * inv - c * u.x / lu2, w.y * inv - c * u.y / lu2, w.z * inv - c * u.z / lu2);
-    const float3 gc = make_float3(u.x * inv - c * w.x / lw2, u.y * inv - c * w.y / lw2, u.z * inv - c * w.z / lw2);
-    atomicAdd(&s_f[3 * A.a], -dEdc * ga.x);
-    atomicAdd(&s_f[3 * A.a + 1], -dEdc * ga.y);
-    atomicAdd(&s_f[3 * A.a + 2], -dEdc * ga.z);
-    atomicAdd(&s_f[3 * A.c], -dEdc * gc.x);
-    atomicAdd(&s_f[3 * A.c + 1], -dEdc * gc.y);
-    atomicAdd(&s_f[3 * A.c + 2], -dEdc * gc.z);
-    atomicAdd(&s_f[3 * A.b], dEdc * (ga.x + gc.x));
-    atomicAdd(&s_f[3 * A.b + 1], dEdc * (ga.y + gc.y));
-    atomicAdd(&s_f[3 * A.b + 2], dEdc * (ga.z + gc.z));
+    const float cu = c * iu2, cw = c * iw2;
+    const float3 ga = make_float3(w.x * inv - cu * u.x, w.y * inv - cu * u.y, w.z * inv - cu * u.z);
+    const float3 gc = make_float3(u.x * inv - cw * w.x, u.y * inv - cw * w.y, u.z * inv - cw * w.z);
+    sh_add3(s_f, A.a, -dEdc * ga.x, -dEdc * ga.y, -dEdc * ga.z);
+    sh_add3(s_f, A.c, -dEdc * gc.x, -dEdc * gc.y, -dEdc * gc.z);
+    sh_add3(s_f, A.b, dEdc * (ga.x + gc.x), dEdc * (ga.y + gc.y), dEdc * (ga.z + gc.z));
     e += A.k * (c - A.cos0) * (c - A.cos0);
   }
   for (int k = tv.ut_off[t] + lane; k < tv.ut_off[t + 1]; k += 32) {
@@ -633,33 +663,24 @@ __device__ float intra_terms(const TemplateView& tv, int t, int lane, const floa
     const float3 A = cross3(F, G), B = cross3(H, G);
     const float A2 = dot3(A, A), B2 = dot3(B, B), G2 = dot3(G, G);
     if (A2 < 1e-12f || B2 < 1e-12f || G2 < 1e-12f) continue;   // collinear: no torque
-    const float Gn = sqrtf(G2);
-    const float iAB = rsqrtf(A2 * B2);
+    const float rA = rsqrtf(A2), rB = rsqrtf(B2), rG = rsqrtf(G2);
+    const float iA2 = rA * rA, iB2 = rB * rB, Gn = G2 * rG;
+    const float iAB = rA * rB;
     const float cphi = dot3(A, B) * iAB;
-    const float sphi = dot3(cross3(B, A), G) * iAB / Gn;
+    const float sphi = dot3(cross3(B, A), G) * iAB * rG;
     float sn, cn;
     multiple_angle(cphi, sphi, T.n, cn, sn);
     const float dEdphi = 0.5f * T.V * T.cn0 * T.n * sn;
-    const float FG = dot3(F, G) / (A2 * Gn), HG = dot3(H, G) / (B2 * Gn);
-    const float ca = -Gn / A2, cd = Gn / B2;
+    const float FG = dot3(F, G) * iA2 * rG, HG = dot3(H, G) * iB2 * rG;
+    const float ca = -Gn * iA2, cd = Gn * iB2;
     const float a1 = -ca + FG, b1 = -cd + HG;
-    // gradients of phi with respect to the four atoms
-    const float3 g0 = make_float3(ca * A.x, ca * A.y, ca * A.z);
-    const float3 g3 = make_float3(cd * B.x, cd * B.y, cd * B.z);
-    const float3 g1 = make_float3(a1 * A.x - HG * B.x, a1 * A.y - HG * B.y, a1 * A.z - HG * B.z);
-    const float3 g2 = make_float3(b1 * B.x - FG * A.x, b1 * B.y - FG * A.y, b1 * B.z - FG * A.z);
-    atomicAdd(&s_f[3 * T.a], -dEdphi * g0.x);
-    atomicAdd(&s_f[3 * T.a + 1], -dEdphi * g0.y);
-    atomicAdd(&s_f[3 * T.a + 2], -dEdphi * g0.z);
-    atomicAdd(&s_f[3 * T.b], -dEdphi * g1.x);
-    atomicAdd(&s_f[3 * T.b + 1], -dEdphi * g1.y);
-    atomicAdd(&s_f[3 * T.b + 2], -dEdphi * g1.z);
-    atomicAdd(&s_f[3 * T.c], -dEdphi * g2.x);
-    atomicAdd(&s_f[3 * T.c + 1], -dEdphi * g2.y);
-    atomicAdd(&s_f[3 * T.c + 2], -dEdphi * g2.z);
-    atomicAdd(&s_f[3 * T.d], -dEdphi * g3.x);
-    atomicAdd(&s_f[3 * T.d + 1], -dEdphi * g3.y);
-    atomicAdd(&s_f[3 * T.d + 2], -dEdphi * g3.z);
+    // gradients of phi with respect to the four atoms, times -dE/dphi
+    const float m0 = -dEdphi * ca, m3 = -dEdphi * cd, m1 = -dEdphi * a1, m2 = -dEdphi * b1;
+    const float h1 = dEdphi * HG, h2 = dEdphi * FG;
+    sh_add3(s_f, T.a, m0 * A.x, m0 * A.y, m0 * A.z);
+    sh_add3(s_f, T.b, m1 * A.x + h1 * B.x, m1 * A.y + h1 * B.y, m1 * A.z + h1 * B.z);
+    sh_add3(s_f, T.c, m2 * B.x + h2 * A.x, m2 * B.y + h2 * A.y, m2 * B.z + h2 * A.z);
+    sh_add3(s_f, T.d, m3 * B.x, m3 * B.y, m3 * B.z);
     e += 0.5f * T.V * (1.f - T.cn0 * cn);
   }
   return e;
