@@ -451,6 +451,11 @@ typedef struct {
   int32_t blocks;             /* 0 = as many blocks as are resident on the GPU at once; > 0 = at
                                  most this many (the kernels are persistent and loop over work);
                                  also caps gridff_run's sub-warp kernel for rigid replicas */
+  int32_t cache_global;       /* FLEX_TERMS with cache_slots = 0: 1 = every atom keeps its 4x4x4
+                                 channel-combined stencil (256 B) between steps in a device buffer
+                                 of 260 B per atom of the set, allocated at the first use; a step
+                                 whose atom stays in its cell reads 256 contiguous bytes instead of
+                                 gathering 16 runs of the grid.  0 = no such buffer */
 } gridff_launch_config;
 
 /* Fix the launch configuration of relaxations of `reps` (NULL: back to the
@@ -470,7 +475,8 @@ typedef struct {
 /* Autotuner: times short relaxations (trial_steps FIRE iterations from the
  * current state, FIRE scalars reset, force threshold as in params) of
  * candidate configurations by coordinate descent over the kernel (and warps
- * per block), the stencil staging (cache slots), the work queue and the L2
+ * per block), the stencil staging (cache slots, or the unique-term kernel's
+ * global stencil cache), the work queue and the L2
  * window, picks the fastest in atom evaluations per second and makes it the
  * replica set's configuration.  The state (positions, velocities, FIRE
  * scalars, status, counters, energies) is restored afterwards.  Allocates

@@ -1588,13 +1588,16 @@ relax_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
 #ifndef GRIDFF_FLEX_WARPS_PER_SM
 #define GRIDFF_FLEX_WARPS_PER_SM 32    // register budget: 65536 / (32 * 32) = 64 per thread
 #endif
-template <int WPB, int KIND>
+// GC: the stencils of every atom are cached in global memory (gval, gkey:
+// the replica's atoms from 16 rep_off[r] float4s and rep_off[r] keys, the
+// layout of the shared-memory cache with one slot per atom), S = 0.
+template <int WPB, int KIND, bool GC>
 __global__ void __launch_bounds__(32 * WPB, GRIDFF_FLEX_WARPS_PER_SM / WPB)
 relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
                         const int* __restrict__ rep_off, const int* __restrict__ order, int n_rep, float* xs,
                         float* vs, float* fdt, float* falpha, int* fnp, int* status, int* steps, double* energy,
                         float* last_x, float* last_f, int nsteps, FireP fp, Control ctl, int use_grid,
-                        int use_intra, int S) {
+                        int use_intra, int S, float4* gval, int* gkey) {
   __shared__ WarpStateXF s_all[WPB];
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -1620,6 +1623,11 @@ relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep
     const int r = order ? order[k] : k;
     const int t = rep_tmpl[r], n = tv.natoms[t], ab = tv.atom_off[t], off = rep_off[r];
     __syncwarp();
+    if (GC && use_grid) {
+      sc.val = gval + 16 * (size_t)off;
+      sc.key = gkey + off;
+      sc.S = n;
+    }
     cache_reset(sc, lane);
     float* const v_r = vs + 3 * (size_t)off;   // this replica's velocities (global memory)
     for (int m = lane; m < 3 * n; m += 32) s.x[m] = xs[3 * (size_t)off + m];
@@ -2372,16 +2380,18 @@ RunSwFn run_sw_fn(int W, int R, int kind) {
 // FP32 four-slot grids get their own instances (the record kind known at
 // compile time); other kinds dispatch at run time.
 using FlexTermsFn = void (*)(GridView, TemplateView, const int*, const int*, const int*, int, float*, float*, float*,
-                             float*, int*, int*, int*, double*, float*, float*, int, FireP, Control, int, int, int);
-template <int K>
+                             float*, int*, int*, int*, double*, float*, float*, int, FireP, Control, int, int, int,
+                             float4*, int*);
+template <int K, bool GC>
 FlexTermsFn flex_terms_fn_k(int wpb) {
-  return wpb == 2 ? relax_flex_terms_kernel<2, K> : wpb == 8 ? relax_flex_terms_kernel<8, K>
-                                                             : relax_flex_terms_kernel<4, K>;
+  return wpb == 2 ? relax_flex_terms_kernel<2, K, GC> : wpb == 8 ? relax_flex_terms_kernel<8, K, GC>
+                                                                 : relax_flex_terms_kernel<4, K, GC>;
 }
-FlexTermsFn flex_terms_fn(int wpb, int kind) {
-  return kind == REC_F32x4 ? flex_terms_fn_k<REC_F32x4>(wpb) : flex_terms_fn_k<-1>(wpb);
+FlexTermsFn flex_terms_fn(int wpb, int kind, bool gc) {
+  if (gc) return kind == REC_F32x4 ? flex_terms_fn_k<REC_F32x4, true>(wpb) : flex_terms_fn_k<-1, true>(wpb);
+  return kind == REC_F32x4 ? flex_terms_fn_k<REC_F32x4, false>(wpb) : flex_terms_fn_k<-1, false>(wpb);
 }
-const void* flex_terms_ptr(int wpb, int kind) { return (const void*)flex_terms_fn(wpb, kind);
+const void* flex_terms_ptr(int wpb, int kind, bool gc) { return (const void*)flex_terms_fn(wpb, kind, gc);
 }
 
 struct KernelShape {
@@ -2409,8 +2419,8 @@ KernelShape shape_of(const gridff_replicas* R, const LaunchCfg& c, int kind) {
       if (R->rigid || c.wpb != kWarpsPerBlock) return k;
       return {(const void*)relax_flex_kernel, kThreads, kWarpsPerBlock, cache_bytes(c.S) * kWarpsPerBlock};
     case GRIDFF_KERNEL_FLEX_TERMS:
-      if (R->rigid || (c.wpb != 2 && c.wpb != 4 && c.wpb != 8)) return k;
-      return {flex_terms_ptr(c.wpb, kind), 32 * c.wpb, c.wpb, flex_terms_warp_bytes(c.S) * c.wpb};
+      if (R->rigid || (c.wpb != 2 && c.wpb != 4 && c.wpb != 8) || (c.gcache && c.S != 0)) return k;
+      return {flex_terms_ptr(c.wpb, kind, c.gcache != 0), 32 * c.wpb, c.wpb, flex_terms_warp_bytes(c.S) * c.wpb};
     default:
       return k;
   }
@@ -2489,6 +2499,17 @@ gridff_status prepare_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_rep
   if (c.blocks < 0) return set_err(ctx, GRIDFF_EINVAL, "block cap %d", c.blocks);
   if (c.queue < 0 || c.queue > (c.kernel == GRIDFF_KERNEL_RIGID_SUBWARP ? 2 : 1))
     return set_err(ctx, GRIDFF_EINVAL, "queue mode %d", c.queue);
+  if ((c.gcache != 0 && c.gcache != 1) || (c.gcache && c.kernel != GRIDFF_KERNEL_FLEX_TERMS))
+    return set_err(ctx, GRIDFF_EINVAL, "cache_global %d with kernel %d", c.gcache, c.kernel);
+  if (c.gcache && !R->gval) {   // one 256-byte stencil and a key per atom of the set
+    if (cudaMalloc(&R->gval, (size_t)R->n_atoms * 256) != cudaSuccess ||
+        cudaMalloc(&R->gkey, (size_t)R->n_atoms * sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(R->gval);
+      R->gval = nullptr;
+      return set_err(ctx, GRIDFF_ENOMEM, "global stencil cache of %d atoms", R->n_atoms);
+    }
+  }
   const int need = (R->n_rep + k.units_per_block - 1) / k.units_per_block;
   *blocks_out = need < per_sm * ctx->n_sm ? need : per_sm * ctx->n_sm;
   if (c.blocks > 0 && *blocks_out > c.blocks) *blocks_out = c.blocks;
@@ -2588,9 +2609,10 @@ gridff_status enqueue_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_rep
       break;
     case GRIDFF_KERNEL_FLEX_TERMS: {
       const int* ord = c.queue ? (const int*)R->order : nullptr;
-      e = launch_ex(flex_terms_fn(c.wpb, kind), blocks, k.threads, k.dyn, s, wp, gv, R->tv, (const int*)R->rep_tmpl,
-                    (const int*)R->rep_off, ord, R->n_rep, R->x, R->v, R->fire_dt, R->fire_alpha, R->fire_nplus,
-                    R->status, R->steps, R->energy, R->last_x, R->last_f, nsteps, fp, ctl, use_grid, use_intra, c.S);
+      e = launch_ex(flex_terms_fn(c.wpb, kind, c.gcache != 0), blocks, k.threads, k.dyn, s, wp, gv, R->tv,
+                    (const int*)R->rep_tmpl, (const int*)R->rep_off, ord, R->n_rep, R->x, R->v, R->fire_dt,
+                    R->fire_alpha, R->fire_nplus, R->status, R->steps, R->energy, R->last_x, R->last_f, nsteps, fp,
+                    ctl, use_grid, use_intra, c.S, R->gval, R->gkey);
       break;
     }
     default:

@@ -175,6 +175,7 @@ struct LaunchCfg {
   int queue = 0;     // work queue in decreasing cost order
   int l2win = 0;     // grid in an L2 persisting access-policy window
   int blocks = 0;    // block cap (0 = every block resident at once)
+  int gcache = 0;    // flexible unique-term kernel: stencil cache in global memory
 };
 
 struct gridff_replicas {
@@ -204,6 +205,8 @@ struct gridff_replicas {
   float4* handoff_p = nullptr; // [n_rep] rigid NVE: quaternion momentum at the end of a head part
   float* last_x = nullptr;     // final evaluation of the last relaxation: rigid [7 n_rep] poses,
   float* last_f = nullptr;     //   [6 n_rep] total force + body torque; flexible [3N] positions, [3N] forces
+  float4* gval = nullptr;      // flexible: global stencil cache [16 N] (atom i of replica r: 16 rep_off[r] + ...)
+  int* gkey = nullptr;         //   [N] cell of each cached stencil (-1 = empty)
   // host copy of offsets
   int* h_rep_off = nullptr;
   int* h_rot_off = nullptr;    // [n_tmpl+1] rotatable bonds (host copy)

@@ -21,6 +21,7 @@ LaunchCfg from_public(const gridff_launch_config& p) {
   c.queue = p.queue;
   c.l2win = p.l2_window;
   c.blocks = p.blocks;
+  c.gcache = p.cache_global;
   return c;
 }
 
@@ -33,12 +34,13 @@ gridff_launch_config to_public(const LaunchCfg& c) {
   p.queue = c.queue;
   p.l2_window = c.l2win;
   p.blocks = c.blocks;
+  p.cache_global = c.gcache;
   return p;
 }
 
 bool same(const LaunchCfg& a, const LaunchCfg& b) {
   return a.kernel == b.kernel && a.W == b.W && a.wpb == b.wpb && a.S == b.S && a.queue == b.queue &&
-         a.l2win == b.l2win && a.blocks == b.blocks;
+         a.l2win == b.l2win && a.blocks == b.blocks && a.gcache == b.gcache;
 }
 
 // One copy of a replica set's mutable state (tuning trials restore it).
@@ -163,7 +165,8 @@ gridff_status gridff_tune(gridff_ctx* ctx, const gridff_grid* grid, gridff_repli
     } else {
       c.W = 32;
     }
-    if (c.kernel != GRIDFF_KERNEL_FLEX_TERMS) c.queue = 0;
+    if (c.kernel != GRIDFF_KERNEL_FLEX_TERMS) c.queue = c.gcache = 0;
+    if (c.gcache) c.S = 0;
     if (c.kernel == GRIDFF_KERNEL_RIGID_QUAD || c.kernel == GRIDFF_KERNEL_FLEX_QUAD) c.wpb = 4;
     for (auto& kv : seen)
       if (same(kv.first, c)) {
@@ -218,12 +221,14 @@ gridff_status gridff_tune(gridff_ctx* ctx, const gridff_grid* grid, gridff_repli
         best = c;
       }
     }
-    // stencil staging
+    // stencil staging: shared-memory slots, or (unique-term kernel) every
+    // atom's stencil in global memory
     if (best.kernel != GRIDFF_KERNEL_RIGID_SUBWARP)
       for (int S : slots) {
         if (st != GRIDFF_OK) break;
         LaunchCfg c = best;
         c.S = S;
+        c.gcache = 0;
         double r = 0;
         if ((st = trial(c, r)) != GRIDFF_OK) break;
         if (r > best_rate) {
@@ -231,6 +236,16 @@ gridff_status gridff_tune(gridff_ctx* ctx, const gridff_grid* grid, gridff_repli
           best = c;
         }
       }
+    if (best.kernel == GRIDFF_KERNEL_FLEX_TERMS && use_grid && st == GRIDFF_OK) {
+      LaunchCfg c = best;
+      c.S = 0;
+      c.gcache = 1;
+      double r = 0;
+      if ((st = trial(c, r)) == GRIDFF_OK && r > best_rate) {
+        best_rate = r;
+        best = c;
+      }
+    }
     // work queue, L2 window
     for (int dim = 0; dim < 2 && st == GRIDFF_OK; ++dim) {
       if (dim == 0 && best.kernel != GRIDFF_KERNEL_FLEX_TERMS) continue;

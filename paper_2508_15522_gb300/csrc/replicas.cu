@@ -483,7 +483,7 @@ void gridff_replicas_destroy(gridff_replicas* R) {
   cudaSetDevice(R->device);
   void* ptrs[] = {R->tmpl_blob, R->rep_tmpl, R->rep_off, R->x, R->v, R->fire_dt, R->fire_alpha,
                   R->fire_nplus, R->status, R->steps, R->energy, R->handoff, R->handoff_p,
-                  R->last_x, R->last_f};
+                  R->last_x, R->last_f, R->gval, R->gkey};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   cudaSetDevice(prev);

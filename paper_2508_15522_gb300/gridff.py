@@ -82,7 +82,7 @@ class LangevinParams(C.Structure):
 class LaunchConfig(C.Structure):
     _fields_ = [("kernel", C.c_int32), ("lanes_per_replica", C.c_int32), ("warps_per_block", C.c_int32),
                 ("cache_slots", C.c_int32), ("queue", C.c_int32), ("l2_window", C.c_int32),
-                ("blocks", C.c_int32)]
+                ("blocks", C.c_int32), ("cache_global", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

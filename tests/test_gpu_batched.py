@@ -83,9 +83,10 @@ def refs(field, uneven):
     return x0, _oracle(field, mols, tof, x0)
 
 
-LAYOUTS = [dict(kernel=3, warps_per_block=w, cache_slots=S, queue=q)
+LAYOUTS = [dict(kernel=3, warps_per_block=w, cache_slots=S, queue=q, cache_global=0)
            for w, S, q in ((2, 0, 1), (4, 32, 1), (8, 64, 0), (4, 70, 0), (8, 16, 1))]
-LAYOUTS += [dict(kernel=2, warps_per_block=4, cache_slots=S, queue=0) for S in (0, 48)]
+LAYOUTS += [dict(kernel=3, warps_per_block=w, cache_slots=0, queue=q, cache_global=1) for w, q in ((8, 1), (2, 0))]
+LAYOUTS += [dict(kernel=2, warps_per_block=4, cache_slots=S, queue=0, cache_global=0) for S in (0, 48)]
 TOL = {1: 2e-6, 5: 2e-5, 20: 2e-4}
 
 
@@ -106,13 +107,28 @@ def _relax_and_compare(G, ctx, grid, mols, tof, x0, ref, configure):
 
 
 @pytest.mark.parametrize("layout", LAYOUTS,
-                         ids=lambda d: "k{kernel}-w{warps_per_block}-S{cache_slots}-q{queue}".format(**d))
+                         ids=lambda d: "k{kernel}-w{warps_per_block}-S{cache_slots}-q{queue}-g{cache_global}".format(**d))
 def test_flex_terms_layouts_match_oracle(G, ctx, field, uneven, refs, layout):
     mols, tof = uneven
     x0, ref = refs
     _relax_and_compare(G, ctx, field[4], mols, tof, x0, ref,
                        lambda reps: reps.set_launch_config(G.LaunchConfig(lanes_per_replica=32, l2_window=0,
                                                                           **layout)))
+
+
+def test_global_stencil_cache_rejected_where_it_does_not_apply(G, ctx, uneven):
+    """cache_global belongs to the unique-term kernel without shared-memory
+    slots: with slots, with another kernel, or with a value other than 0/1
+    set_launch_config returns EINVAL."""
+    mols, tof = uneven
+    reps = G.Replicas(ctx, mols, tof)
+    for bad in (dict(kernel=3, warps_per_block=4, cache_slots=16, queue=1, cache_global=1),
+                dict(kernel=2, warps_per_block=4, cache_slots=0, queue=0, cache_global=1),
+                dict(kernel=3, warps_per_block=4, cache_slots=0, queue=1, cache_global=2)):
+        with pytest.raises(G.GridffError) as e:
+            reps.set_launch_config(G.LaunchConfig(lanes_per_replica=32, l2_window=0, **bad))
+        assert e.value.status == G.EINVAL
+    reps.close()
 
 
 def test_flex_terms_largest_molecule_one_step(G, ctx, field):

@@ -181,8 +181,8 @@ def _uneven(G, ctx, sub):
     return mols, tof, reps, x0
 
 
-@pytest.mark.parametrize("wpb", [8, 2])
-def test_uneven_batch_per_atom_forces(G, ctx, nacl, wpb):
+@pytest.mark.parametrize("wpb,gcache", [(8, 0), (2, 0), (8, 1)])
+def test_uneven_batch_per_atom_forces(G, ctx, nacl, wpb, gcache):
     """The uneven batch (16384 flexible replicas of 10-120 atoms) in the
     unique-term layout with the work queue: per-atom forces (grid +
     intramolecular) and per-replica energies of the final evaluation after
@@ -199,7 +199,8 @@ def test_uneven_batch_per_atom_forces(G, ctx, nacl, wpb):
     sizes = np.array([m.n for m in mols])[tof]
     order = np.argsort(sizes, kind="stable")
     sample = sorted(set(order[np.linspace(0, len(order) - 1, 60).astype(int)].tolist()) | {0, 1, 16382, 16383})
-    reps.set_launch_config(kernel=G.KERNEL_FLEX_TERMS, warps_per_block=wpb, cache_slots=0, queue=1)
+    reps.set_launch_config(kernel=G.KERNEL_FLEX_TERMS, warps_per_block=wpb, cache_slots=0, queue=1,
+                           cache_global=gcache)
     for nsteps in (1, 200):
         reps.set_state(x0.ravel())
         G.relax(ctx, grid, reps, nsteps, G.fire_params(f_conv=0.0), check=False)
@@ -238,7 +239,7 @@ def test_uneven_batch_per_atom_forces(G, ctx, nacl, wpb):
                     print("  ", t, np.linalg.norm(ointra.energy_forces(x[None], m, terms=(t,))[1][0, a]))
             assert (dFa <= gate).all(), (r, m.n, nsteps, dF)
             assert dE <= gate_e, (r, m.n, nsteps, dE)
-        print(f"uneven batch, {wpb} warps per block, {nsteps} iterations: max|dF| {worst_f:.2e} eV/A "
+        print(f"uneven batch, {wpb} warps per block, global stencil cache {gcache}, {nsteps} iterations: max|dF| {worst_f:.2e} eV/A "
               f"(atoms above the floor), max|dE|/atom {worst_e:.2e} eV; {n_below} sampled atoms below the floor, "
               f"max |dF|/max(1, |F|) there {worst_below:.2e}")
     reps.close()
