@@ -2462,11 +2462,13 @@ LaunchCfg default_launch_cfg(const gridff_replicas* R, bool use_grid) {
     }
   } else {
     // measured on 16384 replicas of 10-120 atoms: the unique-term kernel
-    // with the work queue and no stencil staging is fastest
+    // with the work queue and the stencils cached in global memory is
+    // fastest (shared-memory staging costs more occupancy than it saves)
     c.kernel = GRIDFF_KERNEL_FLEX_TERMS;
     c.wpb = 8;
     c.S = 0;
     c.queue = 1;
+    c.gcache = use_grid ? 1 : 0;
   }
   return c;
 }
