@@ -448,13 +448,19 @@ class Replicas:
         return x.reshape(-1, 3), f.reshape(-1, 3)
 
     def set_launch_config(self, cfg=None, **kw):
-        """Fix the relaxation layout (None: the library's heuristic)."""
+        """Fix the relaxation layout (None: the library's heuristic).  Keyword
+        fields are set over the current layout; a layout given shared-memory
+        slots or another kernel this way drops the global stencil cache unless
+        cache_global is among the keywords."""
         if cfg is None and not kw:
             self.ctx.check(lib.gridff_set_launch_config(self.h, None))
             return
         c = self.launch_config() if cfg is None else cfg
         for k, v in kw.items():
             setattr(c, k, v)
+        if "cache_global" not in kw and (kw.get("cache_slots", 0) > 0 or kw.get("kernel", KERNEL_FLEX_TERMS)
+                                          != KERNEL_FLEX_TERMS):
+            c.cache_global = 0
         self.ctx.check(lib.gridff_set_launch_config(self.h, C.byref(c)))
 
     def launch_config(self, use_grid=True) -> LaunchConfig:
