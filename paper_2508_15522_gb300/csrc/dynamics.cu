@@ -1731,15 +1731,16 @@ relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep
 // drift, forces, half kick; c1 = exp(-gamma dt), c2 = sqrt(1 - c1^2).
 // xi of replica r, global step s, component m = 3 i + a:
 //   normal_of(splitmix64(splitmix64(seed ^ splitmix64(r)) ^ (512 s + m))).
-// Layout as relax_flex_terms_kernel (warp per replica, work queue).
+// Layout as relax_flex_terms_kernel (warp per replica, work queue, GC: the
+// global stencil cache).
 // ---------------------------------------------------------------------------
-template <int WPB, int KIND>
+template <int WPB, int KIND, bool GC>
 __global__ void __launch_bounds__(32 * WPB, GRIDFF_FLEX_WARPS_PER_SM / WPB)
 langevin_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tmpl,
                      const int* __restrict__ rep_off, const int* __restrict__ order, int n_rep, float* xs,
                      float* vs, int* status, double* energy, int nsteps, float dt, float c1, float c2,
                      float kT_acc, unsigned long long seed, long long step0, Control ctl, int use_grid,
-                     int use_intra, int S) {
+                     int use_intra, int S, float4* gval, int* gkey) {
   __shared__ WarpState s_all[WPB];
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -1766,6 +1767,11 @@ langevin_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tm
     const int t = rep_tmpl[r], n = tv.natoms[t], ab = tv.atom_off[t], off = rep_off[r];
     const unsigned long long key = splitmix64(seed ^ splitmix64((unsigned long long)r));
     __syncwarp();
+    if (GC && use_grid) {
+      sc.val = gval + 16 * (size_t)off;
+      sc.key = gkey + off;
+      sc.S = n;
+    }
     cache_reset(sc, lane);
     for (int m = lane; m < 3 * n; m += 32) {
       s.x[m] = xs[3 * (size_t)off + m];
@@ -2479,6 +2485,20 @@ gridff_status check_fire_params(gridff_ctx* ctx, const gridff_fire_params& P) {
   return GRIDFF_OK;
 }
 
+// The global stencil cache of a flexible replica set: one 256-byte stencil
+// and a key per atom, allocated at the first use and kept with the set.
+gridff_status ensure_gcache(gridff_ctx* ctx, gridff_replicas* R) {
+  if (R->gval) return GRIDFF_OK;
+  if (cudaMalloc(&R->gval, (size_t)R->n_atoms * 256) != cudaSuccess ||
+      cudaMalloc(&R->gkey, (size_t)R->n_atoms * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(R->gval);
+    R->gval = nullptr;
+    return set_err(ctx, GRIDFF_ENOMEM, "global stencil cache of %d atoms", R->n_atoms);
+  }
+  return GRIDFF_OK;
+}
+
 gridff_status prepare_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_replicas* R, const LaunchCfg& c,
                             int flags, int* blocks_out) {
   const KernelShape k = shape_of(R, c, grid ? grid->kind : REC_F32x4);
@@ -2503,14 +2523,9 @@ gridff_status prepare_relax(gridff_ctx* ctx, const gridff_grid* grid, gridff_rep
     return set_err(ctx, GRIDFF_EINVAL, "queue mode %d", c.queue);
   if ((c.gcache != 0 && c.gcache != 1) || (c.gcache && c.kernel != GRIDFF_KERNEL_FLEX_TERMS))
     return set_err(ctx, GRIDFF_EINVAL, "cache_global %d with kernel %d", c.gcache, c.kernel);
-  if (c.gcache && !R->gval) {   // one 256-byte stencil and a key per atom of the set
-    if (cudaMalloc(&R->gval, (size_t)R->n_atoms * 256) != cudaSuccess ||
-        cudaMalloc(&R->gkey, (size_t)R->n_atoms * sizeof(int)) != cudaSuccess) {
-      cudaGetLastError();
-      cudaFree(R->gval);
-      R->gval = nullptr;
-      return set_err(ctx, GRIDFF_ENOMEM, "global stencil cache of %d atoms", R->n_atoms);
-    }
+  if (c.gcache) {
+    const gridff_status gs = ensure_gcache(ctx, R);
+    if (gs != GRIDFF_OK) return gs;
   }
   const int need = (R->n_rep + k.units_per_block - 1) / k.units_per_block;
   *blocks_out = need < per_sm * ctx->n_sm ? need : per_sm * ctx->n_sm;
@@ -2780,15 +2795,25 @@ gridff_status gridff_langevin(gridff_ctx* ctx, const gridff_grid* grid, gridff_r
   const LaunchCfg c = R->cfg.kernel == GRIDFF_KERNEL_FLEX_TERMS ? R->cfg : default_launch_cfg(R, true);
   const int wpb = c.kernel == GRIDFF_KERNEL_FLEX_TERMS ? c.wpb : 8;
   const int S = c.kernel == GRIDFF_KERNEL_FLEX_TERMS ? c.S : 0;
+  const bool gc = c.kernel == GRIDFF_KERNEL_FLEX_TERMS && c.gcache && S == 0 && use_grid;
+  if (gc) {
+    const gridff_status gs = ensure_gcache(ctx, R);
+    if (gs != GRIDFF_OK) return gs;
+  }
   using LangevinFn = void (*)(GridView, TemplateView, const int*, const int*, const int*, int, float*, float*, int*,
                               double*, int, float, float, float, float, unsigned long long, long long, Control, int,
-                              int, int);
+                              int, int, float4*, int*);
   const bool f32 = !grid || grid->kind == REC_F32x4;
   const LangevinFn lf =
-      f32 ? (wpb == 2 ? langevin_flex_kernel<2, REC_F32x4> : wpb == 4 ? langevin_flex_kernel<4, REC_F32x4>
-                                                                      : langevin_flex_kernel<8, REC_F32x4>)
-          : (wpb == 2 ? langevin_flex_kernel<2, -1> : wpb == 4 ? langevin_flex_kernel<4, -1>
-                                                               : langevin_flex_kernel<8, -1>);
+      gc ? (f32 ? (wpb == 2 ? langevin_flex_kernel<2, REC_F32x4, true>
+                            : wpb == 4 ? langevin_flex_kernel<4, REC_F32x4, true> : langevin_flex_kernel<8, REC_F32x4, true>)
+                : (wpb == 2 ? langevin_flex_kernel<2, -1, true>
+                            : wpb == 4 ? langevin_flex_kernel<4, -1, true> : langevin_flex_kernel<8, -1, true>))
+         : (f32 ? (wpb == 2 ? langevin_flex_kernel<2, REC_F32x4, false>
+                            : wpb == 4 ? langevin_flex_kernel<4, REC_F32x4, false>
+                                       : langevin_flex_kernel<8, REC_F32x4, false>)
+                : (wpb == 2 ? langevin_flex_kernel<2, -1, false>
+                            : wpb == 4 ? langevin_flex_kernel<4, -1, false> : langevin_flex_kernel<8, -1, false>));
   const void* fn = (const void*)lf;
   const size_t dyn = flex_terms_warp_bytes(S) * wpb;
   GRIDFF_CUDA(ctx, set_dyn_smem(fn, dyn));
@@ -2800,7 +2825,8 @@ gridff_status gridff_langevin(gridff_ctx* ctx, const gridff_grid* grid, gridff_r
   GRIDFF_CUDA(ctx, cudaEventRecord(ctx->ev0, s));
   lf<<<blocks, 32 * wpb, dyn, s>>>(gv, R->tv, R->rep_tmpl, R->rep_off, R->order, R->n_rep, R->x, R->v, R->status,
                                    R->energy, nsteps, prm->dt, (float)c1, (float)c2, kT_acc,
-                                   (unsigned long long)prm->seed, (long long)prm->step0, ctl, use_grid, use_intra, S);
+                                   (unsigned long long)prm->seed, (long long)prm->step0, ctl, use_grid, use_intra, S,
+                                   R->gval, R->gkey);
   DevResult h{};
   return finish_launch(ctx, &h);
 }
