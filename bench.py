@@ -503,10 +503,14 @@ def uneven_batch_comparison(G, ctx, grid, sub):
     n_rep = len(tof)
     out = {"replicas": n_rep, "atoms": int(reps.n_atoms), "templates": len(mols), "fire_iterations": 1000,
            "f_conv_eV_per_A": 1e-3, "tolerance_eV": 0.01, "rmsd_threshold_A": 0.1}
-    # trials of 100 iterations: a stencil cache fills on a trial's first
-    # iteration, so short trials understate it against the 1000-iteration calls
-    best, log = G.tune(ctx, grid, reps, G.fire_params(f_conv=0.0), trial_steps=100)
+    # trials as long as the calls they tune (1000 iterations): from random
+    # starts the atoms change cell often in the first iterations, so short
+    # trials understate the stencil caches against the long calls
+    best, log = G.tune(ctx, grid, reps, G.fire_params(f_conv=0.0), trial_steps=1000)
     out["tuned_config"] = best.as_dict()
+    out["tuner_log"] = [[t["warps_per_block"], t["cache_slots"], t["queue"], t["l2_window"], t["cache_global"],
+                         round(t["ms"], 2)] for t in log if t["kernel"] == G.KERNEL_FLEX_TERMS]
+    out["tuner_log_fields"] = "unique-term kernel trials: warps per block, cache slots, queue, L2 window, global cache, ms"
     out["tuner_trials"] = len(log)
 
     def accepted_now():
