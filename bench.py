@@ -506,6 +506,7 @@ def uneven_batch_comparison(G, ctx, grid, sub):
     # trials as long as the calls they tune (1000 iterations): from random
     # starts the atoms change cell often in the first iterations, so short
     # trials understate the stencil caches against the long calls
+    reps.set_state(x0)        # trials relax from the benchmark's starting structures
     best, log = G.tune(ctx, grid, reps, G.fire_params(f_conv=0.0), trial_steps=1000)
     out["tuned_config"] = best.as_dict()
     out["tuner_log"] = [[t["warps_per_block"], t["cache_slots"], t["queue"], t["l2_window"], t["cache_global"],
