@@ -1074,11 +1074,14 @@ __device__ __forceinline__ void sw_forces(const GridView& g, const StencilCache&
     }
   }
   __syncwarp();
-  // contract every atom of the lane (independent chains)
+  // contract every atom of the lane (independent chains, no branch between
+  // them: an atom outside the grid or beyond n reads a valid slot and its
+  // results are dropped by selection)
 #pragma unroll
   for (int k = 0; k < R; ++k) {
-    const int i = k * W + l;
-    if (cl[k].inside) {
+    const int i = min(k * W + l, S - 1);
+    const bool in = cl[k].inside;
+    {
       float wx[4], dwx[4], wy[4], dwy[4], wz[4], dwz[4];
       bspline_weights(cl[k].tx, wx, dwx);
       bspline_weights(cl[k].ty, wy, dwy);
@@ -1121,8 +1124,8 @@ __device__ __forceinline__ void sw_forces(const GridView& g, const StencilCache&
         gy = fmaf(wx[a], sy, gy);
         gz = fmaf(wx[a], sz, gz);
       }
-      const float fx = -gx * g.inv_dx, fy = -gy * g.inv_dy, fz = -gz * g.inv_dz;
-      e += ev;
+      const float fx = in ? -gx * g.inv_dx : 0.f, fy = in ? -gy * g.inv_dy : 0.f, fz = in ? -gz * g.inv_dz : 0.f;
+      e += in ? ev : 0.f;
       Ft[0] += fx;
       Ft[1] += fy;
       Ft[2] += fz;
