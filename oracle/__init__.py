@@ -2,8 +2,10 @@
 
 Plain, slow, obviously-correct numpy / PyTorch-CPU code in float64 (with a
 float32 mirror of the grid interpolation).  It shares no code with the CUDA
-library: only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s
-CPU-baseline leg may import it.  The CUDA product path never calls it.
+library: only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU
+legs may import it (the timed CPU baseline and reference arm, and the FP64
+pairwise reference that the accuracy keys compare finished GPU results
+with, outside every timed region).  The CUDA product path never calls it.
 
 Modules
 -------
