@@ -505,20 +505,28 @@ __device__ __forceinline__ uint32_t pick4(uint32_t w0, uint32_t w1, uint32_t w2,
   return k == 0 ? w0 : k == 1 ? w1 : k == 2 ? w2 : w3;
 }
 
+// 2^x by the PTX instruction ex2.approx.ftz.f32 (relative error about 2^-22).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+constexpr float kLog2e = 1.44269504088896341f;   // log2(e)
+
 // Nonbonded force factor c (F_i = c d, d = x_i - x_j) and energy of one pair
-// (Morse with mixed R_i + R_j and eps_i eps_j, plus Coulomb).  The Morse
-// exponential is the intrinsic __expf (documented bound 2 + 1.16 |x| ulp at
-// argument x: about 1e-6 relative at |x| = 10, where the Morse term of a
-// pair is already e^-10 of its well depth).
-__device__ __forceinline__ void nb_pair(float3 d, float4 pi, float4 pj, float alpha, float& c, float& e) {
+// (Morse with mixed R_i + R_j and eps_i eps_j, plus Coulomb), from per-atom
+// factors prepared once per replica: pi = {k_e q_i, a R_i, eps_i, -} for
+// this lane's atom and pj = {q_j, a R_j, eps_j, -} for the partner, with
+// a = alpha log2(e), so that e^{-alpha (r - R_i - R_j)} = 2^{a R_i + a R_j - a r}.
+__device__ __forceinline__ void nb_pair(float3 d, float4 pi, float4 pj, float alpha, float a, float& c, float& e) {
   const float r2 = dot3(d, d);
   const float ir = rsqrtf(r2);
   const float r = r2 * ir;
-  const float e1 = __expf(-alpha * (r - (pi.y + pj.y)));
+  const float e1 = ex2_approx(fmaf(-a, r, pi.y + pj.y));
   const float ee = pi.z * pj.z;
-  const float qq = GRIDFF_KE * pi.x * pj.x;
-  c = -(2.f * alpha * ee * e1 * (1.f - e1) - qq * ir * ir) * ir;
-  e = ee * e1 * (e1 - 2.f) + qq * ir;
+  const float qr = pi.x * pj.x * ir;                      // k_e q_i q_j / r
+  c = -(2.f * alpha * ee * e1 * (1.f - e1) - qr * ir) * ir;
+  e = ee * e1 * (e1 - 2.f) + qr;
 }
 
 // f[3 i .. 3 i + 2] += (x, y, z) by atomic additions (f in shared memory).
@@ -528,14 +536,24 @@ __device__ __forceinline__ void sh_add3(float* f, int i, float x, float y, float
   atomicAdd(f + 3 * i + 2, z);
 }
 
+// Zero positions and nonbonded factors of the slots n .. (next multiple of
+// 32) - 1, which the nonbonded pass reads for partners outside the molecule.
+__device__ __forceinline__ void pad_pair_slots(float* s_x, float4* s_nb, int n, int lane) {
+  for (int i = n + lane; i < ((n + 31) & ~31); i += 32) {
+    s_x[3 * i] = s_x[3 * i + 1] = s_x[3 * i + 2] = 0.f;
+    s_nb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
 // Steps d = d0 .. d1 of one block pair of the nonbonded pass (below): the
 // pair (this lane's atom, slot (lane + d) mod ring of the block at base) when
-// bit d of act is set.  Adds the pair forces to fi and the energies to e;
+// bit d of act is set.  Slots from n to the next multiple of 32 hold zero
+// positions and factors (written when the replica is loaded).  Adds the pair forces to fi and the energies to e;
 // returns the reactions received on this lane's atom of the partner block.
 template <bool DIAG>
 __device__ __forceinline__ float3 nb_steps(const float* s_x, const float4* s_nb, float3 xi, float4 pi, float alpha,
-                                           uint32_t act, int lane, int base, int ring, int d0, int d1, float3& fi,
-                                           float& e) {
+                                           float a, uint32_t act, int lane, int base, int ring, int d0, int d1,
+                                           float3& fi, float& e) {
   float3 g = make_float3(0.f, 0.f, 0.f);
   int sl = lane + d0, src = lane - d0;
   if (sl >= ring) sl -= ring;
@@ -546,8 +564,9 @@ __device__ __forceinline__ float3 nb_steps(const float* s_x, const float4* s_nb,
     const int j = base + sl;
     const float3 dv = sub3(xi, ld3(s_x, j));
     float c, ep;
-    nb_pair(dv, pi, s_nb[j], alpha, c, ep);
-    const float cx = on ? c * dv.x : 0.f, cy = on ? c * dv.y : 0.f, cz = on ? c * dv.z : 0.f;
+    nb_pair(dv, pi, s_nb[j], alpha, a, c, ep);
+    c = on ? c : 0.f;                      // slots past n hold zeros: dv stays finite
+    const float cx = c * dv.x, cy = c * dv.y, cz = c * dv.z;
     e += on ? ep : 0.f;
     fi.x += cx;
     fi.y += cy;
@@ -582,15 +601,17 @@ __device__ float intra_terms(const TemplateView& tv, int t, int lane, const floa
   // updated by the owners once per block pair.  Which steps d carry a pair
   // (partner inside the molecule, not excluded, counted from this atom) is
   // one 32-bit word per lane and block pair, computed before the steps.
-  // Inactive steps read whatever the partner's slot of s_x / s_nb holds (in
-  // bounds: slots < 128) and add zero by selection.
+  // Inactive steps read the partner's slot of s_x / s_nb (a real atom, or a
+  // zeroed slot below the next multiple of 32) and add zero.
+  const float a2 = alpha * kLog2e;
   const int nblk = (n + 31) >> 5;
   for (int I = 0; I < nblk; ++I) {
     const int i = 32 * I + lane;
     const bool own = i < n;
     const int ii = own ? i : 32 * I;
     const float3 xi = ld3(s_x, ii);
-    const float4 pi = s_nb[ii];
+    float4 pi = s_nb[ii];
+    pi.x *= GRIDFF_KE;
     const uint32_t* ex = tv.excl + 4 * (size_t)(ab + ii);
     float3 fi = make_float3(0.f, 0.f, 0.f);
     for (int J = I; J < nblk; ++J) {
@@ -606,12 +627,12 @@ __device__ float intra_terms(const TemplateView& tv, int t, int lane, const floa
         const int h = m >> 1;
         act &= ((2u << h) - 1u) & ~1u;                          // d = 1 .. m/2
         if (!(m & 1) && lane >= h) act &= ~(1u << h);           // d = m/2 counted from l < m/2
-        gj = nb_steps<true>(s_x, s_nb, xi, pi, alpha, act, lane, base, ring, 1, h, fi, e);
+        gj = nb_steps<true>(s_x, s_nb, xi, pi, alpha, a2, act, lane, base, ring, 1, h, fi, e);
         fi.x += gj.x;
         fi.y += gj.y;
         fi.z += gj.z;
       } else {
-        gj = nb_steps<false>(s_x, s_nb, xi, pi, alpha, act, lane, base, 32, 0, 31, fi, e);
+        gj = nb_steps<false>(s_x, s_nb, xi, pi, alpha, a2, act, lane, base, 32, 0, 31, fi, e);
         if (base + lane < n) {
           float* f = s_f + 3 * (base + lane);
           f[0] += gj.x;
@@ -1634,12 +1655,15 @@ relax_flex_terms_kernel(GridView g, TemplateView tv, const int* __restrict__ rep
     cache_reset(sc, lane);
     float* const v_r = vs + 3 * (size_t)off;   // this replica's velocities (global memory)
     for (int m = lane; m < 3 * n; m += 32) s.x[m] = xs[3 * (size_t)off + m];
-    // nonbonded parameters, and the inverse mass in the free fourth slot
+    // nonbonded factors {q, alpha log2(e) R, eps} and the inverse mass in
+    // the free fourth slot; zeros up to the next multiple of 32 atoms
     for (int i = lane; i < n; i += 32) {
       float4 p = __ldg(&tv.nb[ab + i]);
+      p.y *= tv.alpha * kLog2e;
       p.w = 1.f / __ldg(&tv.body[ab + i]).w;
       s_nb[i] = p;
     }
+    pad_pair_slots(s.x, s_nb, n, lane);
     float dt = fdt[r], al = falpha[r];
     int np = fnp[r], st = status[r], evals = 0;
     float elane = 0.f;
@@ -1780,12 +1804,15 @@ langevin_flex_kernel(GridView g, TemplateView tv, const int* __restrict__ rep_tm
       s.x[m] = xs[3 * (size_t)off + m];
       s.v[m] = vs[3 * (size_t)off + m];
     }
-    // nonbonded parameters, and 1/sqrt(m) in the free fourth slot
+    // nonbonded factors {q, alpha log2(e) R, eps} and 1/sqrt(m) in the
+    // free fourth slot; zeros up to the next multiple of 32 atoms
     for (int i = lane; i < n; i += 32) {
       float4 p = __ldg(&tv.nb[ab + i]);
+      p.y *= tv.alpha * kLog2e;
       p.w = rsqrtf(__ldg(&tv.body[ab + i]).w);
       s_nb[i] = p;
     }
+    pad_pair_slots(s.x, s_nb, n, lane);
     int st = status[r] & ~(GRIDFF_REP_CONVERGED | GRIDFF_REP_ABORTED | GRIDFF_REP_STEPLIMIT);
     int flags = 0, steps_done = 0;
     float elane = flex_forces_terms<float, KIND>(g, use_grid, use_intra, tv, t, ab, n, lane, s, flags, sc, s_nb);

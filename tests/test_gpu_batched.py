@@ -131,6 +131,27 @@ def test_global_stencil_cache_rejected_where_it_does_not_apply(G, ctx, uneven):
     reps.close()
 
 
+def test_global_stencil_cache_changes_nothing_but_the_layout(G, ctx, field, uneven, refs):
+    """The global stencil cache stores the same channel-combined values the
+    gathers produce and the contraction reads them in the same order, so a
+    relaxation and a Langevin run with and without it agree bit for bit."""
+    mols, tof = uneven
+    x0 = np.concatenate([x.ravel() for x in refs[0]])
+    out = {}
+    for gc in (0, 1):
+        reps = G.Replicas(ctx, mols, tof)
+        reps.set_launch_config(kernel=G.KERNEL_FLEX_TERMS, warps_per_block=4, cache_slots=0, queue=1,
+                               cache_global=gc)
+        reps.set_state(x0)
+        G.relax(ctx, field[4], reps, 50, G.fire_params(f_conv=0.0))
+        xr = reps.get_state()[0].copy()
+        G.langevin(ctx, field[4], reps, 30, 1.0, 300.0, 0.01, 5)
+        out[gc] = (xr, reps.get_state()[0].copy(), reps.fire_state()["energy"].copy())
+        reps.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+
+
 def test_flex_terms_largest_molecule_one_step(G, ctx, field):
     mol = synth.random_flexible_molecule(128, 12, 4)
     x0 = [synth.flexible_positions(mol, field[0], 1, seed=131)[0].astype(np.float32)]
