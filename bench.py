@@ -789,10 +789,13 @@ def interpolation_roofline(G, ctx, grid, box, torch, dev, stream, l2_peak):
     out["binned"]["kernels"] = ("bin_count_kernel, scan_tiles/scan_top/scan_apply_kernel, bin_scatter_kernel, "
                                 "eval_sorted_kernel (lane per point); the sort is inside the timed region")
     out["direct"]["kernels"] = "eval_points_kernel (quad of lanes per point, input order)"
-    return {"kernel": "gridff_eval_points, binned layout (counting sort by cell + lane per point)",
-            "atom_evals_per_s": out["binned"]["atom_evals_per_s"], "ms_per_call": out["binned"]["ms_per_call"],
+    best = max(("binned", "direct"), key=lambda k: out[k]["atom_evals_per_s"])   # the faster layout
+    names = {"binned": "gridff_eval_points, binned layout (counting sort by cell + lane per point)",
+             "direct": "gridff_eval_points, direct layout (quad of lanes per point, input order)"}
+    return {"kernel": names[best], "layout": best,
+            "atom_evals_per_s": out[best]["atom_evals_per_s"], "ms_per_call": out[best]["ms_per_call"],
             "points_per_call": n, "points": "uniform over the tile, z0 + [2, 8] A",
-            "roofline": out["binned"]["roofline"], "layouts": out}
+            "roofline": out[best]["roofline"], "layouts": out}
 
 
 def minima_hopping_curve(G, ctx):
