@@ -2517,7 +2517,7 @@ gridff_status check_fire_params(gridff_ctx* ctx, const gridff_fire_params& P) {
 
 // The global stencil cache of a flexible replica set: one 256-byte stencil
 // and a key per atom, allocated at the first use and kept with the set.
-gridff_status ensure_gcache(gridff_ctx* ctx, gridff_replicas* R) {
+static gridff_status ensure_gcache(gridff_ctx* ctx, gridff_replicas* R) {
   if (R->gval) return GRIDFF_OK;
   if (cudaMalloc(&R->gval, (size_t)R->n_atoms * 256) != cudaSuccess ||
       cudaMalloc(&R->gkey, (size_t)R->n_atoms * sizeof(int)) != cudaSuccess) {
