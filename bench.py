@@ -76,25 +76,35 @@ class ClockSampler:
 
     def __init__(self, device_index):
         self.dev = device_index
-        self.rows = []
+        self.rows = []          # (arrival time, fields)
         self.proc = None
+        self.window = None      # (start, end) of the timed region
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.perf_counter()     # sampling is running before the timed region starts
+            while not self.rows and time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.01)
         except (OSError, ValueError):
             self.proc = None
         return self
+
+    def start(self):
+        self.window = (time.perf_counter(), None)
+
+    def stop(self):
+        self.window = (self.window[0], time.perf_counter() + 0.05) if self.window else None
 
     def _read(self):
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) >= 9:
-                self.rows.append(parts)
+                self.rows.append((time.perf_counter(), parts))
 
     def __exit__(self, *a):
         if self.proc:
@@ -105,15 +115,18 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        if not self.rows:
+        rows = [r for t, r in self.rows if self.window and self.window[1] and self.window[0] <= t <= self.window[1]]
+        if not rows:     # none arrived inside the window: the nearest ones around it
+            rows = [r for _, r in self.rows[-3:]]
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if "Active" in r[5 + i]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]
                           and "Not" not in r[5 + i]})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(rows)}
 
 
 # ---------------------------------------------------------------------------
@@ -878,6 +891,7 @@ def run_gpu(args):
     kernel_ms = []
     with ClockSampler(local) as clk:
         torch.cuda.synchronize(dev)
+        clk.start()
         for i in range(args.steps):
             flush.fill_(float(i))
             ev[i][0].record(stream)
@@ -886,6 +900,7 @@ def run_gpu(args):
             evals += res.atom_evals
             kernel_ms.append(ctx.last_kernel_ms())
         torch.cuda.synchronize(dev)
+        clk.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s, evals_all = reduce_over_ranks(sum(step_ms) / 1e3, evals, dist, dev)
     value = evals_all / total_s

@@ -68,3 +68,20 @@ def test_amortised_gain_charges_training_and_credits_its_hits():
     assert bench.amortised_gain(out, 400, 2.5, 1.0)["break_even_batches"] == 0.0   # ahead from the start
     out["mlp"]["hits"] = 400                      # proposals no better than random starts: no break-even
     assert bench.amortised_gain(out, 250, 2.5, 1.0)["break_even_batches"] is None
+
+
+def test_clock_summary_keeps_the_timed_window():
+    """Clock samples count only when they arrived inside the timed region;
+    throttle reasons are read from the same samples."""
+    import bench
+    c = bench.ClockSampler(0)
+    row = lambda mhz, slow: [0, str(mhz), "2070", "900", "x", "Active" if slow else "Not Active",
+                             "Not Active", "Not Active", "Not Active"]
+    c.rows = [(0.5, row(1200, True)), (1.1, row(2070, False)), (1.4, row(2060, False)), (3.0, row(900, True))]
+    c.window = (1.0, 1.5)
+    s = c.summary()
+    assert s["samples"] == 2 and s["sm_mhz"] == 2065 and s["reasons"] == [] and s["sm_max_mhz"] == 2070
+    c.window = (2.0, 2.5)          # nothing inside: the last samples around it
+    assert c.summary()["samples"] == 3
+    c.rows = []
+    assert c.summary()["reasons"] == ["unsampled"]
