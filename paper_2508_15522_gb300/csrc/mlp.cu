@@ -5,6 +5,7 @@
 // proposal kernel that writes replica poses for gridff_relax.
 // Not from the paper: it chooses where GridFF relaxations start.
 #include <cuda_bf16.h>
+#include <stddef.h>
 #include <math.h>
 
 #include <algorithm>
@@ -270,11 +271,18 @@ __global__ void colsum_final_kernel(const float* __restrict__ part, int chunks, 
   db[j] = t;
 }
 
-// Adam on FP32 master parameters; c1 = lr / (1 - b1^t), c2 = 1 / (1 - b2^t).
+// Adam on FP32 master parameters; c1 = lr / (1 - b1^t), c2 = 1 / (1 - b2^t),
+// from the arguments or, when c12 is set, from device memory (the training
+// loop's step counters, which a CUDA graph replay advances on the device).
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
-                            float* __restrict__ v, int n, float b1, float b2, float eps, float c1, float c2) {
+                            float* __restrict__ v, int n, float b1, float b2, float eps, float c1, float c2,
+                            const float* __restrict__ c12) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (c12) {
+    c1 = c12[0];
+    c2 = c12[1];
+  }
   const float gi = g[i];
   const float mi = b1 * m[i] + (1.f - b1) * gi;
   const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
@@ -340,13 +348,38 @@ __global__ void pose_kernel(const float* __restrict__ Y, int rows, float ox, flo
   }
 }
 
+// Counters of the device-side training loop, advanced once per step on the
+// device so that one captured step can be replayed: the random-stream step
+// and loss-history index of the current step, the Adam step t and its
+// bias-correction factors c12 = {lr / (1 - b1^t), 1 / (1 - b2^t)}.
+struct StepCounters {
+  long long next_step, step;
+  int next_k, k;
+  long long t;
+  float c12[2];
+};
+
+// Start of a step: take the next random-stream step and history slot, and
+// (update) advance Adam's t and its bias corrections.
+__global__ void step_begin_kernel(StepCounters* c, double lr, double b1, double b2, int update) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  c->step = c->next_step++;
+  c->k = c->next_k++;
+  if (update) {
+    c->t += 1;
+    c->c12[0] = (float)(lr / (1.0 - pow(b1, (double)c->t)));
+    c->c12[1] = (float)(1.0 / (1.0 - pow(b2, (double)c->t)));
+  }
+}
+
 // Training batch drawn on the device: target b of step `step` is row
 // splitmix64(seed ^ splitmix64(2^20 step + b)) mod n_all of the training set.
 __global__ void sample_targets_kernel(const float* __restrict__ T_all, const float* __restrict__ M_all, int n_all,
-                                      int B, unsigned long long seed, long long step, float* __restrict__ Ts,
-                                      float* __restrict__ Ms) {
+                                      int B, unsigned long long seed, const StepCounters* __restrict__ ctr,
+                                      float* __restrict__ Ts, float* __restrict__ Ms) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
+  const long long step = ctr->step;
   const unsigned long long h = splitmix64(seed ^ splitmix64(((unsigned long long)step << 20) + b));
   const int row = (int)(h % (unsigned long long)n_all);
   for (int j = 0; j < kOut; ++j) Ts[(size_t)b * kOut + j] = T_all[(size_t)row * kOut + j];
@@ -356,10 +389,11 @@ __global__ void sample_targets_kernel(const float* __restrict__ T_all, const flo
 // Training inputs: row m = [descriptor, N(0,1) noise], noise j of row m of
 // step `step` from the counter 64 (2^20 step + m) + j.
 __global__ void train_inputs_kernel(const float* __restrict__ desc, int n_desc, int n_noise, int rows,
-                                    unsigned long long seed, long long step, int Mp, int in_p,
+                                    unsigned long long seed, const StepCounters* __restrict__ ctr, int Mp, int in_p,
                                     __nv_bfloat16* __restrict__ H, __nv_bfloat16* __restrict__ HT) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= Mp * in_p) return;
+  const long long step = ctr->step;
   const int m = idx / in_p, k = idx % in_p;
   float v = 0.f;
   if (m < rows) {
@@ -375,8 +409,10 @@ __global__ void train_inputs_kernel(const float* __restrict__ desc, int n_desc, 
   HT[(size_t)k * Mp + m] = b;
 }
 
-// out[0] = mean of loss[0..n) (one block).
-__global__ void loss_mean_kernel(const float* __restrict__ loss, int n, float* __restrict__ out) {
+// hist[k] = mean of loss[0..n) for the step's history slot k (one block).
+__global__ void loss_mean_kernel(const float* __restrict__ loss, int n, float* __restrict__ hist,
+                                 const StepCounters* __restrict__ ctr) {
+  float* out = hist + ctr->k;
   __shared__ float part[256];
   float s = 0.f;
   for (int i = threadIdx.x; i < n; i += blockDim.x) s += loss[i];
@@ -431,6 +467,7 @@ struct gridff_mlp {
   float* loss_hist = nullptr;
   int loss_cap = 0;
   long long rng_step = 0;
+  StepCounters* ctr = nullptr;     // device step counters of the training loop
 };
 
 namespace {
@@ -537,7 +574,7 @@ void forward_rows(gridff_mlp* m, int rows) {
 // forward, winner-takes-all loss, backward, Adam (unless NO_UPDATE).
 // Enqueued on the context stream, no synchronisation.
 gridff_status enqueue_train(gridff_mlp* m, int n_targets, int K, bool mask_on, const gridff_train_params* tp,
-                            int flags) {
+                            int flags, const StepCounters* ctr = nullptr) {
   gridff_ctx* ctx = m->ctx;
   cudaStream_t s = ctx->stream;
   const int rows = n_targets * K;
@@ -576,12 +613,19 @@ gridff_status enqueue_train(gridff_mlp* m, int n_targets, int K, bool mask_on, c
   }
   GRIDFF_CUDA(ctx, cudaGetLastError());
   if (!(flags & GRIDFF_MLP_NO_UPDATE)) {
-    m->t += 1;
-    const double b1 = tp->beta1, b2 = tp->beta2;
-    const float c1 = (float)(tp->lr / (1.0 - pow(b1, (double)m->t)));
-    const float c2 = (float)(1.0 / (1.0 - pow(b2, (double)m->t)));
+    float c1 = 0.f, c2 = 0.f;
+    if (!ctr) {   // else the step's counters on the device hold t and the factors
+      m->t += 1;
+      const double b1 = tp->beta1, b2 = tp->beta2;
+      c1 = (float)(tp->lr / (1.0 - pow(b1, (double)m->t)));
+      c2 = (float)(1.0 / (1.0 - pow(b2, (double)m->t)));
+    }
     adam_kernel<<<grid1((long long)m->n_params), 256, 0, s>>>(m->P, m->Gr, m->Am, m->Av, (int)m->n_params,
-                                                              tp->beta1, tp->beta2, tp->eps, c1, c2);
+                                                              tp->beta1, tp->beta2, tp->eps, c1, c2,
+                                                              ctr ? reinterpret_cast<const float*>(
+                                                                        reinterpret_cast<const char*>(ctr) +
+                                                                        offsetof(StepCounters, c12))
+                                                                  : nullptr);
     refresh_bf16(m);
   }
   return GRIDFF_OK;
@@ -779,19 +823,46 @@ gridff_status gridff_mlp_train(gridff_mlp* m, int32_t steps, int32_t n_targets, 
     if (dalloc(m, &m->loss_hist, (size_t)steps) != cudaSuccess) return set_err(ctx, GRIDFF_ENOMEM, "loss history");
     m->loss_cap = steps;
   }
+  if (!m->ctr && dalloc(m, &m->ctr, 1) != cudaSuccess) return set_err(ctx, GRIDFF_ENOMEM, "step counters");
   cudaStream_t s = ctx->stream;
   const int Mp = pad16(rows);
   if (n_desc > 0)
     GRIDFF_CUDA(ctx, cudaMemcpyAsync(m->desc, descriptor, n_desc * sizeof(float), cudaMemcpyHostToDevice, s));
-  for (int k = 0; k < steps; ++k) {
-    const long long step = m->rng_step++;
+  // The loop is launch-bound (about 45 small launches per step), so one step
+  // is captured in a CUDA graph and replayed `steps` times; everything that
+  // changes between steps (random-stream step, history slot, Adam t and its
+  // factors) lives in device counters advanced by the graph's first node.
+  StepCounters c0{};
+  c0.next_step = m->rng_step;
+  c0.t = m->t;
+  GRIDFF_CUDA(ctx, cudaMemcpyAsync(m->ctr, &c0, sizeof(c0), cudaMemcpyHostToDevice, s));
+  GRIDFF_CUDA(ctx, cudaStreamSynchronize(s));   // c0 is a host temporary
+  if (steps > 0) {
+    GRIDFF_CUDA(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    step_begin_kernel<<<1, 32, 0, s>>>(m->ctr, tp->lr, tp->beta1, tp->beta2, 1);
     sample_targets_kernel<<<grid1(n_targets, 128), 128, 0, s>>>(m->T_all, m->M_all, m->n_all, n_targets,
-                                                                (unsigned long long)seed, step, m->Ts, m->Ms);
+                                                                (unsigned long long)seed, m->ctr, m->Ts, m->Ms);
     train_inputs_kernel<<<grid1((long long)Mp * m->pads[0]), 256, 0, s>>>(
-        m->desc, n_desc, m->sizes[0] - n_desc, rows, (unsigned long long)seed, step, Mp, m->pads[0], m->H[0],
+        m->desc, n_desc, m->sizes[0] - n_desc, rows, (unsigned long long)seed, m->ctr, Mp, m->pads[0], m->H[0],
         m->HT[0]);
-    if ((st = enqueue_train(m, n_targets, K, m->M_all != nullptr, tp, 0)) != GRIDFF_OK) return st;
-    loss_mean_kernel<<<1, 256, 0, s>>>(m->loss, n_targets, m->loss_hist + k);
+    st = enqueue_train(m, n_targets, K, m->M_all != nullptr, tp, 0, m->ctr);
+    loss_mean_kernel<<<1, 256, 0, s>>>(m->loss, n_targets, m->loss_hist, m->ctr);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (st != GRIDFF_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return st;
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    for (int k = 0; k < steps && e == cudaSuccess; ++k) e = cudaGraphLaunch(exec, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return set_err(ctx, GRIDFF_ECUDA, "training graph: %s", cudaGetErrorString(e));
+    m->rng_step += steps;
+    m->t += steps;
   }
   GRIDFF_CUDA(ctx, cudaGetLastError());
   if (losses && steps > 0)

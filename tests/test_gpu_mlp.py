@@ -233,3 +233,22 @@ def test_device_training_step_matches_oracle(gf, ctx):
     more = net.train(300, 256, 4, desc, seed, gf.train_params(lr=1e-3, tile=TILE))
     assert np.all(np.isfinite(more)) and more[-20:].mean() < more[:20].mean()
     net.close()
+
+
+def test_training_loop_split_over_calls_equals_one_call(gf, ctx):
+    """The training loop replays one captured step whose counters (random
+    stream step, loss slot, Adam t) advance on the device: 2 x 25 steps in
+    two calls give the same parameters and losses, bit for bit, as 50 steps
+    in one call."""
+    Ws, bs = synth.mlp_weights(SIZES, 81)
+    T_all, mask_all = _targets(300, 82)
+    desc = (synth.rng(83).random(64) * 0.5).astype(np.float32)
+    out = []
+    for split in ((50,), (25, 25)):
+        net = gf.MLP(ctx, SIZES)
+        net.set_params(Ws, bs)
+        net.set_targets(T_all, mask_all)
+        ls = np.concatenate([net.train(n, 64, 4, desc, 9, gf.train_params(lr=1e-3, tile=TILE)) for n in split])
+        out.append((net.get_params()[0], ls))
+        net.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
