@@ -686,8 +686,10 @@ gridff_status gridff_mlp_set_targets(gridff_mlp* mlp, int32_t n, const float* ta
  * 64 (2^20 s + m) + j (the generator of gridff_mlp_propose); then the
  * winner-takes-all loss, backward pass and Adam step of
  * gridff_mlp_train_step.  losses (host, may be NULL) receives the mean loss
- * of every step.  n_targets K < 2^20.  Errors: EINVAL (no training set),
- * ENOMEM, ECUDA. */
+ * of every step.  n_targets K < 2^20.  One step is captured in a CUDA graph
+ * on the context's stream and replayed `steps` times (the stream must not
+ * be under capture by the caller); synchronises before returning.
+ * Errors: EINVAL (no training set), ENOMEM, ECUDA. */
 gridff_status gridff_mlp_train(gridff_mlp* mlp, int32_t steps, int32_t n_targets, int32_t K,
                                const float* descriptor, int32_t n_desc, uint64_t seed,
                                const gridff_train_params* params, float* losses);
