@@ -247,18 +247,22 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic():
-    """DRAM bytes (read + write) per launch of the relax kernel from the
-    committed ncu summary, if it was taken on the current kernel source
-    (else None)."""
+def ncu_record():
+    """The committed ncu figures of the relax kernel, if they were taken on
+    the current kernel source (else {})."""
     p = os.path.join(ROOT, "profiles", "relax_rigid_c24h8o6_4096.json")
     try:
         d = json.load(open(p))
     except (OSError, ValueError):
-        return None
-    if d.get("kernel_source_hash") != kernel_source_hash():
-        return None
-    return d.get("dram_bytes_per_launch")
+        return {}
+    return d if d.get("kernel_source_hash") == kernel_source_hash() else {}
+
+
+def ncu_traffic():
+    """DRAM bytes (read + write) per launch of the relax kernel from the
+    committed ncu summary, if it was taken on the current kernel source
+    (else None)."""
+    return ncu_record().get("dram_bytes_per_launch")
 
 
 def measured_peaks():
@@ -950,7 +954,11 @@ def run_gpu(args):
                      "units_per_launch": per_launch_evals, "kernel_ms": k_ms,
                      "peak_source": "measured in this run: streaming read of a 48 MB L2-resident buffer "
                                     "(gridff_probe_read_bandwidth, best of 3 launch shapes)",
-                     "hbm_peak_measured": peaks.get("hbm_gbs"), "hbm_read_this_run": hbm_read},
+                     "hbm_peak_measured": peaks.get("hbm_gbs"), "hbm_read_this_run": hbm_read,
+                     # measured context from the committed capture (None when the kernel changed since):
+                     # the bytes actually read from L2 per eval and the SM issue activity
+                     "l2_read_bytes_per_unit_measured": ncu_record().get("l2_to_l1_bytes_per_eval"),
+                     "sm_issue_active_pct_measured": ncu_record().get("sm_issue_active_pct")},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 7 * 4 * N_REP,
                 "d2h_bytes_per_step": (7 + 6) * 4 * N_REP + (5 * 4 + 8) * N_REP},
         "gpu_launches": 2 * args.steps,     # per step: fire_reset_kernel + the relaxation kernel
